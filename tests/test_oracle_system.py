@@ -1,0 +1,190 @@
+"""Pins for the oracle's assembled system (Sec. 2.5 Eq. 3, Sec. 3.2.2) and its solver.
+
+Checked against things other than the oracle itself: brute-force coupling sets,
+closed-form hinge counts, exact symmetry / positive definiteness, the element-by-
+element (matrix-free) product, the closed-form free fall dv = h g, a FD Jacobian of
+the assembled forces, and a dense Cholesky solve on tiny meshes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_00409_gb300 import workloads as wk
+
+MAT = wk.Material().as_array()
+H_STEP = 1.0 / 200.0
+
+
+def tiny_cloth(nx=6, ny=5, flip_prob=0.3, jitter=0.2, seed=7, contacts=4, pins=(0, 5)):
+    rest, tris, flip = wk.grid_piece(nx, ny, 0.1, 0.08, jitter=jitter, flip_prob=flip_prob, seed=seed)
+    rng = np.random.default_rng(seed)
+    V = nx * ny
+    x = rest.astype(np.float64) + 2e-3 * rng.normal(size=(V, 3))
+    v = 0.05 * rng.normal(size=(V, 3))
+    pairs, w = [], []
+    for _ in range(contacts):
+        while True:
+            p = int(rng.integers(V))
+            t = tris[int(rng.integers(len(tris)))]
+            if p not in t:
+                break
+        pairs.append([p, *t])
+        ww = rng.dirichlet([1, 1, 1])
+        w.append(ww)
+    pairs = np.array(pairs, np.int32).reshape(-1, 4)
+    w = np.array(w).reshape(-1, 3)
+    M = oracle.Mesh(rest, tris, MAT, pins)
+    return M, rest, tris, x, v, pairs, w
+
+
+def test_hinge_count_closed_form():
+    # interior edges of an n x m diagonal-triangulated grid:
+    # (n-1)m + n(m-1) + (n-1)(m-1) edges minus the 2(n-1) + 2(m-1) boundary edges
+    for n, m in [(2, 2), (3, 4), (7, 5), (64, 64)]:
+        rest, tris, _ = wk.grid_piece(n, m, 1.0, 1.0)
+        M = oracle.Mesh(rest, tris, MAT)
+        edges = (n - 1) * m + n * (m - 1) + (n - 1) * (m - 1)
+        assert M.H == edges - 2 * (n - 1) - 2 * (m - 1)
+    rest, tris, _ = wk.grid_piece(64, 64, 1.0, 1.0)
+    assert oracle.Mesh(rest, tris, MAT).H == 11781
+
+
+def test_pattern_equals_brute_force_coupling_set():
+    M, rest, tris, x, v, pairs, w = tiny_cloth()
+    rp, ci = M.pattern(pairs)
+    coupled = np.zeros((M.V, M.V), bool)
+    np.fill_diagonal(coupled, True)
+    for group in list(tris) + list(M.hinges) + list(pairs):
+        for a in group:
+            for b in group:
+                coupled[a, b] = True
+    rows = np.repeat(np.arange(M.V), np.diff(rp))
+    got = np.zeros_like(coupled)
+    got[rows, ci] = True
+    assert (got == coupled).all()
+    assert len(ci) == coupled.sum()
+    for r in range(M.V):  # columns ascending, no duplicates
+        assert (np.diff(ci[rp[r]:rp[r + 1]]) > 0).all()
+
+
+def test_hinge_wings_are_the_opposite_vertices():
+    M, rest, tris, *_ = tiny_cloth(contacts=0)
+    tset = {tuple(sorted(t)) for t in tris}
+    for wa, wb, e0, e1 in M.hinges:
+        assert tuple(sorted((wa, e0, e1))) in tset and tuple(sorted((wb, e0, e1))) in tset
+        assert wa != wb
+
+
+def test_system_symmetric_positive_definite_with_pins_and_contacts():
+    M, rest, tris, x, v, pairs, w = tiny_cloth()
+    rp, ci, vals, b = M.assemble(x, v, pairs, w, H_STEP)
+    A = oracle.dense(rp, ci, vals)
+    np.testing.assert_allclose(A, A.T, rtol=0, atol=1e-14 * np.abs(A).max())
+    np.linalg.cholesky(A)  # raises if not positive definite
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).min() > 0
+    for p in M.pins:  # pin rule
+        assert (b[p] == 0).all()
+        blk = A[3 * p:3 * p + 3]
+        np.testing.assert_array_equal(blk[:, 3 * p:3 * p + 3], M.mass[p] * np.eye(3))
+        assert np.count_nonzero(blk) == 3 and np.count_nonzero(A[:, 3 * p:3 * p + 3]) == 3
+
+
+def test_matrix_free_identity():
+    M, rest, tris, x, v, pairs, w = tiny_cloth(pins=())
+    rp, ci, vals, b = M.assemble(x, v, pairs, w, H_STEP, pins=False)
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        p = rng.normal(size=(M.V, 3))
+        y_mat = oracle.spmv(rp, ci, vals, p)
+        y_free = M.matfree_apply(x, p, pairs, w, H_STEP)
+        np.testing.assert_allclose(y_mat, y_free, rtol=1e-12, atol=1e-14 * np.abs(y_free).max())
+        # and against a dense product
+        np.testing.assert_allclose(oracle.dense(rp, ci, vals) @ p.reshape(-1), y_mat.reshape(-1), rtol=1e-12,
+                                   atol=1e-15)
+
+
+def test_translation_is_mass_only_and_forces_rigid_invariant():
+    M, rest, tris, x, v, pairs, w = tiny_cloth(pins=())
+    rp, ci, vals, b = M.assemble(x, v, pairs, w, H_STEP, pins=False)
+    for t in ([1.0, 0, 0], [0.3, -2.0, 0.7]):
+        T = np.tile(np.array(t), (M.V, 1))
+        y = oracle.spmv(rp, ci, vals, T)
+        np.testing.assert_allclose(y, M.mass[:, None] * T, rtol=1e-10, atol=1e-12 * np.abs(vals).max())
+    f0 = M.forces(x, pairs, w, xt=x)
+    shift = np.array([0.5, -0.2, 1.5])
+    f1 = M.forces(x + shift, pairs, w, xt=x + shift)
+    np.testing.assert_allclose(f1, f0, rtol=1e-9, atol=1e-12 * np.abs(f0).max())
+
+
+def test_assembled_hessian_is_force_jacobian_in_tension():
+    # flat sheet in uniform biaxial tension: the membrane clamp is inactive and every
+    # hinge sits at its rest angle, so -df/dx must equal the assembled K exactly
+    rest, tris, _ = wk.grid_piece(5, 4, 0.1, 0.08, jitter=0.2, seed=3)
+    M = oracle.Mesh(rest, tris, MAT)
+    x = rest.astype(np.float64) * np.array([1.03, 1.05, 1.0])
+    rng = np.random.default_rng(5)
+    pairs = np.array([[0, 6, 7, 11], [13, 1, 2, 6]], np.int32)
+    w = rng.dirichlet([1, 1, 1], size=2)
+    xt = x + 1e-5 * rng.normal(size=x.shape)
+    xt[:, 2] = 0.0
+    x = xt.copy()
+    rp, ci, K = M.hessian(x, pairs, w, xt=xt)
+    Kd = oracle.dense(rp, ci, K)
+    eps = 1e-7
+    J = np.zeros_like(Kd)
+    for j in range(3 * M.V):
+        xp, xm = x.reshape(-1).copy(), x.reshape(-1).copy()
+        xp[j] += eps
+        xm[j] -= eps
+        J[:, j] = (M.forces(xp.reshape(-1, 3), pairs, w, xt) - M.forces(xm.reshape(-1, 3), pairs, w, xt)).reshape(-1) / (2 * eps)
+    np.testing.assert_allclose(Kd, -J, rtol=1e-5, atol=1e-6 * np.abs(Kd).max())
+
+
+def test_rhs_is_h_times_force_at_predicted_positions():
+    M, rest, tris, x, v, pairs, w = tiny_cloth()
+    rp, ci, vals, b = M.assemble(x, v, pairs, w, H_STEP)
+    f = M.forces(x + H_STEP * v, pairs, w, xt=x)
+    f[M.pins] = 0.0
+    np.testing.assert_allclose(b, H_STEP * f, rtol=1e-14, atol=1e-18)
+
+
+@pytest.mark.parametrize("v0", [(0.0, 0.0, 0.0), (0.4, -0.1, 0.2)])
+def test_free_fall_closed_form(v0):
+    # no pins, rest shape, uniform velocity: internal forces vanish at x + h v, A maps
+    # translations to M t, so the exact solution is dv = h g for every vertex
+    rest, tris, _ = wk.grid_piece(9, 7, 0.2, 0.15, jitter=0.2, flip_prob=0.2, seed=9)
+    M = oracle.Mesh(rest, tris, MAT)
+    x = rest.astype(np.float64)
+    v = np.tile(np.array(v0), (M.V, 1))
+    dv, x1, v1, info = M.step(x, v, h=H_STEP, tol=1e-13)
+    np.testing.assert_allclose(dv, np.tile(H_STEP * MAT[5:8], (M.V, 1)), rtol=0, atol=1e-12)
+
+
+def test_pcg_matches_dense_cholesky():
+    M, rest, tris, x, v, pairs, w = tiny_cloth(nx=8, ny=8, contacts=6, pins=(56, 63))
+    rp, ci, vals, b = M.assemble(x, v, pairs, w, H_STEP)
+    A = oracle.dense(rp, ci, vals)
+    L = np.linalg.cholesky(A)
+    ref = np.linalg.solve(L.T, np.linalg.solve(L, b.reshape(-1)))
+    dv, it, rel = oracle.pcg(rp, ci, vals, b, tol=1e-13)
+    assert rel <= 1e-12
+    np.testing.assert_allclose(dv.reshape(-1), ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())
+    assert (dv[M.pins] == 0).all()
+
+
+def test_pcg_reports_non_convergence():
+    M, rest, tris, x, v, pairs, w = tiny_cloth()
+    rp, ci, vals, b = M.assemble(x, v, pairs, w, H_STEP)
+    with pytest.raises(oracle.OracleError):
+        oracle.pcg(rp, ci, vals, b, tol=1e-14, max_iter=2)
+
+
+def test_invalid_mesh_and_pairs_rejected():
+    rest, tris, _ = wk.grid_piece(3, 3, 1.0, 1.0)
+    with pytest.raises(oracle.OracleError):
+        oracle.Mesh(rest, np.array([[0, 1, 9]]), MAT)
+    with pytest.raises(oracle.OracleError):
+        oracle.Mesh(rest, np.array([[0, 1, 1]]), MAT)
+    M = oracle.Mesh(rest, tris, MAT)
+    with pytest.raises(oracle.OracleError):
+        M.pattern(np.array([[0, 0, 1, 2]]))
