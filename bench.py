@@ -1,0 +1,323 @@
+"""Benchmark: implicit-integrator steps/s on the paper-scale cloth (about 1.65M triangles).
+
+One step = the whole hot path through the C ABI (pc_step): dynamic pattern of the step's
+contacts, element evaluation and value assembly, mixed-precision Jacobi-PCG to a
+relative residual of 1e-6, state update. Inputs (rest mesh, state, every step's
+contact pairs) are resident on the device before timing starts.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. With N > 1 (torchrun) every rank runs an independent replica of
+the workload ("replicas only": the path does not shard) and rank 0 reports the
+aggregate over ranks with the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+if HERE not in sys.path:
+    sys.path.insert(0, HERE)
+
+METRIC = "steps/s at 1.65M tris (assemble+PCG to 1e-6); BSR SpMV GB/s vs 8 TB/s"
+FALLBACK_HBM_GBS = 6800.0
+# PCG iterations per step of the paper-scale workload, measured by the CUDA path on
+# GB300 (mixed precision, tol 1e-6); the CPU baseline scales its per-iteration time by it.
+REF_ITERS_PER_STEP = 1500
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="stack3x526")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"])
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--max-iter", type=int, default=20000, help="PCG iteration cap per step (short profiling runs)")
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "block"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name: str):
+    from paper_2008_00409_gb300 import workloads as wk
+    return wk.WORKLOADS[name]()
+
+
+# --------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_hbm():
+    p = os.path.join(HERE, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return float(json.load(open(p))["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# --------------------------------------------------------------------------- CPU oracle sample
+
+
+def oracle_sample(wl, step: int, iters: int = 5):
+    """Time the FP64 oracle on one step of the same workload: pattern + assembly, then
+    `iters` PCG iterations; returns (t_setup, t_per_iter)."""
+    import oracle
+    om = oracle.Mesh.from_workload(wl)
+    pairs, w = wl.contacts(step)
+    t0 = time.perf_counter()
+    rp, ci, vals, b = om.assemble(wl.x0, wl.v0, pairs, w, wl.h)
+    t1 = time.perf_counter()
+    try:
+        oracle.pcg(rp, ci, vals, b, tol=1e-30, max_iter=iters)
+    except oracle.OracleError:
+        pass
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / iters
+
+
+def cpu_baseline(wl, iters_per_step: float):
+    t_setup, t_iter = oracle_sample(wl, 0)
+    per_step = t_setup + iters_per_step * t_iter
+    return {"value": 1.0 / per_step, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 C oracle, single thread: pattern+assembly of step 0 of {wl.name} "
+                       f"({t_setup:.1f} s) + 5 Jacobi-PCG iterations ({t_iter * 1e3:.0f} ms each); per-step time "
+                       f"extrapolated to {iters_per_step:.0f} iterations")}
+
+
+# --------------------------------------------------------------------------- reference arm
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = make_workload(args.workload)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        t_setup, t_iter = oracle_sample(wl, k % max(wl.steps, 1), iters=3)
+        dt = t_setup + REF_ITERS_PER_STEP * t_iter
+        if k >= args.warmup:
+            times.append(dt)
+    per_step = float(np.mean(times))
+    value = 1.0 / per_step
+    out = {"metric": METRIC, "value": value, "unit": "steps/s", "impl": "reference", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl.name, "V": wl.V, "T": wl.T, "contacts_per_step": wl.n_contacts, "tol": args.tol},
+           "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                            "sample": ("per step: FP64 oracle pattern+assembly of the full system + 3 PCG "
+                                       f"iterations, time extrapolated to {REF_ITERS_PER_STEP} iterations")},
+           "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------------- our arm
+
+
+def run_ours(args):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2008_00409_gb300 import build as cuda_build
+    if local == 0:
+        cuda_build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2008_00409_gb300 import pcloth as pc
+
+    wl = make_workload(args.workload)
+    cl = pc.Cloth(wl)
+    prec = pc.PC_PREC_MIXED if args.precision == "mixed" else pc.PC_PREC_FP32
+    precond = pc.PC_PRECOND_BLOCK if args.precond == "block" else pc.PC_PRECOND_JACOBI
+    nsteps = args.warmup + args.steps
+    contacts = [cl.contacts_device(k % max(wl.steps, 1)) for k in range(nsteps)]
+    torch.cuda.synchronize()
+
+    def one_step(k):
+        pd, wd = contacts[k]
+        info, st = cl.step(pd, wd, tol=args.tol, precision=prec, warm_start=pc.PC_WARM_PREV,
+                           max_iter=args.max_iter, precond=precond, allow_not_converged=True)
+        return info
+
+    for k in range(args.warmup):
+        one_step(k)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = pc.pc_launch_count(cl.ctx)
+    pc.pc_spmv_stats(cl.ctx)  # reset
+    pc.pc_set_profiling(cl.ctx, True)
+    iters, rels = [], []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for k in range(args.warmup, nsteps):
+            info = one_step(k)
+            iters.append(info.solve.iters)
+            rels.append(info.solve.rel_res)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    pc.pc_set_profiling(cl.ctx, False)
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = pc.pc_launch_count(cl.ctx) - launches0
+    n_spmv, spmv_ms, nnzb = pc.pc_spmv_stats(cl.ctx)
+    if world > 1:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        dist.barrier()
+    value = world * args.steps / elapsed
+
+    # roofline of the dominant kernel: the fused PCG SpMV (difference form)
+    V = wl.V
+    spmv_bytes = 40 * nnzb + 4 * (V + 1) + 36 * V + 4 * 12 * V
+    avg_spmv_s = (spmv_ms / 1e3) / max(n_spmv, 1)
+    achieved = spmv_bytes / avg_spmv_s / 1e9 if n_spmv else None
+    peak, peak_src = measured_hbm()
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(wl.x0.copy()).pin_memory().numpy()
+        vh = torch.from_numpy(wl.v0.copy()).pin_memory().numpy()
+        host_contacts = [wl.contacts(k % max(wl.steps, 1)) for k in range(nsteps)]
+        host_contacts = [(torch.from_numpy(p).pin_memory().numpy(), torch.from_numpy(w).pin_memory().numpy())
+                         for p, w in host_contacts]
+        cl_e = pc.Cloth(wl)
+        o = pc.pc_step_opts()
+        o.h = wl.h
+        o.solve = pc.solve_opts(tol=args.tol, precision=prec, max_iter=args.max_iter, precond=precond)
+        o.warm_start = pc.PC_WARM_PREV
+        for k in range(args.warmup):
+            pc.pc_step_host(cl_e.ctx, xh, vh, host_contacts[k][0], host_contacts[k][1], o, allow_not_converged=True)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.warmup, nsteps):
+            pc.pc_step_host(cl_e.ctx, xh, vh, host_contacts[k][0], host_contacts[k][1], o, allow_not_converged=True)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        P = wl.n_contacts
+        e2e = {"value": world * args.steps / te, "unit": "steps/s", "h2d_bytes_per_step": 24 * V + 28 * P,
+               "d2h_bytes_per_step": 24 * V}
+        cl_e.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, float(np.mean(iters)) if iters else REF_ITERS_PER_STEP)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "V": V, "T": wl.T, "H": cl.H, "nnzb": int(nnzb),
+                       "contacts_per_step": wl.n_contacts, "precision": args.precision, "tol": args.tol,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (matrix about 440 MB per SpMV)",
+                       "pcg_iters_per_step": float(np.mean(iters)), "max_rel_res": float(np.max(rels))},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "kernel": "spmv_kernel<DIFF,PCG> (fused SpMV + direction update + p.q)",
+                         "bytes_per_launch": spmv_bytes, "peak_source": peak_src,
+                         "avg_launch_us": avg_spmv_s * 1e6, "timed_launches": n_spmv},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
+        }
+        print(json.dumps(out), flush=True)
+    cl.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

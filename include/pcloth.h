@@ -1,0 +1,241 @@
+/*
+ * pcloth.h -- C ABI of the GB300 (sm_103a) implicit-integrator hot path of P-Cloth
+ * (Li, Tang, Manocha et al., SIGGRAPH Asia 2020).
+ *
+ * One time step of the method (Sec. 2.5, Eq. 3) solves
+ *
+ *     (M - h^2 J) dv = h f(x_t + h v_t),        J = df/dx at x_t,
+ *
+ * for the velocity increment dv, where the matrix is assembled anew each step from the
+ * mesh's assembly elements (Sec. 3.2: membrane triangles, bending hinges, contact pairs,
+ * gravity) and its sparsity pattern changes with the step's contact pairs (Sec. 3, first
+ * paragraph). The system is solved with preconditioned conjugate gradients, whose cost
+ * is the block-sparse matrix-vector product (Sec. 3.1).
+ *
+ * Conventions (every entry point):
+ *  - Returns a pc_status; nothing throws or exits across the ABI and device code never
+ *    traps. pc_status_string() turns a code into text.
+ *  - Array arguments are DEVICE pointers owned by the caller, contiguous, 16-byte
+ *    aligned, unless a parameter says "host". Indices are int32, values float32 unless
+ *    stated. Vectors are float[V][3] (x, y, z per vertex).
+ *  - Block matrices are block-CSR with 3x3 blocks ("BSR"): row_ptr[V+1], col_idx[nnzb]
+ *    with columns ascending within a row and the diagonal block always present,
+ *    vals[nnzb][9] row-major blocks. Block capacities must be multiples of 4.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Work is
+ *    stream-ordered; calls that return host-visible results (counts, solve info)
+ *    synchronize the stream before returning.
+ *  - A context (pc_ctx) holds one mesh's rest state and all scratch memory. It is
+ *    allocated once by pc_create; no other call allocates device memory.
+ */
+#ifndef PCLOTH_H
+#define PCLOTH_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PC_API __attribute__((visibility("default")))
+#else
+#define PC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pc_status;
+#define PC_OK 0
+#define PC_ERR_ARG 1            /* invalid argument (null, size, alignment, index out of range) */
+#define PC_ERR_CAPACITY 2       /* output buffer too small; the required size is reported */
+#define PC_ERR_NOT_CONVERGED 3  /* PCG hit max_iter; outputs hold the last iterate and its residual */
+#define PC_ERR_NONFINITE 4      /* NaN/Inf met in the right-hand side or a PCG scalar */
+#define PC_ERR_TIMEOUT 5        /* a bounded device wait gave up */
+#define PC_ERR_CUDA 6           /* a CUDA runtime call failed */
+#define PC_ERR_MESH 7           /* degenerate triangle or an edge shared by more than two triangles */
+
+#define PC_PREC_FP32 0   /* FP32 PCG (FP64 dot products) */
+#define PC_PREC_MIXED 1  /* FP32 PCG with FP64 residual recomputation and refinement */
+
+#define PC_WARM_ZERO 0   /* initial guess dv = 0 */
+#define PC_WARM_PREV 1   /* initial guess = previous step's dv */
+#define PC_WARM_GIVEN 2  /* initial guess = the dv buffer passed in */
+
+typedef struct pc_ctx pc_ctx;
+
+/* Material of the cloth (SI units). Membrane: St. Venant-Kirchhoff, plane stress,
+ * Young's modulus x thickness `young` (N/m) and `poisson`. Bending: dihedral hinges with
+ * stiffness `k_bend` (N m). Contact: hold penalty `k_contact` (N/m). */
+typedef struct {
+    float rho;         /* area density, kg/m^2 */
+    float young;       /* N/m */
+    float poisson;
+    float k_bend;      /* N m */
+    float k_contact;   /* N/m */
+    float gravity[3];  /* m/s^2 */
+} pc_material;
+
+/* Contact pairs of one step (Sec. 4: proximity forces inside the implicit integrator;
+ * here they arrive as input). Pair i couples vertex p = pairs[4i] with triangle
+ * (a, b, c) = pairs[4i+1..4i+3] through barycentric weights w[3i..3i+2] (sum 1). All
+ * four vertices must be distinct and in range. Device pointers; n may be 0. */
+typedef struct {
+    int32_t n;
+    const int32_t *pairs;  /* device [n][4] */
+    const float *w;        /* device [n][3] */
+} pc_contacts;
+
+/* Caller-owned BSR pattern buffers. */
+typedef struct {
+    int32_t *row_ptr;  /* device [V+1] */
+    int32_t *col_idx;  /* device [cap] */
+    int64_t cap;       /* capacity in blocks, multiple of 4 */
+    int64_t nnzb;      /* out: number of blocks */
+} pc_bsr;
+
+#define PC_PRECOND_JACOBI 0  /* inverse of the scalar diagonal of A */
+#define PC_PRECOND_BLOCK 1   /* inverse of each 3x3 diagonal block of A */
+
+typedef struct {
+    double tol;          /* stop when |b - A dv|_2 / |b|_2 <= tol (default 1e-6) */
+    int32_t max_iter;    /* total PCG iterations (default 20000) */
+    int32_t precision;   /* PC_PREC_FP32 or PC_PREC_MIXED */
+    double refresh;      /* PC_PREC_MIXED: recompute the residual in FP64 whenever |r| has
+                            dropped by this factor since the last recomputation (default 1e-2) */
+    int32_t refresh_every; /* PC_PREC_MIXED: ... or after this many iterations (default 1000) */
+    int32_t check_every; /* iterations between convergence checks on the host (default 32) */
+    int32_t precond;     /* PC_PRECOND_JACOBI (default) or PC_PRECOND_BLOCK */
+    int32_t reserved;
+} pc_solve_opts;
+
+typedef struct {
+    int32_t iters;      /* PCG iterations (all inner solves) */
+    int32_t outer;      /* FP64 residual recomputations (PC_PREC_MIXED), 0 for FP32 */
+    double rel_res;     /* |b - A dv| / |b| recomputed in FP64 at exit */
+    double bnorm;       /* |b|_2 */
+} pc_solve_info;
+
+typedef struct {
+    float h;              /* time step, s */
+    pc_solve_opts solve;
+    int32_t warm_start;   /* PC_WARM_ZERO or PC_WARM_PREV */
+} pc_step_opts;
+
+typedef struct {
+    int64_t nnzb;
+    pc_solve_info solve;
+} pc_step_info;
+
+/* Text for a status code (static storage). */
+PC_API const char *pc_status_string(pc_status s);
+
+/* Text of the most recent CUDA runtime failure seen by the library (static storage,
+ * empty if none); PC_ERR_CUDA results point here. */
+PC_API const char *pc_last_cuda_error(void);
+
+/* Fill *o with the defaults named in pc_solve_opts. */
+PC_API void pc_default_solve_opts(pc_solve_opts *o);
+
+/* Create a context for a triangle mesh and precompute its rest state on the GPU:
+ * per-triangle rest edge matrices and areas, lumped masses (rho * area / 3 per incident
+ * triangle), the interior-edge hinges (two triangles per edge) with their rest angle and
+ * coefficient 3|e|^2/(A1 + A2), the static block pattern of the mesh elements, and the
+ * vertex-to-element incidence (Sec. 3.2.1: elements grouped by the rows they touch).
+ *   V, T        vertex and triangle counts (V >= 1, T >= 0, 3T < 2^28)
+ *   tris        device int32[T][3]
+ *   rest        device float[V][3] rest positions (each triangle non-degenerate)
+ *   pins        device int32[n_pins] pinned vertices (their dv is 0), may be NULL if n_pins = 0
+ *   mat         host pointer to the material
+ *   max_contacts  largest contact count any later call will pass
+ * On failure *out is NULL and nothing is leaked. PC_ERR_MESH reports degenerate
+ * triangles and edges shared by three or more triangles. Synchronizes `stream`. */
+PC_API pc_status pc_create(pc_ctx **out, int32_t V, int32_t T, const int32_t *tris, const float *rest, const int32_t *pins,
+                    int32_t n_pins, const pc_material *mat, int32_t max_contacts, void *stream);
+
+/* Release a context and everything it owns (NULL is a no-op). */
+PC_API pc_status pc_destroy(pc_ctx *ctx);
+
+/* Sizes known to the context: V, T, hinge count H and the static (contact-free)
+ * pattern's block count. Host pointers, each may be NULL. */
+PC_API pc_status pc_get_sizes(const pc_ctx *ctx, int32_t *V, int32_t *T, int32_t *H, int64_t *static_nnzb);
+
+/* Copy the hinges found by pc_create: int32[H][4] = (wing0, wing1, edge0, edge1), edge
+ * ordered as in the lower-indexed triangle, hinges sorted by edge key min*V+max; and the
+ * lumped masses float[V]. Device pointers, either may be NULL. */
+PC_API pc_status pc_get_rest(const pc_ctx *ctx, int32_t *hinges, float *mass, void *stream);
+
+/* Sec. 3.2.2, dynamic matrix assembly, pattern half: the step's block pattern is the set
+ * of (row, col) vertex pairs coupled by any triangle, hinge or contact pair of this step,
+ * plus the diagonal, sorted by (row, col) with duplicates removed. The contact keys are
+ * sorted with a key sort and merged into the static pattern (no atomics), so row_ptr and
+ * col_idx are bit-exact and deterministic.
+ * On return A->nnzb holds the block count. If it exceeds A->cap the call returns
+ * PC_ERR_CAPACITY with A->nnzb = required size and col_idx untouched beyond cap.
+ * Synchronizes `stream`. */
+PC_API pc_status pc_assemble_pattern(pc_ctx *ctx, const pc_contacts *contacts, pc_bsr *A, void *stream);
+
+/* Sec. 3.2.2, value half, and Eq. 3: writes
+ *   vals[nnzb][9]  A = M + h^2 sum_e H_e(x_t)   (element Hessians: membrane with its stress
+ *                  clamped to the positive part, Gauss-Newton bending, contact penalty)
+ *   b[V][3]        b = h f(x_t + h v_t)         (f includes gravity)
+ * on the pattern that pc_assemble_pattern produced for the same contacts. Pinned vertex
+ * i: row and column blocks zero except A_ii = m_i I, b_i = 0.
+ * dres (optional, float[V][9], may be NULL) receives the "difference-form" diagonal
+ * D_i = m_i I - sum over pinned neighbours j of the unzeroed block A_ij, with which
+ * (A p)_i = D_i p_i + sum_{j != i} A_ij (p_j - p_i) holds exactly for this model (every
+ * element's Hessian rows sum to zero). Element contributions are combined per row by a
+ * warp-level reduction in a fixed order (no atomics): results are deterministic and
+ * A is bitwise symmetric. x, v: device float[V][3]. Does not synchronize. */
+PC_API pc_status pc_assemble_values(pc_ctx *ctx, const pc_bsr *A, const float *x, const float *v,
+                             const pc_contacts *contacts, float h, float *vals, float *b, float *dres,
+                             void *stream);
+
+/* y = A x for a BSR matrix (V rows). With dres != NULL the product is formed in the
+ * difference form above (the diagonal blocks in vals are not used). */
+PC_API pc_status pc_bsr_spmv(pc_ctx *ctx, const pc_bsr *A, const float *vals, const float *dres, const float *x,
+                      float *y, void *stream);
+
+/* Sec. 2.5: solve A dv = b by preconditioned conjugate gradients (Jacobi: the scalar
+ * diagonal of A, or its 3x3 diagonal blocks). dv holds the initial guess on entry and the
+ * solution on exit. opts == NULL uses the defaults. With dres != NULL the matrix
+ * products use the difference form (more accurate for stiff systems whose rows sum to
+ * the mass).
+ * PC_PREC_FP32: FP32 vectors and products, FP64 dot-product accumulation; stops on the
+ * recurrence residual. The FP64 residual of the FP32 iterate is reported in info.
+ * PC_PREC_MIXED: the matrix and the PCG vectors stay FP32, but the solution is kept as
+ * an FP64 accumulator plus an FP32 increment. Whenever the recurrence residual has
+ * dropped by `refresh` (or every `refresh_every` iterations, and whenever it meets tol),
+ * the increment is added into the accumulator in FP64 and the residual r = b - A dv is
+ * recomputed in FP64 and replaces the recurrence residual, without restarting the search
+ * direction (iterative refinement by residual replacement). The solve stops when the
+ * FP64 residual meets tol.
+ * info (host, may be NULL) receives iterations and the FP64 true relative residual.
+ * Returns PC_ERR_NOT_CONVERGED (dv = last iterate) or PC_ERR_NONFINITE when those occur.
+ * Synchronizes `stream`. */
+PC_API pc_status pc_pcg_solve(pc_ctx *ctx, const pc_bsr *A, const float *vals, const float *dres, const float *b,
+                       float *dv, const pc_solve_opts *opts, pc_solve_info *info, void *stream);
+
+/* One time step on device state: pattern, values (with the difference-form diagonal),
+ * PCG solve, then v += dv, x += h v. Uses buffers owned by the context. dv_out (device
+ * float[V][3], may be NULL) receives dv. Synchronizes `stream`. */
+PC_API pc_status pc_step(pc_ctx *ctx, float *x, float *v, const pc_contacts *contacts, const pc_step_opts *opts,
+                  float *dv_out, pc_step_info *info, void *stream);
+
+/* pc_step on HOST buffers: copies x, v (host float[V][3]) and the contacts (host
+ * int32[n][4], float[n][3]) to the device, runs pc_step, and copies x and v back. Host
+ * buffers may be pageable or pinned. */
+PC_API pc_status pc_step_host(pc_ctx *ctx, float *x_host, float *v_host, int32_t n_contacts, const int32_t *pairs_host,
+                       const float *w_host, const pc_step_opts *opts, pc_step_info *info, void *stream);
+
+/* Kernel launches issued by this context since creation (all entry points). */
+PC_API int64_t pc_launch_count(const pc_ctx *ctx);
+
+/* When enabled, the PCG loop brackets every SpMV launch with CUDA events on its stream
+ * and accumulates their durations; pc_spmv_stats returns (launches, total ms, block
+ * count of the last matrix) and resets the counters. */
+PC_API pc_status pc_set_profiling(pc_ctx *ctx, int32_t enable);
+PC_API pc_status pc_spmv_stats(pc_ctx *ctx, int64_t *launches, double *total_ms, int64_t *nnzb);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCLOTH_H */

@@ -174,7 +174,8 @@ class Mesh:
         return rp, ci, vals
 
     def assemble(self, x, v, pairs=None, w=None, h=1.0 / 200.0, pins=True, pattern=None):
-        """Eq. 3 system: (A = M + h^2 K(x_t), b = h f(x_t + h v_t)) with the pin rule."""
+        """Eq. 3 system: A = M + h^2 K(x_t), b = h (f(x_t) - h K(x_t) v_t) (the first-order
+        expansion of h f(x_t + h v_t), Eq. 2), with the pin rule."""
         pairs, w = self._contacts(pairs, w)
         x = _f64(x).reshape(-1, 3)
         v = _f64(v).reshape(-1, 3)

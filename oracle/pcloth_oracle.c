@@ -15,7 +15,11 @@
  *    incident triangles of rho * A0 / 3).
  *  - Sec. 2.5, Eq. 2-3: backward Euler with a first-order Taylor expansion of f,
  *      (M - h^2 J) dv = h f(x_t + h v_t),   J = df/dx at x_t,
- *    with J replaced by minus the sum of positive-semidefinite element Hessians.
+ *    with J replaced by minus the sum of positive-semidefinite element Hessians K, and
+ *    the right-hand side read to first order as Eq. 2 prescribes:
+ *      f(x_t + h v_t) ~= f(x_t) + h J v_t,  so  b = h (f(x_t) - h K v_t).
+ *    (Evaluating the force at x_t + h v_t without linearising is unstable for the stiff
+ *    membranes of the workloads: it extrapolates rotations into spurious stretch.)
  *  - Sec. 3.2: "assembly elements" forming f and J. The paper names the forces
  *    (stretching, bending, contact, gravity; it cites Bridson et al. 2002 and Otaduy
  *    et al. 2009) but gives no formulas, so this file uses:
@@ -542,14 +546,23 @@ int om_hessian(const om_mesh *M, const double *x, int P, const int *pairs, const
     return OM_OK;
 }
 
-/* Eq. 3: A = M + h^2 K(x_t), b = h f(x_t + h v_t), then pins. `pinned` nonzero applies
- * the pin rule (rows/cols zero, A_ii = m_i I, b_i = 0). */
+/* Eq. 3 with its right-hand side taken to first order, as Eq. 2 prescribes:
+ *   f(x_t + h v_t) ~= f(x_t) + J h v_t,  J = -K(x_t),
+ * so A = M + h^2 K(x_t) and b = h (f(x_t) - h K(x_t) v_t), K the same sum of element
+ * Hessians in both. Then the pin rule if `apply_pins` is nonzero (pinned rows/cols zero,
+ * A_ii = m_i I, b_i = 0). */
 int om_assemble(const om_mesh *M, const double *x, const double *v, int P, const int *pairs, const double *w,
                 double h, int apply_pins, const int *row_ptr, const int *col_idx, double *vals, double *b)
 {
     int V = M->V;
     int st = om_hessian(M, x, P, pairs, w, x, row_ptr, col_idx, vals);
     if (st != OM_OK) return st;
+    double *Kv = malloc(sizeof(double) * 3 * (size_t)V);
+    om_spmv(V, row_ptr, col_idx, vals, v, Kv);
+    st = om_forces(M, x, P, pairs, w, x, b);
+    if (st != OM_OK) { free(Kv); return st; }
+    for (long k = 0; k < 3L * V; ++k) b[k] = h * (b[k] - h * Kv[k]);
+    free(Kv);
     long nnzb = row_ptr[V];
     for (long s = 0; s < 9 * nnzb; ++s) vals[s] *= h * h;
     for (int i = 0; i < V; ++i) {
@@ -557,12 +570,6 @@ int om_assemble(const om_mesh *M, const double *x, const double *v, int P, const
         if (s < 0) return OM_ERR_PATTERN;
         for (int a = 0; a < 3; ++a) vals[9 * s + 4 * a] += M->mass[i];
     }
-    double *xs = malloc(sizeof(double) * 3 * (size_t)V);
-    for (long k = 0; k < 3L * V; ++k) xs[k] = x[k] + h * v[k];
-    st = om_forces(M, xs, P, pairs, w, x, b);
-    free(xs);
-    if (st != OM_OK) return st;
-    for (long k = 0; k < 3L * V; ++k) b[k] *= h;
     if (apply_pins) {
         for (int r = 0; r < V; ++r)
             for (int s = row_ptr[r]; s < row_ptr[r + 1]; ++s) {

@@ -1,0 +1,90 @@
+// Time step driver (Sec. 2.5: each step assembles Eq. 3 anew and solves it) and small
+// ABI utilities.
+#include "pc_internal.cuh"
+
+extern "C" const char *pc_status_string(pc_status s)
+{
+    switch (s) {
+    case PC_OK: return "ok";
+    case PC_ERR_ARG: return "invalid argument";
+    case PC_ERR_CAPACITY: return "output capacity too small";
+    case PC_ERR_NOT_CONVERGED: return "PCG did not converge within max_iter";
+    case PC_ERR_NONFINITE: return "non-finite value in the system or a PCG scalar";
+    case PC_ERR_TIMEOUT: return "bounded device wait timed out";
+    case PC_ERR_CUDA: return "CUDA runtime error";
+    case PC_ERR_MESH: return "invalid mesh (degenerate triangle or non-manifold edge)";
+    default: return "unknown status";
+    }
+}
+
+extern "C" int64_t pc_launch_count(const pc_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" pc_status pc_set_profiling(pc_ctx *ctx, int32_t enable)
+{
+    if (!ctx) return PC_ERR_ARG;
+    ctx->profiling = enable ? 1 : 0;
+    return PC_OK;
+}
+
+extern "C" pc_status pc_spmv_stats(pc_ctx *ctx, int64_t *launches, double *total_ms, int64_t *nnzb)
+{
+    if (!ctx) return PC_ERR_ARG;
+    if (launches) *launches = ctx->spmv_launches;
+    if (total_ms) *total_ms = ctx->spmv_ms;
+    if (nnzb) *nnzb = ctx->spmv_nnzb;
+    ctx->spmv_launches = 0;
+    ctx->spmv_ms = 0.0;
+    return PC_OK;
+}
+
+extern "C" pc_status pc_step(pc_ctx *ctx, float *x, float *v, const pc_contacts *contacts, const pc_step_opts *opts,
+                             float *dv_out, pc_step_info *info, void *stream)
+{
+    if (!ctx || !x || !v || !opts) return PC_ERR_ARG;
+    if (!(opts->h > 0.0f)) return PC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    pc_bsr A{ctx->A_rp, ctx->A_ci, ctx->A_cap, 0};
+    PC_TRY(pc_assemble_pattern(ctx, contacts, &A, stream));
+    PC_TRY(pc_assemble_values(ctx, &A, x, v, contacts, opts->h, ctx->A_vals, ctx->A_b, ctx->A_dres, stream));
+    if (opts->warm_start != PC_WARM_PREV || !ctx->has_prev_dv)
+        PC_CUDA_TRY(cudaMemsetAsync(ctx->A_dv, 0, sizeof(float) * 3 * (size_t)ctx->V, st));
+    pc_solve_info si{};
+    pc_status s = pc_pcg_solve(ctx, &A, ctx->A_vals, ctx->A_dres, ctx->A_b, ctx->A_dv, &opts->solve, &si, stream);
+    if (info) {
+        info->nnzb = A.nnzb;
+        info->solve = si;
+    }
+    if (s != PC_OK && s != PC_ERR_NOT_CONVERGED) return s;
+    ctx->has_prev_dv = 1;
+    PC_TRY(pc_update_state(ctx, x, v, ctx->A_dv, opts->h, st));
+    if (dv_out)
+        PC_CUDA_TRY(cudaMemcpyAsync(dv_out, ctx->A_dv, sizeof(float) * 3 * (size_t)ctx->V, cudaMemcpyDeviceToDevice, st));
+    PC_CUDA_TRY(cudaStreamSynchronize(st));
+    return s;
+}
+
+extern "C" pc_status pc_step_host(pc_ctx *ctx, float *x_host, float *v_host, int32_t n_contacts,
+                                  const int32_t *pairs_host, const float *w_host, const pc_step_opts *opts,
+                                  pc_step_info *info, void *stream)
+{
+    if (!ctx || !x_host || !v_host || !opts) return PC_ERR_ARG;
+    if (n_contacts < 0 || n_contacts > ctx->max_contacts || (n_contacts > 0 && (!pairs_host || !w_host)))
+        return PC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t vb = sizeof(float) * 3 * (size_t)ctx->V;
+    float *dx = ctx->h_state, *dvel = ctx->h_state + 3ll * ctx->V;
+    PC_CUDA_TRY(cudaMemcpyAsync(dx, x_host, vb, cudaMemcpyHostToDevice, st));
+    PC_CUDA_TRY(cudaMemcpyAsync(dvel, v_host, vb, cudaMemcpyHostToDevice, st));
+    if (n_contacts > 0) {
+        PC_CUDA_TRY(cudaMemcpyAsync(ctx->h_pairs, pairs_host, sizeof(int32_t) * 4 * (size_t)n_contacts,
+                                    cudaMemcpyHostToDevice, st));
+        PC_CUDA_TRY(cudaMemcpyAsync(ctx->h_w, w_host, sizeof(float) * 3 * (size_t)n_contacts, cudaMemcpyHostToDevice, st));
+    }
+    pc_contacts c{n_contacts, ctx->h_pairs, ctx->h_w};
+    pc_status s = pc_step(ctx, dx, dvel, &c, opts, nullptr, info, stream);
+    if (s != PC_OK && s != PC_ERR_NOT_CONVERGED) return s;
+    PC_CUDA_TRY(cudaMemcpyAsync(x_host, dx, vb, cudaMemcpyDeviceToHost, st));
+    PC_CUDA_TRY(cudaMemcpyAsync(v_host, dvel, vb, cudaMemcpyDeviceToHost, st));
+    PC_CUDA_TRY(cudaStreamSynchronize(st));
+    return s;
+}

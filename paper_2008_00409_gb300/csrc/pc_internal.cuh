@@ -1,0 +1,214 @@
+// Internal definitions shared by the CUDA translation units of libpcloth.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/pcloth.h"
+
+// ------------------------------------------------------------------------- error handling
+
+#define PC_CUDA_TRY(expr)                                                                   \
+    do {                                                                                    \
+        cudaError_t _e = (expr);                                                            \
+        if (_e != cudaSuccess) {                                                            \
+            pc_note_cuda_error(_e, #expr, __FILE__, __LINE__);                              \
+            return PC_ERR_CUDA;                                                             \
+        }                                                                                   \
+    } while (0)
+
+#define PC_TRY(expr)                 \
+    do {                             \
+        pc_status _s = (expr);       \
+        if (_s != PC_OK) return _s;  \
+    } while (0)
+
+void pc_note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// device error bits (ctx->d_err)
+#define PC_DERR_INDEX 1u      // an index was out of range
+#define PC_DERR_PAIR 2u       // a contact pair repeats a vertex
+#define PC_DERR_MESH 4u       // non-manifold edge / degenerate triangle
+#define PC_DERR_CAPACITY 8u   // output capacity exceeded
+#define PC_DERR_NONFINITE 16u // NaN / Inf met
+
+// element reference encoding in incidence lists: type(2) | local(2) | id(28)
+#define PC_REF_TRI 0u
+#define PC_REF_HINGE 1u
+#define PC_REF_CONTACT 2u
+__host__ __device__ inline uint32_t pc_ref(uint32_t type, uint32_t local, uint32_t id)
+{
+    return (type << 30) | (local << 28) | id;
+}
+__host__ __device__ inline uint32_t pc_ref_type(uint32_t r) { return r >> 30; }
+__host__ __device__ inline uint32_t pc_ref_local(uint32_t r) { return (r >> 28) & 3u; }
+__host__ __device__ inline uint32_t pc_ref_id(uint32_t r) { return r & 0x0FFFFFFFu; }
+
+// per-element buffer strides (floats)
+#define PC_TRI_STRIDE 64     // 9 forces + 6 upper 3x3 Hessian blocks (54) + 1 pad
+#define PC_HINGE_STRIDE 24   // 12 forces + 12 scaled angle gradient
+#define PC_CONTACT_STRIDE 20 // 12 forces + normal(3) + weights(3) + scale(1) + pad
+
+// PCG scalar block, lives in device memory
+struct pc_scalars {
+    double rz;       // r.z of the current iterate
+    double pq;       // p.q of the current direction
+    double rr;       // r.r
+    double bb;       // b.b
+    double alpha, beta;
+    double tol2;     // tol^2 * bb, stop threshold on rr
+    int32_t iter;
+    int32_t max_iter;
+    int32_t done;     // 1 converged / stopped
+    int32_t status;   // pc_status of the solve
+    uint32_t counter; // last-block reduction ticket
+    uint32_t pad;
+};
+
+// ------------------------------------------------------------------------- radix sort scratch
+struct pc_sort_scratch {
+    uint64_t *keys_alt = nullptr;
+    uint32_t *vals_alt = nullptr;
+    uint32_t *hist = nullptr;      // [256 * tiles]
+    int64_t cap = 0;               // keys capacity
+    int64_t hist_cap = 0;
+};
+
+struct pc_ctx {
+    int device = 0;
+    int32_t V = 0, T = 0, H = 0;
+    int32_t max_contacts = 0;
+    int32_t n_pins = 0;
+    pc_material mat{};
+    float mu = 0, lam = 0;
+    int num_sms = 0;
+
+    // rest data
+    int32_t *tri = nullptr;        // [T][3]
+    float *rest = nullptr;         // [V][3]
+    float *tri_dmi = nullptr;      // [T][4] inverse rest edge matrix
+    float *tri_area = nullptr;     // [T]
+    float *tri_rgram = nullptr;    // [T][6] rest Gram (11, 22, 12) as (hi, lo) float pairs
+    float *mass = nullptr;         // [V]
+    uint8_t *pinned = nullptr;     // [V]
+    int32_t *hinge = nullptr;      // [H][4] wing0, wing1, edge0, edge1
+    float *hcoef = nullptr;        // [H] 2 kb c_h
+    float *hrest = nullptr;        // [H] rest angle
+
+    // static pattern and incidence
+    int64_t snnz = 0;
+    int32_t *srp = nullptr;        // [V+1]
+    int32_t *scol = nullptr;       // [snnz]
+    int32_t *vinc_ptr = nullptr;   // [V+1]
+    uint32_t *vinc = nullptr;      // [3T + 4H] element refs grouped by vertex
+
+    // per-step contact data
+    uint64_t *dkeys = nullptr;     // [6 * maxP] dynamic pattern keys (sorted)
+    uint64_t *dnew = nullptr;      // [6 * maxP] keys not in the static pattern
+    int32_t *dflag = nullptr;      // [6 * maxP + 1]
+    int32_t *dscan = nullptr;      // [6 * maxP + 1]
+    uint64_t *ckeys = nullptr;     // [4 * maxP] incidence keys (vertex)
+    uint32_t *cinc = nullptr;      // [4 * maxP] contact refs grouped by vertex
+    int32_t *cinc_ptr = nullptr;   // [V+1]
+    int32_t n_new = 0;
+    int32_t n_contacts = 0;        // contacts of the last pattern call
+    const int32_t *last_pairs = nullptr;
+
+    // element buffers
+    float *tri_buf = nullptr;      // [T][PC_TRI_STRIDE]
+    float *hinge_buf = nullptr;    // [H][PC_HINGE_STRIDE]
+    float *cont_buf = nullptr;     // [maxP][PC_CONTACT_STRIDE]
+
+    // solver scratch
+    float *r = nullptr, *z = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr, *dinv = nullptr;
+    float *dtmp = nullptr;         // inner solution (mixed precision)
+    float *rhs32 = nullptr;        // inner right-hand side (mixed precision)
+    double *x64 = nullptr, *r64 = nullptr;
+    double *partials = nullptr;    // [max_blocks][4]
+    pc_scalars *sc = nullptr;      // device scalars
+    pc_scalars *sc_host = nullptr; // pinned host mirror
+    int32_t max_red_blocks = 0;
+
+    // context-owned step system
+    int32_t *A_rp = nullptr, *A_ci = nullptr;
+    int64_t A_cap = 0;
+    float *A_vals = nullptr, *A_dres = nullptr, *A_b = nullptr, *A_dv = nullptr;
+    int has_prev_dv = 0;
+
+    // host-buffer step staging
+    float *h_state = nullptr;      // device [2][V][3]
+    int32_t *h_pairs = nullptr;    // device [maxP][4]
+    float *h_w = nullptr;          // device [maxP][3]
+
+    // generic scratch
+    pc_sort_scratch sort;
+    uint32_t *d_err = nullptr;     // device error bits
+    uint32_t *h_err = nullptr;     // pinned host mirror
+    int64_t *d_count = nullptr;    // device scalar (counts)
+    int64_t *h_count = nullptr;    // pinned host mirror
+    int32_t *scan_tmp = nullptr;   // block sums for scans
+    int64_t scan_tmp_cap = 0;
+
+    // profiling
+    int profiling = 0;
+    int64_t launches = 0;
+    int64_t spmv_launches = 0;
+    double spmv_ms = 0.0;
+    int64_t spmv_nnzb = 0;
+    cudaEvent_t ev[2 * 64] = {};
+    int ev_used = 0;
+};
+
+// launch bookkeeping: every kernel launch in the library goes through this
+#define PC_LAUNCH(ctx, kernel, grid, block, smem, stream, ...)                          \
+    do {                                                                              \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                   \
+        (ctx)->launches++;                                                            \
+        cudaError_t _le = cudaGetLastError();                                         \
+        if (_le != cudaSuccess) {                                                     \
+            pc_note_cuda_error(_le, #kernel, __FILE__, __LINE__);                     \
+            return PC_ERR_CUDA;                                                       \
+        }                                                                             \
+    } while (0)
+
+inline unsigned pc_blocks(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 0x7FFFFFFF) b = 0x7FFFFFFF;
+    return (unsigned)b;
+}
+
+inline bool pc_aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// ------------------------------------------------------------------------- shared helpers (host side)
+pc_status pc_radix_sort(pc_ctx *ctx, uint64_t *keys, uint32_t *vals, int64_t n, int bits, cudaStream_t st);
+pc_status pc_exclusive_scan(pc_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, cudaStream_t st);
+pc_status pc_sort_reserve(pc_ctx *ctx, int64_t n);
+pc_status pc_read_errors(pc_ctx *ctx, cudaStream_t st, uint32_t *bits);
+pc_status pc_setup_rest(pc_ctx *ctx, cudaStream_t st);
+pc_status pc_update_state(pc_ctx *ctx, float *x, float *v, const float *dv, float h, cudaStream_t st);
+pc_status pc_solver_alloc(pc_ctx *ctx);
+
+inline int pc_bits_for(int64_t n)
+{
+    int b = 0;
+    while (b < 63 && ((int64_t)1 << b) < n) ++b;
+    return b < 1 ? 1 : b;
+}
+
+// ------------------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ void pc_set_err(uint32_t *err, uint32_t bit) { atomicOr(err, bit); }
+
+// lower_bound over a sorted uint64 array
+__device__ __forceinline__ int64_t pc_lower_bound_u64(const uint64_t *a, int64_t n, uint64_t key)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}

@@ -1,0 +1,798 @@
+// Preconditioned conjugate gradients on the assembled system (Sec. 2.5: the linear
+// equations are solved with a preconditioned conjugate gradient solver; Sec. 3.1: the
+// SpMV is the most expensive operator and vector operations are data parallel).
+//
+// Per iteration two kernels run:
+//   spmv:   p = z + beta p_prev (own rows), q = A p with p_i formed on the fly at the
+//           gathered columns, partial p.q                         -> alpha = rz / pq
+//   update: x += alpha p, r -= alpha q, z = D^-1 r, partial r.z, r.r -> beta, convergence
+// The matrix rows of each 128-row tile are staged into shared memory with 16-byte
+// vector loads (coalesced, one pass over the blocks), then two threads per row consume
+// them. Dot products accumulate in FP64; each kernel's last block to finish sums the
+// per-block partials in a fixed order, so every reduction is deterministic.
+//
+// Mixed precision (PC_PREC_MIXED): the solution is an FP64 accumulator plus the FP32
+// increment the iterations build; at refresh points the increment is folded into the
+// accumulator and the residual is recomputed in FP64 and replaces the recurrence
+// residual, keeping the search direction (residual replacement). FP64 appears only in
+// that residual, the dot-product reductions and the accumulator update.
+#include <math.h>
+#include <string.h>
+
+#include "pc_internal.cuh"
+
+#define SP_THREADS 256
+#define SP_ROWS 128
+#define SP_CAP 1536
+#define SP_SMEM_BYTES ((SP_CAP * 9 + 16) * 4 + (SP_CAP + 16) * 4)
+#define EW_THREADS 256
+#define RED_SLOTS 4
+
+// ------------------------------------------------------------------------- reductions
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-reduce `n` doubles (n <= RED_SLOTS) in a fixed tree; thread 0 gets the sums.
+__device__ __forceinline__ void block_sum_d(double *v, int n)
+{
+    __shared__ double s[RED_SLOTS][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k < n; ++k) {
+        double w = warp_sum_d(v[k]);
+        if (lane == 0) s[k][warp] = w;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int k = 0; k < n; ++k) {
+            double w = lane < nw ? s[k][lane] : 0.0;
+            v[k] = warp_sum_d(w);
+        }
+    }
+    __syncthreads();
+}
+
+// Write this block's partial sums; returns true (in all threads) in the block that
+// arrives last, with the grand totals in v[] of thread 0 (summed in block order).
+__device__ bool last_block_reduce(double *v, int n, double *partials, uint32_t *counter)
+{
+    __shared__ bool s_last;
+    block_sum_d(v, n);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < n; ++k) partials[(int64_t)blockIdx.x * RED_SLOTS + k] = v[k];
+        __threadfence();
+        uint32_t t = atomicAdd(counter, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double acc[RED_SLOTS] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
+        for (int k = 0; k < n; ++k) acc[k] += __ldcg(partials + (int64_t)i * RED_SLOTS + k);
+    block_sum_d(acc, n);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < n; ++k) v[k] = acc[k];
+        *counter = 0u;
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------------- SpMV
+
+struct SpmvArgs {
+    int V;
+    const int32_t *rp;
+    const int32_t *ci;
+    const float *vals;
+    const float *dres;   // difference-form diagonal, or null
+    const float *xin;    // vector (or z in PCG mode)
+    const float *pold;   // previous direction (PCG mode) or null
+    float *y;            // result
+    float *pnew;         // receives the formed direction, or null
+    double *partials;    // p.q partials (PCG mode) or null
+    pc_scalars *sc;      // PCG scalars or null
+};
+
+template <bool DIFF, bool PCG>
+__global__ void __launch_bounds__(SP_THREADS) spmv_kernel(SpmvArgs a)
+{
+    extern __shared__ float4 smem4[];
+    float *s_vals = reinterpret_cast<float *>(smem4);
+    int32_t *s_cols = reinterpret_cast<int32_t *>(s_vals + SP_CAP * 9 + 16);
+    float beta = 0.0f;
+    if (PCG) {
+        if (a.sc->done) return;
+        beta = (float)a.sc->beta;
+    }
+    const int ntiles = (a.V + SP_ROWS - 1) / SP_ROWS;
+    const int half = threadIdx.x & 1;
+    double dot_acc = 0.0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int r0 = tile * SP_ROWS, r1 = min(r0 + SP_ROWS, a.V);
+        const int b0 = a.rp[r0], b1 = a.rp[r1];
+        const bool staged = (b1 - b0) <= SP_CAP;
+        int vo = 0, co = 0;
+        if (staged) {
+            const int64_t f0 = 9ll * b0, f1 = 9ll * b1;
+            const int64_t al0 = f0 & ~3ll, al1 = (f1 + 3) & ~3ll;
+            const float4 *src = reinterpret_cast<const float4 *>(a.vals + al0);
+            const int nv = (int)((al1 - al0) >> 2);
+            for (int i = threadIdx.x; i < nv; i += SP_THREADS) smem4[i] = src[i];
+            const int c0 = b0 & ~3, c1 = (b1 + 3) & ~3;
+            const int4 *csrc = reinterpret_cast<const int4 *>(a.ci + c0);
+            int4 *cdst = reinterpret_cast<int4 *>(s_cols);
+            for (int i = threadIdx.x; i < ((c1 - c0) >> 2); i += SP_THREADS) cdst[i] = csrc[i];
+            vo = (int)(f0 - al0);
+            co = b0 - c0;
+            __syncthreads();
+        }
+        const int row = r0 + (threadIdx.x >> 1);
+        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+        float xj0 = 0.f, xj1 = 0.f, xj2 = 0.f;
+        if (row < r1) {
+            if (DIFF || PCG) {
+                xj0 = a.xin[3 * row];
+                xj1 = a.xin[3 * row + 1];
+                xj2 = a.xin[3 * row + 2];
+                if (PCG) {
+                    xj0 = fmaf(beta, a.pold[3 * row], xj0);
+                    xj1 = fmaf(beta, a.pold[3 * row + 1], xj1);
+                    xj2 = fmaf(beta, a.pold[3 * row + 2], xj2);
+                }
+            }
+            const int rb = a.rp[row], re = a.rp[row + 1];
+            for (int b = rb + half; b < re; b += 2) {
+                int col;
+                const float *B;
+                if (staged) {
+                    col = s_cols[co + (b - b0)];
+                    B = s_vals + vo + 9 * (b - b0);
+                } else {
+                    col = a.ci[b];
+                    B = a.vals + 9ll * b;
+                }
+                if (DIFF && col == row) continue;
+                float v0 = a.xin[3 * col], v1 = a.xin[3 * col + 1], v2 = a.xin[3 * col + 2];
+                if (PCG) {
+                    v0 = fmaf(beta, a.pold[3 * col], v0);
+                    v1 = fmaf(beta, a.pold[3 * col + 1], v1);
+                    v2 = fmaf(beta, a.pold[3 * col + 2], v2);
+                }
+                if (DIFF) {
+                    v0 -= xj0;
+                    v1 -= xj1;
+                    v2 -= xj2;
+                }
+                acc0 = fmaf(B[0], v0, fmaf(B[1], v1, fmaf(B[2], v2, acc0)));
+                acc1 = fmaf(B[3], v0, fmaf(B[4], v1, fmaf(B[5], v2, acc1)));
+                acc2 = fmaf(B[6], v0, fmaf(B[7], v1, fmaf(B[8], v2, acc2)));
+            }
+        }
+        acc0 += __shfl_xor_sync(0xffffffffu, acc0, 1);
+        acc1 += __shfl_xor_sync(0xffffffffu, acc1, 1);
+        acc2 += __shfl_xor_sync(0xffffffffu, acc2, 1);
+        if (row < r1 && half == 0) {
+            if (DIFF) {
+                const float *D = a.dres + 9ll * row;
+                acc0 = fmaf(D[0], xj0, fmaf(D[1], xj1, fmaf(D[2], xj2, acc0)));
+                acc1 = fmaf(D[3], xj0, fmaf(D[4], xj1, fmaf(D[5], xj2, acc1)));
+                acc2 = fmaf(D[6], xj0, fmaf(D[7], xj1, fmaf(D[8], xj2, acc2)));
+            }
+            a.y[3 * row] = acc0;
+            a.y[3 * row + 1] = acc1;
+            a.y[3 * row + 2] = acc2;
+            if (PCG) {
+                a.pnew[3 * row] = xj0;
+                a.pnew[3 * row + 1] = xj1;
+                a.pnew[3 * row + 2] = xj2;
+                dot_acc += (double)xj0 * (double)acc0 + (double)xj1 * (double)acc1 + (double)xj2 * (double)acc2;
+            }
+        }
+        if (staged) __syncthreads();
+    }
+    if (PCG) {
+        double v[1] = {dot_acc};
+        if (last_block_reduce(v, 1, a.partials, &a.sc->counter) && threadIdx.x == 0) {
+            pc_scalars *s = a.sc;
+            double pq = v[0];
+            s->pq = pq;
+            double alpha = s->rz / pq;
+            if (!(pq > 0.0) || !isfinite(alpha)) {
+                s->status = PC_ERR_NONFINITE;
+                s->done = 1;
+                alpha = 0.0;
+            }
+            s->alpha = alpha;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------- preconditioner
+
+// z = D^-1 r for one row: scalar Jacobi (3 floats per row) or 3x3 block (9 floats).
+template <bool BLOCK>
+__device__ __forceinline__ void apply_precond(const float *__restrict__ dinv, int row, const float r[3], float z[3])
+{
+    if (BLOCK) {
+        const float *D = dinv + 9ll * row;
+        z[0] = D[0] * r[0] + D[1] * r[1] + D[2] * r[2];
+        z[1] = D[3] * r[0] + D[4] * r[1] + D[5] * r[2];
+        z[2] = D[6] * r[0] + D[7] * r[1] + D[8] * r[2];
+    } else {
+        const float *D = dinv + 3ll * row;
+        z[0] = D[0] * r[0];
+        z[1] = D[1] * r[1];
+        z[2] = D[2] * r[2];
+    }
+}
+
+// Inverse of the diagonal (scalar entries, or the whole 3x3 block computed in FP64).
+template <bool BLOCK>
+__global__ void dinv_kernel(int V, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const float *__restrict__ vals, float *__restrict__ dinv, uint32_t *err)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= V) return;
+    int s = -1;
+    for (int k = rp[r]; k < rp[r + 1]; ++k)
+        if (ci[k] == r) { s = k; break; }
+    double B[9];
+    for (int e = 0; e < 9; ++e) B[e] = s >= 0 ? (double)vals[9ll * s + e] : 0.0;
+    bool ok = s >= 0 && B[0] > 0.0 && B[4] > 0.0 && B[8] > 0.0 && isfinite(B[0] + B[4] + B[8]);
+    if (!BLOCK) {
+        for (int a = 0; a < 3; ++a) dinv[3ll * r + a] = ok ? (float)(1.0 / B[4 * a]) : 1.0f;
+    } else {
+        double c00 = B[4] * B[8] - B[5] * B[7], c01 = B[2] * B[7] - B[1] * B[8], c02 = B[1] * B[5] - B[2] * B[4];
+        double c10 = B[5] * B[6] - B[3] * B[8], c11 = B[0] * B[8] - B[2] * B[6], c12 = B[2] * B[3] - B[0] * B[5];
+        double c20 = B[3] * B[7] - B[4] * B[6], c21 = B[1] * B[6] - B[0] * B[7], c22 = B[0] * B[4] - B[1] * B[3];
+        double det = B[0] * c00 + B[1] * c10 + B[2] * c20;
+        ok = ok && det > 0.0 && isfinite(det);
+        double inv[9] = {c00, c01, c02, c10, c11, c12, c20, c21, c22};
+        for (int e = 0; e < 9; ++e) dinv[9ll * r + e] = ok ? (float)(inv[e] / det) : (e % 4 == 0 ? 1.0f : 0.0f);
+    }
+    if (!ok) pc_set_err(err, PC_DERR_NONFINITE);
+}
+
+// ------------------------------------------------------------------------- vector kernels
+
+// Per row: x += alpha p; r -= alpha q; z = D^-1 r; partial (r.z, r.r); the last block
+// computes beta and applies the stop tests.
+template <bool BLOCK>
+__global__ void __launch_bounds__(EW_THREADS) pcg_update_kernel(int V, float *__restrict__ x,
+                                                                 const float *__restrict__ p, float *__restrict__ r,
+                                                                 const float *__restrict__ q,
+                                                                 const float *__restrict__ dinv,
+                                                                 float *__restrict__ z, double *partials,
+                                                                 pc_scalars *sc)
+{
+    if (sc->done) return;
+    const float alpha = (float)sc->alpha;
+    double rz = 0.0, rr = 0.0;
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
+        float ri[3], zi[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int64_t i = 3ll * row + a;
+            x[i] = fmaf(alpha, p[i], x[i]);
+            ri[a] = fmaf(-alpha, q[i], r[i]);
+            r[i] = ri[a];
+        }
+        apply_precond<BLOCK>(dinv, row, ri, zi);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            z[3ll * row + a] = zi[a];
+            rz += (double)ri[a] * (double)zi[a];
+            rr += (double)ri[a] * (double)ri[a];
+        }
+    }
+    double v[2] = {rz, rr};
+    if (last_block_reduce(v, 2, partials, &sc->counter) && threadIdx.x == 0) {
+        double rz_new = v[0];
+        sc->beta = rz_new / sc->rz;
+        sc->rz = rz_new;
+        sc->rr = v[1];
+        sc->iter += 1;
+        if (!isfinite(v[1]) || !isfinite(sc->beta)) {
+            sc->status = PC_ERR_NONFINITE;
+            sc->done = 1;
+        } else if (v[1] <= sc->tol2) {
+            sc->status = PC_OK;
+            sc->done = 1;
+        } else if (sc->iter >= sc->max_iter) {
+            sc->status = PC_ERR_NOT_CONVERGED;
+            sc->done = 1;
+        }
+    }
+}
+
+// Per row: r = b - q (q = A x0, or null for a zero guess), z = D^-1 r, pold = 0;
+// partial (r.z, r.r, b.b); the last block initialises the scalars.
+template <bool BLOCK>
+__global__ void __launch_bounds__(EW_THREADS) pcg_init_kernel(int V, const float *__restrict__ b,
+                                                               const float *__restrict__ q, float *__restrict__ r,
+                                                               const float *__restrict__ dinv,
+                                                               float *__restrict__ z, float *__restrict__ pold,
+                                                               double tol, int max_iter, double *partials,
+                                                               pc_scalars *sc)
+{
+    double rz = 0.0, rr = 0.0, bb = 0.0;
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
+        float ri[3], zi[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int64_t i = 3ll * row + a;
+            float bi = b[i];
+            ri[a] = q ? bi - q[i] : bi;
+            r[i] = ri[a];
+            pold[i] = 0.0f;
+            bb += (double)bi * (double)bi;
+        }
+        apply_precond<BLOCK>(dinv, row, ri, zi);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            z[3ll * row + a] = zi[a];
+            rz += (double)ri[a] * (double)zi[a];
+            rr += (double)ri[a] * (double)ri[a];
+        }
+    }
+    double v[3] = {rz, rr, bb};
+    if (last_block_reduce(v, 3, partials, &sc->counter) && threadIdx.x == 0) {
+        sc->rz = v[0];
+        sc->rr = v[1];
+        sc->bb = v[2];
+        sc->tol2 = tol * tol * v[2];
+        sc->alpha = 0.0;
+        sc->beta = 0.0;
+        sc->pq = 0.0;
+        sc->iter = 0;
+        sc->max_iter = max_iter;
+        sc->status = PC_OK;
+        sc->done = 0;
+        if (!isfinite(v[2]) || !isfinite(v[1])) {
+            sc->status = PC_ERR_NONFINITE;
+            sc->done = 1;
+        } else if (v[1] <= sc->tol2) {
+            sc->done = 1;
+        } else if (max_iter <= 0) {
+            sc->status = PC_ERR_NOT_CONVERGED;
+            sc->done = 1;
+        }
+    }
+}
+
+// (A x)_row in FP64 from FP32 blocks, x in FP64 or FP32 (standard or difference form).
+template <typename XT, bool DIFF>
+__device__ __forceinline__ void row_product64(int row, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                              const float *__restrict__ vals, const float *__restrict__ dres,
+                                              const XT *__restrict__ x, double acc[3])
+{
+    double xj[3] = {(double)x[3ll * row], (double)x[3ll * row + 1], (double)x[3ll * row + 2]};
+    acc[0] = acc[1] = acc[2] = 0.0;
+    for (int k = rp[row]; k < rp[row + 1]; ++k) {
+        int c = ci[k];
+        if (DIFF && c == row) continue;
+        const float *B = vals + 9ll * k;
+        double xc[3] = {(double)x[3ll * c], (double)x[3ll * c + 1], (double)x[3ll * c + 2]};
+        if (DIFF)
+            for (int d = 0; d < 3; ++d) xc[d] -= xj[d];
+        for (int a2 = 0; a2 < 3; ++a2)
+            acc[a2] += (double)B[3 * a2] * xc[0] + (double)B[3 * a2 + 1] * xc[1] + (double)B[3 * a2 + 2] * xc[2];
+    }
+    if (DIFF) {
+        const float *D = dres + 9ll * row;
+        for (int a2 = 0; a2 < 3; ++a2)
+            acc[a2] += (double)D[3 * a2] * xj[0] + (double)D[3 * a2 + 1] * xj[1] + (double)D[3 * a2 + 2] * xj[2];
+    }
+}
+
+// FP64 residual of an FP32 vector x: partial (r.r, b.b) only (reporting).
+template <bool DIFF>
+__global__ void __launch_bounds__(EW_THREADS) residual_check_kernel(int V, const int32_t *__restrict__ rp,
+                                                                    const int32_t *__restrict__ ci,
+                                                                    const float *__restrict__ vals,
+                                                                    const float *__restrict__ dres,
+                                                                    const float *__restrict__ b,
+                                                                    const float *__restrict__ x, double *partials,
+                                                                    pc_scalars *sc)
+{
+    double rr = 0.0, bb = 0.0;
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
+        double acc[3];
+        row_product64<float, DIFF>(row, rp, ci, vals, dres, x, acc);
+        for (int a2 = 0; a2 < 3; ++a2) {
+            double bv = (double)b[3ll * row + a2];
+            double rv = bv - acc[a2];
+            rr += rv * rv;
+            bb += bv * bv;
+        }
+    }
+    double v[2] = {rr, bb};
+    if (last_block_reduce(v, 2, partials, &sc->counter) && threadIdx.x == 0) {
+        sc->rr = v[0];
+        sc->bb = v[1];
+    }
+}
+
+// Residual replacement: r64 = b - A x64 in FP64; r = (float) r64, z = D^-1 r; partial
+// (r.z, r64.r64, b.b). The last block installs r.z and the FP64 residual as the
+// iteration's scalars (keeping beta and the search direction), and either starts the
+// solve (`first`) or decides whether it has converged.
+template <bool DIFF, bool BLOCK>
+__global__ void __launch_bounds__(EW_THREADS) residual_replace_kernel(
+    int V, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const float *__restrict__ vals,
+    const float *__restrict__ dres, const float *__restrict__ b, const double *__restrict__ x64,
+    const float *__restrict__ dinv, float *__restrict__ r, float *__restrict__ z, float *__restrict__ pold, int first,
+    double tol, int max_iter, double *partials, pc_scalars *sc)
+{
+    double rz = 0.0, rr = 0.0, bb = 0.0;
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
+        double acc[3];
+        row_product64<double, DIFF>(row, rp, ci, vals, dres, x64, acc);
+        float ri[3], zi[3];
+        for (int a2 = 0; a2 < 3; ++a2) {
+            const int64_t i = 3ll * row + a2;
+            double bv = (double)b[i];
+            double rv = bv - acc[a2];
+            rr += rv * rv;
+            bb += bv * bv;
+            ri[a2] = (float)rv;
+            r[i] = ri[a2];
+            if (first) pold[i] = 0.0f;
+        }
+        apply_precond<BLOCK>(dinv, row, ri, zi);
+        for (int a2 = 0; a2 < 3; ++a2) {
+            z[3ll * row + a2] = zi[a2];
+            rz += (double)ri[a2] * (double)zi[a2];
+        }
+    }
+    double v[3] = {rz, rr, bb};
+    if (last_block_reduce(v, 3, partials, &sc->counter) && threadIdx.x == 0) {
+        sc->rz = v[0];
+        sc->rr = v[1];
+        if (first) {
+            sc->bb = v[2];
+            sc->tol2 = tol * tol * v[2];
+            sc->alpha = 0.0;
+            sc->beta = 0.0;
+            sc->pq = 0.0;
+            sc->iter = 0;
+            sc->max_iter = max_iter;
+        }
+        sc->status = PC_OK;
+        sc->done = 0;
+        if (!isfinite(v[1]) || !isfinite(v[2])) {
+            sc->status = PC_ERR_NONFINITE;
+            sc->done = 1;
+        } else if (v[1] <= sc->tol2) {
+            sc->done = 1;
+        } else if (sc->iter >= sc->max_iter) {
+            sc->status = PC_ERR_NOT_CONVERGED;
+            sc->done = 1;
+        }
+    }
+}
+
+// x64 += x32; x32 = 0
+__global__ void fold_kernel(int64_t n, float *x32, double *x64)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x64[i] += (double)x32[i];
+        x32[i] = 0.0f;
+    }
+}
+__global__ void f64_to_f32_kernel(int64_t n, const double *a, float *o)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        o[i] = (float)a[i];
+}
+__global__ void f32_to_f64_kernel(int64_t n, const float *a, double *o)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        o[i] = (double)a[i];
+}
+__global__ void state_update_kernel(int64_t n, float *x, float *v, const float *dv, float h)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float vi = v[i] + dv[i];
+        v[i] = vi;
+        x[i] = fmaf(h, vi, x[i]);
+    }
+}
+
+// ------------------------------------------------------------------------- host side
+
+static int spmv_grid(const pc_ctx *c)
+{
+    int tiles = (c->V + SP_ROWS - 1) / SP_ROWS;
+    int g = c->num_sms * 3;
+    return tiles < g ? (tiles > 0 ? tiles : 1) : g;
+}
+static int ew_grid(const pc_ctx *c, int64_t n)
+{
+    int64_t b = (n + EW_THREADS - 1) / EW_THREADS;
+    int64_t g = (int64_t)c->num_sms * 8;
+    if (b < 1) b = 1;
+    return (int)(b < g ? b : g);
+}
+
+pc_status pc_solver_alloc(pc_ctx *c)
+{
+    const int64_t n = 3ll * c->V;
+    PC_CUDA_TRY(cudaMalloc(&c->r, sizeof(float) * n));
+    PC_CUDA_TRY(cudaMalloc(&c->z, sizeof(float) * n));
+    PC_CUDA_TRY(cudaMalloc(&c->p0, sizeof(float) * n));
+    PC_CUDA_TRY(cudaMalloc(&c->p1, sizeof(float) * n));
+    PC_CUDA_TRY(cudaMalloc(&c->q, sizeof(float) * n));
+    PC_CUDA_TRY(cudaMalloc(&c->dinv, sizeof(float) * 3 * n));
+    PC_CUDA_TRY(cudaMalloc(&c->dtmp, sizeof(float) * n));
+    PC_CUDA_TRY(cudaMalloc(&c->rhs32, sizeof(float) * n));
+    PC_CUDA_TRY(cudaMalloc(&c->x64, sizeof(double) * n));
+    PC_CUDA_TRY(cudaMalloc(&c->r64, sizeof(double) * n));
+    c->max_red_blocks = c->num_sms * 16;
+    PC_CUDA_TRY(cudaMalloc(&c->partials, sizeof(double) * RED_SLOTS * c->max_red_blocks));
+    PC_CUDA_TRY(cudaMalloc(&c->sc, sizeof(pc_scalars)));
+    PC_CUDA_TRY(cudaMemset(c->sc, 0, sizeof(pc_scalars)));
+    PC_CUDA_TRY(cudaMallocHost(&c->sc_host, sizeof(pc_scalars)));
+    PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM_BYTES));
+    PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM_BYTES));
+    PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM_BYTES));
+    PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM_BYTES));
+    for (int i = 0; i < 2; ++i) PC_CUDA_TRY(cudaEventCreate(&c->ev[i]));
+    c->ev_used = 2;
+    return PC_OK;
+}
+
+static pc_status check_bsr(const pc_bsr *A, const float *vals)
+{
+    if (!A || !A->row_ptr || !A->col_idx || !vals) return PC_ERR_ARG;
+    if ((A->cap & 3) != 0 || A->nnzb < 0 || A->nnzb > A->cap) return PC_ERR_ARG;
+    if (!pc_aligned16(A->col_idx) || !pc_aligned16(vals)) return PC_ERR_ARG;
+    return PC_OK;
+}
+
+static pc_status launch_spmv(pc_ctx *c, const SpmvArgs &a, bool diff, bool pcg, cudaStream_t st)
+{
+    const int g = spmv_grid(c);
+    if (diff && pcg) PC_LAUNCH(c, (spmv_kernel<true, true>), g, SP_THREADS, SP_SMEM_BYTES, st, a);
+    else if (diff) PC_LAUNCH(c, (spmv_kernel<true, false>), g, SP_THREADS, SP_SMEM_BYTES, st, a);
+    else if (pcg) PC_LAUNCH(c, (spmv_kernel<false, true>), g, SP_THREADS, SP_SMEM_BYTES, st, a);
+    else PC_LAUNCH(c, (spmv_kernel<false, false>), g, SP_THREADS, SP_SMEM_BYTES, st, a);
+    return PC_OK;
+}
+
+extern "C" pc_status pc_bsr_spmv(pc_ctx *ctx, const pc_bsr *A, const float *vals, const float *dres, const float *x,
+                                 float *y, void *stream)
+{
+    if (!ctx || !x || !y) return PC_ERR_ARG;
+    PC_TRY(check_bsr(A, vals));
+    SpmvArgs a{};
+    a.V = ctx->V;
+    a.rp = A->row_ptr;
+    a.ci = A->col_idx;
+    a.vals = vals;
+    a.dres = dres;
+    a.xin = x;
+    a.y = y;
+    return launch_spmv(ctx, a, dres != nullptr, false, (cudaStream_t)stream);
+}
+
+extern "C" void pc_default_solve_opts(pc_solve_opts *o)
+{
+    if (!o) return;
+    o->tol = 1e-6;
+    o->max_iter = 20000;
+    o->precision = PC_PREC_FP32;
+    o->refresh = 1e-2;
+    o->refresh_every = 1000;
+    o->check_every = 32;
+    o->precond = PC_PRECOND_JACOBI;
+    o->reserved = 0;
+}
+
+struct SolveCtx {
+    pc_ctx *c;
+    const pc_bsr *A;
+    const float *vals, *dres, *b;
+    bool diff, block;
+    cudaStream_t st;
+};
+
+static pc_status read_scalars(pc_ctx *c, cudaStream_t st)
+{
+    PC_CUDA_TRY(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(pc_scalars), cudaMemcpyDeviceToHost, st));
+    PC_CUDA_TRY(cudaStreamSynchronize(st));
+    return PC_OK;
+}
+
+#define DISPATCH2(ctx, kern, diff, block, grid, thr, st, ...)                                           \
+    do {                                                                                                  \
+        if (diff && block) PC_LAUNCH(ctx, (kern<true, true>), grid, thr, 0, st, __VA_ARGS__);             \
+        else if (diff) PC_LAUNCH(ctx, (kern<true, false>), grid, thr, 0, st, __VA_ARGS__);               \
+        else if (block) PC_LAUNCH(ctx, (kern<false, true>), grid, thr, 0, st, __VA_ARGS__);              \
+        else PC_LAUNCH(ctx, (kern<false, false>), grid, thr, 0, st, __VA_ARGS__);                        \
+    } while (0)
+
+// fold the FP32 increment into the FP64 accumulator and replace the residual
+static pc_status replace_residual(const SolveCtx &s, float *x32, int first, double tol, int max_iter)
+{
+    pc_ctx *c = s.c;
+    const int64_t n = 3ll * c->V;
+    if (!first) PC_LAUNCH(c, fold_kernel, ew_grid(c, n), EW_THREADS, 0, s.st, n, x32, c->x64);
+    DISPATCH2(c, residual_replace_kernel, s.diff, s.block, ew_grid(c, c->V), EW_THREADS, s.st, c->V, s.A->row_ptr,
+              s.A->col_idx, s.vals, s.dres, s.b, c->x64, c->dinv, c->r, c->z, c->p0, first, tol, max_iter,
+              c->partials, c->sc);
+    return PC_OK;
+}
+
+static pc_status launch_iterations(const SolveCtx &s, float *x, int count, float **pa, float **pb)
+{
+    pc_ctx *c = s.c;
+    SpmvArgs a{};
+    a.V = c->V;
+    a.rp = s.A->row_ptr;
+    a.ci = s.A->col_idx;
+    a.vals = s.vals;
+    a.dres = s.dres;
+    a.xin = c->z;
+    a.y = c->q;
+    a.partials = c->partials;
+    a.sc = c->sc;
+    for (int k = 0; k < count; ++k) {
+        a.pold = *pa;
+        a.pnew = *pb;
+        bool timed = c->profiling && k == 0;
+        if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[0], s.st));
+        PC_TRY(launch_spmv(c, a, s.diff, true, s.st));
+        if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[1], s.st));
+        if (s.block)
+            PC_LAUNCH(c, pcg_update_kernel<true>, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, x, *pb, c->r, c->q,
+                      c->dinv, c->z, c->partials, c->sc);
+        else
+            PC_LAUNCH(c, pcg_update_kernel<false>, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, x, *pb, c->r, c->q,
+                      c->dinv, c->z, c->partials, c->sc);
+        float *t = *pa; *pa = *pb; *pb = t;
+        if (timed) {
+            float ms = 0.f;
+            PC_CUDA_TRY(cudaEventSynchronize(c->ev[1]));
+            PC_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+            c->spmv_ms += ms;
+            c->spmv_launches += 1;
+            c->spmv_nnzb = s.A->nnzb;
+        }
+    }
+    return PC_OK;
+}
+
+extern "C" pc_status pc_pcg_solve(pc_ctx *ctx, const pc_bsr *A, const float *vals, const float *dres, const float *b,
+                                  float *dv, const pc_solve_opts *opts, pc_solve_info *info, void *stream)
+{
+    if (!ctx || !b || !dv) return PC_ERR_ARG;
+    PC_TRY(check_bsr(A, vals));
+    pc_solve_opts o;
+    pc_default_solve_opts(&o);
+    if (opts) o = *opts;
+    if (!(o.tol > 0.0) || o.max_iter < 0 || (o.precision != PC_PREC_FP32 && o.precision != PC_PREC_MIXED) ||
+        (o.precond != PC_PRECOND_JACOBI && o.precond != PC_PRECOND_BLOCK) || !(o.refresh > 0.0 && o.refresh < 1.0))
+        return PC_ERR_ARG;
+    if (o.check_every < 1) o.check_every = 32;
+    if (o.refresh_every < 1) o.refresh_every = 1000;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int V = ctx->V;
+    const int64_t n = 3ll * V;
+    SolveCtx s{ctx, A, vals, dres, b, dres != nullptr, o.precond == PC_PRECOND_BLOCK, st};
+    PC_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), st));
+    if (s.block)
+        PC_LAUNCH(ctx, dinv_kernel<true>, pc_blocks(V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals, ctx->dinv,
+                  ctx->d_err);
+    else
+        PC_LAUNCH(ctx, dinv_kernel<false>, pc_blocks(V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals, ctx->dinv,
+                  ctx->d_err);
+    uint32_t bits = 0;
+    PC_TRY(pc_read_errors(ctx, st, &bits));
+    if (bits) return PC_ERR_NONFINITE;
+
+    const bool mixed = o.precision == PC_PREC_MIXED;
+    float *x = mixed ? ctx->dtmp : dv;  // mixed: FP32 increment since the last fold
+    int replacements = 0;
+    if (mixed) {
+        PC_LAUNCH(ctx, f32_to_f64_kernel, ew_grid(ctx, n), EW_THREADS, 0, st, n, dv, ctx->x64);
+        PC_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(float) * n, st));
+        PC_TRY(replace_residual(s, x, 1, o.tol, o.max_iter));
+    } else {
+        SpmvArgs a{};
+        a.V = V;
+        a.rp = A->row_ptr;
+        a.ci = A->col_idx;
+        a.vals = vals;
+        a.dres = dres;
+        a.xin = dv;
+        a.y = ctx->q;
+        PC_TRY(launch_spmv(ctx, a, s.diff, false, st));
+        if (s.block)
+            PC_LAUNCH(ctx, pcg_init_kernel<true>, ew_grid(ctx, V), EW_THREADS, 0, st, V, b, ctx->q, ctx->r, ctx->dinv,
+                      ctx->z, ctx->p0, o.tol, o.max_iter, ctx->partials, ctx->sc);
+        else
+            PC_LAUNCH(ctx, pcg_init_kernel<false>, ew_grid(ctx, V), EW_THREADS, 0, st, V, b, ctx->q, ctx->r, ctx->dinv,
+                      ctx->z, ctx->p0, o.tol, o.max_iter, ctx->partials, ctx->sc);
+    }
+    PC_TRY(read_scalars(ctx, st));
+    float *pa = ctx->p0, *pb = ctx->p1;
+    double rr_last = ctx->sc_host->rr;
+    int iter_last = 0;
+    int launched = 0;
+    for (;;) {
+        const pc_scalars h = *ctx->sc_host;
+        if (h.done) {
+            // mixed: a converged recurrence residual is confirmed by an FP64 replacement
+            if (mixed && h.status == PC_OK && h.rr > 0.0 && h.iter > iter_last) {
+                PC_TRY(replace_residual(s, x, 0, o.tol, o.max_iter));
+                ++replacements;
+                PC_TRY(read_scalars(ctx, st));
+                rr_last = ctx->sc_host->rr;
+                iter_last = ctx->sc_host->iter;
+                continue;
+            }
+            break;
+        }
+        if (launched >= o.max_iter + o.check_every) break;
+        if (mixed && h.iter > iter_last &&
+            (h.rr <= rr_last * o.refresh * o.refresh || h.iter - iter_last >= o.refresh_every)) {
+            PC_TRY(replace_residual(s, x, 0, o.tol, o.max_iter));
+            ++replacements;
+            PC_TRY(read_scalars(ctx, st));
+            rr_last = ctx->sc_host->rr;
+            iter_last = ctx->sc_host->iter;
+            continue;
+        }
+        int chunk = o.check_every;
+        if (launched == 0 && chunk > 8) chunk = 8;
+        PC_TRY(launch_iterations(s, x, chunk, &pa, &pb));
+        launched += chunk;
+        PC_TRY(read_scalars(ctx, st));
+    }
+    const pc_scalars fin = *ctx->sc_host;
+    pc_solve_info inf{};
+    inf.iters = fin.iter;
+    inf.outer = replacements;
+    pc_status status = (pc_status)fin.status;
+    double rr = fin.rr, bb = fin.bb;
+    if (mixed) {
+        if (fin.iter > iter_last) {  // stopped early (limit / breakdown): fold what there is
+            PC_LAUNCH(ctx, fold_kernel, ew_grid(ctx, n), EW_THREADS, 0, st, n, x, ctx->x64);
+        }
+        PC_LAUNCH(ctx, f64_to_f32_kernel, ew_grid(ctx, n), EW_THREADS, 0, st, n, ctx->x64, dv);
+        if (fin.iter > iter_last) {
+            if (s.diff) PC_LAUNCH(ctx, residual_check_kernel<true>, ew_grid(ctx, V), EW_THREADS, 0, st, V, A->row_ptr,
+                                  A->col_idx, vals, dres, b, dv, ctx->partials, ctx->sc);
+            else PC_LAUNCH(ctx, residual_check_kernel<false>, ew_grid(ctx, V), EW_THREADS, 0, st, V, A->row_ptr,
+                           A->col_idx, vals, dres, b, dv, ctx->partials, ctx->sc);
+            PC_TRY(read_scalars(ctx, st));
+            rr = ctx->sc_host->rr;
+            bb = ctx->sc_host->bb;
+        }
+    } else {
+        if (s.diff) PC_LAUNCH(ctx, residual_check_kernel<true>, ew_grid(ctx, V), EW_THREADS, 0, st, V, A->row_ptr,
+                              A->col_idx, vals, dres, b, dv, ctx->partials, ctx->sc);
+        else PC_LAUNCH(ctx, residual_check_kernel<false>, ew_grid(ctx, V), EW_THREADS, 0, st, V, A->row_ptr,
+                       A->col_idx, vals, dres, b, dv, ctx->partials, ctx->sc);
+        PC_TRY(read_scalars(ctx, st));
+        rr = ctx->sc_host->rr;
+        bb = ctx->sc_host->bb;
+    }
+    inf.bnorm = sqrt(bb);
+    inf.rel_res = bb > 0 ? sqrt(rr / bb) : 0.0;
+    if (info) *info = inf;
+    PC_CUDA_TRY(cudaStreamSynchronize(st));
+    return status;
+}
+
+pc_status pc_update_state(pc_ctx *c, float *x, float *v, const float *dv, float h, cudaStream_t st)
+{
+    const int64_t n = 3ll * c->V;
+    PC_LAUNCH(c, state_update_kernel, ew_grid(c, n), EW_THREADS, 0, st, n, x, v, dv, h);
+    return PC_OK;
+}

@@ -1,0 +1,337 @@
+"""Thin Python binding of libpcloth (include/pcloth.h), same entry-point names.
+
+Argument marshalling only: every step of the hot path runs in the CUDA library. PyTorch
+supplies device memory and the current stream. Importing this module loads the library
+and raises if it has not been built (``paper_2008_00409_gb300.build.build()``); there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+c_int32, c_int64, c_float, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double, ctypes.c_void_p
+
+PC_OK, PC_ERR_ARG, PC_ERR_CAPACITY, PC_ERR_NOT_CONVERGED, PC_ERR_NONFINITE, PC_ERR_TIMEOUT, PC_ERR_CUDA, PC_ERR_MESH = range(8)
+PC_PREC_FP32, PC_PREC_MIXED = 0, 1
+PC_PRECOND_JACOBI, PC_PRECOND_BLOCK = 0, 1
+PC_WARM_ZERO, PC_WARM_PREV = 0, 1
+
+
+class pc_material(ctypes.Structure):
+    _fields_ = [("rho", c_float), ("young", c_float), ("poisson", c_float), ("k_bend", c_float),
+                ("k_contact", c_float), ("gravity", c_float * 3)]
+
+
+class pc_contacts(ctypes.Structure):
+    _fields_ = [("n", c_int32), ("pairs", c_void_p), ("w", c_void_p)]
+
+
+class pc_bsr(ctypes.Structure):
+    _fields_ = [("row_ptr", c_void_p), ("col_idx", c_void_p), ("cap", c_int64), ("nnzb", c_int64)]
+
+
+class pc_solve_opts(ctypes.Structure):
+    _fields_ = [("tol", c_double), ("max_iter", c_int32), ("precision", c_int32), ("refresh", c_double),
+                ("refresh_every", c_int32), ("check_every", c_int32), ("precond", c_int32), ("reserved", c_int32)]
+
+
+class pc_solve_info(ctypes.Structure):
+    _fields_ = [("iters", c_int32), ("outer", c_int32), ("rel_res", c_double), ("bnorm", c_double)]
+
+    def as_dict(self):
+        return {"iters": self.iters, "outer": self.outer, "rel_res": self.rel_res, "bnorm": self.bnorm}
+
+
+class pc_step_opts(ctypes.Structure):
+    _fields_ = [("h", c_float), ("solve", pc_solve_opts), ("warm_start", c_int32)]
+
+
+class pc_step_info(ctypes.Structure):
+    _fields_ = [("nnzb", c_int64), ("solve", pc_solve_info)]
+
+
+class PcError(RuntimeError):
+    def __init__(self, status: int, what: str, required: int | None = None):
+        self.status = status
+        self.required = required
+        msg = f"{what}: {_lib.pc_status_string(status).decode()} (status {status})"
+        if status == PC_ERR_CUDA:
+            msg += f" [{_lib.pc_last_cuda_error().decode()}]"
+        super().__init__(msg)
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libpcloth.so is not built ({path}); run paper_2008_00409_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    L.pc_status_string.restype = ctypes.c_char_p
+    L.pc_status_string.argtypes = [c_int32]
+    L.pc_last_cuda_error.restype = ctypes.c_char_p
+    L.pc_last_cuda_error.argtypes = []
+    L.pc_default_solve_opts.argtypes = [P(pc_solve_opts)]
+    L.pc_default_solve_opts.restype = None
+    L.pc_create.argtypes = [P(c_void_p), c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_int32, P(pc_material),
+                            c_int32, c_void_p]
+    L.pc_destroy.argtypes = [c_void_p]
+    L.pc_get_sizes.argtypes = [c_void_p, P(c_int32), P(c_int32), P(c_int32), P(c_int64)]
+    L.pc_get_rest.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    L.pc_assemble_pattern.argtypes = [c_void_p, P(pc_contacts), P(pc_bsr), c_void_p]
+    L.pc_assemble_values.argtypes = [c_void_p, P(pc_bsr), c_void_p, c_void_p, P(pc_contacts), c_float, c_void_p,
+                                     c_void_p, c_void_p, c_void_p]
+    L.pc_bsr_spmv.argtypes = [c_void_p, P(pc_bsr), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    L.pc_pcg_solve.argtypes = [c_void_p, P(pc_bsr), c_void_p, c_void_p, c_void_p, c_void_p, P(pc_solve_opts),
+                               P(pc_solve_info), c_void_p]
+    L.pc_step.argtypes = [c_void_p, c_void_p, c_void_p, P(pc_contacts), P(pc_step_opts), c_void_p, P(pc_step_info),
+                          c_void_p]
+    L.pc_step_host.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, P(pc_step_opts),
+                               P(pc_step_info), c_void_p]
+    L.pc_launch_count.restype = c_int64
+    L.pc_launch_count.argtypes = [c_void_p]
+    L.pc_set_profiling.argtypes = [c_void_p, c_int32]
+    L.pc_spmv_stats.argtypes = [c_void_p, P(c_int64), P(c_double), P(c_int64)]
+    for name in ("pc_create", "pc_destroy", "pc_get_sizes", "pc_get_rest", "pc_assemble_pattern",
+                 "pc_assemble_values", "pc_bsr_spmv", "pc_pcg_solve", "pc_step", "pc_step_host",
+                 "pc_set_profiling", "pc_spmv_stats"):
+        getattr(L, name).restype = c_int32
+    return L
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+# --------------------------------------------------------------------------- marshalling
+
+
+def _stream(stream=None) -> c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return c_void_p(stream.cuda_stream)
+
+
+def _ptr(t) -> c_void_p:
+    if t is None:
+        return c_void_p(None)
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return c_void_p(t.data_ptr())
+
+
+def _check(status: int, what: str, required: int | None = None):
+    if status != PC_OK:
+        raise PcError(status, what, required)
+
+
+def material_struct(m) -> pc_material:
+    """pc_material from a workloads.Material (or anything with the same fields)."""
+    s = pc_material()
+    s.rho, s.young, s.poisson, s.k_bend, s.k_contact = m.rho, m.young, m.poisson, m.k_bend, m.k_contact
+    for i in range(3):
+        s.gravity[i] = m.gravity[i]
+    return s
+
+
+def contacts_struct(pairs=None, w=None) -> pc_contacts:
+    c = pc_contacts()
+    if pairs is None or pairs.shape[0] == 0:
+        c.n, c.pairs, c.w = 0, None, None
+    else:
+        c.n = int(pairs.shape[0])
+        c.pairs = pairs.data_ptr()
+        c.w = w.data_ptr()
+    return c
+
+
+def bsr_struct(row_ptr, col_idx, nnzb: int = 0) -> pc_bsr:
+    A = pc_bsr()
+    A.row_ptr = row_ptr.data_ptr()
+    A.col_idx = col_idx.data_ptr()
+    A.cap = (col_idx.numel() // 4) * 4
+    A.nnzb = nnzb
+    return A
+
+
+def solve_opts(tol=1e-6, max_iter=20000, precision=PC_PREC_FP32, refresh=1e-2, refresh_every=1000, check_every=32,
+               precond=PC_PRECOND_JACOBI):
+    o = pc_solve_opts()
+    o.tol, o.max_iter, o.precision, o.refresh, o.refresh_every, o.check_every, o.precond = (
+        tol, max_iter, precision, refresh, refresh_every, check_every, precond)
+    o.reserved = 0
+    return o
+
+
+# --------------------------------------------------------------------------- entry points
+
+
+def pc_create(V, T, tris, rest, pins, material, max_contacts, stream=None):
+    h = c_void_p()
+    npin = 0 if pins is None else int(pins.numel())
+    m = material if isinstance(material, pc_material) else material_struct(material)
+    st = _lib.pc_create(ctypes.byref(h), int(V), int(T), _ptr(tris), _ptr(rest), _ptr(pins) if npin else c_void_p(None),
+                        npin, ctypes.byref(m), int(max_contacts), _stream(stream))
+    _check(st, "pc_create")
+    return h
+
+
+def pc_destroy(ctx):
+    _check(_lib.pc_destroy(ctx), "pc_destroy")
+
+
+def pc_get_sizes(ctx):
+    V, T, H, S = c_int32(), c_int32(), c_int32(), c_int64()
+    _check(_lib.pc_get_sizes(ctx, ctypes.byref(V), ctypes.byref(T), ctypes.byref(H), ctypes.byref(S)), "pc_get_sizes")
+    return V.value, T.value, H.value, S.value
+
+
+def pc_get_rest(ctx, hinges=None, mass=None, stream=None):
+    _check(_lib.pc_get_rest(ctx, _ptr(hinges), _ptr(mass), _stream(stream)), "pc_get_rest")
+
+
+def pc_assemble_pattern(ctx, pairs, w, row_ptr, col_idx, stream=None) -> int:
+    A = bsr_struct(row_ptr, col_idx)
+    c = contacts_struct(pairs, w)
+    st = _lib.pc_assemble_pattern(ctx, ctypes.byref(c), ctypes.byref(A), _stream(stream))
+    _check(st, "pc_assemble_pattern", int(A.nnzb) if st == PC_ERR_CAPACITY else None)
+    return int(A.nnzb)
+
+
+def pc_assemble_values(ctx, row_ptr, col_idx, nnzb, x, v, pairs, w, h, vals, b, dres=None, stream=None):
+    A = bsr_struct(row_ptr, col_idx, nnzb)
+    c = contacts_struct(pairs, w)
+    st = _lib.pc_assemble_values(ctx, ctypes.byref(A), _ptr(x), _ptr(v), ctypes.byref(c), float(h), _ptr(vals),
+                                 _ptr(b), _ptr(dres), _stream(stream))
+    _check(st, "pc_assemble_values")
+
+
+def pc_bsr_spmv(ctx, row_ptr, col_idx, nnzb, vals, dres, x, y, stream=None):
+    A = bsr_struct(row_ptr, col_idx, nnzb)
+    _check(_lib.pc_bsr_spmv(ctx, ctypes.byref(A), _ptr(vals), _ptr(dres), _ptr(x), _ptr(y), _stream(stream)),
+           "pc_bsr_spmv")
+
+
+def pc_pcg_solve(ctx, row_ptr, col_idx, nnzb, vals, dres, b, dv, opts=None, stream=None, allow_not_converged=False):
+    A = bsr_struct(row_ptr, col_idx, nnzb)
+    info = pc_solve_info()
+    o = opts if opts is not None else solve_opts()
+    st = _lib.pc_pcg_solve(ctx, ctypes.byref(A), _ptr(vals), _ptr(dres), _ptr(b), _ptr(dv), ctypes.byref(o),
+                           ctypes.byref(info), _stream(stream))
+    if not (allow_not_converged and st == PC_ERR_NOT_CONVERGED):
+        _check(st, "pc_pcg_solve")
+    return info, st
+
+
+def pc_step(ctx, x, v, pairs, w, opts: pc_step_opts, dv_out=None, stream=None, allow_not_converged=False):
+    info = pc_step_info()
+    c = contacts_struct(pairs, w)
+    st = _lib.pc_step(ctx, _ptr(x), _ptr(v), ctypes.byref(c), ctypes.byref(opts), _ptr(dv_out), ctypes.byref(info),
+                      _stream(stream))
+    if not (allow_not_converged and st == PC_ERR_NOT_CONVERGED):
+        _check(st, "pc_step")
+    return info, st
+
+
+def pc_step_host(ctx, x: np.ndarray, v: np.ndarray, pairs: np.ndarray, w: np.ndarray, opts: pc_step_opts,
+                 stream=None, allow_not_converged=False):
+    """Host-buffer step: x, v (float32 [V,3], updated in place), pairs int32 [P,4], w float32 [P,3]."""
+    assert x.dtype == np.float32 and v.dtype == np.float32 and x.flags.c_contiguous and v.flags.c_contiguous
+    info = pc_step_info()
+    P = 0 if pairs is None else int(pairs.shape[0])
+    pp = pairs.ctypes.data_as(c_void_p) if P else c_void_p(None)
+    wp = w.ctypes.data_as(c_void_p) if P else c_void_p(None)
+    st = _lib.pc_step_host(ctx, x.ctypes.data_as(c_void_p), v.ctypes.data_as(c_void_p), P, pp, wp,
+                           ctypes.byref(opts), ctypes.byref(info), _stream(stream))
+    if not (allow_not_converged and st == PC_ERR_NOT_CONVERGED):
+        _check(st, "pc_step_host")
+    return info, st
+
+
+def pc_launch_count(ctx) -> int:
+    return int(_lib.pc_launch_count(ctx))
+
+
+def pc_set_profiling(ctx, enable: bool):
+    _check(_lib.pc_set_profiling(ctx, int(bool(enable))), "pc_set_profiling")
+
+
+def pc_spmv_stats(ctx):
+    n, ms, nnzb = c_int64(), c_double(), c_int64()
+    _check(_lib.pc_spmv_stats(ctx, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(nnzb)), "pc_spmv_stats")
+    return n.value, ms.value, nnzb.value
+
+
+# --------------------------------------------------------------------------- convenience
+
+
+class Cloth:
+    """One cloth on the GPU: a context plus device copies of the workload's state."""
+
+    def __init__(self, wl, max_contacts: int | None = None, device="cuda"):
+        self.wl = wl
+        dev = torch.device(device)
+        self.device = dev
+        self.tris = torch.from_numpy(np.ascontiguousarray(wl.tris, np.int32)).to(dev)
+        self.rest = torch.from_numpy(np.ascontiguousarray(wl.rest, np.float32)).to(dev)
+        self.pins = torch.from_numpy(np.ascontiguousarray(wl.pins, np.int32)).to(dev)
+        self.max_contacts = wl.n_contacts if max_contacts is None else max_contacts
+        self.ctx = pc_create(wl.V, wl.T, self.tris, self.rest, self.pins, wl.material, self.max_contacts)
+        self.V, self.T, self.H, self.static_nnzb = pc_get_sizes(self.ctx)
+        self.x = torch.from_numpy(np.ascontiguousarray(wl.x0, np.float32)).to(dev)
+        self.v = torch.from_numpy(np.ascontiguousarray(wl.v0, np.float32)).to(dev)
+        self.h = wl.h
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            pc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def contacts_device(self, step: int):
+        pairs, w = self.wl.contacts(step)
+        if pairs.shape[0] == 0:
+            return None, None
+        return (torch.from_numpy(pairs).to(self.device), torch.from_numpy(w).to(self.device))
+
+    def alloc_system(self, extra_blocks: int = 0):
+        cap = ((self.static_nnzb + 6 * self.max_contacts + extra_blocks) + 3) // 4 * 4
+        dev = self.device
+        return {
+            "row_ptr": torch.zeros(self.V + 1, dtype=torch.int32, device=dev),
+            "col_idx": torch.zeros(cap, dtype=torch.int32, device=dev),
+            "vals": torch.zeros(cap * 9, dtype=torch.float32, device=dev),
+            "b": torch.zeros(self.V * 3, dtype=torch.float32, device=dev),
+            "dres": torch.zeros(self.V * 9, dtype=torch.float32, device=dev),
+        }
+
+    def assemble(self, pairs=None, w=None, x=None, v=None, sysbuf=None):
+        """Pattern + values of this step's system; returns the buffers and nnzb."""
+        s = sysbuf if sysbuf is not None else self.alloc_system()
+        nnzb = pc_assemble_pattern(self.ctx, pairs, w, s["row_ptr"], s["col_idx"])
+        pc_assemble_values(self.ctx, s["row_ptr"], s["col_idx"], nnzb, self.x if x is None else x,
+                           self.v if v is None else v, pairs, w, self.h, s["vals"], s["b"], s["dres"])
+        s["nnzb"] = nnzb
+        return s
+
+    def step(self, pairs=None, w=None, tol=1e-6, precision=PC_PREC_FP32, warm_start=PC_WARM_ZERO, max_iter=20000,
+             dv_out=None, precond=PC_PRECOND_JACOBI, allow_not_converged=False):
+        o = pc_step_opts()
+        o.h = self.h
+        o.solve = solve_opts(tol=tol, max_iter=max_iter, precision=precision, precond=precond)
+        o.warm_start = warm_start
+        info, st = pc_step(self.ctx, self.x, self.v, pairs, w, o, dv_out, allow_not_converged=allow_not_converged)
+        return info, st

@@ -1,0 +1,313 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Pattern (row_ptr, col_idx): bit-exact. Block values: within the per-block tolerance of
+_helpers. dv: within 1e-5 relative L2 of the oracle solved to 1e-12. The oracle is fed
+the GPU's own FP32 state cast exactly to FP64 (Sec. 2.5 Eq. 3 at the same x_t, v_t).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2008_00409_gb300 import workloads as wk
+from tests import _helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pc():
+    from paper_2008_00409_gb300 import build
+    build.build()
+    from paper_2008_00409_gb300 import pcloth
+    return pcloth
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _setup(pc, wl, step=0):
+    cl = pc.Cloth(wl)
+    om = oracle.Mesh.from_workload(wl)
+    pairs, w = wl.contacts(step)
+    pd, wd = cl.contacts_device(step)
+    return cl, om, pairs, w, pd, wd
+
+
+CASES = {
+    "square64": lambda: wk.small_square(),
+    "ragged37x29-contacts": lambda: H.small_contact_cloth(),
+    "stack3x21-interlayer": lambda: H.small_stack(),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_rest_state_matches_oracle(pc, case):
+    wl = CASES[case]()
+    cl, om, *_ = _setup(pc, wl)
+    assert cl.H == om.H
+    hinges = torch.zeros((max(cl.H, 1), 4), dtype=torch.int32, device="cuda")
+    mass = torch.zeros(cl.V, dtype=torch.float32, device="cuda")
+    pc.pc_get_rest(cl.ctx, hinges, mass)
+    np.testing.assert_array_equal(_np(hinges)[: cl.H], om.hinges)
+    np.testing.assert_allclose(_np(mass), om.mass, rtol=2e-7)
+    assert cl.static_nnzb == len(om.pattern()[1])
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_pattern_bit_exact(pc, case):
+    wl = CASES[case]()
+    cl, om, pairs, w, pd, wd = _setup(pc, wl)
+    for step in range(2):
+        pairs, w = wl.contacts(step)
+        pd, wd = cl.contacts_device(step)
+        s = cl.alloc_system()
+        nnzb = pc.pc_assemble_pattern(cl.ctx, pd, wd, s["row_ptr"], s["col_idx"])
+        rp, ci = om.pattern(pairs)
+        assert nnzb == len(ci)
+        np.testing.assert_array_equal(_np(s["row_ptr"]), rp)
+        np.testing.assert_array_equal(_np(s["col_idx"])[:nnzb], ci)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_values_and_rhs_match_oracle(pc, case):
+    wl = CASES[case]()
+    cl, om, pairs, w, pd, wd = _setup(pc, wl)
+    # a non-trivial state: perturbed positions and velocities
+    rng = np.random.default_rng(3)
+    x = wl.x0 + (2e-4 * rng.normal(size=wl.x0.shape)).astype(np.float32)
+    v = (0.05 * rng.normal(size=wl.x0.shape)).astype(np.float32)
+    cl.x.copy_(torch.from_numpy(x))
+    cl.v.copy_(torch.from_numpy(v))
+    s = cl.assemble(pd, wd)
+    nnzb = s["nnzb"]
+    rp, ci, vals_ref, b_ref = om.assemble(x.astype(np.float64), v.astype(np.float64), pairs, w, wl.h)
+    vals = _np(s["vals"])[: 9 * nnzb].reshape(-1, 3, 3)
+    excess = H.block_errors(rp, ci, vals, vals_ref)
+    assert excess.max() <= 0, f"worst block excess {excess.max():.3e}"
+    b = _np(s["b"]).reshape(-1, 3)
+    assert H.rel_l2(b, b_ref) <= 1e-5
+    # bitwise symmetry: block (i, j) is the transpose of block (j, i)
+    rows = np.repeat(np.arange(cl.V), np.diff(rp))
+    key = rows.astype(np.int64) * cl.V + ci
+    tkey = ci.astype(np.int64) * cl.V + rows
+    order = np.argsort(key)
+    tpos = order[np.searchsorted(key[order], tkey)]
+    np.testing.assert_array_equal(vals, vals[tpos].transpose(0, 2, 1))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_difference_diagonal_and_spmv(pc, case):
+    wl = CASES[case]()
+    cl, om, pairs, w, pd, wd = _setup(pc, wl)
+    s = cl.assemble(pd, wd)
+    nnzb = s["nnzb"]
+    x = wl.x0.astype(np.float64)
+    v = wl.v0.astype(np.float64)
+    rp, ci, vals_ref, _ = om.assemble(x, v, pairs, w, wl.h)
+    _, _, vals_nopin, _ = om.assemble(x, v, pairs, w, wl.h, pins=False)
+    # D_i = m_i I - sum over pinned neighbours j of the unzeroed block A_ij
+    D_ref = np.tile(np.eye(3), (cl.V, 1, 1)) * om.mass[:, None, None]
+    rows = np.repeat(np.arange(cl.V), np.diff(rp))
+    for sl in np.nonzero(om.pinned[ci] & (ci != rows) & ~om.pinned[rows])[0]:
+        D_ref[rows[sl]] -= vals_nopin[sl]
+    D = _np(s["dres"]).reshape(-1, 3, 3)
+    np.testing.assert_allclose(D, D_ref, rtol=1e-5, atol=1e-7 * np.abs(D_ref).max())
+    rng = np.random.default_rng(5)
+    for trial in range(2):
+        p = rng.normal(size=(cl.V, 3)).astype(np.float32)
+        if trial == 1:  # a smooth vector: translation plus a small ripple
+            p = (np.array([0.3, -0.2, 1.0]) + 1e-3 * p).astype(np.float32)
+        y_ref = oracle.spmv(rp, ci, vals_ref, p.astype(np.float64))
+        scale = oracle.spmv(rp, ci, np.abs(vals_ref), np.abs(p.astype(np.float64)))
+        pt = torch.from_numpy(p.reshape(-1)).cuda()
+        for dres in (None, s["dres"]):
+            y = torch.zeros_like(pt)
+            pc.pc_bsr_spmv(cl.ctx, s["row_ptr"], s["col_idx"], nnzb, s["vals"], dres, pt, y)
+            err = np.abs(_np(y).reshape(-1, 3) - y_ref)
+            assert (err <= 1e-5 * scale + 1e-30).all()
+        # the difference form is exact on translations: y = M t
+        if trial == 1:
+            t = torch.from_numpy(np.tile(np.array([0.3, -0.2, 1.0], np.float32), cl.V)).cuda()
+            y = torch.zeros_like(t)
+            pc.pc_bsr_spmv(cl.ctx, s["row_ptr"], s["col_idx"], nnzb, s["vals"], s["dres"], t, y)
+            yt = oracle.spmv(rp, ci, vals_ref, _np(t).reshape(-1, 3).astype(np.float64))
+            assert H.rel_l2(_np(y), yt) <= 1e-5
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_pcg_solution_matches_oracle(pc, case, precision):
+    wl = CASES[case]()
+    cl, om, pairs, w, pd, wd = _setup(pc, wl)
+    s = cl.assemble(pd, wd)
+    x = wl.x0.astype(np.float64)
+    rp, ci, vals_ref, b_ref = om.assemble(x, wl.v0.astype(np.float64), pairs, w, wl.h)
+    dv_ref, it_ref, _ = oracle.pcg(rp, ci, vals_ref, b_ref, tol=1e-12)
+    prec = pc.PC_PREC_FP32 if precision == "fp32" else pc.PC_PREC_MIXED
+    tol = 1e-6 if precision == "fp32" else 1e-9
+    dv = torch.zeros(cl.V * 3, device="cuda")
+    info, st = pc.pc_pcg_solve(cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"], s["dres"], s["b"], dv,
+                               pc.solve_opts(tol=tol, precision=prec, max_iter=50000))
+    err = H.rel_l2(_np(dv), dv_ref)
+    if precision == "mixed":
+        assert info.rel_res <= 2 * tol
+        assert err <= H.DV_RTOL, f"dv rel err {err:.3e}"
+    else:
+        # FP32 PCG stops on its FP32 recurrence residual; the FP64 residual of an FP32
+        # iterate of these stiff systems stalls near 1e-5, so the FP32 form is held to
+        # the accuracy its own residual allows
+        assert info.rel_res <= 1e-4
+        assert err <= 1e-4, f"dv rel err {err:.3e} (true residual {info.rel_res:.2e})"
+    assert (_np(dv).reshape(-1, 3)[wl.pins] == 0).all()
+
+
+def test_twenty_step_trajectory_small_square(pc):
+    """64 x 64 cloth, 20 steps: per-step dv parity with the oracle fed the same state."""
+    wl = wk.small_square()
+    cl = pc.Cloth(wl)
+    om = oracle.Mesh.from_workload(wl)
+    dv = torch.zeros(cl.V * 3, device="cuda")
+    worst = 0.0
+    for step in range(wl.steps):
+        x = _np(cl.x).astype(np.float64)
+        v = _np(cl.v).astype(np.float64)
+        info, st = cl.step(tol=1e-9, precision=pc.PC_PREC_MIXED, dv_out=dv)
+        dv_ref, _, _, oinfo = om.step(x, v, h=wl.h, tol=1e-12)
+        err = H.rel_l2(_np(dv), dv_ref)
+        worst = max(worst, err)
+        assert err <= H.DV_RTOL, f"step {step}: rel err {err:.3e}"
+    # the state really moved and stayed finite
+    assert np.isfinite(_np(cl.x)).all() and np.abs(_np(cl.x) - wl.x0).max() > 1e-3
+
+
+def test_benchmark_tolerance_both_precisions(pc):
+    """At tol 1e-6 the mixed form meets the FP64 residual; plain FP32 converges on its
+    recurrence residual and reports a true residual within two decades of it."""
+    wl = wk.small_square()
+    cl = pc.Cloth(wl)
+    info, st = cl.step(tol=1e-6, precision=pc.PC_PREC_FP32)
+    assert st == pc.PC_OK and info.solve.rel_res <= 1e-4
+    info, st = cl.step(tol=1e-6, precision=pc.PC_PREC_MIXED)
+    assert st == pc.PC_OK and info.solve.rel_res <= 1e-6
+
+
+# ------------------------------------------------------------------------- edge cases
+
+
+def test_isolated_vertices_are_reported(pc):
+    # vertices in no triangle have zero lumped mass, so A is singular there: the solve
+    # must report it instead of producing NaNs
+    rest = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [2, 2, 2], [3, 3, 3]], np.float32)
+    tris = np.array([[0, 1, 2]], np.int32)
+    wl = wk.Workload("tiny", rest, tris, np.zeros(0, np.int32), rest.copy(), np.zeros_like(rest), 1 / 200,
+                     wk.Material(), [], 0)
+    cl = pc.Cloth(wl, max_contacts=0)
+    with pytest.raises(pc.PcError) as e:
+        cl.step(tol=1e-10, precision=pc.PC_PREC_MIXED)
+    assert e.value.status == pc.PC_ERR_NONFINITE
+
+
+def test_single_triangle_free_fall(pc):
+    rest = np.array([[0, 0, 0], [0.01, 0, 0], [0, 0.01, 0]], np.float32)
+    wl = wk.Workload("one", rest, np.array([[0, 1, 2]], np.int32), np.zeros(0, np.int32), rest.copy(),
+                     np.zeros_like(rest), 1 / 200, wk.Material(), [], 0)
+    cl = pc.Cloth(wl, max_contacts=0)
+    assert cl.H == 0 and cl.static_nnzb == 9
+    dv = torch.zeros(9, device="cuda")
+    cl.step(tol=1e-10, precision=pc.PC_PREC_MIXED, dv_out=dv)
+    np.testing.assert_allclose(_np(dv).reshape(-1, 3), np.tile([0, 0, -9.81 / 200], (3, 1)), atol=1e-7)
+
+
+def test_free_fall_unpinned_sheet(pc):
+    rest, tris, _ = wk.grid_piece(9, 7, 0.2, 0.15, jitter=0.2, flip_prob=0.2, seed=9)
+    wl = wk.Workload("ff", rest, tris, np.zeros(0, np.int32), rest.copy(), np.zeros_like(rest), 1 / 200,
+                     wk.Material(), [], 0)
+    cl = pc.Cloth(wl, max_contacts=0)
+    dv = torch.zeros(cl.V * 3, device="cuda")
+    cl.step(tol=1e-10, precision=pc.PC_PREC_MIXED, dv_out=dv)
+    np.testing.assert_allclose(_np(dv).reshape(-1, 3), np.tile([0, 0, -9.81 / 200], (cl.V, 1)), atol=1e-7)
+
+
+def test_capacity_error_reports_required(pc):
+    wl = H.small_contact_cloth()
+    cl = pc.Cloth(wl)
+    pd, wd = cl.contacts_device(0)
+    s = cl.alloc_system()
+    need = pc.pc_assemble_pattern(cl.ctx, pd, wd, s["row_ptr"], s["col_idx"])
+    small = torch.zeros((need // 4) * 4 - 4, dtype=torch.int32, device="cuda")
+    with pytest.raises(pc.PcError) as e:
+        pc.pc_assemble_pattern(cl.ctx, pd, wd, s["row_ptr"], small)
+    assert e.value.status == pc.PC_ERR_CAPACITY and e.value.required == need
+
+
+def test_invalid_contact_rejected(pc):
+    wl = H.small_contact_cloth()
+    cl = pc.Cloth(wl)
+    pairs, w = wl.contacts(0)
+    bad = pairs.copy()
+    bad[0, 1] = bad[0, 0]  # p repeated in its own triangle
+    s = cl.alloc_system()
+    with pytest.raises(pc.PcError) as e:
+        pc.pc_assemble_pattern(cl.ctx, torch.from_numpy(bad).cuda(), torch.from_numpy(w).cuda(), s["row_ptr"],
+                               s["col_idx"])
+    assert e.value.status == pc.PC_ERR_ARG
+    bad = pairs.copy()
+    bad[1, 2] = cl.V + 5
+    with pytest.raises(pc.PcError) as e:
+        pc.pc_assemble_pattern(cl.ctx, torch.from_numpy(bad).cuda(), torch.from_numpy(w).cuda(), s["row_ptr"],
+                               s["col_idx"])
+    assert e.value.status == pc.PC_ERR_ARG
+
+
+def test_invalid_mesh_rejected(pc):
+    rest = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0], [2, 0, 0]], np.float32)
+    for tris in ([[0, 1, 7]], [[0, 1, 1]], [[0, 1, 2], [1, 0, 3], [0, 1, 4]]):
+        t = torch.tensor(tris, dtype=torch.int32, device="cuda")
+        with pytest.raises(pc.PcError):
+            pc.pc_create(5, len(tris), t, torch.from_numpy(rest).cuda(), None, wk.Material(), 0)
+
+
+def test_nonfinite_state_and_not_converged(pc):
+    wl = wk.small_square()
+    cl = pc.Cloth(wl)
+    info, st = cl.step(tol=1e-12, max_iter=3, allow_not_converged=True)
+    assert st == pc.PC_ERR_NOT_CONVERGED and info.solve.iters == 3 and info.solve.rel_res > 1e-12
+    cl2 = pc.Cloth(wl)
+    cl2.x[10, 2] = float("nan")
+    with pytest.raises(pc.PcError) as e:
+        cl2.step(tol=1e-6)
+    assert e.value.status == pc.PC_ERR_NONFINITE
+
+
+def test_host_buffer_step_matches_device_step(pc):
+    wl = H.small_contact_cloth()
+    a = pc.Cloth(wl)
+    b = pc.Cloth(wl)
+    pairs, w = wl.contacts(0)
+    pd, wd = a.contacts_device(0)
+    a.step(pd, wd, tol=1e-8, precision=pc.PC_PREC_MIXED)
+    xh = wl.x0.copy()
+    vh = wl.v0.copy()
+    o = pc.pc_step_opts()
+    o.h = wl.h
+    o.solve = pc.solve_opts(tol=1e-8, precision=pc.PC_PREC_MIXED)
+    o.warm_start = pc.PC_WARM_ZERO
+    pc.pc_step_host(b.ctx, xh, vh, pairs, w, o)
+    np.testing.assert_array_equal(xh, _np(a.x))
+    np.testing.assert_array_equal(vh, _np(a.v))
+
+
+def test_deterministic_repeat(pc):
+    wl = H.small_contact_cloth()
+    outs = []
+    for _ in range(2):
+        cl = pc.Cloth(wl)
+        pd, wd = cl.contacts_device(0)
+        s = cl.assemble(pd, wd)
+        dv = torch.zeros(cl.V * 3, device="cuda")
+        pc.pc_pcg_solve(cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"], s["dres"], s["b"], dv)
+        outs.append((_np(s["vals"]).copy(), _np(s["b"]).copy(), _np(dv).copy()))
+    for u, v in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(u, v)

@@ -140,12 +140,51 @@ def test_assembled_hessian_is_force_jacobian_in_tension():
     np.testing.assert_allclose(Kd, -J, rtol=1e-5, atol=1e-6 * np.abs(Kd).max())
 
 
-def test_rhs_is_h_times_force_at_predicted_positions():
+def test_rhs_is_first_order_expansion_of_force_at_predicted_positions():
+    # b = h f(x + h v) to first order in h v (Eq. 2): the gap to the literal evaluation
+    # is h * O(|h v|^2), so it shrinks 4x when h v halves; for a system whose forces are
+    # linear in x (contacts and gravity only, frozen contact frames) it is exact
+    # (flat sheet in biaxial tension: there the clamped, Gauss-Newton K is the exact -J)
+    M, rest, tris, x, v, pairs, w = tiny_cloth(pins=())
+    xt = rest.astype(np.float64) * np.array([1.03, 1.05, 1.0])
+    gaps = []
+    for s in (1.0, 0.5, 0.25):
+        vv = 0.1 * s * v
+        _, _, _, b = M.assemble(xt, vv, pairs, w, H_STEP, pins=False)
+        f = M.forces(xt + H_STEP * vv, pairs, w, xt=xt)
+        gaps.append(np.linalg.norm(b - H_STEP * f))
+    assert 3.5 < gaps[0] / gaps[1] < 4.5 and 3.5 < gaps[1] / gaps[2] < 4.5
+    mat = MAT.copy()
+    mat[1] = 1e-9  # membrane off (tiny modulus keeps the mesh valid)
+    mat[3] = 0.0   # bending off
+    Ml = oracle.Mesh(rest, tris, mat)
+    _, _, _, b = Ml.assemble(x, v, pairs, w, H_STEP, pins=False)
+    f = Ml.forces(x + H_STEP * v, pairs, w, xt=x)
+    np.testing.assert_allclose(b, H_STEP * f, rtol=1e-9, atol=1e-9 * np.abs(b).max())
+
+
+def test_rhs_matches_dense_linearisation_with_pins():
     M, rest, tris, x, v, pairs, w = tiny_cloth()
     rp, ci, vals, b = M.assemble(x, v, pairs, w, H_STEP)
-    f = M.forces(x + H_STEP * v, pairs, w, xt=x)
-    f[M.pins] = 0.0
-    np.testing.assert_allclose(b, H_STEP * f, rtol=1e-14, atol=1e-18)
+    _, _, K = M.hessian(x, pairs, w, xt=x, pattern=(rp, ci))
+    Kd = oracle.dense(rp, ci, K)
+    ref = H_STEP * (M.forces(x, pairs, w, xt=x).reshape(-1) - H_STEP * Kd @ v.reshape(-1))
+    ref = ref.reshape(-1, 3)
+    ref[M.pins] = 0.0
+    np.testing.assert_allclose(b, ref, rtol=1e-12, atol=1e-15)
+
+
+def test_twenty_steps_stay_bounded():
+    # the 64 x 64 cloth hanging from two corners: free-falling parts gain h g per step,
+    # nothing may grow faster than that (a diverging integrator fails here)
+    wl = wk.small_square()
+    M = oracle.Mesh.from_workload(wl)
+    x = wl.x0.astype(np.float64)
+    v = wl.v0.astype(np.float64)
+    for step in range(20):
+        dv, x, v, info = M.step(x, v, h=wl.h, tol=1e-9)
+        assert np.abs(v).max() <= (step + 1) * H_STEP * 9.81 * 1.5 + 0.1
+    assert np.isfinite(x).all()
 
 
 @pytest.mark.parametrize("v0", [(0.0, 0.0, 0.0), (0.4, -0.1, 0.2)])
