@@ -32,6 +32,7 @@ void pc_note_cuda_error(cudaError_t e, const char *what, const char *file, int l
 #define PC_DERR_MESH 4u       // non-manifold edge / degenerate triangle
 #define PC_DERR_CAPACITY 8u   // output capacity exceeded
 #define PC_DERR_NONFINITE 16u // NaN / Inf met
+#define PC_DERR_TIMEOUT 32u   // a bounded device wait gave up
 
 // element reference encoding in incidence lists: type(2) | local(2) | id(28)
 #define PC_REF_TRI 0u

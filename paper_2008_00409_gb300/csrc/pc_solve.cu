@@ -2,14 +2,15 @@
 // equations are solved with a preconditioned conjugate gradient solver; Sec. 3.1: the
 // SpMV is the most expensive operator and vector operations are data parallel).
 //
-// Per iteration two kernels run:
-//   spmv:   p = z + beta p_prev (own rows), q = A p with p_i formed on the fly at the
-//           gathered columns, partial p.q                         -> alpha = rz / pq
-//   update: x += alpha p, r -= alpha q, z = D^-1 r, partial r.z, r.r -> beta, convergence
-// The matrix rows of each 128-row tile are staged into shared memory with 16-byte
-// vector loads (coalesced, one pass over the blocks), then two threads per row consume
-// them. Dot products accumulate in FP64; each kernel's last block to finish sums the
-// per-block partials in a fixed order, so every reduction is deterministic.
+// Per iteration three kernels run:
+//   direction: p = z + beta p                                        (in place)
+//   spmv:      q = A p, partial p.q                                  -> alpha = rz / pq
+//   update:    x += alpha p, r -= alpha q, z = D^-1 r, partial r.z, r.r -> beta, stop test
+// (the SpMV kernel, a bulk-copy pipelined stream over the blocks, is in pc_spmv.cuh).
+// Dot products accumulate in FP64; each kernel's last block to finish sums the
+// per-block partials in a fixed order, so every reduction is deterministic. The
+// direction p and the preconditioned residual z are float4 per vertex (padded) so
+// that the SpMV gathers them with one 16-byte load each.
 //
 // Mixed precision (PC_PREC_MIXED): the solution is an FP64 accumulator plus the FP32
 // increment the iterations build; at refresh points the increment is folded into the
@@ -21,10 +22,6 @@
 
 #include "pc_internal.cuh"
 
-#define SP_THREADS 256
-#define SP_ROWS 128
-#define SP_CAP 1536
-#define SP_SMEM_BYTES ((SP_CAP * 9 + 16) * 4 + (SP_CAP + 16) * 4)
 #define EW_THREADS 256
 #define RED_SLOTS 4
 
@@ -81,135 +78,7 @@ __device__ bool last_block_reduce(double *v, int n, double *partials, uint32_t *
     return true;
 }
 
-// ------------------------------------------------------------------------- SpMV
-
-struct SpmvArgs {
-    int V;
-    const int32_t *rp;
-    const int32_t *ci;
-    const float *vals;
-    const float *dres;   // difference-form diagonal, or null
-    const float *xin;    // vector (or z in PCG mode)
-    const float *pold;   // previous direction (PCG mode) or null
-    float *y;            // result
-    float *pnew;         // receives the formed direction, or null
-    double *partials;    // p.q partials (PCG mode) or null
-    pc_scalars *sc;      // PCG scalars or null
-};
-
-template <bool DIFF, bool PCG>
-__global__ void __launch_bounds__(SP_THREADS) spmv_kernel(SpmvArgs a)
-{
-    extern __shared__ float4 smem4[];
-    float *s_vals = reinterpret_cast<float *>(smem4);
-    int32_t *s_cols = reinterpret_cast<int32_t *>(s_vals + SP_CAP * 9 + 16);
-    float beta = 0.0f;
-    if (PCG) {
-        if (a.sc->done) return;
-        beta = (float)a.sc->beta;
-    }
-    const int ntiles = (a.V + SP_ROWS - 1) / SP_ROWS;
-    const int half = threadIdx.x & 1;
-    double dot_acc = 0.0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int r0 = tile * SP_ROWS, r1 = min(r0 + SP_ROWS, a.V);
-        const int b0 = a.rp[r0], b1 = a.rp[r1];
-        const bool staged = (b1 - b0) <= SP_CAP;
-        int vo = 0, co = 0;
-        if (staged) {
-            const int64_t f0 = 9ll * b0, f1 = 9ll * b1;
-            const int64_t al0 = f0 & ~3ll, al1 = (f1 + 3) & ~3ll;
-            const float4 *src = reinterpret_cast<const float4 *>(a.vals + al0);
-            const int nv = (int)((al1 - al0) >> 2);
-            for (int i = threadIdx.x; i < nv; i += SP_THREADS) smem4[i] = src[i];
-            const int c0 = b0 & ~3, c1 = (b1 + 3) & ~3;
-            const int4 *csrc = reinterpret_cast<const int4 *>(a.ci + c0);
-            int4 *cdst = reinterpret_cast<int4 *>(s_cols);
-            for (int i = threadIdx.x; i < ((c1 - c0) >> 2); i += SP_THREADS) cdst[i] = csrc[i];
-            vo = (int)(f0 - al0);
-            co = b0 - c0;
-            __syncthreads();
-        }
-        const int row = r0 + (threadIdx.x >> 1);
-        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
-        float xj0 = 0.f, xj1 = 0.f, xj2 = 0.f;
-        if (row < r1) {
-            if (DIFF || PCG) {
-                xj0 = a.xin[3 * row];
-                xj1 = a.xin[3 * row + 1];
-                xj2 = a.xin[3 * row + 2];
-                if (PCG) {
-                    xj0 = fmaf(beta, a.pold[3 * row], xj0);
-                    xj1 = fmaf(beta, a.pold[3 * row + 1], xj1);
-                    xj2 = fmaf(beta, a.pold[3 * row + 2], xj2);
-                }
-            }
-            const int rb = a.rp[row], re = a.rp[row + 1];
-            for (int b = rb + half; b < re; b += 2) {
-                int col;
-                const float *B;
-                if (staged) {
-                    col = s_cols[co + (b - b0)];
-                    B = s_vals + vo + 9 * (b - b0);
-                } else {
-                    col = a.ci[b];
-                    B = a.vals + 9ll * b;
-                }
-                if (DIFF && col == row) continue;
-                float v0 = a.xin[3 * col], v1 = a.xin[3 * col + 1], v2 = a.xin[3 * col + 2];
-                if (PCG) {
-                    v0 = fmaf(beta, a.pold[3 * col], v0);
-                    v1 = fmaf(beta, a.pold[3 * col + 1], v1);
-                    v2 = fmaf(beta, a.pold[3 * col + 2], v2);
-                }
-                if (DIFF) {
-                    v0 -= xj0;
-                    v1 -= xj1;
-                    v2 -= xj2;
-                }
-                acc0 = fmaf(B[0], v0, fmaf(B[1], v1, fmaf(B[2], v2, acc0)));
-                acc1 = fmaf(B[3], v0, fmaf(B[4], v1, fmaf(B[5], v2, acc1)));
-                acc2 = fmaf(B[6], v0, fmaf(B[7], v1, fmaf(B[8], v2, acc2)));
-            }
-        }
-        acc0 += __shfl_xor_sync(0xffffffffu, acc0, 1);
-        acc1 += __shfl_xor_sync(0xffffffffu, acc1, 1);
-        acc2 += __shfl_xor_sync(0xffffffffu, acc2, 1);
-        if (row < r1 && half == 0) {
-            if (DIFF) {
-                const float *D = a.dres + 9ll * row;
-                acc0 = fmaf(D[0], xj0, fmaf(D[1], xj1, fmaf(D[2], xj2, acc0)));
-                acc1 = fmaf(D[3], xj0, fmaf(D[4], xj1, fmaf(D[5], xj2, acc1)));
-                acc2 = fmaf(D[6], xj0, fmaf(D[7], xj1, fmaf(D[8], xj2, acc2)));
-            }
-            a.y[3 * row] = acc0;
-            a.y[3 * row + 1] = acc1;
-            a.y[3 * row + 2] = acc2;
-            if (PCG) {
-                a.pnew[3 * row] = xj0;
-                a.pnew[3 * row + 1] = xj1;
-                a.pnew[3 * row + 2] = xj2;
-                dot_acc += (double)xj0 * (double)acc0 + (double)xj1 * (double)acc1 + (double)xj2 * (double)acc2;
-            }
-        }
-        if (staged) __syncthreads();
-    }
-    if (PCG) {
-        double v[1] = {dot_acc};
-        if (last_block_reduce(v, 1, a.partials, &a.sc->counter) && threadIdx.x == 0) {
-            pc_scalars *s = a.sc;
-            double pq = v[0];
-            s->pq = pq;
-            double alpha = s->rz / pq;
-            if (!(pq > 0.0) || !isfinite(alpha)) {
-                s->status = PC_ERR_NONFINITE;
-                s->done = 1;
-                alpha = 0.0;
-            }
-            s->alpha = alpha;
-        }
-    }
-}
+#include "pc_spmv.cuh"
 
 // ------------------------------------------------------------------------- preconditioner
 
@@ -263,28 +132,30 @@ __global__ void dinv_kernel(int V, const int32_t *__restrict__ rp, const int32_t
 // computes beta and applies the stop tests.
 template <bool BLOCK>
 __global__ void __launch_bounds__(EW_THREADS) pcg_update_kernel(int V, float *__restrict__ x,
-                                                                 const float *__restrict__ p, float *__restrict__ r,
-                                                                 const float *__restrict__ q,
+                                                                 const float4 *__restrict__ p4,
+                                                                 float *__restrict__ r, const float *__restrict__ q,
                                                                  const float *__restrict__ dinv,
-                                                                 float *__restrict__ z, double *partials,
+                                                                 float4 *__restrict__ z4, double *partials,
                                                                  pc_scalars *sc)
 {
     if (sc->done) return;
     const float alpha = (float)sc->alpha;
     double rz = 0.0, rr = 0.0;
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
+        const float4 pv = p4[row];
+        const float pp[3] = {pv.x, pv.y, pv.z};
         float ri[3], zi[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const int64_t i = 3ll * row + a;
-            x[i] = fmaf(alpha, p[i], x[i]);
+            x[i] = fmaf(alpha, pp[a], x[i]);
             ri[a] = fmaf(-alpha, q[i], r[i]);
             r[i] = ri[a];
         }
         apply_precond<BLOCK>(dinv, row, ri, zi);
+        z4[row] = make_float4(zi[0], zi[1], zi[2], 0.f);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            z[3ll * row + a] = zi[a];
             rz += (double)ri[a] * (double)zi[a];
             rr += (double)ri[a] * (double)ri[a];
         }
@@ -315,7 +186,7 @@ template <bool BLOCK>
 __global__ void __launch_bounds__(EW_THREADS) pcg_init_kernel(int V, const float *__restrict__ b,
                                                                const float *__restrict__ q, float *__restrict__ r,
                                                                const float *__restrict__ dinv,
-                                                               float *__restrict__ z, float *__restrict__ pold,
+                                                               float4 *__restrict__ z4, float4 *__restrict__ pold4,
                                                                double tol, int max_iter, double *partials,
                                                                pc_scalars *sc)
 {
@@ -328,13 +199,13 @@ __global__ void __launch_bounds__(EW_THREADS) pcg_init_kernel(int V, const float
             float bi = b[i];
             ri[a] = q ? bi - q[i] : bi;
             r[i] = ri[a];
-            pold[i] = 0.0f;
             bb += (double)bi * (double)bi;
         }
+        pold4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
         apply_precond<BLOCK>(dinv, row, ri, zi);
+        z4[row] = make_float4(zi[0], zi[1], zi[2], 0.f);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            z[3ll * row + a] = zi[a];
             rz += (double)ri[a] * (double)zi[a];
             rr += (double)ri[a] * (double)ri[a];
         }
@@ -425,7 +296,7 @@ template <bool DIFF, bool BLOCK>
 __global__ void __launch_bounds__(EW_THREADS) residual_replace_kernel(
     int V, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const float *__restrict__ vals,
     const float *__restrict__ dres, const float *__restrict__ b, const double *__restrict__ x64,
-    const float *__restrict__ dinv, float *__restrict__ r, float *__restrict__ z, float *__restrict__ pold, int first,
+    const float *__restrict__ dinv, float *__restrict__ r, float4 *__restrict__ z4, float4 *__restrict__ pold4, int first,
     double tol, int max_iter, double *partials, pc_scalars *sc)
 {
     double rz = 0.0, rr = 0.0, bb = 0.0;
@@ -441,13 +312,11 @@ __global__ void __launch_bounds__(EW_THREADS) residual_replace_kernel(
             bb += bv * bv;
             ri[a2] = (float)rv;
             r[i] = ri[a2];
-            if (first) pold[i] = 0.0f;
         }
+        if (first) pold4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
         apply_precond<BLOCK>(dinv, row, ri, zi);
-        for (int a2 = 0; a2 < 3; ++a2) {
-            z[3ll * row + a2] = zi[a2];
-            rz += (double)ri[a2] * (double)zi[a2];
-        }
+        z4[row] = make_float4(zi[0], zi[1], zi[2], 0.f);
+        for (int a2 = 0; a2 < 3; ++a2) rz += (double)ri[a2] * (double)zi[a2];
     }
     double v[3] = {rz, rr, bb};
     if (last_block_reduce(v, 3, partials, &sc->counter) && threadIdx.x == 0) {
@@ -508,7 +377,7 @@ __global__ void state_update_kernel(int64_t n, float *x, float *v, const float *
 static int spmv_grid(const pc_ctx *c)
 {
     int tiles = (c->V + SP_ROWS - 1) / SP_ROWS;
-    int g = c->num_sms * 3;
+    int g = c->num_sms * SP_CTAS_PER_SM;
     return tiles < g ? (tiles > 0 ? tiles : 1) : g;
 }
 static int ew_grid(const pc_ctx *c, int64_t n)
@@ -523,9 +392,8 @@ pc_status pc_solver_alloc(pc_ctx *c)
 {
     const int64_t n = 3ll * c->V;
     PC_CUDA_TRY(cudaMalloc(&c->r, sizeof(float) * n));
-    PC_CUDA_TRY(cudaMalloc(&c->z, sizeof(float) * n));
-    PC_CUDA_TRY(cudaMalloc(&c->p0, sizeof(float) * n));
-    PC_CUDA_TRY(cudaMalloc(&c->p1, sizeof(float) * n));
+    PC_CUDA_TRY(cudaMalloc(&c->z, sizeof(float4) * c->V));
+    PC_CUDA_TRY(cudaMalloc(&c->p0, sizeof(float4) * c->V));
     PC_CUDA_TRY(cudaMalloc(&c->q, sizeof(float) * n));
     PC_CUDA_TRY(cudaMalloc(&c->dinv, sizeof(float) * 3 * n));
     PC_CUDA_TRY(cudaMalloc(&c->dtmp, sizeof(float) * n));
@@ -577,6 +445,7 @@ extern "C" pc_status pc_bsr_spmv(pc_ctx *ctx, const pc_bsr *A, const float *vals
     a.dres = dres;
     a.xin = x;
     a.y = y;
+    a.err = ctx->d_err;
     return launch_spmv(ctx, a, dres != nullptr, false, (cudaStream_t)stream);
 }
 
@@ -623,12 +492,27 @@ static pc_status replace_residual(const SolveCtx &s, float *x32, int first, doub
     const int64_t n = 3ll * c->V;
     if (!first) PC_LAUNCH(c, fold_kernel, ew_grid(c, n), EW_THREADS, 0, s.st, n, x32, c->x64);
     DISPATCH2(c, residual_replace_kernel, s.diff, s.block, ew_grid(c, c->V), EW_THREADS, s.st, c->V, s.A->row_ptr,
-              s.A->col_idx, s.vals, s.dres, s.b, c->x64, c->dinv, c->r, c->z, c->p0, first, tol, max_iter,
+              s.A->col_idx, s.vals, s.dres, s.b, c->x64, c->dinv, c->r, (float4 *)c->z, (float4 *)c->p0, first, tol,
+              max_iter,
               c->partials, c->sc);
     return PC_OK;
 }
 
-static pc_status launch_iterations(const SolveCtx &s, float *x, int count, float **pa, float **pb)
+// p = z + beta p, in place (beta = 0 right after a start, where p was zeroed)
+__global__ void __launch_bounds__(EW_THREADS) pcg_direction_kernel(int V, const float4 *__restrict__ z4,
+                                                                    float4 *__restrict__ p4, const pc_scalars *sc)
+{
+    if (sc->done) return;
+    const float beta = (float)sc->beta;
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
+        const float4 z = z4[row], p = p4[row];
+        p4[row] = make_float4(fmaf(beta, p.x, z.x), fmaf(beta, p.y, z.y), fmaf(beta, p.z, z.z), 0.f);
+    }
+}
+
+// `count` PCG iterations: p = z + beta p; q = A p (and p.q -> alpha); x, r, z update
+// (and r.z -> beta, stop tests). Kernels exit at once when the scalars say done.
+static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
 {
     pc_ctx *c = s.c;
     SpmvArgs a{};
@@ -637,24 +521,24 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count, float
     a.ci = s.A->col_idx;
     a.vals = s.vals;
     a.dres = s.dres;
-    a.xin = c->z;
+    a.x4 = (const float4 *)c->p0;
     a.y = c->q;
     a.partials = c->partials;
     a.sc = c->sc;
+    a.err = c->d_err;
     for (int k = 0; k < count; ++k) {
-        a.pold = *pa;
-        a.pnew = *pb;
         bool timed = c->profiling && k == 0;
+        PC_LAUNCH(c, pcg_direction_kernel, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (const float4 *)c->z,
+                  (float4 *)c->p0, c->sc);
         if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[0], s.st));
         PC_TRY(launch_spmv(c, a, s.diff, true, s.st));
         if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[1], s.st));
         if (s.block)
-            PC_LAUNCH(c, pcg_update_kernel<true>, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, x, *pb, c->r, c->q,
-                      c->dinv, c->z, c->partials, c->sc);
+            PC_LAUNCH(c, pcg_update_kernel<true>, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, x,
+                      (const float4 *)c->p0, c->r, c->q, c->dinv, (float4 *)c->z, c->partials, c->sc);
         else
-            PC_LAUNCH(c, pcg_update_kernel<false>, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, x, *pb, c->r, c->q,
-                      c->dinv, c->z, c->partials, c->sc);
-        float *t = *pa; *pa = *pb; *pb = t;
+            PC_LAUNCH(c, pcg_update_kernel<false>, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, x,
+                      (const float4 *)c->p0, c->r, c->q, c->dinv, (float4 *)c->z, c->partials, c->sc);
         if (timed) {
             float ms = 0.f;
             PC_CUDA_TRY(cudaEventSynchronize(c->ev[1]));
@@ -711,16 +595,16 @@ extern "C" pc_status pc_pcg_solve(pc_ctx *ctx, const pc_bsr *A, const float *val
         a.dres = dres;
         a.xin = dv;
         a.y = ctx->q;
+        a.err = ctx->d_err;
         PC_TRY(launch_spmv(ctx, a, s.diff, false, st));
         if (s.block)
             PC_LAUNCH(ctx, pcg_init_kernel<true>, ew_grid(ctx, V), EW_THREADS, 0, st, V, b, ctx->q, ctx->r, ctx->dinv,
-                      ctx->z, ctx->p0, o.tol, o.max_iter, ctx->partials, ctx->sc);
+                      (float4 *)ctx->z, (float4 *)ctx->p0, o.tol, o.max_iter, ctx->partials, ctx->sc);
         else
             PC_LAUNCH(ctx, pcg_init_kernel<false>, ew_grid(ctx, V), EW_THREADS, 0, st, V, b, ctx->q, ctx->r, ctx->dinv,
-                      ctx->z, ctx->p0, o.tol, o.max_iter, ctx->partials, ctx->sc);
+                      (float4 *)ctx->z, (float4 *)ctx->p0, o.tol, o.max_iter, ctx->partials, ctx->sc);
     }
     PC_TRY(read_scalars(ctx, st));
-    float *pa = ctx->p0, *pb = ctx->p1;
     double rr_last = ctx->sc_host->rr;
     int iter_last = 0;
     int launched = 0;
@@ -750,11 +634,12 @@ extern "C" pc_status pc_pcg_solve(pc_ctx *ctx, const pc_bsr *A, const float *val
         }
         int chunk = o.check_every;
         if (launched == 0 && chunk > 8) chunk = 8;
-        PC_TRY(launch_iterations(s, x, chunk, &pa, &pb));
+        PC_TRY(launch_iterations(s, x, chunk));
         launched += chunk;
         PC_TRY(read_scalars(ctx, st));
     }
     const pc_scalars fin = *ctx->sc_host;
+    if (fin.status == PC_ERR_TIMEOUT) return PC_ERR_TIMEOUT;
     pc_solve_info inf{};
     inf.iters = fin.iter;
     inf.outer = replacements;

@@ -1,0 +1,261 @@
+// Block-sparse (3x3) matrix-vector product, the dominant operator of the solve (Sec. 3.1).
+//
+// Persistent CTAs, four per SM. In each CTA a producer warp streams the CTA's 32-row
+// tiles of the matrix (the tile's contiguous run of 36-byte blocks and of column
+// indices) into a 2-stage shared-memory ring with 1-D bulk copies (cp.async.bulk)
+// completing on mbarriers, while 4 consumer warps compute the current tile with four
+// threads per row. Row pointers, the row's own vector entries and the difference-form
+// diagonal of the next tile are prefetched into registers before the current tile is
+// computed, so the only latency left on a tile's critical path is the gather of the
+// neighbours' vector entries. Tiles whose blocks exceed a stage (rows with many contacts)
+// are read directly from global memory.
+//
+// PCG mode computes q = A p and its p.q partial, with p stored as float4 per vertex so
+// that each gather is one 16-byte load.
+// Difference form (dres given): y_j = D_j x_j + sum_i A_ji (x_i - x_j); the diagonal
+// block then multiplies x_j - x_j = 0 and needs no special case.
+#pragma once
+
+#include "pc_tma.cuh"
+
+#ifndef SP_ROWS
+#define SP_ROWS 32                         // rows per tile
+#endif
+#ifndef SP_STAGES
+#define SP_STAGES 2
+#endif
+#ifndef SP_CAP_PER_ROW
+#define SP_CAP_PER_ROW 18                  // stage capacity in blocks per row
+#endif
+#ifndef SP_CTAS_PER_SM
+#define SP_CTAS_PER_SM 4
+#endif
+#define SP_TPR 4                           // threads per row
+#define SP_CWARPS (SP_ROWS * SP_TPR / 32)  // consumer warps
+#define SP_THREADS (32 * (SP_CWARPS + 1))  // + 1 producer warp
+#define SP_CAP (SP_ROWS * SP_CAP_PER_ROW)  // blocks per stage
+#define SP_VAL_BYTES ((SP_CAP * 36 + 32 + 15) / 16 * 16)
+#define SP_COL_BYTES ((SP_CAP * 4 + 32 + 15) / 16 * 16)
+#define SP_STAGE_BYTES (SP_VAL_BYTES + SP_COL_BYTES)
+#define SP_SMEM_BYTES (SP_STAGES * SP_STAGE_BYTES)
+#define SP_WAIT_BUDGET (1ll << 31)         // cycles (about a second) before a wait gives up
+
+struct SpmvArgs {
+    int V;
+    const int32_t *rp;
+    const int32_t *ci;
+    const float *vals;
+    const float *dres;    // difference-form diagonal, or null
+    const float *xin;     // plain mode: x as float[V][3]
+    const float4 *x4;     // PCG mode: the search direction p as float4[V]
+    float *y;             // result, float[V][3]
+    double *partials;     // PCG mode: p.q partials
+    pc_scalars *sc;       // PCG mode: scalars
+    uint32_t *err;        // error bits (timeouts)
+};
+
+template <bool PCG>
+__device__ __forceinline__ float4 spmv_gather(const SpmvArgs &a, int c)
+{
+    if (PCG) {
+        return a.x4[c];
+    } else {
+        return make_float4(a.xin[3ll * c], a.xin[3ll * c + 1], a.xin[3ll * c + 2], 0.f);
+    }
+}
+
+__device__ __forceinline__ void spmv_fma(const float *B, float4 u, float &a0, float &a1, float &a2)
+{
+    a0 = fmaf(B[0], u.x, fmaf(B[1], u.y, fmaf(B[2], u.z, a0)));
+    a1 = fmaf(B[3], u.x, fmaf(B[4], u.y, fmaf(B[5], u.z, a1)));
+    a2 = fmaf(B[6], u.x, fmaf(B[7], u.y, fmaf(B[8], u.z, a2)));
+}
+
+// What a consumer thread needs about its own row, loaded one tile ahead.
+struct SpmvRow {
+    int row, rb, re;
+    float4 xj;
+    float D[9];
+};
+
+template <bool DIFF, bool PCG>
+__device__ __forceinline__ void spmv_load_row(const SpmvArgs &a, int tile, int t, SpmvRow &r)
+{
+    r.row = tile * SP_ROWS + t / SP_TPR;
+    r.rb = r.re = 0;
+    r.xj = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r.row < a.V) {
+        r.rb = a.rp[r.row];
+        r.re = a.rp[r.row + 1];
+        if (DIFF || PCG) r.xj = spmv_gather<PCG>(a, r.row);
+        if (DIFF && (t & (SP_TPR - 1)) == 0) {
+#pragma unroll
+            for (int e = 0; e < 9; ++e) r.D[e] = a.dres[9ll * r.row + e];
+        }
+    }
+}
+
+template <bool DIFF, bool PCG>
+__global__ void __launch_bounds__(SP_THREADS, SP_CTAS_PER_SM) spmv_kernel(SpmvArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t full_bar[SP_STAGES], empty_bar[SP_STAGES];
+    __shared__ int stage_info[SP_STAGES][4];  // b0, value offset, column offset, staged
+    __shared__ int s_timeout;
+    if (PCG && a.sc->done) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < SP_STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], SP_CWARPS);
+        }
+        s_timeout = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int ntiles = (a.V + SP_ROWS - 1) / SP_ROWS;
+    double dot_acc = 0.0;
+    bool timed_out = false;
+
+    if (warp == SP_CWARPS) {
+        // ---------------- producer
+        if (lane == 0) {
+            int issued = 0;
+            for (int k = 0;; ++k) {
+                const int tile = blockIdx.x + k * gridDim.x;
+                if (tile >= ntiles) break;
+                const int s = k % SP_STAGES;
+                const uint32_t ph = (uint32_t)(k / SP_STAGES) & 1u;
+                if (k >= SP_STAGES && !mbar_wait_bounded(&empty_bar[s], ph ^ 1u, SP_WAIT_BUDGET)) {
+                    timed_out = true;
+                    break;
+                }
+                if (*(volatile int *)&s_timeout) break;
+                const int r0 = tile * SP_ROWS, r1 = min(r0 + SP_ROWS, a.V);
+                const int b0 = a.rp[r0], b1 = a.rp[r1];
+                unsigned char *base = smem_raw + s * SP_STAGE_BYTES;
+                if (b1 - b0 <= SP_CAP) {
+                    const int64_t f0 = 9ll * b0, al0 = f0 & ~3ll, al1 = (9ll * b1 + 3) & ~3ll;
+                    const int c0 = b0 & ~3, c1 = (b1 + 3) & ~3;
+                    const uint32_t vbytes = (uint32_t)((al1 - al0) * 4), cbytes = (uint32_t)((c1 - c0) * 4);
+                    stage_info[s][0] = b0;
+                    stage_info[s][1] = (int)(f0 - al0);
+                    stage_info[s][2] = b0 - c0;
+                    stage_info[s][3] = 1;
+                    mbar_arrive_expect_tx(&full_bar[s], vbytes + cbytes);
+                    bulk_g2s(base, a.vals + al0, vbytes, &full_bar[s]);
+                    bulk_g2s(base + SP_VAL_BYTES, a.ci + c0, cbytes, &full_bar[s]);
+                } else {
+                    stage_info[s][0] = b0;
+                    stage_info[s][1] = 0;
+                    stage_info[s][2] = 0;
+                    stage_info[s][3] = 0;
+                    mbar_arrive(&full_bar[s]);
+                }
+                ++issued;
+            }
+            // drain: the copies of the last stages issued must have landed before exit
+            for (int k = issued - 1; k >= 0 && k >= issued - SP_STAGES; --k)
+                if (!mbar_wait_bounded(&full_bar[k % SP_STAGES], (uint32_t)(k / SP_STAGES) & 1u, SP_WAIT_BUDGET))
+                    timed_out = true;
+        }
+    } else {
+        // ---------------- consumers
+        const int t = threadIdx.x;  // 0 .. SP_ROWS * SP_TPR - 1
+        const int j = t & (SP_TPR - 1);
+        SpmvRow nxt;
+        if ((int)blockIdx.x < ntiles) spmv_load_row<DIFF, PCG>(a, blockIdx.x, t, nxt);
+        for (int k = 0;; ++k) {
+            const int tile = blockIdx.x + k * gridDim.x;
+            if (tile >= ntiles) break;
+            const SpmvRow cur = nxt;
+            if (tile + (int)gridDim.x < ntiles) spmv_load_row<DIFF, PCG>(a, tile + gridDim.x, t, nxt);
+            const int s = k % SP_STAGES;
+            const uint32_t ph = (uint32_t)(k / SP_STAGES) & 1u;
+            const bool ok = mbar_wait_bounded(&full_bar[s], ph, SP_WAIT_BUDGET);
+            if (!__all_sync(0xffffffffu, ok)) {  // the whole warp leaves together
+                timed_out = true;
+                break;
+            }
+            const int b0 = stage_info[s][0], vo = stage_info[s][1], co = stage_info[s][2];
+            const bool staged = stage_info[s][3] != 0;
+            const float *s_vals = reinterpret_cast<const float *>(smem_raw + s * SP_STAGE_BYTES) + vo;
+            const int32_t *s_cols = reinterpret_cast<const int32_t *>(smem_raw + s * SP_STAGE_BYTES + SP_VAL_BYTES) + co;
+            float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+            const float4 xj = cur.xj;
+            int b = cur.rb + j;
+            for (; b + SP_TPR < cur.re; b += 2 * SP_TPR) {
+                int cA, cB;
+                const float *BA, *BB;
+                if (staged) {
+                    cA = s_cols[b - b0];
+                    cB = s_cols[b + SP_TPR - b0];
+                    BA = s_vals + 9 * (b - b0);
+                    BB = s_vals + 9 * (b + SP_TPR - b0);
+                } else {
+                    cA = a.ci[b];
+                    cB = a.ci[b + SP_TPR];
+                    BA = a.vals + 9ll * b;
+                    BB = a.vals + 9ll * (b + SP_TPR);
+                }
+                float4 uA = spmv_gather<PCG>(a, cA), uB = spmv_gather<PCG>(a, cB);
+                if (DIFF) {
+                    uA.x -= xj.x; uA.y -= xj.y; uA.z -= xj.z;
+                    uB.x -= xj.x; uB.y -= xj.y; uB.z -= xj.z;
+                }
+                spmv_fma(BA, uA, acc0, acc1, acc2);
+                spmv_fma(BB, uB, acc0, acc1, acc2);
+            }
+            if (b < cur.re) {
+                const int c = staged ? s_cols[b - b0] : a.ci[b];
+                const float *B = staged ? s_vals + 9 * (b - b0) : a.vals + 9ll * b;
+                float4 u = spmv_gather<PCG>(a, c);
+                if (DIFF) { u.x -= xj.x; u.y -= xj.y; u.z -= xj.z; }
+                spmv_fma(B, u, acc0, acc1, acc2);
+            }
+            // the stage is no longer read by this warp: release it before the epilogue
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty_bar[s]);
+#pragma unroll
+            for (int o = 1; o < SP_TPR; o <<= 1) {
+                acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+                acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+                acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+            }
+            if (cur.row < a.V && j == 0) {
+                if (DIFF) spmv_fma(cur.D, xj, acc0, acc1, acc2);
+                a.y[3ll * cur.row] = acc0;
+                a.y[3ll * cur.row + 1] = acc1;
+                a.y[3ll * cur.row + 2] = acc2;
+                if (PCG) {
+                    dot_acc +=(double)xj.x * (double)acc0 + (double)xj.y * (double)acc1 + (double)xj.z * (double)acc2;
+                }
+            }
+        }
+    }
+    if (timed_out) {
+        s_timeout = 1;
+        atomicOr(a.err, PC_DERR_TIMEOUT);
+        if (PCG) {
+            a.sc->status = PC_ERR_TIMEOUT;
+            a.sc->done = 1;
+        }
+    }
+    if (PCG) {
+        double v[1] = {dot_acc};
+        if (last_block_reduce(v, 1, a.partials, &a.sc->counter) && threadIdx.x == 0) {
+            pc_scalars *s = a.sc;
+            double pq = v[0];
+            s->pq = pq;
+            double alpha = s->rz / pq;
+            if (s->status == PC_ERR_TIMEOUT) {
+                alpha = 0.0;
+            } else if (!(pq > 0.0) || !isfinite(alpha)) {
+                s->status = PC_ERR_NONFINITE;
+                s->done = 1;
+                alpha = 0.0;
+            }
+            s->alpha = alpha;
+        }
+    }
+}
