@@ -245,9 +245,11 @@ def run_ours(args):
         dist.barrier()
     value = world * args.steps / elapsed
 
-    # roofline of the dominant kernel: the fused PCG SpMV (difference form)
+    # roofline of the dominant kernel: the PCG SpMV q = A p in the difference form.
+    # Algorithmic bytes per launch: blocks and column indices (40 per block), row
+    # pointers (4 (V+1)), difference diagonal (36 V), p read once (float4, 16 V), q (12 V)
     V = wl.V
-    spmv_bytes = 40 * nnzb + 4 * (V + 1) + 36 * V + 4 * 12 * V
+    spmv_bytes = 40 * nnzb + 4 * (V + 1) + 36 * V + 16 * V + 12 * V
     avg_spmv_s = (spmv_ms / 1e3) / max(n_spmv, 1)
     achieved = spmv_bytes / avg_spmv_s / 1e9 if n_spmv else None
     peak, peak_src = measured_hbm()
@@ -300,7 +302,7 @@ def run_ours(args):
                        "pcg_iters_per_step": float(np.mean(iters)), "max_rel_res": float(np.max(rels))},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": None,
-                         "kernel": "spmv_kernel<DIFF,PCG> (fused SpMV + direction update + p.q)",
+                         "kernel": "spmv_kernel<true,true> (q = A p, difference form, with p.q)",
                          "bytes_per_launch": spmv_bytes, "peak_source": peak_src,
                          "avg_launch_us": avg_spmv_s * 1e6, "timed_launches": n_spmv},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
