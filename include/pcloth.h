@@ -213,6 +213,26 @@ PC_API pc_status pc_bsr_spmv(pc_ctx *ctx, const pc_bsr *A, const float *vals, co
 PC_API pc_status pc_pcg_solve(pc_ctx *ctx, const pc_bsr *A, const float *vals, const float *dres, const float *b,
                        float *dv, const pc_solve_opts *opts, pc_solve_info *info, void *stream);
 
+/* Allocation-free variant of pc_pcg_solve (the paper has no counterpart): the same
+ * solver, options and results, for callers that cannot allocate device memory and so
+ * cannot hold a context -- for example a plug-in inside a host application that owns
+ * and pre-reserves all GPU memory itself, or a real-time loop that must never call
+ * cudaMalloc because an allocation can synchronize the device and stall the frame.
+ * All scratch (PCG vectors, FP64 accumulator, reduction partials and scalars) lives in
+ * one static device array inside the library sized for PC_STATIC_MAX_ROWS rows (about
+ * 2.2 MB, held by every GPU that loads the library until the process exits); nothing is
+ * allocated. The caller passes the system (V rows, as for pc_pcg_solve) and the output.
+ * V > PC_STATIC_MAX_ROWS returns PC_ERR_CAPACITY before any device work.
+ * The first call on a device looks up the array's device address and sets the kernels'
+ * shared-memory limit for that device (make it before any stream capture). Every call
+ * on a device shares the array and clears its scalars on entry; calls that overlap on
+ * the GPU (concurrent streams, or several host threads on one device) race and must be
+ * serialized by the caller. Synchronizes `stream`. */
+#define PC_STATIC_MAX_ROWS 16384
+PC_API pc_status pc_pcg_solve_static(int32_t V, const pc_bsr *A, const float *vals, const float *dres,
+                                     const float *b, float *dv, const pc_solve_opts *opts, pc_solve_info *info,
+                                     void *stream);
+
 /* One time step on device state: pattern, values (with the difference-form diagonal),
  * PCG solve, then v += dv, x += h v. Uses buffers owned by the context. dv_out (device
  * float[V][3], may be NULL) receives dv. Synchronizes `stream`. */

@@ -20,6 +20,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "pc_internal.cuh"
 
 #define EW_THREADS 256
@@ -551,8 +553,19 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
     return PC_OK;
 }
 
+static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals, const float *dres,
+                                const float *b, float *dv, const pc_solve_opts *opts, pc_solve_info *info,
+                                void *stream);
+
 extern "C" pc_status pc_pcg_solve(pc_ctx *ctx, const pc_bsr *A, const float *vals, const float *dres, const float *b,
                                   float *dv, const pc_solve_opts *opts, pc_solve_info *info, void *stream)
+{
+    return pcg_solve_impl(ctx, A, vals, dres, b, dv, opts, info, stream);
+}
+
+static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals, const float *dres,
+                                const float *b, float *dv, const pc_solve_opts *opts, pc_solve_info *info,
+                                void *stream)
 {
     if (!ctx || !b || !dv) return PC_ERR_ARG;
     PC_TRY(check_bsr(A, vals));
@@ -680,4 +693,93 @@ pc_status pc_update_state(pc_ctx *c, float *x, float *v, const float *dv, float 
     const int64_t n = 3ll * c->V;
     PC_LAUNCH(c, state_update_kernel, ew_grid(c, n), EW_THREADS, 0, st, n, x, v, dv, h);
     return PC_OK;
+}
+
+// ------------------------------------------------------------------------- allocation-free solve
+//
+// pc_pcg_solve_static runs the same PCG kernels as pc_pcg_solve, but every scratch
+// vector, reduction partial and scalar it needs lives in the file-scope array below
+// instead of in a context, so the call allocates nothing. The array is sized for
+// PC_STATIC_MAX_ROWS rows; each GPU that loads the library holds it (about 2.2 MB) until
+// the process exits. All calls on a device share it.
+
+#define PC_STATIC_MAX_BLOCKS 2048  // reduction partials: enough for 8 blocks per SM up to 256 SMs
+
+struct pc_static_scratch {
+    float r[3 * PC_STATIC_MAX_ROWS];
+    float4 z[PC_STATIC_MAX_ROWS];
+    float4 p[PC_STATIC_MAX_ROWS];
+    float q[3 * PC_STATIC_MAX_ROWS];
+    float dinv[9 * PC_STATIC_MAX_ROWS];
+    float dtmp[3 * PC_STATIC_MAX_ROWS];
+    double x64[3 * PC_STATIC_MAX_ROWS];
+    double partials[RED_SLOTS * PC_STATIC_MAX_BLOCKS];
+    pc_scalars sc;
+    uint32_t err;
+};
+
+static __device__ __align__(256) pc_static_scratch g_pcg_scratch;
+
+// Device address of g_pcg_scratch for the current device, looked up once per device
+// (host code may not use the symbol itself as a device pointer). The same set-up also
+// raises the SpMV kernels' dynamic shared-memory limit, which pc_create does for
+// context-based calls.
+static pc_status static_scratch_address(pc_static_scratch **out, int *device)
+{
+    static std::mutex mu;
+    static void *addr[256] = {};
+    int dev = 0;
+    PC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return PC_ERR_ARG;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        PC_CUDA_TRY(cudaGetSymbolAddress(&p, g_pcg_scratch));
+        PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SP_SMEM_BYTES));
+        PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SP_SMEM_BYTES));
+        PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SP_SMEM_BYTES));
+        PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SP_SMEM_BYTES));
+        addr[dev] = p;
+    }
+    *out = static_cast<pc_static_scratch *>(addr[dev]);
+    *device = dev;
+    return PC_OK;
+}
+
+extern "C" pc_status pc_pcg_solve_static(int32_t V, const pc_bsr *A, const float *vals, const float *dres,
+                                         const float *b, float *dv, const pc_solve_opts *opts, pc_solve_info *info,
+                                         void *stream)
+{
+    if (V < 1 || V > PC_STATIC_MAX_ROWS) return PC_ERR_CAPACITY;
+    if (!A || !vals || !b || !dv) return PC_ERR_ARG;
+    pc_static_scratch *S = nullptr;
+    int dev = 0;
+    PC_TRY(static_scratch_address(&S, &dev));
+    pc_ctx tmp;  // a view of the static scratch; owns nothing
+    tmp.device = dev;
+    tmp.V = V;
+    PC_CUDA_TRY(cudaDeviceGetAttribute(&tmp.num_sms, cudaDevAttrMultiProcessorCount, dev));
+    if (8 * tmp.num_sms > PC_STATIC_MAX_BLOCKS) return PC_ERR_CAPACITY;
+    pc_scalars host_sc{};
+    uint32_t host_err = 0;
+    tmp.r = S->r;
+    tmp.z = reinterpret_cast<float *>(S->z);
+    tmp.p0 = reinterpret_cast<float *>(S->p);
+    tmp.q = S->q;
+    tmp.dinv = S->dinv;
+    tmp.dtmp = S->dtmp;
+    tmp.x64 = S->x64;
+    tmp.partials = S->partials;
+    tmp.max_red_blocks = PC_STATIC_MAX_BLOCKS;
+    tmp.sc = &S->sc;
+    tmp.d_err = &S->err;
+    tmp.sc_host = &host_sc;
+    tmp.h_err = &host_err;
+    // the previous call's scalars (and its reduction ticket) must not leak into this one
+    PC_CUDA_TRY(cudaMemsetAsync(&S->sc, 0, sizeof(pc_scalars), (cudaStream_t)stream));
+    return pcg_solve_impl(&tmp, A, vals, dres, b, dv, opts, info, stream);
 }

@@ -89,6 +89,8 @@ def _load():
     L.pc_bsr_spmv.argtypes = [c_void_p, P(pc_bsr), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     L.pc_pcg_solve.argtypes = [c_void_p, P(pc_bsr), c_void_p, c_void_p, c_void_p, c_void_p, P(pc_solve_opts),
                                P(pc_solve_info), c_void_p]
+    L.pc_pcg_solve_static.argtypes = [c_int32, P(pc_bsr), c_void_p, c_void_p, c_void_p, c_void_p,
+                                      P(pc_solve_opts), P(pc_solve_info), c_void_p]
     L.pc_step.argtypes = [c_void_p, c_void_p, c_void_p, P(pc_contacts), P(pc_step_opts), c_void_p, P(pc_step_info),
                           c_void_p]
     L.pc_step_host.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, P(pc_step_opts),
@@ -98,7 +100,7 @@ def _load():
     L.pc_set_profiling.argtypes = [c_void_p, c_int32]
     L.pc_spmv_stats.argtypes = [c_void_p, P(c_int64), P(c_double), P(c_int64)]
     for name in ("pc_create", "pc_destroy", "pc_get_sizes", "pc_get_rest", "pc_assemble_pattern",
-                 "pc_assemble_values", "pc_bsr_spmv", "pc_pcg_solve", "pc_step", "pc_step_host",
+                 "pc_assemble_values", "pc_bsr_spmv", "pc_pcg_solve", "pc_pcg_solve_static", "pc_step", "pc_step_host",
                  "pc_set_profiling", "pc_spmv_stats"):
         getattr(L, name).restype = c_int32
     return L
@@ -228,6 +230,19 @@ def pc_pcg_solve(ctx, row_ptr, col_idx, nnzb, vals, dres, b, dv, opts=None, stre
                            ctypes.byref(info), _stream(stream))
     if not (allow_not_converged and st == PC_ERR_NOT_CONVERGED):
         _check(st, "pc_pcg_solve")
+    return info, st
+
+
+def pc_pcg_solve_static(V, row_ptr, col_idx, nnzb, vals, dres, b, dv, opts=None, stream=None,
+                        allow_not_converged=False):
+    """pc_pcg_solve without a context: all scratch in the library's static device array."""
+    A = bsr_struct(row_ptr, col_idx, nnzb)
+    info = pc_solve_info()
+    o = opts if opts is not None else solve_opts()
+    st = _lib.pc_pcg_solve_static(int(V), ctypes.byref(A), _ptr(vals), _ptr(dres), _ptr(b), _ptr(dv),
+                                  ctypes.byref(o), ctypes.byref(info), _stream(stream))
+    if not (allow_not_converged and st == PC_ERR_NOT_CONVERGED):
+        _check(st, "pc_pcg_solve_static")
     return info, st
 
 
