@@ -181,6 +181,27 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# --------------------------------------------------------------------------- ranks
+
+
+def max_over_ranks(seconds: float, world: int) -> float:
+    """The slowest rank's time (every rank gets it); a barrier follows the reduction."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def aggregate_steps_per_s(world: int, steps: int, slowest_seconds: float) -> float:
+    """Whole-job throughput of independent replicas: all ranks' steps over the slowest time."""
+    return world * steps / slowest_seconds
+
+
 # --------------------------------------------------------------------------- our arm
 
 
@@ -238,12 +259,8 @@ def run_ours(args):
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = pc.pc_launch_count(cl.ctx) - launches0
     n_spmv, spmv_ms, nnzb = pc.pc_spmv_stats(cl.ctx)
-    if world > 1:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-        dist.barrier()
-    value = world * args.steps / elapsed
+    elapsed = max_over_ranks(elapsed, world)
+    value = aggregate_steps_per_s(world, args.steps, elapsed)
 
     # roofline of the dominant kernel: the PCG SpMV q = A p in the difference form.
     # Algorithmic bytes per launch: blocks and column indices (40 per block), row
@@ -276,13 +293,10 @@ def run_ours(args):
         for k in range(args.warmup, nsteps):
             pc.pc_step_host(cl_e.ctx, xh, vh, host_contacts[k][0], host_contacts[k][1], o, allow_not_converged=True)
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(time.perf_counter() - t0, world)
         P = wl.n_contacts
-        e2e = {"value": world * args.steps / te, "unit": "steps/s", "h2d_bytes_per_step": 24 * V + 28 * P,
+        e2e = {"value": aggregate_steps_per_s(world, args.steps, te), "unit": "steps/s",
+               "h2d_bytes_per_step": 24 * V + 28 * P,
                "d2h_bytes_per_step": 24 * V}
         cl_e.close()
 
