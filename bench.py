@@ -264,9 +264,10 @@ def run_ours(args):
 
     # roofline of the dominant kernel: the PCG SpMV q = A p in the difference form.
     # Algorithmic bytes per launch: blocks and column indices (40 per block), row
-    # pointers (4 (V+1)), difference diagonal (36 V), p read once (float4, 16 V), q (12 V)
+    # pointers (4 (V+1)), difference diagonal (36 V), p read once and q written (float4,
+    # 16 V each)
     V = wl.V
-    spmv_bytes = 40 * nnzb + 4 * (V + 1) + 36 * V + 16 * V + 12 * V
+    spmv_bytes = 40 * nnzb + 4 * (V + 1) + 36 * V + 16 * V + 16 * V
     avg_spmv_s = (spmv_ms / 1e3) / max(n_spmv, 1)
     achieved = spmv_bytes / avg_spmv_s / 1e9 if n_spmv else None
     peak, peak_src = measured_hbm()

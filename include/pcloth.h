@@ -220,7 +220,7 @@ PC_API pc_status pc_pcg_solve(pc_ctx *ctx, const pc_bsr *A, const float *vals, c
  * cudaMalloc because an allocation can synchronize the device and stall the frame.
  * All scratch (PCG vectors, FP64 accumulator, reduction partials and scalars) lives in
  * one static device array inside the library sized for PC_STATIC_MAX_ROWS rows (about
- * 2.2 MB, held by every GPU that loads the library until the process exits); nothing is
+ * 2.7 MB, held by every GPU that loads the library until the process exits); nothing is
  * allocated. The caller passes the system (V rows, as for pc_pcg_solve) and the output.
  * V > PC_STATIC_MAX_ROWS returns PC_ERR_CAPACITY before any device work.
  * The first call on a device looks up the array's device address and sets the kernels'

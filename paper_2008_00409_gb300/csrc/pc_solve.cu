@@ -7,10 +7,11 @@
 //   spmv:      q = A p, partial p.q                                  -> alpha = rz / pq
 //   update:    x += alpha p, r -= alpha q, z = D^-1 r, partial r.z, r.r -> beta, stop test
 // (the SpMV kernel, a bulk-copy pipelined stream over the blocks, is in pc_spmv.cuh).
-// Dot products accumulate in FP64; each kernel's last block to finish sums the
+// Dot products: FP32 within a thread, FP64 across threads; each kernel's last block sums the
 // per-block partials in a fixed order, so every reduction is deterministic. The
-// direction p and the preconditioned residual z are float4 per vertex (padded) so
-// that the SpMV gathers them with one 16-byte load each.
+// internal vectors (r, z, p, q, the FP32 increment, Jacobi) are float4 per vertex
+// (padded) so that every access is one coalesced 16-byte load and each SpMV gather is
+// a single load.
 //
 // Mixed precision (PC_PREC_MIXED): the solution is an FP64 accumulator plus the FP32
 // increment the iterations build; at refresh points the increment is folded into the
@@ -84,27 +85,26 @@ __device__ bool last_block_reduce(double *v, int n, double *partials, uint32_t *
 
 // ------------------------------------------------------------------------- preconditioner
 
-// z = D^-1 r for one row: scalar Jacobi (3 floats per row) or 3x3 block (9 floats).
+// z = D^-1 r for one row. Scalar Jacobi: one float4 (three inverses) per row; block
+// Jacobi: three float4 per row (the rows of the inverse 3x3 block).
 template <bool BLOCK>
-__device__ __forceinline__ void apply_precond(const float *__restrict__ dinv, int row, const float r[3], float z[3])
+__device__ __forceinline__ float4 apply_precond(const float4 *__restrict__ dinv4, int row, float4 r)
 {
     if (BLOCK) {
-        const float *D = dinv + 9ll * row;
-        z[0] = D[0] * r[0] + D[1] * r[1] + D[2] * r[2];
-        z[1] = D[3] * r[0] + D[4] * r[1] + D[5] * r[2];
-        z[2] = D[6] * r[0] + D[7] * r[1] + D[8] * r[2];
-    } else {
-        const float *D = dinv + 3ll * row;
-        z[0] = D[0] * r[0];
-        z[1] = D[1] * r[1];
-        z[2] = D[2] * r[2];
+        const float4 a = dinv4[3ll * row], b = dinv4[3ll * row + 1], c = dinv4[3ll * row + 2];
+        return make_float4(a.x * r.x + a.y * r.y + a.z * r.z, b.x * r.x + b.y * r.y + b.z * r.z,
+                           c.x * r.x + c.y * r.y + c.z * r.z, 0.f);
     }
+    const float4 d = dinv4[row];
+    return make_float4(d.x * r.x, d.y * r.y, d.z * r.z, 0.f);
 }
+
+__device__ __forceinline__ float dot3(float4 a, float4 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
 
 // Inverse of the diagonal (scalar entries, or the whole 3x3 block computed in FP64).
 template <bool BLOCK>
 __global__ void dinv_kernel(int V, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                            const float *__restrict__ vals, float *__restrict__ dinv, uint32_t *err)
+                            const float *__restrict__ vals, float4 *__restrict__ dinv4, uint32_t *err)
 {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= V) return;
@@ -115,54 +115,64 @@ __global__ void dinv_kernel(int V, const int32_t *__restrict__ rp, const int32_t
     for (int e = 0; e < 9; ++e) B[e] = s >= 0 ? (double)vals[9ll * s + e] : 0.0;
     bool ok = s >= 0 && B[0] > 0.0 && B[4] > 0.0 && B[8] > 0.0 && isfinite(B[0] + B[4] + B[8]);
     if (!BLOCK) {
-        for (int a = 0; a < 3; ++a) dinv[3ll * r + a] = ok ? (float)(1.0 / B[4 * a]) : 1.0f;
+        dinv4[r] = ok ? make_float4((float)(1.0 / B[0]), (float)(1.0 / B[4]), (float)(1.0 / B[8]), 0.f)
+                      : make_float4(1.f, 1.f, 1.f, 0.f);
     } else {
         double c00 = B[4] * B[8] - B[5] * B[7], c01 = B[2] * B[7] - B[1] * B[8], c02 = B[1] * B[5] - B[2] * B[4];
         double c10 = B[5] * B[6] - B[3] * B[8], c11 = B[0] * B[8] - B[2] * B[6], c12 = B[2] * B[3] - B[0] * B[5];
         double c20 = B[3] * B[7] - B[4] * B[6], c21 = B[1] * B[6] - B[0] * B[7], c22 = B[0] * B[4] - B[1] * B[3];
         double det = B[0] * c00 + B[1] * c10 + B[2] * c20;
         ok = ok && det > 0.0 && isfinite(det);
-        double inv[9] = {c00, c01, c02, c10, c11, c12, c20, c21, c22};
-        for (int e = 0; e < 9; ++e) dinv[9ll * r + e] = ok ? (float)(inv[e] / det) : (e % 4 == 0 ? 1.0f : 0.0f);
+        if (ok) {
+            dinv4[3ll * r] = make_float4((float)(c00 / det), (float)(c01 / det), (float)(c02 / det), 0.f);
+            dinv4[3ll * r + 1] = make_float4((float)(c10 / det), (float)(c11 / det), (float)(c12 / det), 0.f);
+            dinv4[3ll * r + 2] = make_float4((float)(c20 / det), (float)(c21 / det), (float)(c22 / det), 0.f);
+        } else {
+            dinv4[3ll * r] = make_float4(1.f, 0.f, 0.f, 0.f);
+            dinv4[3ll * r + 1] = make_float4(0.f, 1.f, 0.f, 0.f);
+            dinv4[3ll * r + 2] = make_float4(0.f, 0.f, 1.f, 0.f);
+        }
     }
     if (!ok) pc_set_err(err, PC_DERR_NONFINITE);
 }
 
 // ------------------------------------------------------------------------- vector kernels
+//
+// Internal PCG vectors are float4 per row (x, y, z, pad): one coalesced 16-byte access
+// per row and array. Each thread sums its rows' dot-product terms in FP32; the sums
+// across threads and blocks are FP64 (last_block_reduce).
 
 // Per row: x += alpha p; r -= alpha q; z = D^-1 r; partial (r.z, r.r); the last block
 // computes beta and applies the stop tests.
 template <bool BLOCK>
-__global__ void __launch_bounds__(EW_THREADS) pcg_update_kernel(int V, float *__restrict__ x,
+__global__ void __launch_bounds__(EW_THREADS) pcg_update_kernel(int V, float4 *__restrict__ x4,
                                                                  const float4 *__restrict__ p4,
-                                                                 float *__restrict__ r, const float *__restrict__ q,
-                                                                 const float *__restrict__ dinv,
+                                                                 float4 *__restrict__ r4,
+                                                                 const float4 *__restrict__ q4,
+                                                                 const float4 *__restrict__ dinv4,
                                                                  float4 *__restrict__ z4, double *partials,
                                                                  pc_scalars *sc)
 {
     if (sc->done) return;
     const float alpha = (float)sc->alpha;
-    double rz = 0.0, rr = 0.0;
+    float rz = 0.f, rr = 0.f;
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
-        const float4 pv = p4[row];
-        const float pp[3] = {pv.x, pv.y, pv.z};
-        float ri[3], zi[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int64_t i = 3ll * row + a;
-            x[i] = fmaf(alpha, pp[a], x[i]);
-            ri[a] = fmaf(-alpha, q[i], r[i]);
-            r[i] = ri[a];
-        }
-        apply_precond<BLOCK>(dinv, row, ri, zi);
-        z4[row] = make_float4(zi[0], zi[1], zi[2], 0.f);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            rz += (double)ri[a] * (double)zi[a];
-            rr += (double)ri[a] * (double)ri[a];
-        }
+        const float4 p = p4[row], q = q4[row];
+        float4 x = x4[row], r = r4[row];
+        x.x = fmaf(alpha, p.x, x.x);
+        x.y = fmaf(alpha, p.y, x.y);
+        x.z = fmaf(alpha, p.z, x.z);
+        r.x = fmaf(-alpha, q.x, r.x);
+        r.y = fmaf(-alpha, q.y, r.y);
+        r.z = fmaf(-alpha, q.z, r.z);
+        const float4 z = apply_precond<BLOCK>(dinv4, row, r);
+        x4[row] = x;
+        r4[row] = r;
+        z4[row] = z;
+        rz += dot3(r, z);
+        rr += dot3(r, r);
     }
-    double v[2] = {rz, rr};
+    double v[2] = {(double)rz, (double)rr};
     if (last_block_reduce(v, 2, partials, &sc->counter) && threadIdx.x == 0) {
         double rz_new = v[0];
         sc->beta = rz_new / sc->rz;
@@ -182,35 +192,29 @@ __global__ void __launch_bounds__(EW_THREADS) pcg_update_kernel(int V, float *__
     }
 }
 
-// Per row: r = b - q (q = A x0, or null for a zero guess), z = D^-1 r, pold = 0;
+// Per row: r = b - q (q = A x0 as float[V][3]), z = D^-1 r, p = 0, increment x = 0;
 // partial (r.z, r.r, b.b); the last block initialises the scalars.
 template <bool BLOCK>
 __global__ void __launch_bounds__(EW_THREADS) pcg_init_kernel(int V, const float *__restrict__ b,
-                                                               const float *__restrict__ q, float *__restrict__ r,
-                                                               const float *__restrict__ dinv,
-                                                               float4 *__restrict__ z4, float4 *__restrict__ pold4,
-                                                               double tol, int max_iter, double *partials,
-                                                               pc_scalars *sc)
+                                                               const float *__restrict__ q,
+                                                               float4 *__restrict__ r4,
+                                                               const float4 *__restrict__ dinv4,
+                                                               float4 *__restrict__ z4, float4 *__restrict__ p4,
+                                                               float4 *__restrict__ x4, double tol, int max_iter,
+                                                               double *partials, pc_scalars *sc)
 {
     double rz = 0.0, rr = 0.0, bb = 0.0;
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
-        float ri[3], zi[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int64_t i = 3ll * row + a;
-            float bi = b[i];
-            ri[a] = q ? bi - q[i] : bi;
-            r[i] = ri[a];
-            bb += (double)bi * (double)bi;
-        }
-        pold4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
-        apply_precond<BLOCK>(dinv, row, ri, zi);
-        z4[row] = make_float4(zi[0], zi[1], zi[2], 0.f);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            rz += (double)ri[a] * (double)zi[a];
-            rr += (double)ri[a] * (double)ri[a];
-        }
+        const float b0 = b[3ll * row], b1 = b[3ll * row + 1], b2 = b[3ll * row + 2];
+        const float4 r = make_float4(b0 - q[3ll * row], b1 - q[3ll * row + 1], b2 - q[3ll * row + 2], 0.f);
+        const float4 z = apply_precond<BLOCK>(dinv4, row, r);
+        r4[row] = r;
+        z4[row] = z;
+        p4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
+        x4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rz += (double)dot3(r, z);
+        rr += (double)dot3(r, r);
+        bb += (double)b0 * b0 + (double)b1 * b1 + (double)b2 * b2;
     }
     double v[3] = {rz, rr, bb};
     if (last_block_reduce(v, 3, partials, &sc->counter) && threadIdx.x == 0) {
@@ -293,32 +297,32 @@ __global__ void __launch_bounds__(EW_THREADS) residual_check_kernel(int V, const
 // Residual replacement: r64 = b - A x64 in FP64; r = (float) r64, z = D^-1 r; partial
 // (r.z, r64.r64, b.b). The last block installs r.z and the FP64 residual as the
 // iteration's scalars (keeping beta and the search direction), and either starts the
-// solve (`first`) or decides whether it has converged.
+// solve (`first`: p = 0) or decides whether it has converged.
 template <bool DIFF, bool BLOCK>
 __global__ void __launch_bounds__(EW_THREADS) residual_replace_kernel(
     int V, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const float *__restrict__ vals,
     const float *__restrict__ dres, const float *__restrict__ b, const double *__restrict__ x64,
-    const float *__restrict__ dinv, float *__restrict__ r, float4 *__restrict__ z4, float4 *__restrict__ pold4, int first,
-    double tol, int max_iter, double *partials, pc_scalars *sc)
+    const float4 *__restrict__ dinv4, float4 *__restrict__ r4, float4 *__restrict__ z4, float4 *__restrict__ p4,
+    int first, double tol, int max_iter, double *partials, pc_scalars *sc)
 {
     double rz = 0.0, rr = 0.0, bb = 0.0;
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
         double acc[3];
         row_product64<double, DIFF>(row, rp, ci, vals, dres, x64, acc);
-        float ri[3], zi[3];
+        float rf[3];
         for (int a2 = 0; a2 < 3; ++a2) {
-            const int64_t i = 3ll * row + a2;
-            double bv = (double)b[i];
+            double bv = (double)b[3ll * row + a2];
             double rv = bv - acc[a2];
             rr += rv * rv;
             bb += bv * bv;
-            ri[a2] = (float)rv;
-            r[i] = ri[a2];
+            rf[a2] = (float)rv;
         }
-        if (first) pold4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
-        apply_precond<BLOCK>(dinv, row, ri, zi);
-        z4[row] = make_float4(zi[0], zi[1], zi[2], 0.f);
-        for (int a2 = 0; a2 < 3; ++a2) rz += (double)ri[a2] * (double)zi[a2];
+        const float4 r = make_float4(rf[0], rf[1], rf[2], 0.f);
+        const float4 z = apply_precond<BLOCK>(dinv4, row, r);
+        r4[row] = r;
+        z4[row] = z;
+        if (first) p4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rz += (double)dot3(r, z);
     }
     double v[3] = {rz, rr, bb};
     if (last_block_reduce(v, 3, partials, &sc->counter) && threadIdx.x == 0) {
@@ -347,12 +351,25 @@ __global__ void __launch_bounds__(EW_THREADS) residual_replace_kernel(
     }
 }
 
-// x64 += x32; x32 = 0
-__global__ void fold_kernel(int64_t n, float *x32, double *x64)
+// x64 += increment; increment = 0 (per row, float4 increment)
+__global__ void fold_kernel(int V, float4 *x4, double *x64)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        x64[i] += (double)x32[i];
-        x32[i] = 0.0f;
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
+        const float4 d = x4[row];
+        x64[3ll * row] += (double)d.x;
+        x64[3ll * row + 1] += (double)d.y;
+        x64[3ll * row + 2] += (double)d.z;
+        x4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+// dv += increment (FP32 solve)
+__global__ void add_increment_kernel(int V, const float4 *x4, float *dv)
+{
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
+        const float4 d = x4[row];
+        dv[3ll * row] += d.x;
+        dv[3ll * row + 1] += d.y;
+        dv[3ll * row + 2] += d.z;
     }
 }
 __global__ void f64_to_f32_kernel(int64_t n, const double *a, float *o)
@@ -393,12 +410,12 @@ static int ew_grid(const pc_ctx *c, int64_t n)
 pc_status pc_solver_alloc(pc_ctx *c)
 {
     const int64_t n = 3ll * c->V;
-    PC_CUDA_TRY(cudaMalloc(&c->r, sizeof(float) * n));
+    PC_CUDA_TRY(cudaMalloc(&c->r, sizeof(float4) * c->V));
     PC_CUDA_TRY(cudaMalloc(&c->z, sizeof(float4) * c->V));
     PC_CUDA_TRY(cudaMalloc(&c->p0, sizeof(float4) * c->V));
-    PC_CUDA_TRY(cudaMalloc(&c->q, sizeof(float) * n));
-    PC_CUDA_TRY(cudaMalloc(&c->dinv, sizeof(float) * 3 * n));
-    PC_CUDA_TRY(cudaMalloc(&c->dtmp, sizeof(float) * n));
+    PC_CUDA_TRY(cudaMalloc(&c->q, sizeof(float4) * c->V));
+    PC_CUDA_TRY(cudaMalloc(&c->dinv, sizeof(float4) * 3 * c->V));
+    PC_CUDA_TRY(cudaMalloc(&c->dtmp, sizeof(float4) * c->V));
     PC_CUDA_TRY(cudaMalloc(&c->rhs32, sizeof(float) * n));
     PC_CUDA_TRY(cudaMalloc(&c->x64, sizeof(double) * n));
     PC_CUDA_TRY(cudaMalloc(&c->r64, sizeof(double) * n));
@@ -491,12 +508,10 @@ static pc_status read_scalars(pc_ctx *c, cudaStream_t st)
 static pc_status replace_residual(const SolveCtx &s, float *x32, int first, double tol, int max_iter)
 {
     pc_ctx *c = s.c;
-    const int64_t n = 3ll * c->V;
-    if (!first) PC_LAUNCH(c, fold_kernel, ew_grid(c, n), EW_THREADS, 0, s.st, n, x32, c->x64);
+    if (!first) PC_LAUNCH(c, fold_kernel, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (float4 *)x32, c->x64);
     DISPATCH2(c, residual_replace_kernel, s.diff, s.block, ew_grid(c, c->V), EW_THREADS, s.st, c->V, s.A->row_ptr,
-              s.A->col_idx, s.vals, s.dres, s.b, c->x64, c->dinv, c->r, (float4 *)c->z, (float4 *)c->p0, first, tol,
-              max_iter,
-              c->partials, c->sc);
+              s.A->col_idx, s.vals, s.dres, s.b, c->x64, (const float4 *)c->dinv, (float4 *)c->r, (float4 *)c->z,
+              (float4 *)c->p0, first, tol, max_iter, c->partials, c->sc);
     return PC_OK;
 }
 
@@ -524,7 +539,7 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
     a.vals = s.vals;
     a.dres = s.dres;
     a.x4 = (const float4 *)c->p0;
-    a.y = c->q;
+    a.y4 = (float4 *)c->q;
     a.partials = c->partials;
     a.sc = c->sc;
     a.err = c->d_err;
@@ -536,11 +551,13 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
         PC_TRY(launch_spmv(c, a, s.diff, true, s.st));
         if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[1], s.st));
         if (s.block)
-            PC_LAUNCH(c, pcg_update_kernel<true>, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, x,
-                      (const float4 *)c->p0, c->r, c->q, c->dinv, (float4 *)c->z, c->partials, c->sc);
+            PC_LAUNCH(c, pcg_update_kernel<true>, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (float4 *)x,
+                      (const float4 *)c->p0, (float4 *)c->r, (const float4 *)c->q, (const float4 *)c->dinv,
+                      (float4 *)c->z, c->partials, c->sc);
         else
-            PC_LAUNCH(c, pcg_update_kernel<false>, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, x,
-                      (const float4 *)c->p0, c->r, c->q, c->dinv, (float4 *)c->z, c->partials, c->sc);
+            PC_LAUNCH(c, pcg_update_kernel<false>, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (float4 *)x,
+                      (const float4 *)c->p0, (float4 *)c->r, (const float4 *)c->q, (const float4 *)c->dinv,
+                      (float4 *)c->z, c->partials, c->sc);
         if (timed) {
             float ms = 0.f;
             PC_CUDA_TRY(cudaEventSynchronize(c->ev[1]));
@@ -567,7 +584,7 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
                                 const float *b, float *dv, const pc_solve_opts *opts, pc_solve_info *info,
                                 void *stream)
 {
-    if (!ctx || !b || !dv) return PC_ERR_ARG;
+    if (!ctx || !b || !dv || !pc_aligned16(dv)) return PC_ERR_ARG;
     PC_TRY(check_bsr(A, vals));
     pc_solve_opts o;
     pc_default_solve_opts(&o);
@@ -583,21 +600,23 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
     SolveCtx s{ctx, A, vals, dres, b, dres != nullptr, o.precond == PC_PRECOND_BLOCK, st};
     PC_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), st));
     if (s.block)
-        PC_LAUNCH(ctx, dinv_kernel<true>, pc_blocks(V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals, ctx->dinv,
-                  ctx->d_err);
+        PC_LAUNCH(ctx, dinv_kernel<true>, pc_blocks(V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals,
+                  (float4 *)ctx->dinv, ctx->d_err);
     else
-        PC_LAUNCH(ctx, dinv_kernel<false>, pc_blocks(V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals, ctx->dinv,
-                  ctx->d_err);
+        PC_LAUNCH(ctx, dinv_kernel<false>, pc_blocks(V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals,
+                  (float4 *)ctx->dinv, ctx->d_err);
     uint32_t bits = 0;
     PC_TRY(pc_read_errors(ctx, st, &bits));
     if (bits) return PC_ERR_NONFINITE;
 
     const bool mixed = o.precision == PC_PREC_MIXED;
-    float *x = mixed ? ctx->dtmp : dv;  // mixed: FP32 increment since the last fold
+    // the iterations build an FP32 increment (float4 per row) on top of the initial dv:
+    // mixed folds it into the FP64 accumulator, FP32 adds it to dv at the end
+    float *x = ctx->dtmp;
     int replacements = 0;
     if (mixed) {
         PC_LAUNCH(ctx, f32_to_f64_kernel, ew_grid(ctx, n), EW_THREADS, 0, st, n, dv, ctx->x64);
-        PC_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(float) * n, st));
+        PC_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(float4) * V, st));
         PC_TRY(replace_residual(s, x, 1, o.tol, o.max_iter));
     } else {
         SpmvArgs a{};
@@ -607,15 +626,17 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
         a.vals = vals;
         a.dres = dres;
         a.xin = dv;
-        a.y = ctx->q;
+        a.y = ctx->rhs32;  // A dv as float[V][3]
         a.err = ctx->d_err;
         PC_TRY(launch_spmv(ctx, a, s.diff, false, st));
         if (s.block)
-            PC_LAUNCH(ctx, pcg_init_kernel<true>, ew_grid(ctx, V), EW_THREADS, 0, st, V, b, ctx->q, ctx->r, ctx->dinv,
-                      (float4 *)ctx->z, (float4 *)ctx->p0, o.tol, o.max_iter, ctx->partials, ctx->sc);
+            PC_LAUNCH(ctx, pcg_init_kernel<true>, ew_grid(ctx, V), EW_THREADS, 0, st, V, b, ctx->rhs32,
+                      (float4 *)ctx->r, (const float4 *)ctx->dinv, (float4 *)ctx->z, (float4 *)ctx->p0, (float4 *)x,
+                      o.tol, o.max_iter, ctx->partials, ctx->sc);
         else
-            PC_LAUNCH(ctx, pcg_init_kernel<false>, ew_grid(ctx, V), EW_THREADS, 0, st, V, b, ctx->q, ctx->r, ctx->dinv,
-                      (float4 *)ctx->z, (float4 *)ctx->p0, o.tol, o.max_iter, ctx->partials, ctx->sc);
+            PC_LAUNCH(ctx, pcg_init_kernel<false>, ew_grid(ctx, V), EW_THREADS, 0, st, V, b, ctx->rhs32,
+                      (float4 *)ctx->r, (const float4 *)ctx->dinv, (float4 *)ctx->z, (float4 *)ctx->p0, (float4 *)x,
+                      o.tol, o.max_iter, ctx->partials, ctx->sc);
     }
     PC_TRY(read_scalars(ctx, st));
     double rr_last = ctx->sc_host->rr;
@@ -660,7 +681,7 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
     double rr = fin.rr, bb = fin.bb;
     if (mixed) {
         if (fin.iter > iter_last) {  // stopped early (limit / breakdown): fold what there is
-            PC_LAUNCH(ctx, fold_kernel, ew_grid(ctx, n), EW_THREADS, 0, st, n, x, ctx->x64);
+            PC_LAUNCH(ctx, fold_kernel, ew_grid(ctx, V), EW_THREADS, 0, st, V, (float4 *)x, ctx->x64);
         }
         PC_LAUNCH(ctx, f64_to_f32_kernel, ew_grid(ctx, n), EW_THREADS, 0, st, n, ctx->x64, dv);
         if (fin.iter > iter_last) {
@@ -673,6 +694,7 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
             bb = ctx->sc_host->bb;
         }
     } else {
+        PC_LAUNCH(ctx, add_increment_kernel, ew_grid(ctx, V), EW_THREADS, 0, st, V, (const float4 *)x, dv);
         if (s.diff) PC_LAUNCH(ctx, residual_check_kernel<true>, ew_grid(ctx, V), EW_THREADS, 0, st, V, A->row_ptr,
                               A->col_idx, vals, dres, b, dv, ctx->partials, ctx->sc);
         else PC_LAUNCH(ctx, residual_check_kernel<false>, ew_grid(ctx, V), EW_THREADS, 0, st, V, A->row_ptr,
@@ -700,18 +722,19 @@ pc_status pc_update_state(pc_ctx *c, float *x, float *v, const float *dv, float 
 // pc_pcg_solve_static runs the same PCG kernels as pc_pcg_solve, but every scratch
 // vector, reduction partial and scalar it needs lives in the file-scope array below
 // instead of in a context, so the call allocates nothing. The array is sized for
-// PC_STATIC_MAX_ROWS rows; each GPU that loads the library holds it (about 2.2 MB) until
+// PC_STATIC_MAX_ROWS rows; each GPU that loads the library holds it (about 2.7 MB) until
 // the process exits. All calls on a device share it.
 
 #define PC_STATIC_MAX_BLOCKS 2048  // reduction partials: enough for 8 blocks per SM up to 256 SMs
 
 struct pc_static_scratch {
-    float r[3 * PC_STATIC_MAX_ROWS];
+    float4 r[PC_STATIC_MAX_ROWS];
     float4 z[PC_STATIC_MAX_ROWS];
     float4 p[PC_STATIC_MAX_ROWS];
-    float q[3 * PC_STATIC_MAX_ROWS];
-    float dinv[9 * PC_STATIC_MAX_ROWS];
-    float dtmp[3 * PC_STATIC_MAX_ROWS];
+    float4 q[PC_STATIC_MAX_ROWS];
+    float4 dinv[3 * PC_STATIC_MAX_ROWS];
+    float4 dtmp[PC_STATIC_MAX_ROWS];
+    float rhs32[3 * PC_STATIC_MAX_ROWS];
     double x64[3 * PC_STATIC_MAX_ROWS];
     double partials[RED_SLOTS * PC_STATIC_MAX_BLOCKS];
     pc_scalars sc;
@@ -766,12 +789,13 @@ extern "C" pc_status pc_pcg_solve_static(int32_t V, const pc_bsr *A, const float
     if (8 * tmp.num_sms > PC_STATIC_MAX_BLOCKS) return PC_ERR_CAPACITY;
     pc_scalars host_sc{};
     uint32_t host_err = 0;
-    tmp.r = S->r;
+    tmp.r = reinterpret_cast<float *>(S->r);
     tmp.z = reinterpret_cast<float *>(S->z);
     tmp.p0 = reinterpret_cast<float *>(S->p);
-    tmp.q = S->q;
-    tmp.dinv = S->dinv;
-    tmp.dtmp = S->dtmp;
+    tmp.q = reinterpret_cast<float *>(S->q);
+    tmp.dinv = reinterpret_cast<float *>(S->dinv);
+    tmp.dtmp = reinterpret_cast<float *>(S->dtmp);
+    tmp.rhs32 = S->rhs32;
     tmp.x64 = S->x64;
     tmp.partials = S->partials;
     tmp.max_red_blocks = PC_STATIC_MAX_BLOCKS;

@@ -48,7 +48,8 @@ struct SpmvArgs {
     const float *dres;    // difference-form diagonal, or null
     const float *xin;     // plain mode: x as float[V][3]
     const float4 *x4;     // PCG mode: the search direction p as float4[V]
-    float *y;             // result, float[V][3]
+    float *y;             // plain mode: result, float[V][3]
+    float4 *y4;           // PCG mode: q = A p as float4[V]
     double *partials;     // PCG mode: p.q partials
     pc_scalars *sc;       // PCG mode: scalars
     uint32_t *err;        // error bits (timeouts)
@@ -114,7 +115,8 @@ __global__ void __launch_bounds__(SP_THREADS, SP_CTAS_PER_SM) spmv_kernel(SpmvAr
     }
     __syncthreads();
     const int ntiles = (a.V + SP_ROWS - 1) / SP_ROWS;
-    double dot_acc = 0.0;
+    // p.q of this thread's rows: FP32 with Kahan compensation (FP64 across threads)
+    float dot_acc = 0.f, dot_c = 0.f;
     bool timed_out = false;
 
     if (warp == SP_CWARPS) {
@@ -224,11 +226,19 @@ __global__ void __launch_bounds__(SP_THREADS, SP_CTAS_PER_SM) spmv_kernel(SpmvAr
             }
             if (cur.row < a.V && j == 0) {
                 if (DIFF) spmv_fma(cur.D, xj, acc0, acc1, acc2);
-                a.y[3ll * cur.row] = acc0;
-                a.y[3ll * cur.row + 1] = acc1;
-                a.y[3ll * cur.row + 2] = acc2;
                 if (PCG) {
-                    dot_acc +=(double)xj.x * (double)acc0 + (double)xj.y * (double)acc1 + (double)xj.z * (double)acc2;
+                    a.y4[cur.row] = make_float4(acc0, acc1, acc2, 0.f);
+                } else {
+                    a.y[3ll * cur.row] = acc0;
+                    a.y[3ll * cur.row + 1] = acc1;
+                    a.y[3ll * cur.row + 2] = acc2;
+                }
+                if (PCG) {
+                    const float term = fmaf(xj.x, acc0, fmaf(xj.y, acc1, xj.z * acc2));
+                    const float yk = term - dot_c;
+                    const float tk = dot_acc + yk;
+                    dot_c = (tk - dot_acc) - yk;
+                    dot_acc = tk;
                 }
             }
         }
@@ -242,7 +252,7 @@ __global__ void __launch_bounds__(SP_THREADS, SP_CTAS_PER_SM) spmv_kernel(SpmvAr
         }
     }
     if (PCG) {
-        double v[1] = {dot_acc};
+        double v[1] = {(double)dot_acc - (double)dot_c};
         if (last_block_reduce(v, 1, a.partials, &a.sc->counter) && threadIdx.x == 0) {
             pc_scalars *s = a.sc;
             double pq = v[0];
