@@ -213,6 +213,35 @@ PC_API pc_status pc_bsr_spmv(pc_ctx *ctx, const pc_bsr *A, const float *vals, co
 PC_API pc_status pc_pcg_solve(pc_ctx *ctx, const pc_bsr *A, const float *vals, const float *dres, const float *b,
                        float *dv, const pc_solve_opts *opts, pc_solve_info *info, void *stream);
 
+/* Batched solve of many independent systems (garments) in ONE persistent PCG launch.
+ * The context holds the union of the garments' meshes; instance k owns the contiguous
+ * rows inst_rows[k] .. inst_rows[k+1]-1 (host array of n_inst + 1 entries, first 0, last
+ * V, every instance at least 32 rows, n_inst <= 4096) and no matrix block may couple two
+ * instances (checked: PC_ERR_ARG). Each instance runs Jacobi-PCG with its own scalars
+ * and stop test |b_k - A_k dv_k| / |b_k| <= tol, with FP64 residual replacement as in
+ * PC_PREC_MIXED (refresh, refresh_every); finished instances drop out while the others
+ * continue. The launch is cooperative (all CTAs co-resident) with bounded grid-wide
+ * waits (PC_ERR_TIMEOUT instead of a hang). On the first call for a matrix shape an
+ * autotuner times short solves for 1..4 CTAs per SM and keeps the fastest
+ * (pc_batched_config reports the choice). info: host array of n_inst results, may be
+ * NULL. Returns the first non-OK instance status. Synchronizes `stream`.
+ * (The paper solves one garment system per step; batching is this library's extension.) */
+PC_API pc_status pc_pcg_solve_batched(pc_ctx *ctx, const pc_bsr *A, const float *vals, const float *dres,
+                                      const float *b, float *dv, int32_t n_inst, const int32_t *inst_rows,
+                                      const pc_solve_opts *opts, pc_solve_info *info, void *stream);
+
+/* Launch shape chosen by the batched autotuner (0 if none yet) and the timings (ms) of
+ * the candidates 1..4 CTAs per SM (0 where not tried). Host pointers, may be NULL. */
+PC_API pc_status pc_batched_config(pc_ctx *ctx, int32_t *blocks_per_sm, float *tune_ms);
+
+/* One batched time step: the dynamic pattern of the whole union (synchronous), then a
+ * CUDA graph holding value assembly, the persistent batched solve and v += dv,
+ * x += h v, replayed (updated in place) from step to step. Instances as for
+ * pc_pcg_solve_batched; info receives one result per instance. */
+PC_API pc_status pc_step_batched(pc_ctx *ctx, float *x, float *v, const pc_contacts *contacts, int32_t n_inst,
+                                 const int32_t *inst_rows, const pc_step_opts *opts, pc_solve_info *info,
+                                 void *stream);
+
 /* Allocation-free variant of pc_pcg_solve (the paper has no counterpart): the same
  * solver, options and results, for callers that cannot allocate device memory and so
  * cannot hold a context -- for example a plug-in inside a host application that owns

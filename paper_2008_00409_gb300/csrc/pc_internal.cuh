@@ -151,6 +151,9 @@ struct pc_ctx {
     int32_t *scan_tmp = nullptr;   // block sums for scans
     int64_t scan_tmp_cap = 0;
 
+    // batched solver state (pc_batched.cu)
+    void *batched = nullptr;
+
     // profiling
     int profiling = 0;
     int64_t launches = 0;
@@ -191,6 +194,8 @@ pc_status pc_read_errors(pc_ctx *ctx, cudaStream_t st, uint32_t *bits);
 pc_status pc_setup_rest(pc_ctx *ctx, cudaStream_t st);
 pc_status pc_update_state(pc_ctx *ctx, float *x, float *v, const float *dv, float h, cudaStream_t st);
 pc_status pc_solver_alloc(pc_ctx *ctx);
+pc_status pc_batched_alloc(pc_ctx *ctx);
+void pc_batched_free(pc_ctx *ctx);
 
 inline int pc_bits_for(int64_t n)
 {

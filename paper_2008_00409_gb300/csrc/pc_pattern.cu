@@ -263,6 +263,7 @@ __global__ void rowptr_from_keys_kernel(int V, const uint64_t *ukeys, int64_t n,
 static void free_ctx(pc_ctx *c)
 {
     if (!c) return;
+    pc_batched_free(c);
     void *ptrs[] = {c->tri, c->rest, c->tri_dmi, c->tri_area, c->tri_rgram, c->mass, c->pinned, c->hinge, c->hcoef,
                     c->hrest, c->srp, c->scol, c->vinc_ptr, c->vinc, c->dkeys, c->dnew, c->dflag, c->dscan, c->ckeys,
                     c->cinc, c->cinc_ptr, c->tri_buf, c->hinge_buf, c->cont_buf, c->r, c->z, c->p0, c->p1, c->q,
@@ -441,6 +442,7 @@ static pc_status create_impl(pc_ctx *c, const int32_t *tris, const float *rest, 
     PC_TRY(dalloc(&c->A_dv, 3ll * V));
     PC_CUDA_TRY(cudaMemsetAsync(c->A_dv, 0, sizeof(float) * 3 * (size_t)V, st));
     PC_TRY(pc_solver_alloc(c));
+    PC_TRY(pc_batched_alloc(c));
     PC_CUDA_TRY(cudaStreamSynchronize(st));
     return PC_OK;
 }

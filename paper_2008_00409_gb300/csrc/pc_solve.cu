@@ -57,7 +57,7 @@ __device__ __forceinline__ void block_sum_d(double *v, int n)
 
 // Write this block's partial sums; returns true (in all threads) in the block that
 // arrives last, with the grand totals in v[] of thread 0 (summed in block order).
-__device__ bool last_block_reduce(double *v, int n, double *partials, uint32_t *counter)
+static __device__ bool last_block_reduce(double *v, int n, double *partials, uint32_t *counter)
 {
     __shared__ bool s_last;
     block_sum_d(v, n);

@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(SP_THREADS, SP_CTAS_PER_SM) spmv_kernel(SpmvAr
                 if (!mbar_wait_bounded(&full_bar[k % SP_STAGES], (uint32_t)(k / SP_STAGES) & 1u, SP_WAIT_BUDGET))
                     timed_out = true;
         }
+        __syncwarp();  // the producer warp reconverges before any block-wide barrier
     } else {
         // ---------------- consumers
         const int t = threadIdx.x;  // 0 .. SP_ROWS * SP_TPR - 1

@@ -93,6 +93,11 @@ def _load():
                                       P(pc_solve_opts), P(pc_solve_info), c_void_p]
     L.pc_step.argtypes = [c_void_p, c_void_p, c_void_p, P(pc_contacts), P(pc_step_opts), c_void_p, P(pc_step_info),
                           c_void_p]
+    L.pc_pcg_solve_batched.argtypes = [c_void_p, P(pc_bsr), c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                                       c_void_p, P(pc_solve_opts), c_void_p, c_void_p]
+    L.pc_step_batched.argtypes = [c_void_p, c_void_p, c_void_p, P(pc_contacts), c_int32, c_void_p, P(pc_step_opts),
+                                  c_void_p, c_void_p]
+    L.pc_batched_config.argtypes = [c_void_p, P(c_int32), c_void_p]
     L.pc_step_host.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, P(pc_step_opts),
                                P(pc_step_info), c_void_p]
     L.pc_launch_count.restype = c_int64
@@ -101,6 +106,7 @@ def _load():
     L.pc_spmv_stats.argtypes = [c_void_p, P(c_int64), P(c_double), P(c_int64)]
     for name in ("pc_create", "pc_destroy", "pc_get_sizes", "pc_get_rest", "pc_assemble_pattern",
                  "pc_assemble_values", "pc_bsr_spmv", "pc_pcg_solve", "pc_pcg_solve_static", "pc_step", "pc_step_host",
+                 "pc_pcg_solve_batched", "pc_step_batched", "pc_batched_config",
                  "pc_set_profiling", "pc_spmv_stats"):
         getattr(L, name).restype = c_int32
     return L
@@ -244,6 +250,45 @@ def pc_pcg_solve_static(V, row_ptr, col_idx, nnzb, vals, dres, b, dv, opts=None,
     if not (allow_not_converged and st == PC_ERR_NOT_CONVERGED):
         _check(st, "pc_pcg_solve_static")
     return info, st
+
+
+def _inst_array(inst_rows):
+    arr = np.ascontiguousarray(np.asarray(inst_rows, dtype=np.int32))
+    return arr, arr.ctypes.data_as(c_void_p)
+
+
+def pc_pcg_solve_batched(ctx, row_ptr, col_idx, nnzb, vals, dres, b, dv, inst_rows, opts=None, stream=None,
+                         allow_not_converged=False):
+    """Batched solve; returns (list of per-instance pc_solve_info, status)."""
+    A = bsr_struct(row_ptr, col_idx, nnzb)
+    arr, ptr = _inst_array(inst_rows)
+    n = len(arr) - 1
+    infos = (pc_solve_info * n)()
+    o = opts if opts is not None else solve_opts()
+    st = _lib.pc_pcg_solve_batched(ctx, ctypes.byref(A), _ptr(vals), _ptr(dres), _ptr(b), _ptr(dv), n, ptr,
+                                   ctypes.byref(o), ctypes.cast(infos, c_void_p), _stream(stream))
+    if not (allow_not_converged and st == PC_ERR_NOT_CONVERGED):
+        _check(st, "pc_pcg_solve_batched")
+    return list(infos), st
+
+
+def pc_step_batched(ctx, x, v, pairs, w, inst_rows, opts: pc_step_opts, stream=None, allow_not_converged=False):
+    arr, ptr = _inst_array(inst_rows)
+    n = len(arr) - 1
+    infos = (pc_solve_info * n)()
+    c = contacts_struct(pairs, w)
+    st = _lib.pc_step_batched(ctx, _ptr(x), _ptr(v), ctypes.byref(c), n, ptr, ctypes.byref(opts),
+                              ctypes.cast(infos, c_void_p), _stream(stream))
+    if not (allow_not_converged and st == PC_ERR_NOT_CONVERGED):
+        _check(st, "pc_step_batched")
+    return list(infos), st
+
+
+def pc_batched_config(ctx):
+    bps = c_int32()
+    ms = (c_float * 4)()
+    _check(_lib.pc_batched_config(ctx, ctypes.byref(bps), ctypes.cast(ms, c_void_p)), "pc_batched_config")
+    return bps.value, list(ms)
 
 
 def pc_step(ctx, x, v, pairs, w, opts: pc_step_opts, dv_out=None, stream=None, allow_not_converged=False):

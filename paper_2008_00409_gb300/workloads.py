@@ -119,10 +119,12 @@ class Workload:
     material: Material
     sheets: list
     seed: int
-    contact_kind: str = "none"    # none | grid | interlayer
+    contact_kind: str = "none"    # none | grid | interlayer | batch
     contact_frac: float = 0.0
     contact_radius: int = 8
     steps: int = 1
+    parts: list = None            # batch: the garments, in row order
+    inst_rows: np.ndarray = None  # batch: first row of each garment, then V
 
     @property
     def V(self) -> int:
@@ -134,6 +136,8 @@ class Workload:
 
     @property
     def n_contacts(self) -> int:
+        if self.contact_kind == "batch":
+            return int(sum(p.n_contacts for p in self.parts))
         return int(round(self.contact_frac * self.V)) if self.contact_kind != "none" else 0
 
     def contacts(self, step: int):
@@ -144,6 +148,13 @@ class Workload:
             return grid_contacts(self, step)
         if self.contact_kind == "interlayer":
             return interlayer_contacts(self, step)
+        if self.contact_kind == "batch":
+            ps, ws = [], []
+            for part, vb in zip(self.parts, self.inst_rows[:-1]):
+                p, w = part.contacts(step)
+                ps.append(p + np.int32(vb))
+                ws.append(w)
+            return np.concatenate(ps).astype(np.int32), np.concatenate(ws).astype(np.float32)
         raise ValueError(self.contact_kind)
 
 
@@ -270,6 +281,32 @@ def garment_batch(count: int = 64, *, seed: int, tmin: float = 2e3, tmax: float 
     tcount = np.exp(np.log(tmin) + u * (np.log(tmax) - np.log(tmin)))
     sides = np.round(np.sqrt(tcount / 2.0)).astype(int) + 1
     return [garment(int(s), seed=seed, stream=1000 + 16 * k) for k, s in enumerate(sides)]
+
+
+def batch_union(parts, name: str = "batch") -> Workload:
+    """Disjoint union of workloads, stacked in row order (one block-diagonal system).
+
+    Vertex indices of part k are shifted by inst_rows[k]; contacts are each part's own,
+    shifted the same way, so no element couples two parts.
+    """
+    offs = np.cumsum([0] + [p.V for p in parts])
+    toffs = np.cumsum([0] + [p.T for p in parts])
+    rest = np.concatenate([p.rest for p in parts])
+    tris = np.concatenate([p.tris + np.int32(o) for p, o in zip(parts, offs[:-1])]).astype(np.int32)
+    pins = np.concatenate([p.pins + np.int32(o) for p, o in zip(parts, offs[:-1])]).astype(np.int32)
+    sheets = []
+    for p, vo, to in zip(parts, offs[:-1], toffs[:-1]):
+        for s in p.sheets:
+            sheets.append(Sheet(s.nx, s.ny, s.vbase + int(vo), s.tbase + int(to), s.flip))
+    return Workload(name, rest, tris, pins, np.concatenate([p.x0 for p in parts]),
+                    np.concatenate([p.v0 for p in parts]), parts[0].h, parts[0].material, sheets, parts[0].seed,
+                    contact_kind="batch", steps=parts[0].steps, parts=list(parts),
+                    inst_rows=offs.astype(np.int32))
+
+
+def garment_batch_union(count: int = 64, *, seed: int = 20080409 + 4, tmin: float = 2e3, tmax: float = 2e5):
+    """The batched workload: `count` log-uniform garments as one union (block diagonal)."""
+    return batch_union(garment_batch(count, seed=seed, tmin=tmin, tmax=tmax), name=f"batch{count}")
 
 
 # --------------------------------------------------------------------------- contacts

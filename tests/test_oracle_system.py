@@ -227,3 +227,17 @@ def test_invalid_mesh_and_pairs_rejected():
     M = oracle.Mesh(rest, tris, MAT)
     with pytest.raises(oracle.OracleError):
         M.pattern(np.array([[0, 0, 1, 2]]))
+
+
+def test_batch_union_keeps_garments_disjoint():
+    parts = [wk.garment(s, seed=5, stream=10 * k, contact_frac=0.05) for k, s in enumerate([6, 9, 7])]
+    u = wk.batch_union(parts)
+    assert u.V == sum(p.V for p in parts) and u.T == sum(p.T for p in parts)
+    assert list(u.inst_rows) == [0, 36, 117, 166]
+    inst = np.searchsorted(u.inst_rows, u.tris, side="right") - 1
+    assert (inst == inst[:, :1]).all()
+    pairs, w = u.contacts(0)
+    pi = np.searchsorted(u.inst_rows, pairs, side="right") - 1
+    assert (pi == pi[:, :1]).all() and len(pairs) == u.n_contacts
+    M = oracle.Mesh.from_workload(u)
+    assert M.H == sum(oracle.Mesh.from_workload(p).H for p in parts)
