@@ -3,19 +3,20 @@
 // PCG launch (cooperative, all CTAs co-resident), and a batched time step that captures
 // value assembly, the solve and the state update in a CUDA graph.
 //
-// Instances own contiguous row ranges [inst_rows[k], inst_rows[k+1]) of at least 32 rows,
-// so a 32-row tile touches at most two instances. Every reduction is segmented by
-// instance through per-tile partial slots (first-row instance, last-row instance) that
-// one CTA per instance sums in tile order, so results are deterministic. Phases are
-// separated by a software grid barrier whose waits are bounded; a timeout aborts the
-// launch with PC_ERR_TIMEOUT instead of hanging. Per iteration:
-//   direction  p = z + beta_k p                   (rows of active instances)
-//   spmv       q = A p, tile partials of p.q      (the bulk-copy pipelined SpMV)
-//   alpha      alpha_k = rz_k / pq_k              (one CTA per instance)
-//   update     x += alpha p, r -= alpha q, z = D^-1 r, tile partials of r.z, r.r
-//   beta       beta_k, stop tests, refresh requests
-// and, when some instance asks for it, FP64 residual replacement (fold the FP32
-// increment into the FP64 accumulator, r = b - A x64 in FP64, new scalars).
+// Instances own contiguous row ranges [inst_rows[k], inst_rows[k+1]) of at least 32 rows.
+// Every phase walks a work list of the instances still iterating (rebuilt by each CTA in
+// shared memory when an instance finishes), one entry per (instance, 32-row tile), split
+// into equal contiguous chunks, one per CTA; finished instances cost nothing. A CTA meets
+// each instance in one run of its chunk and delivers one partial sum per instance; the
+// CTA that delivers last sums the instance's slots in CTA order (deterministic) and sets
+// the instance's scalars, so no separate scalar phase is needed. Phases are separated by
+// a software grid barrier whose waits are bounded; a timeout aborts the launch with
+// PC_ERR_TIMEOUT instead of hanging. Per iteration (three grid barriers):
+//   direction  p = z + beta_k p                   (fold x into x64 after a refresh)
+//   spmv       q = A p, p.q -> alpha_k            (the bulk-copy pipelined SpMV)
+//   update     x += alpha p, r -= alpha q, z = D^-1 r, r.z, r.r -> beta_k, stop tests
+// and, when some instance asks for it, FP64 residual replacement for those instances
+// (r = b - A (x64 + x) in FP64, new scalars).
 #include <math.h>
 #include <string.h>
 
@@ -78,38 +79,142 @@ static __device__ bool last_block_reduce(double *v, int n, double *partials, uin
 
 // ------------------------------------------------------------------------- device state
 
+#define BT_MAX_INST 1024
+
 struct bt_inst {
     double rz, rr, bb, tol2, alpha, beta, pq, rr_last;
     int32_t iter, iter_last, done, status;
-    int32_t refresh, pad0, pad1, pad2;
+    int32_t refresh;  // FP64 residual requested (set by the update phase, cleared by the next SpMV phase)
+    int32_t arrive;   // CTAs that delivered their partial sums in the current phase
+    int32_t pad0, pad1;
 };
 
 struct bt_global {
-    uint32_t bar_count;   // grid barrier arrivals
-    uint32_t bar_gen;     // grid barrier generation
-    uint32_t abort;       // set on timeout
-    uint32_t n_active[2]; // instances still iterating (slot by iteration parity)
-    uint32_t n_refresh[2];
-    uint32_t pad;
+    uint32_t bar_count;     // grid barrier arrivals
+    uint32_t bar_gen;       // grid barrier generation
+    uint32_t abort;         // set on timeout
+    uint32_t gen;           // bumped whenever an instance finishes
+    uint32_t n_refresh[2];  // refresh requests, by iteration parity
+    uint32_t pad[2];
 };
 
 struct BtArgs {
-    int V, n_inst, ntiles;
+    int V, n_inst;
     const int32_t *rp, *ci;
     const float *vals, *dres, *b;
     const int32_t *inst_rows;  // [n_inst + 1]
-    const int32_t *row_inst;   // [V]
     float4 *r4, *z4, *p4, *q4, *x4;
     const float4 *dinv4;
     double *x64;
     float *dv;
-    double *tp_a, *tp_b;       // tile partials [ntiles][3] for the first-row / last-row instance
+    double *part;              // [(ntiles + n_inst) * 3] partial sums, one slot per (CTA, instance)
     bt_inst *inst;
     bt_global *g;
     uint32_t *err;
     double tol, refresh;
     int max_iter, refresh_every;
 };
+
+// The work list of one phase: the listed instances in order, each contributing one entry
+// per 32-row tile it touches (a tile shared by two instances gives one entry to each, and
+// an entry covers only its own instance's rows). Entries are split into equal contiguous
+// chunks, one per CTA, so a CTA meets each instance in one run of entries and delivers
+// one partial sum per instance it touches.
+struct bt_list {
+    int n;      // listed instances
+    int total;  // entries
+    int chunk;  // entries per CTA
+    int pref[BT_MAX_INST + 1];
+    short id[BT_MAX_INST];
+};
+
+enum { BT_LIST_ACTIVE = 0, BT_LIST_REFRESH = 1, BT_LIST_ALL = 2 };
+
+__device__ __forceinline__ int bt_tiles_of(int r0, int r1) { return (r1 - 1) / BT_TILE - r0 / BT_TILE + 1; }
+
+// Built by every CTA from the instance flags (all threads call; ends with a barrier).
+__device__ void bt_build_list(const BtArgs &a, int mode, bt_list &L)
+{
+    __shared__ int s_w[2][8];
+    const int n = a.n_inst, T = blockDim.x;
+    const int per = (n + T - 1) / T;
+    const int k0 = min(n, (int)threadIdx.x * per), k1 = min(n, k0 + per);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
+    int cnt = 0, ent = 0;
+    for (int k = k0; k < k1; ++k) {
+        const bt_inst &I = a.inst[k];
+        const bool on = mode == BT_LIST_ALL ? true
+                      : mode == BT_LIST_ACTIVE ? __ldcg(&I.done) == 0
+                                               : (__ldcg(&I.refresh) != 0 && __ldcg(&I.done) == 0);
+        if (on) {
+            ++cnt;
+            ent += bt_tiles_of(a.inst_rows[k], a.inst_rows[k + 1]);
+        }
+    }
+    // block-wide exclusive scan of (cnt, ent)
+    int ic = cnt, ie = ent;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int uc = __shfl_up_sync(0xffffffffu, ic, o), ue = __shfl_up_sync(0xffffffffu, ie, o);
+        if (lane >= o) { ic += uc; ie += ue; }
+    }
+    if (lane == 31) { s_w[0][warp] = ic; s_w[1][warp] = ie; }
+    __syncthreads();
+    int bc = 0, be = 0, tc = 0, te = 0;
+    for (int w = 0; w < nw; ++w) {
+        if (w < warp) { bc += s_w[0][w]; be += s_w[1][w]; }
+        tc += s_w[0][w];
+        te += s_w[1][w];
+    }
+    int pos = bc + ic - cnt, e = be + ie - ent;
+    for (int k = k0; k < k1; ++k) {
+        const bt_inst &I = a.inst[k];
+        const bool on = mode == BT_LIST_ALL ? true
+                      : mode == BT_LIST_ACTIVE ? __ldcg(&I.done) == 0
+                                               : (__ldcg(&I.refresh) != 0 && __ldcg(&I.done) == 0);
+        if (on) {
+            L.id[pos] = (short)k;
+            L.pref[pos] = e;
+            ++pos;
+            e += bt_tiles_of(a.inst_rows[k], a.inst_rows[k + 1]);
+        }
+    }
+    if (threadIdx.x == 0) {
+        L.n = tc;
+        L.total = te;
+        L.pref[tc] = te;
+        L.chunk = (te + gridDim.x - 1) / gridDim.x;
+    }
+    __syncthreads();
+}
+
+// list position holding entry j (largest m with pref[m] <= j)
+__device__ __forceinline__ int bt_find(const bt_list &L, int j)
+{
+    int lo = 0, hi = L.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.pref[mid] <= j) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One run of entries of this CTA's chunk: list position m, entries [j, je), rows [ra, rb).
+struct bt_seg {
+    int m, k, j, je, ra, rb;
+};
+
+__device__ __forceinline__ void bt_seg_at(const BtArgs &a, const bt_list &L, int m, int j, int jend, bt_seg &s)
+{
+    s.m = m;
+    s.k = L.id[m];
+    s.j = j;
+    s.je = min(jend, L.pref[m + 1]);
+    const int r0 = a.inst_rows[s.k], r1 = a.inst_rows[s.k + 1];
+    const int tb = r0 / BT_TILE;
+    s.ra = max(r0, (tb + (s.j - L.pref[m])) * BT_TILE);
+    s.rb = min(r1, (tb + (s.je - 1 - L.pref[m]) + 1) * BT_TILE);
+}
 
 // ------------------------------------------------------------------------- grid barrier
 
@@ -156,91 +261,206 @@ __device__ bool bt_grid_sync(bt_global *g)
     return s_ok != 0;
 }
 
-// ------------------------------------------------------------------------- segmented tile sums
+// ------------------------------------------------------------------------- per-instance sums
 
-// Warp-level: 32 lanes hold one row each (or nothing); write the tile's partial sums of
-// `n` quantities split by instance into tp_a (first row's instance) and tp_b (others).
-__device__ __forceinline__ void bt_tile_partials(const BtArgs &a, int tile, int row_inst_lane, bool valid,
-                                                 const float *vals3, int n)
+// Barrier over the threads taking part: the whole CTA, or only the SpMV consumer warps
+// (named barrier 1; the producer warp never joins it).
+__device__ __forceinline__ void bt_group_bar(bool consumers)
 {
-    const int lane = threadIdx.x & 31;
-    const int first_inst = __shfl_sync(0xffffffffu, valid ? row_inst_lane : -1, 0);
-    const bool in_a = valid && row_inst_lane == first_inst;
-    const bool in_b = valid && row_inst_lane != first_inst;
-    for (int q = 0; q < n; ++q) {
-        double va = in_a ? (double)vals3[q] : 0.0, vb = in_b ? (double)vals3[q] : 0.0;
-        va = bt_warp_sum(va);
-        vb = bt_warp_sum(vb);
-        if (lane == 0) {
-            a.tp_a[3ll * tile + q] = va;
-            a.tp_b[3ll * tile + q] = vb;
-        }
-    }
+    if (consumers) asm volatile("bar.sync 1, %0;" ::"r"(SP_CWARPS * 32) : "memory");
+    else __syncthreads();
 }
 
-// Sum of quantity q over instance k's tiles, in tile order (one CTA, all threads call).
-__device__ double bt_instance_sum(const BtArgs &a, int k, int q)
+// Sum NQ values over the group's threads; the result is valid in thread 0.
+template <int NQ>
+__device__ void bt_group_sum(double (&v)[NQ], bool consumers)
 {
-    const int r0 = a.inst_rows[k], r1 = a.inst_rows[k + 1];
-    const int t0 = r0 / BT_TILE, t1 = (r1 - 1) / BT_TILE;
-    double acc = 0.0;
-    for (int t = t0 + threadIdx.x; t <= t1; t += blockDim.x) {
-        // the tile's first-row instance is k exactly when the tile starts inside k
-        const int first_row = t * BT_TILE;
-        const bool a_is_k = first_row >= r0;
-        acc += a_is_k ? __ldcg(a.tp_a + 3ll * t + q) : __ldcg(a.tp_b + 3ll * t + q);
+    __shared__ double s[NQ][SP_CWARPS + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = consumers ? SP_CWARPS : (int)(blockDim.x >> 5);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const double w = bt_warp_sum(v[q]);
+        if (lane == 0) s[q][warp] = w;
     }
-    double v[1] = {acc};
-    block_sum_d(v, 1);
-    return v[0];  // valid in thread 0
+    bt_group_bar(consumers);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += s[q][w];
+            v[q] = t;
+        }
+    }
+    bt_group_bar(consumers);
+}
+
+// Deliver this CTA's partial sums for the instance at list position m (slot = the CTA's
+// first entry of that instance). The CTA that delivers last sums all slots of the
+// instance in CTA order (a fixed order, so the result is deterministic) and returns
+// true with the totals in thread 0.
+template <int NQ>
+__device__ bool bt_deliver(const BtArgs &a, const bt_list &L, const bt_seg &sg, double (&v)[NQ], bool consumers)
+{
+    __shared__ int s_last;
+    bt_group_sum<NQ>(v, consumers);
+    const int c = L.chunk;
+    const int p0 = L.pref[sg.m], p1 = L.pref[sg.m + 1];
+    const int blo = p0 / c, bhi = (p1 - 1) / c;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) a.part[3ll * sg.j + q] = v[q];
+        __threadfence();
+        const int old = atomicAdd(&a.inst[sg.k].arrive, 1);
+        const bool last = old == bhi - blo;
+        if (last) {
+            a.inst[sg.k].arrive = 0;
+            __threadfence();
+        }
+        s_last = last ? 1 : 0;
+    }
+    bt_group_bar(consumers);
+    if (!s_last) return false;
+    const int nthr = consumers ? SP_CWARPS * 32 : (int)blockDim.x;
+    double w[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) w[q] = 0.0;
+    for (int bb = blo + (int)threadIdx.x; bb <= bhi; bb += nthr) {
+        const int64_t slot = max(bb * c, p0);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) w[q] += __ldcg(a.part + 3 * slot + q);
+    }
+    bt_group_sum<NQ>(w, consumers);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = w[q];
+    return true;
+}
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
+{
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
 }
 
 // ------------------------------------------------------------------------- phases
 
-__device__ __forceinline__ bool bt_active(const BtArgs &a, int k) { return __ldcg(&a.inst[k].done) == 0; }
+#define BT_U 2  // rows per thread in flight in the vector phases
 
-// p = z + beta p for active rows
-__device__ void bt_phase_direction(const BtArgs &a)
+// Direction p = z + beta p over the listed rows; rows of an instance that has just
+// taken an FP64 residual first fold the FP32 increment into the FP64 accumulator.
+__device__ void bt_phase_direction(const BtArgs &a, const bt_list &L)
 {
-    const int stride = gridDim.x * blockDim.x;
-    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < a.V; row += stride) {
-        const int k = a.row_inst[row];
-        if (!bt_active(a, k)) continue;
-        const float beta = (float)__ldcg(&a.inst[k].beta);
-        const float4 z = __ldcg(a.z4 + row), p = __ldcg(a.p4 + row);
-        a.p4[row] = make_float4(fmaf(beta, p.x, z.x), fmaf(beta, p.y, z.y), fmaf(beta, p.z, z.z), 0.f);
+    const int c = L.chunk, j0 = blockIdx.x * c, j1 = min(L.total, j0 + c);
+    if (j0 >= j1) return;
+    const int T = blockDim.x;
+    for (int m = bt_find(L, j0), j = j0; j < j1; ++m) {
+        bt_seg sg;
+        bt_seg_at(a, L, m, j, j1, sg);
+        j = sg.je;
+        const float beta = (float)__ldcg(&a.inst[sg.k].beta);
+        const bool fold = __ldcg(&a.inst[sg.k].refresh) != 0;
+        for (int base = sg.ra + (int)threadIdx.x; base < sg.rb; base += BT_U * T) {
+            float4 z[BT_U], p[BT_U];
+#pragma unroll
+            for (int u = 0; u < BT_U; ++u) {
+                const int row = base + u * T;
+                if (row < sg.rb) {
+                    z[u] = a.z4[row];
+                    p[u] = a.p4[row];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < BT_U; ++u) {
+                const int row = base + u * T;
+                if (row < sg.rb)
+                    a.p4[row] = make_float4(fmaf(beta, p[u].x, z[u].x), fmaf(beta, p[u].y, z[u].y),
+                                            fmaf(beta, p[u].z, z[u].z), 0.f);
+            }
+            if (fold) {
+#pragma unroll
+                for (int u = 0; u < BT_U; ++u) {
+                    const int row = base + u * T;
+                    if (row < sg.rb) {
+                        const float4 d = a.x4[row];
+                        a.x64[3ll * row] += (double)d.x;
+                        a.x64[3ll * row + 1] += (double)d.y;
+                        a.x64[3ll * row + 2] += (double)d.z;
+                        a.x4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+            }
+        }
     }
 }
 
-// q = A p with the bulk-copy stage ring; tile partials of p.q. `kbase` continues the
-// mbarrier phase count across calls.
-template <bool DIFF>
-__device__ void bt_phase_spmv(const BtArgs &a, unsigned char *smem_raw, uint64_t *full_bar, uint64_t *empty_bar,
-                              int (*stage_info)[4], int kbase)
+// Row bounds of a consumer thread's row, loaded one entry ahead.
+struct BtRow {
+    int row, rb, re;
+    bool on;
+};
+
+__device__ __forceinline__ void bt_load_row(const BtArgs &a, int tile, int ra, int rb, int t, BtRow &r)
 {
-    __shared__ float s_rowdot[BT_TILE];
-    __shared__ int s_rowinst[BT_TILE];
+    r.row = tile * BT_TILE + t / SP_TPR;
+    r.on = r.row >= ra && r.row < rb;
+    r.rb = r.re = 0;
+    if (r.on) {
+        r.rb = a.rp[r.row];
+        r.re = a.rp[r.row + 1];
+    }
+}
+
+// Entry e of this CTA's chunk, walked in order by the producer and by the consumers.
+struct bt_cursor {
+    int m, k, p0, p1, r0, r1, tb;
+};
+
+__device__ __forceinline__ void bt_cursor_load(const BtArgs &a, const bt_list &L, int m, bt_cursor &cu)
+{
+    cu.m = m;
+    cu.k = L.id[m];
+    cu.p0 = L.pref[m];
+    cu.p1 = L.pref[m + 1];
+    cu.r0 = a.inst_rows[cu.k];
+    cu.r1 = a.inst_rows[cu.k + 1];
+    cu.tb = cu.r0 / BT_TILE;
+}
+
+// q = A p over the listed rows with the bulk-copy stage ring, and p.q per instance; the
+// CTA that completes an instance's p.q sets its alpha. `kbase` continues the mbarrier
+// phase count across calls.
+template <bool DIFF>
+__device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *smem_raw, uint64_t *full_bar,
+                              uint64_t *empty_bar, int (*stage_info)[4], int kbase, int par)
+{
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ntiles = a.ntiles;
+    const int c = L.chunk, j0 = blockIdx.x * c, j1 = min(L.total, j0 + c);
+    const int nent = max(0, j1 - j0);
+    // the refresh counter of the previous iteration has been read by every CTA
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.g->n_refresh[par ^ 1] = 0u;
     bool timed_out = false;
     if (warp == SP_CWARPS) {
-        if (lane == 0) {
+        if (lane == 0 && nent > 0) {
+            bt_cursor cu;
+            bt_cursor_load(a, L, bt_find(L, j0), cu);
             int issued = 0;
-            for (int k = 0;; ++k) {
-                const int tile = blockIdx.x + k * gridDim.x;
-                if (tile >= ntiles) break;
-                const int kg = kbase + k;
+            for (int e = 0; e < nent; ++e) {
+                const int j = j0 + e;
+                if (j >= cu.p1) bt_cursor_load(a, L, cu.m + 1, cu);
+                const int tile = cu.tb + (j - cu.p0);
+                const int ra = max(cu.r0, tile * BT_TILE), rb = min(cu.r1, tile * BT_TILE + BT_TILE);
+                const int kg = kbase + e;
                 const int s = kg % SP_STAGES;
                 const uint32_t ph = (uint32_t)(kg / SP_STAGES) & 1u;
                 if (kg >= SP_STAGES && !mbar_wait_bounded(&empty_bar[s], ph ^ 1u, SP_WAIT_BUDGET)) {
                     timed_out = true;
                     break;
                 }
-                const int r0 = tile * SP_ROWS, r1 = min(r0 + SP_ROWS, a.V);
-                const bool any_active = bt_active(a, a.row_inst[r0]) || bt_active(a, a.row_inst[r1 - 1]);
-                const int b0 = a.rp[r0], b1 = a.rp[r1];
+                const int b0 = a.rp[ra], b1 = a.rp[rb];
                 unsigned char *base = smem_raw + s * SP_STAGE_BYTES;
-                if (any_active && b1 - b0 <= SP_CAP) {
+                if (b1 - b0 <= SP_CAP) {
                     const int64_t f0 = 9ll * b0, al0 = f0 & ~3ll, al1 = (9ll * b1 + 3) & ~3ll;
                     const int c0 = b0 & ~3, c1 = (b1 + 3) & ~3;
                     const uint32_t vbytes = (uint32_t)((al1 - al0) * 4), cbytes = (uint32_t)((c1 - c0) * 4);
@@ -260,57 +480,88 @@ __device__ void bt_phase_spmv(const BtArgs &a, unsigned char *smem_raw, uint64_t
                 }
                 ++issued;
             }
-            for (int k = issued - 1; k >= 0 && k >= issued - SP_STAGES; --k) {
-                const int kg = kbase + k;
+            // drain: the copies of the last stages issued must have landed before the phase ends
+            for (int e = issued - 1; e >= 0 && e >= issued - SP_STAGES; --e) {
+                const int kg = kbase + e;
                 if (!mbar_wait_bounded(&full_bar[kg % SP_STAGES], (uint32_t)(kg / SP_STAGES) & 1u, SP_WAIT_BUDGET))
                     timed_out = true;
             }
         }
         __syncwarp();  // the producer warp reconverges before any block-wide barrier
-    }
-    // consumers: the producer warp does not take part, so they meet on named barrier 1
-    for (int k = 0; warp < SP_CWARPS; ++k) {
-        const int tile = blockIdx.x + k * gridDim.x;
-        if (tile >= ntiles) break;
-        const int kg = kbase + k;
-        const int s = kg % SP_STAGES;
-        const uint32_t ph = (uint32_t)(kg / SP_STAGES) & 1u;
-        const int r0 = tile * SP_ROWS;
+    } else if (nent > 0) {
+        const int t = threadIdx.x;
+        const int jl = t & (SP_TPR - 1);
+        bt_cursor cu;
+        bt_cursor_load(a, L, bt_find(L, j0), cu);
+        int seg_start = j0;
+        float dot = 0.f, dot_c = 0.f;
+        BtRow nxt;
         {
-            const int t = threadIdx.x;
-            const int j = t & (SP_TPR - 1);
+            const int tile = cu.tb + (j0 - cu.p0);
+            bt_load_row(a, tile, max(cu.r0, tile * BT_TILE), min(cu.r1, tile * BT_TILE + BT_TILE), t, nxt);
+        }
+        for (int e = 0; e < nent; ++e) {
+            const int j = j0 + e;
+            const BtRow cur = nxt;
+            // prefetch the next entry's rows (it may belong to the next instance)
+            if (e + 1 < nent) {
+                const int jn = j + 1;
+                int m2 = cu.m;
+                int tb2 = cu.tb, p02 = cu.p0, r02 = cu.r0, r12 = cu.r1;
+                if (jn >= cu.p1) {
+                    m2 = cu.m + 1;
+                    const int k2 = L.id[m2];
+                    p02 = L.pref[m2];
+                    r02 = a.inst_rows[k2];
+                    r12 = a.inst_rows[k2 + 1];
+                    tb2 = r02 / BT_TILE;
+                }
+                const int tile2 = tb2 + (jn - p02);
+                bt_load_row(a, tile2, max(r02, tile2 * BT_TILE), min(r12, tile2 * BT_TILE + BT_TILE), t, nxt);
+            }
+            // the row's own p and difference-form diagonal: in flight while the stage lands
+            float4 xj = make_float4(0.f, 0.f, 0.f, 0.f);
+            float D[9];
+            if (cur.on) {
+                xj = a.p4[cur.row];
+                if (DIFF && jl == 0) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) D[q] = a.dres[9ll * cur.row + q];
+                }
+            }
+            const int kg = kbase + e;
+            const int s = kg % SP_STAGES;
+            const uint32_t ph = (uint32_t)(kg / SP_STAGES) & 1u;
             // after a timeout the warp stops waiting but keeps the barrier sequence
             const bool ok = timed_out ? false : mbar_wait_bounded(&full_bar[s], ph, SP_WAIT_BUDGET);
             if (!__all_sync(0xffffffffu, ok)) {
                 timed_out = true;
-                if ((t & (SP_TPR - 1)) == 0) {
-                    s_rowdot[t / SP_TPR] = 0.f;
-                    s_rowinst[t / SP_TPR] = -1;
-                }
             } else {
                 const int b0 = stage_info[s][0], vo = stage_info[s][1], co = stage_info[s][2];
                 const bool staged = stage_info[s][3] != 0;
                 const float *s_vals = reinterpret_cast<const float *>(smem_raw + s * SP_STAGE_BYTES) + vo;
                 const int32_t *s_cols =
                     reinterpret_cast<const int32_t *>(smem_raw + s * SP_STAGE_BYTES + SP_VAL_BYTES) + co;
-                const int row = r0 + t / SP_TPR;
                 float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
-                float4 xj = make_float4(0.f, 0.f, 0.f, 0.f);
-                int kinst = -1;
-                bool act = false;
-                if (row < a.V) {
-                    kinst = a.row_inst[row];
-                    act = bt_active(a, kinst);
-                }
-                if (act) {
-                    xj = __ldcg(a.p4 + row);
-                    const int rb = a.rp[row], re = a.rp[row + 1];
-                    for (int bb = rb + j; bb < re; bb += SP_TPR) {
-                        const int c = staged ? s_cols[bb - b0] : a.ci[bb];
-                        const float *B = staged ? s_vals + 9 * (bb - b0) : a.vals + 9ll * bb;
-                        float4 u = __ldcg(a.p4 + c);
-                        if (DIFF) { u.x -= xj.x; u.y -= xj.y; u.z -= xj.z; }
-                        spmv_fma(B, u, acc0, acc1, acc2);
+                // up to four blocks per thread in flight; p is not written in this phase, so
+                // the gathers may hit L1 (the grid barrier's acquire orders them after the
+                // direction phase's writes)
+                for (int bb = cur.rb + jl; bb < cur.re; bb += 4 * SP_TPR) {
+                    float4 u[4];
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const int bw = bb + w * SP_TPR;
+                        if (bw < cur.re) u[w] = a.p4[staged ? s_cols[bw - b0] : a.ci[bw]];
+                    }
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const int bw = bb + w * SP_TPR;
+                        if (bw < cur.re) {
+                            const float *B = staged ? s_vals + 9 * (bw - b0) : a.vals + 9ll * bw;
+                            float4 uw = u[w];
+                            if (DIFF) { uw.x -= xj.x; uw.y -= xj.y; uw.z -= xj.z; }
+                            spmv_fma(B, uw, acc0, acc1, acc2);
+                        }
                     }
                 }
                 __syncwarp();
@@ -321,26 +572,41 @@ __device__ void bt_phase_spmv(const BtArgs &a, unsigned char *smem_raw, uint64_t
                     acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
                     acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
                 }
-                if (j == 0) {
-                    float d = 0.f;
-                    if (act) {
-                        if (DIFF) spmv_fma(a.dres + 9ll * row, xj, acc0, acc1, acc2);
-                        a.q4[row] = make_float4(acc0, acc1, acc2, 0.f);
-                        d = fmaf(xj.x, acc0, fmaf(xj.y, acc1, xj.z * acc2));
-                    }
-                    s_rowdot[t / SP_TPR] = d;
-                    s_rowinst[t / SP_TPR] = (row < a.V) ? kinst : -1;
+                if (cur.on && jl == 0) {
+                    if (DIFF) spmv_fma(D, xj, acc0, acc1, acc2);
+                    a.q4[cur.row] = make_float4(acc0, acc1, acc2, 0.f);
+                    kahan_add(dot, dot_c, fmaf(xj.x, acc0, fmaf(xj.y, acc1, xj.z * acc2)));
                 }
             }
+            // end of this instance's run in the chunk: deliver p.q
+            if (j + 1 == cu.p1 || e + 1 == nent) {
+                bt_seg sg;
+                sg.m = cu.m;
+                sg.k = cu.k;
+                sg.j = seg_start;
+                double v[1] = {(double)dot - (double)dot_c};
+                if (bt_deliver<1>(a, L, sg, v, true) && threadIdx.x == 0) {
+                    bt_inst &I = a.inst[cu.k];
+                    I.refresh = 0;  // the direction phase has folded the increment
+                    if (!I.done) {
+                        const double pq = v[0];
+                        double alpha = I.rz / pq;
+                        I.pq = pq;
+                        if (!(pq > 0.0) || !isfinite(alpha)) {
+                            I.status = PC_ERR_NONFINITE;
+                            I.done = 1;
+                            alpha = 0.0;
+                            atomicAdd(&a.g->gen, 1u);
+                        }
+                        I.alpha = alpha;
+                    }
+                }
+                dot = 0.f;
+                dot_c = 0.f;
+                seg_start = j + 1;
+                if (e + 1 < nent) bt_cursor_load(a, L, cu.m + 1, cu);
+            }
         }
-        asm volatile("bar.sync 1, %0;" ::"r"(SP_CWARPS * 32) : "memory");
-        if (warp == 0) {
-            const int row = r0 + lane;
-            const float d = s_rowdot[lane];
-            const int ki = s_rowinst[lane];
-            bt_tile_partials(a, tile, ki < 0 ? 0 : ki, row < a.V && ki >= 0, &d, 1);
-        }
-        asm volatile("bar.sync 1, %0;" ::"r"(SP_CWARPS * 32) : "memory");
     }
     if (timed_out) {
         atomicExch(&a.g->abort, 1u);
@@ -348,70 +614,101 @@ __device__ void bt_phase_spmv(const BtArgs &a, unsigned char *smem_raw, uint64_t
     }
 }
 
-// x += alpha p; r -= alpha q; z = D^-1 r; tile partials of (r.z, r.r)
-__device__ void bt_phase_update(const BtArgs &a)
+// x += alpha p; r -= alpha q; z = D^-1 r; (r.z, r.r) per instance. The CTA completing an
+// instance's sums sets beta and decides: go on, refresh with an FP64 residual, or stop.
+__device__ void bt_phase_update(const BtArgs &a, const bt_list &L, int par)
 {
-    const int lane = threadIdx.x & 31;
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile < a.ntiles; tile += nwarps) {
-        const int row = tile * BT_TILE + lane;
-        const bool valid = row < a.V;
-        int k = valid ? a.row_inst[row] : 0;
-        float dots[2] = {0.f, 0.f};
-        if (valid && bt_active(a, k)) {
-            const float alpha = (float)__ldcg(&a.inst[k].alpha);
-            const float4 p = __ldcg(a.p4 + row), q = __ldcg(a.q4 + row);
-            float4 x = __ldcg(a.x4 + row), r = __ldcg(a.r4 + row);
-            x.x = fmaf(alpha, p.x, x.x); x.y = fmaf(alpha, p.y, x.y); x.z = fmaf(alpha, p.z, x.z);
-            r.x = fmaf(-alpha, q.x, r.x); r.y = fmaf(-alpha, q.y, r.y); r.z = fmaf(-alpha, q.z, r.z);
-            const float4 d = a.dinv4[row];
-            const float4 z = make_float4(d.x * r.x, d.y * r.y, d.z * r.z, 0.f);
-            a.x4[row] = x;
-            a.r4[row] = r;
-            a.z4[row] = z;
-            dots[0] = fmaf(r.x, z.x, fmaf(r.y, z.y, r.z * z.z));
-            dots[1] = fmaf(r.x, r.x, fmaf(r.y, r.y, r.z * r.z));
+    const int c = L.chunk, j0 = blockIdx.x * c, j1 = min(L.total, j0 + c);
+    if (j0 >= j1) return;
+    const int T = blockDim.x;
+    for (int m = bt_find(L, j0), j = j0; j < j1; ++m) {
+        bt_seg sg;
+        bt_seg_at(a, L, m, j, j1, sg);
+        j = sg.je;
+        const float alpha = (float)__ldcg(&a.inst[sg.k].alpha);
+        float rz = 0.f, rz_c = 0.f, rr = 0.f, rr_c = 0.f;
+        for (int base = sg.ra + (int)threadIdx.x; base < sg.rb; base += BT_U * T) {
+            float4 p[BT_U], q[BT_U], x[BT_U], r[BT_U], d[BT_U];
+#pragma unroll
+            for (int u = 0; u < BT_U; ++u) {
+                const int row = base + u * T;
+                if (row < sg.rb) {
+                    p[u] = a.p4[row];
+                    q[u] = a.q4[row];
+                    x[u] = a.x4[row];
+                    r[u] = a.r4[row];
+                    d[u] = a.dinv4[row];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < BT_U; ++u) {
+                const int row = base + u * T;
+                if (row < sg.rb) {
+                    float4 xx = x[u], rv = r[u];
+                    xx.x = fmaf(alpha, p[u].x, xx.x); xx.y = fmaf(alpha, p[u].y, xx.y); xx.z = fmaf(alpha, p[u].z, xx.z);
+                    rv.x = fmaf(-alpha, q[u].x, rv.x); rv.y = fmaf(-alpha, q[u].y, rv.y); rv.z = fmaf(-alpha, q[u].z, rv.z);
+                    const float4 z = make_float4(d[u].x * rv.x, d[u].y * rv.y, d[u].z * rv.z, 0.f);
+                    a.x4[row] = xx;
+                    a.r4[row] = rv;
+                    a.z4[row] = z;
+                    kahan_add(rz, rz_c, fmaf(rv.x, z.x, fmaf(rv.y, z.y, rv.z * z.z)));
+                    kahan_add(rr, rr_c, fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, rv.z * rv.z)));
+                }
+            }
         }
-        bt_tile_partials(a, tile, k, valid, dots, 2);
+        double v[2] = {(double)rz - (double)rz_c, (double)rr - (double)rr_c};
+        if (bt_deliver<2>(a, L, sg, v, false) && threadIdx.x == 0) {
+            bt_inst &I = a.inst[sg.k];
+            if (!I.done) {
+                const double rzn = v[0], rrn = v[1];
+                I.beta = rzn / I.rz;
+                I.rz = rzn;
+                I.rr = rrn;
+                I.iter += 1;
+                if (!isfinite(rrn) || !isfinite(I.beta)) {
+                    I.status = PC_ERR_NONFINITE;
+                    I.done = 1;
+                    atomicAdd(&a.g->gen, 1u);
+                } else if (rrn <= I.tol2 || rrn <= I.rr_last * a.refresh * a.refresh ||
+                           I.iter - I.iter_last >= a.refresh_every) {
+                    I.refresh = 1;  // confirm or refresh with an FP64 residual
+                    atomicAdd(&a.g->n_refresh[par], 1u);
+                } else if (I.iter >= a.max_iter) {
+                    I.status = PC_ERR_NOT_CONVERGED;
+                    I.done = 1;
+                    atomicAdd(&a.g->gen, 1u);
+                }
+            }
+        }
     }
 }
 
-// Fold the FP32 increment into the FP64 accumulator (rows of instances asking for it)
-__device__ void bt_phase_fold(const BtArgs &a)
-{
-    const int stride = gridDim.x * blockDim.x;
-    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < a.V; row += stride) {
-        const int k = a.row_inst[row];
-        if (__ldcg(&a.inst[k].refresh) == 0) continue;
-        const float4 d = __ldcg(a.x4 + row);
-        a.x64[3ll * row] += (double)d.x;
-        a.x64[3ll * row + 1] += (double)d.y;
-        a.x64[3ll * row + 2] += (double)d.z;
-        a.x4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-}
-
-// r = b - A x64 in FP64 for rows of refreshing instances; z = D^-1 r; p = 0 when
-// starting; tile partials of (r.z, r64.r64, b.b)
+// r = b - A (x64 + x) in FP64 over the listed rows; z = D^-1 r; p = 0 when starting;
+// (r.z, r.r, b.b) per instance. The CTA completing an instance's sums sets its scalars
+// (start) or takes the refresh result (convergence confirmed, or go on).
 template <bool DIFF>
-__device__ void bt_phase_residual(const BtArgs &a, bool start)
+__device__ void bt_phase_residual(const BtArgs &a, const bt_list &L, bool start)
 {
-    const int lane = threadIdx.x & 31;
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile < a.ntiles; tile += nwarps) {
-        const int row = tile * BT_TILE + lane;
-        const bool valid = row < a.V;
-        int k = valid ? a.row_inst[row] : 0;
-        float dots[3] = {0.f, 0.f, 0.f};
-        double rr64 = 0.0, bb64 = 0.0;
-        if (valid && __ldcg(&a.inst[k].refresh) != 0) {
-            double xj[3] = {__ldcg(a.x64 + 3ll * row), __ldcg(a.x64 + 3ll * row + 1), __ldcg(a.x64 + 3ll * row + 2)};
+    const int c = L.chunk, j0 = blockIdx.x * c, j1 = min(L.total, j0 + c);
+    if (j0 >= j1) return;
+    const int T = blockDim.x;
+    for (int m = bt_find(L, j0), j = j0; j < j1; ++m) {
+        bt_seg sg;
+        bt_seg_at(a, L, m, j, j1, sg);
+        j = sg.je;
+        double rz = 0.0, rr = 0.0, bb = 0.0;
+        for (int row = sg.ra + (int)threadIdx.x; row < sg.rb; row += T) {
+            const float4 xo = __ldcg(a.x4 + row);
+            const double xj[3] = {__ldcg(a.x64 + 3ll * row) + (double)xo.x, __ldcg(a.x64 + 3ll * row + 1) + (double)xo.y,
+                                  __ldcg(a.x64 + 3ll * row + 2) + (double)xo.z};
             double acc[3] = {0.0, 0.0, 0.0};
             for (int kk = a.rp[row]; kk < a.rp[row + 1]; ++kk) {
-                const int c = a.ci[kk];
-                if (DIFF && c == row) continue;
+                const int col = a.ci[kk];
+                if (DIFF && col == row) continue;
                 const float *B = a.vals + 9ll * kk;
-                double xc[3] = {__ldcg(a.x64 + 3ll * c), __ldcg(a.x64 + 3ll * c + 1), __ldcg(a.x64 + 3ll * c + 2)};
+                const float4 xc4 = __ldcg(a.x4 + col);
+                double xc[3] = {__ldcg(a.x64 + 3ll * col) + (double)xc4.x, __ldcg(a.x64 + 3ll * col + 1) + (double)xc4.y,
+                                __ldcg(a.x64 + 3ll * col + 2) + (double)xc4.z};
                 if (DIFF)
                     for (int d = 0; d < 3; ++d) xc[d] -= xj[d];
                 for (int q = 0; q < 3; ++q)
@@ -426,8 +723,8 @@ __device__ void bt_phase_residual(const BtArgs &a, bool start)
             for (int q = 0; q < 3; ++q) {
                 const double bv = (double)a.b[3ll * row + q];
                 const double rv = bv - acc[q];
-                rr64 += rv * rv;
-                bb64 += bv * bv;
+                rr += rv * rv;
+                bb += bv * bv;
                 rf[q] = (float)rv;
             }
             const float4 d = a.dinv4[row];
@@ -436,17 +733,29 @@ __device__ void bt_phase_residual(const BtArgs &a, bool start)
             a.r4[row] = r;
             a.z4[row] = z;
             if (start) a.p4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
-            dots[0] = fmaf(r.x, z.x, fmaf(r.y, z.y, r.z * z.z));
+            rz += (double)fmaf(r.x, z.x, fmaf(r.y, z.y, r.z * z.z));
         }
-        // rr and bb need FP64 resolution: pass them through the FP64 slots directly
-        const int first_inst = __shfl_sync(0xffffffffu, valid ? k : -1, 0);
-        const bool in_a = valid && k == first_inst, in_b = valid && k != first_inst;
-        double v[3] = {(double)dots[0], rr64, bb64};
-        for (int q = 0; q < 3; ++q) {
-            double va = bt_warp_sum(in_a ? v[q] : 0.0), vb = bt_warp_sum(in_b ? v[q] : 0.0);
-            if (lane == 0) {
-                a.tp_a[3ll * tile + q] = va;
-                a.tp_b[3ll * tile + q] = vb;
+        double v[3] = {rz, rr, bb};
+        if (bt_deliver<3>(a, L, sg, v, false) && threadIdx.x == 0) {
+            bt_inst &I = a.inst[sg.k];
+            const double rzn = v[0], rrn = v[1];
+            if (start) {
+                const double bbn = v[2];
+                I.rz = rzn; I.rr = rrn; I.bb = bbn; I.tol2 = a.tol * a.tol * bbn;
+                I.alpha = 0.0; I.beta = 0.0; I.pq = 0.0; I.rr_last = rrn;
+                I.iter = 0; I.iter_last = 0; I.refresh = 0; I.status = PC_OK;
+                I.done = (rrn <= I.tol2 || !isfinite(rrn)) ? 1 : 0;
+                if (!isfinite(rrn)) I.status = PC_ERR_NONFINITE;
+                if (!I.done && a.max_iter <= 0) { I.done = 1; I.status = PC_ERR_NOT_CONVERGED; }
+            } else {
+                I.rz = rzn;
+                I.rr = rrn;
+                I.rr_last = rrn;
+                I.iter_last = I.iter;
+                if (!isfinite(rrn)) { I.status = PC_ERR_NONFINITE; I.done = 1; }
+                else if (rrn <= I.tol2) { I.status = PC_OK; I.done = 1; }
+                else if (I.iter >= a.max_iter) { I.status = PC_ERR_NOT_CONVERGED; I.done = 1; }
+                if (I.done) atomicAdd(&a.g->gen, 1u);
             }
         }
     }
@@ -455,12 +764,13 @@ __device__ void bt_phase_residual(const BtArgs &a, bool start)
 // ------------------------------------------------------------------------- the persistent kernel
 
 template <bool DIFF>
-__global__ void __launch_bounds__(SP_THREADS) batched_pcg_kernel(BtArgs a)
+__global__ void __launch_bounds__(SP_THREADS, 4) batched_pcg_kernel(BtArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t full_bar[SP_STAGES], empty_bar[SP_STAGES];
     __shared__ int stage_info[SP_STAGES][4];
-    __shared__ int s_flag[2];
+    __shared__ bt_list L;
+    __shared__ uint32_t s_gen, s_ref;
     if (threadIdx.x == 0) {
         for (int s = 0; s < SP_STAGES; ++s) {
             mbar_init(&full_bar[s], 1);
@@ -469,118 +779,46 @@ __global__ void __launch_bounds__(SP_THREADS) batched_pcg_kernel(BtArgs a)
         mbar_fence_init();
     }
     __syncthreads();
-    // tiles this CTA takes in each SpMV phase (continues the mbarrier phase count)
-    const int my_tiles = a.ntiles > (int)blockIdx.x ? (a.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    int kbase = 0;
+    int kbase = 0;  // entries this CTA has staged so far (mbarrier phase count)
 
-    // ---- start: x64 = dv0, x = 0 (done on the host side), r = b - A x64, z, p = 0
-    for (int k = blockIdx.x; k < a.n_inst; k += gridDim.x)
-        if (threadIdx.x == 0) {
-            a.inst[k].refresh = 1;
-            a.inst[k].done = 0;
-        }
-    if (!bt_grid_sync(a.g)) return;
-    bt_phase_residual<DIFF>(a, true);
-    if (!bt_grid_sync(a.g)) return;
-    for (int k = blockIdx.x; k < a.n_inst; k += gridDim.x) {
-        const double rz = bt_instance_sum(a, k, 0), rr = bt_instance_sum(a, k, 1), bb = bt_instance_sum(a, k, 2);
-        if (threadIdx.x == 0) {
-            bt_inst &I = a.inst[k];
-            I.rz = rz; I.rr = rr; I.bb = bb; I.tol2 = a.tol * a.tol * bb;
-            I.alpha = 0.0; I.beta = 0.0; I.pq = 0.0; I.rr_last = rr;
-            I.iter = 0; I.iter_last = 0; I.refresh = 0; I.status = PC_OK;
-            I.done = (rr <= I.tol2 || !isfinite(rr)) ? 1 : 0;
-            if (!isfinite(rr)) I.status = PC_ERR_NONFINITE;
-            if (!I.done && a.max_iter <= 0) { I.done = 1; I.status = PC_ERR_NOT_CONVERGED; }
-        }
-    }
+    // ---- start: x64 = dv0 and x = 0 (set before launch); r = b - A x64, z, p = 0
+    bt_build_list(a, BT_LIST_ALL, L);
+    bt_phase_residual<DIFF>(a, L, true);
     if (!bt_grid_sync(a.g)) return;
 
+    uint32_t my_gen = 0xffffffffu;
+    bool stale = true;
     for (int it = 0;; ++it) {
         const int par = it & 1;
-        // termination: count active instances (every CTA computes the same number)
-        if (threadIdx.x == 0) {
-            int active = 0;
-            for (int k = 0; k < a.n_inst; ++k) active += __ldcg(&a.inst[k].done) == 0;
-            s_flag[0] = active;
-        }
+        if (threadIdx.x == 0) s_gen = ld_acquire_gpu(&a.g->gen);
         __syncthreads();
-        if (s_flag[0] == 0) break;
+        if (stale || s_gen != my_gen) {
+            bt_build_list(a, BT_LIST_ACTIVE, L);
+            my_gen = s_gen;
+            stale = false;
+        }
+        if (L.n == 0) break;
 
-        bt_phase_direction(a);
+        bt_phase_direction(a, L);
         if (!bt_grid_sync(a.g)) return;
-        bt_phase_spmv<DIFF>(a, smem_raw, full_bar, empty_bar, stage_info, kbase);
-        kbase += my_tiles;
-        if (!bt_grid_sync(a.g)) return;
-        for (int k = blockIdx.x; k < a.n_inst; k += gridDim.x) {
-            if (!bt_active(a, k)) continue;
-            const double pq = bt_instance_sum(a, k, 0);
-            if (threadIdx.x == 0) {
-                bt_inst &I = a.inst[k];
-                I.pq = pq;
-                double alpha = I.rz / pq;
-                if (!(pq > 0.0) || !isfinite(alpha)) {
-                    I.status = PC_ERR_NONFINITE;
-                    I.done = 1;
-                    alpha = 0.0;
-                }
-                I.alpha = alpha;
-            }
+        bt_phase_spmv<DIFF>(a, L, smem_raw, full_bar, empty_bar, stage_info, kbase, par);
+        {
+            const int c = L.chunk, j0 = blockIdx.x * c;
+            kbase += max(0, min(L.total, j0 + c) - j0);
         }
         if (!bt_grid_sync(a.g)) return;
-        bt_phase_update(a);
+        bt_phase_update(a, L, par);
         if (!bt_grid_sync(a.g)) return;
-        for (int k = blockIdx.x; k < a.n_inst; k += gridDim.x) {
-            if (!bt_active(a, k)) continue;
-            const double rz = bt_instance_sum(a, k, 0), rr = bt_instance_sum(a, k, 1);
-            if (threadIdx.x == 0) {
-                bt_inst &I = a.inst[k];
-                I.beta = rz / I.rz;
-                I.rz = rz;
-                I.rr = rr;
-                I.iter += 1;
-                if (!isfinite(rr) || !isfinite(I.beta)) {
-                    I.status = PC_ERR_NONFINITE;
-                    I.done = 1;
-                } else if (rr <= I.tol2 || rr <= I.rr_last * a.refresh * a.refresh ||
-                           I.iter - I.iter_last >= a.refresh_every) {
-                    I.refresh = 1;  // confirm or refresh with an FP64 residual
-                    atomicAdd(&a.g->n_refresh[par], 1u);
-                } else if (I.iter >= a.max_iter) {
-                    I.status = PC_ERR_NOT_CONVERGED;
-                    I.done = 1;
-                }
-            }
-        }
-        if (!bt_grid_sync(a.g)) return;
-        if (threadIdx.x == 0) s_flag[1] = (int)ld_acquire_gpu(&a.g->n_refresh[par]);
+        if (threadIdx.x == 0) s_ref = ld_acquire_gpu(&a.g->n_refresh[par]);
         __syncthreads();
-        if (s_flag[1] > 0) {
-            bt_phase_fold(a);
+        if (s_ref > 0) {
+            bt_build_list(a, BT_LIST_REFRESH, L);
+            stale = true;
+            bt_phase_residual<DIFF>(a, L, false);
             if (!bt_grid_sync(a.g)) return;
-            bt_phase_residual<DIFF>(a, false);
-            if (!bt_grid_sync(a.g)) return;
-            for (int k = blockIdx.x; k < a.n_inst; k += gridDim.x) {
-                if (__ldcg(&a.inst[k].refresh) == 0) continue;
-                const double rz = bt_instance_sum(a, k, 0), rr = bt_instance_sum(a, k, 1);
-                if (threadIdx.x == 0) {
-                    bt_inst &I = a.inst[k];
-                    I.rz = rz;
-                    I.rr = rr;
-                    I.rr_last = rr;
-                    I.iter_last = I.iter;
-                    I.refresh = 0;
-                    if (!isfinite(rr)) { I.status = PC_ERR_NONFINITE; I.done = 1; }
-                    else if (rr <= I.tol2) { I.status = PC_OK; I.done = 1; }
-                    else if (I.iter >= a.max_iter) { I.status = PC_ERR_NOT_CONVERGED; I.done = 1; }
-                }
-            }
         }
-        // the counter of the other parity is free again: clear it for the next iteration
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.g->n_refresh[par ^ 1] = 0u;
-        if (!bt_grid_sync(a.g)) return;
     }
-    // ---- finish: fold what is left and write dv = x64 (FP32)
+    // ---- finish: dv = x64 + x (FP32)
     const int stride = gridDim.x * blockDim.x;
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < a.V; row += stride) {
         const float4 d = __ldcg(a.x4 + row);
@@ -639,7 +877,7 @@ __global__ void bt_start_kernel(int V, const float *dv, double *x64, float4 *x4)
 
 struct pc_batched_state {
     int32_t *row_inst = nullptr;   // [V]
-    double *tp_a = nullptr, *tp_b = nullptr;
+    double *part = nullptr;        // [(ntiles + max_inst) * 3]
     bt_inst *inst = nullptr;       // [max_inst]
     bt_global *g = nullptr;
     int32_t *inst_rows = nullptr;  // [max_inst + 1]
@@ -653,8 +891,6 @@ struct pc_batched_state {
 };
 
 static pc_batched_state *bt_state(pc_ctx *c);
-
-#define BT_MAX_INST 4096
 
 static pc_status bt_prepare(pc_ctx *c, pc_batched_state **out)
 {
@@ -678,6 +914,7 @@ static pc_status bt_launch(pc_ctx *c, pc_batched_state *B, const BtArgs &args, b
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     PC_CUDA_TRY(cudaMemsetAsync(B->g, 0, sizeof(bt_global), st));
+    PC_CUDA_TRY(cudaMemsetAsync(B->inst, 0, sizeof(bt_inst) * (size_t)args.n_inst, st));
     BtArgs a = args;
     if (diff) PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, batched_pcg_kernel<true>, a));
     else PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, batched_pcg_kernel<false>, a));
@@ -706,14 +943,12 @@ static pc_status bt_enqueue(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, con
     BtArgs a{};
     a.V = V;
     a.n_inst = n_inst;
-    a.ntiles = (V + BT_TILE - 1) / BT_TILE;
     a.rp = A->row_ptr;
     a.ci = A->col_idx;
     a.vals = vals;
     a.dres = dres;
     a.b = b;
     a.inst_rows = B->inst_rows;
-    a.row_inst = B->row_inst;
     a.r4 = (float4 *)c->r;
     a.z4 = (float4 *)c->z;
     a.p4 = (float4 *)c->p0;
@@ -722,8 +957,7 @@ static pc_status bt_enqueue(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, con
     a.dinv4 = (const float4 *)c->dinv;
     a.x64 = c->x64;
     a.dv = dv;
-    a.tp_a = B->tp_a;
-    a.tp_b = B->tp_b;
+    a.part = B->part;
     a.inst = B->inst;
     a.g = B->g;
     a.err = c->d_err;
@@ -926,8 +1160,7 @@ pc_status pc_batched_alloc(pc_ctx *c)
     const int64_t ntiles = (c->V + BT_TILE - 1) / BT_TILE;
     B->max_inst = BT_MAX_INST;
     PC_CUDA_TRY(cudaMalloc(&B->row_inst, sizeof(int32_t) * (size_t)c->V));
-    PC_CUDA_TRY(cudaMalloc(&B->tp_a, sizeof(double) * 3 * (size_t)ntiles));
-    PC_CUDA_TRY(cudaMalloc(&B->tp_b, sizeof(double) * 3 * (size_t)ntiles));
+    PC_CUDA_TRY(cudaMalloc(&B->part, sizeof(double) * 3 * (size_t)(ntiles + BT_MAX_INST)));
     PC_CUDA_TRY(cudaMalloc(&B->inst, sizeof(bt_inst) * BT_MAX_INST));
     PC_CUDA_TRY(cudaMalloc(&B->g, sizeof(bt_global)));
     PC_CUDA_TRY(cudaMalloc(&B->inst_rows, sizeof(int32_t) * (BT_MAX_INST + 1)));
@@ -946,8 +1179,7 @@ void pc_batched_free(pc_ctx *c)
     if (B->graph_exec) cudaGraphExecDestroy(B->graph_exec);
     if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
     cudaFree(B->row_inst);
-    cudaFree(B->tp_a);
-    cudaFree(B->tp_b);
+    cudaFree(B->part);
     cudaFree(B->inst);
     cudaFree(B->g);
     cudaFree(B->inst_rows);
