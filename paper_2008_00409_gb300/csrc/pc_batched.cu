@@ -108,6 +108,7 @@ struct BtArgs {
     double *x64;
     float *dv;
     double *part;              // [(ntiles + n_inst) * 3] partial sums, one slot per (CTA, instance)
+    double *part_pq;           // [(ntiles + n_inst) * SP_CWARPS] p.q per (strided run, consumer warp)
     bt_inst *inst;
     bt_global *g;
     uint32_t *err;
@@ -295,9 +296,10 @@ __device__ void bt_group_sum(double (&v)[NQ], bool consumers)
     bt_group_bar(consumers);
 }
 
-// Deliver this CTA's partial sums for the instance at list position m (slot = the CTA's
-// first entry of that instance). The CTA that delivers last sums all slots of the
-// instance in CTA order (a fixed order, so the result is deterministic) and returns
+// Deliver this CTA's partial sums for the instance at list position m into the slot of
+// the CTA's first entry of that instance (CTA b takes entries [b*chunk, (b+1)*chunk), so
+// the instance's slots are max(b*chunk, p0) for the CTAs b whose chunk meets [p0, p1)).
+// The CTA that delivers last sums the slots in CTA order (deterministic) and returns
 // true with the totals in thread 0.
 template <int NQ>
 __device__ bool bt_deliver(const BtArgs &a, const bt_list &L, const bt_seg &sg, double (&v)[NQ], bool consumers)
@@ -428,16 +430,27 @@ __device__ __forceinline__ void bt_cursor_load(const BtArgs &a, const bt_list &L
     cu.tb = cu.r0 / BT_TILE;
 }
 
-// q = A p over the listed rows with the bulk-copy stage ring, and p.q per instance; the
-// CTA that completes an instance's p.q sets its alpha. `kbase` continues the mbarrier
-// phase count across calls.
+// Entries this CTA takes in the strided order (b, b+G, b+2G, ... below the total).
+__device__ __forceinline__ int bt_strided_count(const bt_list &L)
+{
+    return (int)blockIdx.x < L.total ? (L.total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+}
+
+// q = A p over the listed rows with the bulk-copy stage ring. Entries are taken in the
+// strided order (CTA b: b, b+G, b+2G, ...), so that at any time the CTAs work on one
+// narrow band of rows. A CTA still meets each instance in one run of consecutive entries
+// (an instance's entries are contiguous), beginning at p0 + ((b - p0) mod G); each
+// consumer warp stores its p.q over the run in that entry's slot, so the instance's
+// slots are entries p0 .. p0 + min(G, p1 - p0) - 1, one per CTA taking part, and they
+// are summed where alpha is needed (bt_alpha). `kbase` continues the mbarrier phase
+// count across calls.
 template <bool DIFF>
 __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *smem_raw, uint64_t *full_bar,
                               uint64_t *empty_bar, int (*stage_info)[4], int kbase, int par)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = L.chunk, j0 = blockIdx.x * c, j1 = min(L.total, j0 + c);
-    const int nent = max(0, j1 - j0);
+    const int G = gridDim.x, j0 = blockIdx.x;
+    const int nent = bt_strided_count(L);
     // the refresh counter of the previous iteration has been read by every CTA
     if (blockIdx.x == 0 && threadIdx.x == 0) a.g->n_refresh[par ^ 1] = 0u;
     bool timed_out = false;
@@ -447,8 +460,8 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
             bt_cursor_load(a, L, bt_find(L, j0), cu);
             int issued = 0;
             for (int e = 0; e < nent; ++e) {
-                const int j = j0 + e;
-                if (j >= cu.p1) bt_cursor_load(a, L, cu.m + 1, cu);
+                const int j = j0 + e * G;
+                if (j >= cu.p1) bt_cursor_load(a, L, bt_find(L, j), cu);
                 const int tile = cu.tb + (j - cu.p0);
                 const int ra = max(cu.r0, tile * BT_TILE), rb = min(cu.r1, tile * BT_TILE + BT_TILE);
                 const int kg = kbase + e;
@@ -501,15 +514,14 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
             bt_load_row(a, tile, max(cu.r0, tile * BT_TILE), min(cu.r1, tile * BT_TILE + BT_TILE), t, nxt);
         }
         for (int e = 0; e < nent; ++e) {
-            const int j = j0 + e;
+            const int j = j0 + e * G;
             const BtRow cur = nxt;
             // prefetch the next entry's rows (it may belong to the next instance)
             if (e + 1 < nent) {
-                const int jn = j + 1;
-                int m2 = cu.m;
+                const int jn = j + G;
                 int tb2 = cu.tb, p02 = cu.p0, r02 = cu.r0, r12 = cu.r1;
                 if (jn >= cu.p1) {
-                    m2 = cu.m + 1;
+                    const int m2 = bt_find(L, jn);
                     const int k2 = L.id[m2];
                     p02 = L.pref[m2];
                     r02 = a.inst_rows[k2];
@@ -578,33 +590,14 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
                     kahan_add(dot, dot_c, fmaf(xj.x, acc0, fmaf(xj.y, acc1, xj.z * acc2)));
                 }
             }
-            // end of this instance's run in the chunk: deliver p.q
-            if (j + 1 == cu.p1 || e + 1 == nent) {
-                bt_seg sg;
-                sg.m = cu.m;
-                sg.k = cu.k;
-                sg.j = seg_start;
-                double v[1] = {(double)dot - (double)dot_c};
-                if (bt_deliver<1>(a, L, sg, v, true) && threadIdx.x == 0) {
-                    bt_inst &I = a.inst[cu.k];
-                    I.refresh = 0;  // the direction phase has folded the increment
-                    if (!I.done) {
-                        const double pq = v[0];
-                        double alpha = I.rz / pq;
-                        I.pq = pq;
-                        if (!(pq > 0.0) || !isfinite(alpha)) {
-                            I.status = PC_ERR_NONFINITE;
-                            I.done = 1;
-                            alpha = 0.0;
-                            atomicAdd(&a.g->gen, 1u);
-                        }
-                        I.alpha = alpha;
-                    }
-                }
+            // end of this instance's run: the warp's p.q goes to the run's slot
+            if (j + G >= cu.p1 || e + 1 == nent) {
+                const double w = bt_warp_sum((double)dot - (double)dot_c);
+                if (lane == 0) a.part_pq[(int64_t)SP_CWARPS * seg_start + warp] = w;
                 dot = 0.f;
                 dot_c = 0.f;
-                seg_start = j + 1;
-                if (e + 1 < nent) bt_cursor_load(a, L, cu.m + 1, cu);
+                seg_start = j + G;
+                if (e + 1 < nent) bt_cursor_load(a, L, bt_find(L, j + G), cu);
             }
         }
     }
@@ -612,6 +605,52 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
         atomicExch(&a.g->abort, 1u);
         atomicOr(a.err, PC_DERR_TIMEOUT);
     }
+}
+
+// alpha of the instance at list position m from its p.q slots, summed in slot order by
+// every CTA that needs it (all get the same value); the CTA holding the instance's first
+// entry records it. Returns alpha to all threads.
+__device__ float bt_alpha(const BtArgs &a, const bt_list &L, const bt_seg &sg)
+{
+    __shared__ float s_alpha;
+    const int p0 = L.pref[sg.m], p1 = L.pref[sg.m + 1];
+    static_assert(SP_CWARPS == 4, "a p.q slot is four doubles (two double2)");
+    const int n = min((int)gridDim.x, p1 - p0);
+    const double2 *slots = reinterpret_cast<const double2 *>(a.part_pq + (int64_t)SP_CWARPS * p0);
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int i = threadIdx.x; i < n; i += 2 * blockDim.x) {
+        const int i2 = i + blockDim.x;
+        const double2 x0 = __ldcg(slots + 2 * i), x1 = __ldcg(slots + 2 * i + 1);
+        double2 y0 = make_double2(0.0, 0.0), y1 = make_double2(0.0, 0.0);
+        if (i2 < n) {
+            y0 = __ldcg(slots + 2 * i2);
+            y1 = __ldcg(slots + 2 * i2 + 1);
+        }
+        acc0 += (x0.x + x0.y) + (x1.x + x1.y);
+        acc1 += (y0.x + y0.y) + (y1.x + y1.y);
+    }
+    double v[1] = {acc0 + acc1};
+    bt_group_sum<1>(v, false);
+    if (threadIdx.x == 0) {
+        bt_inst &I = a.inst[sg.k];
+        const double pq = v[0];
+        double alpha = __ldcg(&I.rz) / pq;
+        const bool bad = !(pq > 0.0) || !isfinite(alpha);
+        if (bad) alpha = 0.0;
+        if (sg.j == p0) {  // the instance's first entry is in this CTA's chunk
+            I.refresh = 0;  // the direction phase has folded the increment
+            I.pq = pq;
+            I.alpha = alpha;
+            if (bad) {
+                I.status = PC_ERR_NONFINITE;
+                I.done = 1;
+                atomicAdd(&a.g->gen, 1u);
+            }
+        }
+        s_alpha = (float)alpha;
+    }
+    __syncthreads();
+    return s_alpha;
 }
 
 // x += alpha p; r -= alpha q; z = D^-1 r; (r.z, r.r) per instance. The CTA completing an
@@ -625,7 +664,7 @@ __device__ void bt_phase_update(const BtArgs &a, const bt_list &L, int par)
         bt_seg sg;
         bt_seg_at(a, L, m, j, j1, sg);
         j = sg.je;
-        const float alpha = (float)__ldcg(&a.inst[sg.k].alpha);
+        const float alpha = bt_alpha(a, L, sg);
         float rz = 0.f, rz_c = 0.f, rr = 0.f, rr_c = 0.f;
         for (int base = sg.ra + (int)threadIdx.x; base < sg.rb; base += BT_U * T) {
             float4 p[BT_U], q[BT_U], x[BT_U], r[BT_U], d[BT_U];
@@ -802,10 +841,7 @@ __global__ void __launch_bounds__(SP_THREADS, 4) batched_pcg_kernel(BtArgs a)
         bt_phase_direction(a, L);
         if (!bt_grid_sync(a.g)) return;
         bt_phase_spmv<DIFF>(a, L, smem_raw, full_bar, empty_bar, stage_info, kbase, par);
-        {
-            const int c = L.chunk, j0 = blockIdx.x * c;
-            kbase += max(0, min(L.total, j0 + c) - j0);
-        }
+        kbase += bt_strided_count(L);
         if (!bt_grid_sync(a.g)) return;
         bt_phase_update(a, L, par);
         if (!bt_grid_sync(a.g)) return;
@@ -878,6 +914,7 @@ __global__ void bt_start_kernel(int V, const float *dv, double *x64, float4 *x4)
 struct pc_batched_state {
     int32_t *row_inst = nullptr;   // [V]
     double *part = nullptr;        // [(ntiles + max_inst) * 3]
+    double *part_pq = nullptr;     // [(ntiles + max_inst) * SP_CWARPS]
     bt_inst *inst = nullptr;       // [max_inst]
     bt_global *g = nullptr;
     int32_t *inst_rows = nullptr;  // [max_inst + 1]
@@ -958,6 +995,7 @@ static pc_status bt_enqueue(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, con
     a.x64 = c->x64;
     a.dv = dv;
     a.part = B->part;
+    a.part_pq = B->part_pq;
     a.inst = B->inst;
     a.g = B->g;
     a.err = c->d_err;
@@ -1161,6 +1199,7 @@ pc_status pc_batched_alloc(pc_ctx *c)
     B->max_inst = BT_MAX_INST;
     PC_CUDA_TRY(cudaMalloc(&B->row_inst, sizeof(int32_t) * (size_t)c->V));
     PC_CUDA_TRY(cudaMalloc(&B->part, sizeof(double) * 3 * (size_t)(ntiles + BT_MAX_INST)));
+    PC_CUDA_TRY(cudaMalloc(&B->part_pq, sizeof(double) * SP_CWARPS * (size_t)(ntiles + BT_MAX_INST)));
     PC_CUDA_TRY(cudaMalloc(&B->inst, sizeof(bt_inst) * BT_MAX_INST));
     PC_CUDA_TRY(cudaMalloc(&B->g, sizeof(bt_global)));
     PC_CUDA_TRY(cudaMalloc(&B->inst_rows, sizeof(int32_t) * (BT_MAX_INST + 1)));
@@ -1180,6 +1219,7 @@ void pc_batched_free(pc_ctx *c)
     if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
     cudaFree(B->row_inst);
     cudaFree(B->part);
+    cudaFree(B->part_pq);
     cudaFree(B->inst);
     cudaFree(B->g);
     cudaFree(B->inst_rows);
