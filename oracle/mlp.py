@@ -130,16 +130,25 @@ def normalize_targets(T, stats) -> np.ndarray:
 # --------------------------------------------------------------------------- network
 
 
-def forward(params, Xn):
-    """Pre-activations and activations of every layer for standardised inputs Xn."""
+def _r(a, bf16: bool):
+    return bf16_round(a) if bf16 else a
+
+
+def forward(params, Xn, bf16: bool = False):
+    """Pre-activations and activations of every layer for standardised inputs Xn.
+
+    With bf16=True the values that the tensor-core kernels feed to their BF16 matrix
+    products (inputs, weights, hidden activations) are rounded to bfloat16 first; sums,
+    biases and the output stay in FP64."""
     P = unpack(params)
-    Xn = np.asarray(Xn, dtype=np.float64).reshape(-1, N_IN)
-    Z1 = Xn @ P["W1"].T + P["b1"]
-    H1 = np.maximum(Z1, 0.0)
-    Z2 = H1 @ P["W2"].T + P["b2"]
-    H2 = np.maximum(Z2, 0.0)
-    Y = H2 @ P["W3"].T + P["b3"]
-    return {"Z1": Z1, "H1": H1, "Z2": Z2, "H2": H2, "Y": Y}
+    W1, W2, W3 = (_r(P[k], bf16) for k in ("W1", "W2", "W3"))
+    Xn = _r(np.asarray(Xn, dtype=np.float64).reshape(-1, N_IN), bf16)
+    Z1 = Xn @ W1.T + P["b1"]
+    H1 = _r(np.maximum(Z1, 0.0), bf16)
+    Z2 = H1 @ W2.T + P["b2"]
+    H2 = _r(np.maximum(Z2, 0.0), bf16)
+    Y = H2 @ W3.T + P["b3"]
+    return {"Z1": Z1, "H1": H1, "Z2": Z2, "H2": H2, "Y": Y, "X": Xn}
 
 
 def loss(params, Xn, Tn) -> float:
@@ -148,20 +157,26 @@ def loss(params, Xn, Tn) -> float:
     return 0.5 * float(np.sum((Y - Tn) ** 2)) / Y.shape[0]
 
 
-def grad(params, Xn, Tn) -> np.ndarray:
-    """Gradient of `loss` by back-propagation through the three layers."""
+def grad(params, Xn, Tn, bf16: bool = False) -> np.ndarray:
+    """Gradient of `loss` by back-propagation through the three layers.
+
+    With bf16=True, besides the forward rounding, the backward signals that enter BF16
+    matrix products (dY, dZ2, dZ1) are rounded to bfloat16; bias gradients use the
+    unrounded signals."""
     P = unpack(params)
-    Xn = np.asarray(Xn, dtype=np.float64).reshape(-1, N_IN)
+    W2, W3 = _r(P["W2"], bf16), _r(P["W3"], bf16)
     Tn = np.asarray(Tn, dtype=np.float64).reshape(-1, N_OUT)
-    a = forward(params, Xn)
-    N = Xn.shape[0]
+    a = forward(params, Xn, bf16)
+    N = a["X"].shape[0]
     dY = (a["Y"] - Tn) / N
-    g = {"W3": dY.T @ a["H2"], "b3": dY.sum(0)}
-    dZ2 = (dY @ P["W3"]) * (a["Z2"] > 0.0)
-    g["W2"] = dZ2.T @ a["H1"]
+    dYr = _r(dY, bf16)
+    g = {"W3": dYr.T @ a["H2"], "b3": dY.sum(0)}
+    dZ2 = (dYr @ W3) * (a["Z2"] > 0.0)
+    dZ2r = _r(dZ2, bf16)
+    g["W2"] = dZ2r.T @ a["H1"]
     g["b2"] = dZ2.sum(0)
-    dZ1 = (dZ2 @ P["W2"]) * (a["Z1"] > 0.0)
-    g["W1"] = dZ1.T @ Xn
+    dZ1 = (dZ2r @ W2) * (a["Z1"] > 0.0)
+    g["W1"] = _r(dZ1, bf16).T @ a["X"]
     g["b1"] = dZ1.sum(0)
     return pack(g)
 
@@ -178,10 +193,10 @@ def adam_step(params, m, v, g, t: int, lr: float = 1e-3, beta1: float = 0.9, bet
     return params - lr * mhat / (np.sqrt(vhat) + eps), m, v
 
 
-def predict(params, stats, X, dv_prev, pinned=None) -> np.ndarray:
+def predict(params, stats, X, dv_prev, pinned=None, bf16: bool = False) -> np.ndarray:
     """Initial guess dv0 = dv_prev + de-standardised network output (0 at pins)."""
     _, _, my, sy = split_stats(stats)
-    Y = forward(params, normalize_inputs(X, stats))["Y"]
+    Y = forward(params, normalize_inputs(X, stats), bf16)["Y"]
     dv0 = np.asarray(dv_prev, dtype=np.float64).reshape(-1, 3) + Y * sy + my
     if pinned is not None:
         dv0[np.asarray(pinned, bool)] = 0.0

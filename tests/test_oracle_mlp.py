@@ -146,3 +146,40 @@ def test_predict_of_a_silent_network():
                                     (-1.0 - 2.0 ** -9, -1.0), (3.0e-3, 0.0030059814453125)])
 def test_bf16_rounding_ties_to_even(x, want):
     assert mlp.bf16_round(np.array([x]))[0] == want
+
+
+def test_bf16_mode_is_exact_on_representable_values():
+    # sparse +-1 weights, inputs in {-1, 0, 1}, half-integer biases and a batch of 8 keep
+    # every rounded quantity (inputs, weights, H1, H2, dY, dZ2, dZ1) a short binary
+    # fraction, exactly representable in bfloat16, so both modes must agree exactly
+    rng = np.random.default_rng(12)
+    W1 = np.zeros((64, 12))
+    for r in range(64):
+        W1[r, rng.choice(12, 3, replace=False)] = rng.choice([-1.0, 1.0], 3)
+    I = np.eye(64)
+    W2 = I[rng.permutation(64)] - I[rng.permutation(64)]
+    W3 = np.zeros((3, 64))
+    cols = rng.permutation(64)[:12].reshape(3, 4)
+    for o in range(3):
+        W3[o, cols[o]] = rng.choice([-1.0, 1.0], 4)
+    P = {"W1": W1, "b1": rng.integers(-2, 3, 64) * 0.5, "W2": W2, "b2": rng.integers(-2, 3, 64) * 0.5,
+         "W3": W3, "b3": rng.integers(-2, 3, 3) * 0.5}
+    p = mlp.pack(P)
+    X = rng.integers(-1, 2, (8, 12)).astype(float)
+    T = rng.integers(-4, 5, (8, 3)) * 0.5
+    a = mlp.forward(p, X)
+    assert a["H1"].max() > 0 and a["H2"].max() > 0  # the case is not trivial
+    assert np.array_equal(mlp.forward(p, X, bf16=True)["Y"], a["Y"])
+    g = mlp.grad(p, X, T)
+    assert np.count_nonzero(g) > 100
+    assert np.array_equal(mlp.grad(p, X, T, bf16=True), g)
+
+
+def test_bf16_mode_stays_within_the_rounding_bound():
+    p = mlp.init_params(5)
+    X, T = _rand_batch(64, 21)
+    ye, yb = mlp.forward(p, X)["Y"], mlp.forward(p, X, bf16=True)["Y"]
+    rel = np.linalg.norm(yb - ye) / np.linalg.norm(ye)
+    assert 1e-4 < rel < 2e-2  # rounding really happens, at the size 2^-8 predicts
+    ge, gb = mlp.grad(p, X, T), mlp.grad(p, X, T, bf16=True)
+    assert np.linalg.norm(gb - ge) / np.linalg.norm(ge) < 3e-2
