@@ -58,6 +58,9 @@ typedef int32_t pc_status;
 #define PC_WARM_ZERO 0   /* initial guess dv = 0 */
 #define PC_WARM_PREV 1   /* initial guess = previous step's dv */
 #define PC_WARM_GIVEN 2  /* initial guess = the dv buffer passed in */
+#define PC_WARM_MLP 3    /* learned guess (pc_set_warm_mlp), judged against the previous-step and zero
+                            guesses: the one with the lowest CG energy 1/2 g.A g - b.g (the smallest
+                            A-norm error) starts the solve */
 
 typedef struct pc_ctx pc_ctx;
 
@@ -116,12 +119,19 @@ typedef struct {
 typedef struct {
     float h;              /* time step, s */
     pc_solve_opts solve;
-    int32_t warm_start;   /* PC_WARM_ZERO or PC_WARM_PREV */
+    int32_t warm_start;   /* PC_WARM_ZERO, PC_WARM_PREV or PC_WARM_MLP */
+    float *feat_out;      /* device float[V][PC_MLP_IN] or NULL: receives this step's warm-start
+                             features (computed after assembly, before the solve) */
 } pc_step_opts;
 
 typedef struct {
     int64_t nnzb;
     pc_solve_info solve;
+    int32_t guess;         /* initial guess used: PC_WARM_ZERO, PC_WARM_PREV or PC_WARM_MLP */
+    int32_t pad;
+    double guess_res[3];   /* PC_WARM_MLP: |b - A g| / |b| of the zero, previous and learned
+                              guesses (FP64); -1 when not evaluated */
+    double guess_energy[3]; /* PC_WARM_MLP: 1/2 g.A g - b.g of the same guesses (0 for zero) */
 } pc_step_info;
 
 /* Text for a status code (static storage). */
@@ -216,7 +226,7 @@ PC_API pc_status pc_pcg_solve(pc_ctx *ctx, const pc_bsr *A, const float *vals, c
 /* Batched solve of many independent systems (garments) in ONE persistent PCG launch.
  * The context holds the union of the garments' meshes; instance k owns the contiguous
  * rows inst_rows[k] .. inst_rows[k+1]-1 (host array of n_inst + 1 entries, first 0, last
- * V, every instance at least 32 rows, n_inst <= 4096) and no matrix block may couple two
+ * V, every instance at least 32 rows, n_inst <= 1024) and no matrix block may couple two
  * instances (checked: PC_ERR_ARG). Each instance runs Jacobi-PCG with its own scalars
  * and stop test |b_k - A_k dv_k| / |b_k| <= tol, with FP64 residual replacement as in
  * PC_PREC_MIXED (refresh, refresh_every); finished instances drop out while the others
@@ -273,6 +283,83 @@ PC_API pc_status pc_step(pc_ctx *ctx, float *x, float *v, const pc_contacts *con
  * buffers may be pageable or pinned. */
 PC_API pc_status pc_step_host(pc_ctx *ctx, float *x_host, float *v_host, int32_t n_contacts, const int32_t *pairs_host,
                        const float *w_host, const pc_step_opts *opts, pc_step_info *info, void *stream);
+
+/* ---------------------------------------------------------------- learned warm start
+ * The paper has no learned component; this is an extension built on its integrator. A
+ * per-vertex MLP predicts the initial guess of the Eq. 3 solve:
+ *   features (PC_MLP_IN = 12 per vertex): v_i; the previous step's dv_i; the internal
+ *     force per unit mass at the first-order end-of-step position,
+ *     (b_i / h - m_i g) / m_i with b the assembled right-hand side; the mean of the
+ *     previous dv over the vertex's mesh-edge neighbours;
+ *   network: 12 -> 64 -> 64 -> 3 with ReLU, on inputs standardised by stats
+ *     (mu_x[12], sd_x[12], mu_y[3], sd_y[3]); it predicts the change of dv from the
+ *     previous step: dv0 = dv_prev + sd_y * y + mu_y;
+ *   params: float[PC_MLP_NPARAMS] = W1[64][12], b1[64], W2[64][64], b2[64], W3[3][64],
+ *     b3[3] (row-major [out][in]).
+ * Every matrix product runs on the tensor cores with BF16 operands (weights, standardised
+ * inputs, activations and back-propagated signals rounded to BF16) and FP32
+ * accumulation; the FP32 params are the master weights. Training minimises
+ * L = 1/(2n) sum over rows and outputs of (y - t)^2, t the standardised target
+ * dv - dv_prev, with Adam. All pointers are device pointers unless stated. */
+#define PC_MLP_IN 12
+#define PC_MLP_HIDDEN 64
+#define PC_MLP_OUT 3
+#define PC_MLP_NPARAMS 5187
+#define PC_MLP_NSTATS 30
+
+typedef struct pc_mlp pc_mlp;  /* training state: Adam moments, step count, reduction scratch */
+
+typedef struct {
+    float lr, beta1, beta2, eps;
+} pc_adam_opts;
+
+/* The 12 raw features of every vertex of a cloth state: v, dv_prev (float[V][3]), b the
+ * right-hand side assembled for this state (pc_assemble_values), h the time step.
+ * feat: float[V][12]. Does not synchronize. */
+PC_API pc_status pc_mlp_features(pc_ctx *ctx, const float *v, const float *dv_prev, const float *b, float h,
+                                 float *feat, void *stream);
+
+/* Create / destroy training state (on the current device). */
+PC_API pc_status pc_mlp_create(pc_mlp **out);
+PC_API pc_status pc_mlp_destroy(pc_mlp *m);
+/* Zero the Adam moments and the step count. */
+PC_API pc_status pc_mlp_reset(pc_mlp *m, void *stream);
+
+/* Training rows: feat float[*][12] as pc_mlp_features writes it and target float[*][3]
+ * the solution dv of the same step (pc_step's dv_out); the network's target is
+ * dv - dv_prev, dv_prev being features 3..5 of the row.
+ * Standardisation statistics of n training rows: per-column mean and population standard
+ * deviation (FP64 sums, floor 1e-12) of the 12 features and of the 3 target components,
+ * written to stats float[PC_MLP_NSTATS]. Deterministic. Does not synchronize. */
+PC_API pc_status pc_mlp_stats(pc_mlp *m, int64_t n, const float *feat, const float *target, float *stats,
+                              void *stream);
+
+/* Inference: dv0[r] = dv_prev[r] + sd_y * net((feat[r] - mu_x) / sd_x) + mu_y for n rows
+ * (dv_prev may be NULL = 0); rows with fixed[r] != 0 (uint8[n], may be NULL) get 0.
+ * Does not synchronize. */
+PC_API pc_status pc_mlp_infer(int64_t n, const float *params, const float *stats, const float *feat,
+                              const float *dv_prev, const uint8_t *fixed, float *dv0, void *stream);
+
+/* Gradient of L over a batch of n rows: rows (int32[n], may be NULL = rows 0..n-1) index
+ * feat and target (training rows as above). grad: float[NPARAMS]
+ * (partials summed in a fixed order: deterministic). loss (host, may be NULL) receives L
+ * and then the call synchronizes `stream`. */
+PC_API pc_status pc_mlp_grad(pc_mlp *m, int64_t n, const int32_t *rows, const float *params, const float *stats,
+                             const float *feat, const float *target, float *grad, double *loss, void *stream);
+
+/* One Adam step on params (in place) with the gradient of that batch. */
+PC_API pc_status pc_mlp_train_step(pc_mlp *m, int64_t n, const int32_t *rows, float *params, const float *stats,
+                                   const float *feat, const float *target, const pc_adam_opts *o, double *loss,
+                                   void *stream);
+
+/* One Adam step on params with a given gradient (float[NPARAMS]). */
+PC_API pc_status pc_mlp_adam_apply(pc_mlp *m, float *params, const float *grad, const pc_adam_opts *o,
+                                   void *stream);
+
+/* Attach a trained network to a context for PC_WARM_MLP steps (the pointers are kept,
+ * not copied; NULL, NULL detaches). Allocates the context's feature and guess scratch
+ * on first use. */
+PC_API pc_status pc_set_warm_mlp(pc_ctx *ctx, const float *params, const float *stats);
 
 /* Kernel launches issued by this context since creation (all entry points). */
 PC_API int64_t pc_launch_count(const pc_ctx *ctx);

@@ -46,13 +46,23 @@ extern "C" pc_status pc_step(pc_ctx *ctx, float *x, float *v, const pc_contacts 
     pc_bsr A{ctx->A_rp, ctx->A_ci, ctx->A_cap, 0};
     PC_TRY(pc_assemble_pattern(ctx, contacts, &A, stream));
     PC_TRY(pc_assemble_values(ctx, &A, x, v, contacts, opts->h, ctx->A_vals, ctx->A_b, ctx->A_dres, stream));
-    if (opts->warm_start != PC_WARM_PREV || !ctx->has_prev_dv)
-        PC_CUDA_TRY(cudaMemsetAsync(ctx->A_dv, 0, sizeof(float) * 3 * (size_t)ctx->V, st));
+    // A_dv holds the previous step's dv (zeros before the first step); choose the guess
+    if (!ctx->has_prev_dv) PC_CUDA_TRY(cudaMemsetAsync(ctx->A_dv, 0, sizeof(float) * 3 * (size_t)ctx->V, st));
+    int32_t guess = PC_WARM_ZERO;
+    double guess_res[3], guess_energy[3];
+    PC_TRY(pc_warm_guess(ctx, &A, v, opts->h, opts->warm_start, opts->feat_out, &guess, guess_res, guess_energy,
+                         st));
     pc_solve_info si{};
     pc_status s = pc_pcg_solve(ctx, &A, ctx->A_vals, ctx->A_dres, ctx->A_b, ctx->A_dv, &opts->solve, &si, stream);
     if (info) {
         info->nnzb = A.nnzb;
         info->solve = si;
+        info->guess = guess;
+        info->pad = 0;
+        for (int k = 0; k < 3; ++k) {
+            info->guess_res[k] = guess_res[k];
+            info->guess_energy[k] = guess_energy[k];
+        }
     }
     if (s != PC_OK && s != PC_ERR_NOT_CONVERGED) return s;
     ctx->has_prev_dv = 1;

@@ -103,6 +103,9 @@ struct pc_ctx {
     int32_t *scol = nullptr;       // [snnz]
     int32_t *vinc_ptr = nullptr;   // [V+1]
     uint32_t *vinc = nullptr;      // [3T + 4H] element refs grouped by vertex
+    int64_t enn = 0;
+    int32_t *erp = nullptr;        // [V+1] edge one-rings (CSR)
+    int32_t *ecol = nullptr;       // [enn] edge neighbours, sorted per vertex
 
     // per-step contact data
     uint64_t *dkeys = nullptr;     // [6 * maxP] dynamic pattern keys (sorted)
@@ -154,6 +157,12 @@ struct pc_ctx {
     // batched solver state (pc_batched.cu)
     void *batched = nullptr;
 
+    // learned warm start (pc_mlp.cu): caller-owned network, context-owned scratch
+    const float *mlp_params = nullptr;  // device [PC_MLP_NPARAMS]
+    const float *mlp_stats = nullptr;   // device [PC_MLP_NSTATS]
+    float *mlp_feat = nullptr;          // [V][12]
+    float *mlp_dv = nullptr;            // [V][3]
+
     // profiling
     int profiling = 0;
     int64_t launches = 0;
@@ -196,6 +205,11 @@ pc_status pc_update_state(pc_ctx *ctx, float *x, float *v, const float *dv, floa
 pc_status pc_solver_alloc(pc_ctx *ctx);
 pc_status pc_batched_alloc(pc_ctx *ctx);
 void pc_batched_free(pc_ctx *ctx);
+pc_status pc_guess_eval(pc_ctx *c, const pc_bsr *A, const float *vals, const float *dres, const float *b,
+                        const float *x, double *rr, double *bb, double *energy, cudaStream_t st);
+pc_status pc_warm_guess(pc_ctx *c, const pc_bsr *A, const float *v, float h, int32_t mode, float *feat_out,
+                        int32_t *guess, double *guess_res, double *guess_energy, cudaStream_t st);
+void pc_mlp_ctx_free(pc_ctx *c);
 
 inline int pc_bits_for(int64_t n)
 {

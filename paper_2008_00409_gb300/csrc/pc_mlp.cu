@@ -1,0 +1,834 @@
+// Learned warm start: a per-vertex MLP (12 -> 64 -> 64 -> 3, ReLU) that predicts the
+// initial guess of the Eq. 3 solve, its training (forward, back-propagation, Adam) and
+// the step's choice among the learned, previous-step and zero guesses by their residual.
+// The paper has no learned component; this is an extension built on its integrator.
+//
+// Features of vertex i (12): v_i, dv_prev_i, (b_i / h - m_i g) / m_i (the internal force
+// per unit mass at the first-order end-of-step position, from the assembled right-hand
+// side b = h (f(x_t) - h K v_t) + h M g), and the mean of dv_prev over the edge one-ring.
+// Inputs and targets are standardised with training-set statistics; the network predicts
+// the change dv - dv_prev, so the guess is dv0 = dv_prev + sd_y * y + mu_y (0 at pins).
+//
+// Every matrix product runs on the tensor cores as warp-level BF16 MMAs (m16n8k16, FP32
+// accumulation): a warp owns 16 rows and carries them through all layers in registers
+// (the accumulator fragment of one layer is the operand fragment of the next). Training
+// stages the tile's BF16 activations and back-propagated signals in shared memory and
+// forms the weight gradients dW = dZ^T H as MMAs over the rows (operands transposed by
+// ldmatrix.trans); per-CTA partial gradients are summed in a fixed order (deterministic)
+// by the kernel that applies Adam to the FP32 master weights.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "pc_internal.cuh"
+#include "pc_tma.cuh"
+
+#define MLP_IN 12
+#define MLP_HID 64
+#define MLP_OUT 3
+#define OFF_W1 0
+#define OFF_B1 (OFF_W1 + MLP_HID * MLP_IN)
+#define OFF_W2 (OFF_B1 + MLP_HID)
+#define OFF_B2 (OFF_W2 + MLP_HID * MLP_HID)
+#define OFF_W3 (OFF_B2 + MLP_HID)
+#define OFF_B3 (OFF_W3 + MLP_OUT * MLP_HID)
+static_assert(OFF_B3 + MLP_OUT == PC_MLP_NPARAMS, "parameter layout");
+static_assert(2 * MLP_IN + 2 * MLP_OUT == PC_MLP_NSTATS, "statistics layout");
+
+#define WP16 24  // shared-memory pitch (BF16 elements) of 16-wide rows: conflict-free fragment loads
+#define WP64 72  // pitch of 64-wide rows
+#define MLP_WARPS 8
+#define MLP_THREADS (32 * MLP_WARPS)
+#define MLP_TILE (16 * MLP_WARPS)  // rows per CTA tile
+
+// ------------------------------------------------------------------------- tensor-core helpers
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x (low half) = lo
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// D += A (16x16, row) * B (16x8, col), BF16 inputs, FP32 accumulation
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const __nv_bfloat16 *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ void ldsm_x2_t(uint32_t &r0, uint32_t &r1, const __nv_bfloat16 *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ void st_pair(__nv_bfloat16 *base, int row, int pitch, int col, uint32_t v)
+{
+    *reinterpret_cast<uint32_t *>(base + row * pitch + col) = v;
+}
+
+// ------------------------------------------------------------------------- weights in shared memory
+
+// BF16 copies of the weights in the layouts the fragments read: W[n][k] rows (forward,
+// B[k][n] = W[n][k]) and transposes (backward, B[k][n] = W[k][n]); zero padding of the
+// 12 inputs to 16 and of the 3 outputs to 8 (forward) or 16 (backward operands).
+struct MlpW {
+    __nv_bfloat16 w1[MLP_HID * WP16];
+    __nv_bfloat16 w2[MLP_HID * WP64];
+    __nv_bfloat16 w3[8 * WP64];
+    __nv_bfloat16 w2t[MLP_HID * WP64];
+    __nv_bfloat16 w3t[MLP_HID * WP16];
+    float b1[MLP_HID], b2[MLP_HID], b3[8];
+    float mx[16], sx[16], my[4], sy[4];
+};
+
+__device__ void mlp_stage(MlpW &s, const float *P, const float *stats, bool backward)
+{
+    const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+    for (int i = threadIdx.x; i < MLP_HID * WP16; i += blockDim.x) {
+        const int n = i / WP16, k = i % WP16;
+        s.w1[i] = k < MLP_IN ? __float2bfloat16_rn(P[OFF_W1 + n * MLP_IN + k]) : z;
+        if (backward) s.w3t[i] = k < MLP_OUT ? __float2bfloat16_rn(P[OFF_W3 + k * MLP_HID + n]) : z;
+    }
+    for (int i = threadIdx.x; i < MLP_HID * WP64; i += blockDim.x) {
+        const int n = i / WP64, k = i % WP64;
+        s.w2[i] = k < MLP_HID ? __float2bfloat16_rn(P[OFF_W2 + n * MLP_HID + k]) : z;
+        if (backward) s.w2t[i] = k < MLP_HID ? __float2bfloat16_rn(P[OFF_W2 + k * MLP_HID + n]) : z;
+    }
+    for (int i = threadIdx.x; i < 8 * WP64; i += blockDim.x) {
+        const int n = i / WP64, k = i % WP64;
+        s.w3[i] = (n < MLP_OUT && k < MLP_HID) ? __float2bfloat16_rn(P[OFF_W3 + n * MLP_HID + k]) : z;
+    }
+    for (int i = threadIdx.x; i < MLP_HID; i += blockDim.x) {
+        s.b1[i] = P[OFF_B1 + i];
+        s.b2[i] = P[OFF_B2 + i];
+    }
+    if (threadIdx.x < 8) s.b3[threadIdx.x] = threadIdx.x < MLP_OUT ? P[OFF_B3 + threadIdx.x] : 0.f;
+    if (threadIdx.x < 16) {
+        const int j = threadIdx.x;
+        s.mx[j] = j < MLP_IN ? stats[j] : 0.f;
+        s.sx[j] = j < MLP_IN ? stats[MLP_IN + j] : 1.f;
+    }
+    if (threadIdx.x < 4) {
+        const int j = threadIdx.x;
+        s.my[j] = j < MLP_OUT ? stats[2 * MLP_IN + j] : 0.f;
+        s.sy[j] = j < MLP_OUT ? stats[2 * MLP_IN + MLP_OUT + j] : 1.f;
+    }
+}
+
+// ------------------------------------------------------------------------- per-warp network
+
+// Operand fragment of 16 standardised input rows (rows r0 = base + g and r0 + 8, columns
+// 2c, 2c+1 and 2c+8, 2c+9; columns 12..15 are zero padding). Rows at or past n are zero.
+__device__ __forceinline__ void mlp_load_x(const MlpW &s, const float *feat, const int32_t *rows, int64_t n,
+                                           int64_t base, uint32_t (&ax)[4])
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int64_t r = base + g + 8 * h;
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (r < n) {
+            const float *x = feat + (int64_t)MLP_IN * (rows ? (int64_t)rows[r] : r);
+            const int k0 = 2 * c, k1 = 8 + 2 * c;
+            v[0] = (x[k0] - s.mx[k0]) / s.sx[k0];
+            v[1] = (x[k0 + 1] - s.mx[k0 + 1]) / s.sx[k0 + 1];
+            if (k1 < MLP_IN) {
+                v[2] = (x[k1] - s.mx[k1]) / s.sx[k1];
+                v[3] = (x[k1 + 1] - s.mx[k1 + 1]) / s.sx[k1 + 1];
+            }
+        }
+        ax[h] = pack_bf16(v[0], v[1]);      // a0a1 (row g) / a2a3 (row g+8)
+        ax[2 + h] = pack_bf16(v[2], v[3]);  // a4a5 / a6a7
+    }
+}
+
+// bias + ReLU of a 16x64 accumulator, as BF16 operand fragments of the next layer;
+// mask bit (4 nt + e) records Z > 0. With `store`, the BF16 activations are also written
+// to the warp's 16 shared-memory rows.
+__device__ __forceinline__ void mlp_relu_pack(float (&acc)[8][4], uint32_t (&a)[4][4], uint32_t &mask,
+                                              __nv_bfloat16 *store)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    mask = 0u;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        float h[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const bool pos = acc[nt][e] > 0.f;
+            mask |= (pos ? 1u : 0u) << (4 * nt + e);
+            h[e] = pos ? acc[nt][e] : 0.f;
+        }
+        const uint32_t lo = pack_bf16(h[0], h[1]), hi = pack_bf16(h[2], h[3]);
+        a[nt >> 1][(nt & 1) * 2] = lo;
+        a[nt >> 1][(nt & 1) * 2 + 1] = hi;
+        if (store) {
+            st_pair(store, g, WP64, 8 * nt + 2 * c, lo);
+            st_pair(store, g + 8, WP64, 8 * nt + 2 * c, hi);
+        }
+    }
+}
+
+// Z = A (16 x 16 kk) * W^T + bias, W as [64][pitch] BF16 rows (B[k][n] = W[n][k])
+template <int KSTEPS, int PITCH>
+__device__ __forceinline__ void mlp_layer64(const uint32_t (&a)[KSTEPS][4], const __nv_bfloat16 *W, const float *bias,
+                                            float (&acc)[8][4])
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const float b0 = bias ? bias[8 * nt + 2 * c] : 0.f, b1 = bias ? bias[8 * nt + 2 * c + 1] : 0.f;
+        acc[nt][0] = b0;
+        acc[nt][1] = b1;
+        acc[nt][2] = b0;
+        acc[nt][3] = b1;
+        const uint32_t *row = reinterpret_cast<const uint32_t *>(W + (8 * nt + g) * PITCH);
+#pragma unroll
+        for (int kk = 0; kk < KSTEPS; ++kk) mma_bf16(acc[nt], a[kk], row[8 * kk + c], row[8 * kk + 4 + c]);
+    }
+}
+
+// The forward pass of one warp's 16 rows: y (16 x 8 accumulator, outputs 0..2 real) and
+// the ReLU masks; optionally stores X, H1, H2 (BF16) for the weight gradients.
+__device__ __forceinline__ void mlp_forward(const MlpW &s, const uint32_t (&ax)[4], float (&y)[4], uint32_t &m1,
+                                            uint32_t &m2, uint32_t (&a2)[4][4], __nv_bfloat16 *h1s,
+                                            __nv_bfloat16 *h2s)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    float acc[8][4];
+    const uint32_t ax1[1][4] = {{ax[0], ax[1], ax[2], ax[3]}};
+    mlp_layer64<1, WP16>(ax1, s.w1, s.b1, acc);
+    uint32_t a1[4][4];
+    mlp_relu_pack(acc, a1, m1, h1s);
+    mlp_layer64<4, WP64>(a1, s.w2, s.b2, acc);
+    mlp_relu_pack(acc, a2, m2, h2s);
+    y[0] = s.b3[2 * c];
+    y[1] = s.b3[2 * c + 1];
+    y[2] = y[0];
+    y[3] = y[1];
+    const uint32_t *row = reinterpret_cast<const uint32_t *>(s.w3 + g * WP64);
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) mma_bf16(y, a2[kk], row[8 * kk + c], row[8 * kk + 4 + c]);
+}
+
+// ------------------------------------------------------------------------- inference
+
+// dv0 = dv_prev + sd_y * net(standardised feat) + mu_y; rows with fixed[r] != 0 get 0.
+__global__ void __launch_bounds__(MLP_THREADS) mlp_infer_kernel(int64_t n, const float *params, const float *stats,
+                                                                const float *feat, const float *dv_prev,
+                                                                const uint8_t *fixed, float *dv0)
+{
+    __shared__ MlpW s;
+    mlp_stage(s, params, stats, false);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    const int64_t nwarps = (int64_t)gridDim.x * MLP_WARPS;
+    for (int64_t t = (int64_t)blockIdx.x * MLP_WARPS + (threadIdx.x >> 5); t * 16 < n; t += nwarps) {
+        const int64_t base = 16 * t;
+        uint32_t ax[4], a2[4][4], m1, m2;
+        float y[4];
+        mlp_load_x(s, feat, nullptr, n, base, ax);
+        mlp_forward(s, ax, y, m1, m2, a2, nullptr, nullptr);
+        if (c < 2) {  // lanes c = 0 hold outputs 0, 1; c = 1 holds output 2
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t r = base + g + 8 * h;
+                if (r >= n) continue;
+                const bool fx = fixed && fixed[r];
+                for (int e = 0; e < 2; ++e) {
+                    const int o = 2 * c + e;
+                    if (o >= MLP_OUT) break;
+                    const float d = dv_prev ? dv_prev[3 * r + o] : 0.f;
+                    dv0[3 * r + o] = fx ? 0.f : fmaf(y[2 * h + e], s.sy[o], s.my[o]) + d;
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------- training
+
+struct MlpTrainSmem {
+    MlpW w;
+    __nv_bfloat16 xs[MLP_TILE * WP16];
+    __nv_bfloat16 h1[MLP_TILE * WP64];
+    __nv_bfloat16 h2[MLP_TILE * WP64];
+    __nv_bfloat16 dz1[MLP_TILE * WP64];
+    __nv_bfloat16 dz2[MLP_TILE * WP64];
+    __nv_bfloat16 dy[MLP_TILE * WP16];
+    float db[MLP_WARPS][2 * MLP_HID + 8];
+    double loss[MLP_WARPS];
+};
+
+// One CTA per block of tiles: forward and back-propagation of each 128-row tile, then
+// the tile's weight gradients as MMAs over its rows; writes the CTA's gradient and loss
+// partials. The target of a row is its step's dv minus dv_prev (features 3..5),
+// standardised; dL/dy = (y - t) / n_total for L = 1/(2 n_total) sum (y - t)^2.
+__global__ void __launch_bounds__(MLP_THREADS) mlp_train_kernel(int64_t n, const int32_t *rows, const float *params,
+                                                                const float *stats, const float *feat,
+                                                                const float *target, float *part, double *loss_part)
+{
+    extern __shared__ __align__(128) unsigned char mlp_smem_raw[];
+    MlpTrainSmem &S = *reinterpret_cast<MlpTrainSmem *>(mlp_smem_raw);
+    mlp_stage(S.w, params, stats, true);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    // zero the padding columns that no fragment store writes (x 12..15 stay from the pack,
+    // dY 8..15 are written as zero pairs below)
+    __syncthreads();
+    const float inv_n = 1.f / (float)n;
+    float gw2[4][4] = {}, gw1[4] = {}, gw3[4] = {};
+    float db1[8][2] = {}, db2[8][2] = {}, db3[2] = {0.f, 0.f};
+    double loss = 0.0;
+    const int64_t ntiles = (n + MLP_TILE - 1) / MLP_TILE;
+    __nv_bfloat16 *xs = S.xs + 16 * warp * WP16, *h1 = S.h1 + 16 * warp * WP64, *h2 = S.h2 + 16 * warp * WP64;
+    __nv_bfloat16 *dz1 = S.dz1 + 16 * warp * WP64, *dz2 = S.dz2 + 16 * warp * WP64, *dys = S.dy + 16 * warp * WP16;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t base = tile * MLP_TILE + 16 * warp;
+        // ---- forward
+        uint32_t ax[4], a[4][4], m1, m2;
+        float y[4];
+        mlp_load_x(S.w, feat, rows, n, base, ax);
+        st_pair(xs, g, WP16, 2 * c, ax[0]);
+        st_pair(xs, g + 8, WP16, 2 * c, ax[1]);
+        st_pair(xs, g, WP16, 8 + 2 * c, ax[2]);
+        st_pair(xs, g + 8, WP16, 8 + 2 * c, ax[3]);
+        mlp_forward(S.w, ax, y, m1, m2, a, h1, h2);
+        // ---- output error (columns 2c, 2c+1 of rows g, g+8)
+        float dyv[4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t r = base + g + 8 * h;
+            for (int e = 0; e < 2; ++e) {
+                const int o = 2 * c + e;
+                float d = 0.f;
+                if (r < n && o < MLP_OUT) {
+                    const int64_t R = rows ? (int64_t)rows[r] : r;
+                    const float raw = target[3 * R + o] - feat[MLP_IN * R + 3 + o];  // dv - dv_prev
+                    const float tn = (raw - S.w.my[o]) / S.w.sy[o];
+                    const float err = y[2 * h + e] - tn;
+                    loss += (double)err * (double)err;
+                    d = err * inv_n;
+                }
+                dyv[2 * h + e] = d;
+            }
+        }
+        db3[0] += dyv[0] + dyv[2];
+        db3[1] += dyv[1] + dyv[3];
+        const uint32_t ady[4] = {pack_bf16(dyv[0], dyv[1]), pack_bf16(dyv[2], dyv[3]), 0u, 0u};
+        st_pair(dys, g, WP16, 2 * c, ady[0]);
+        st_pair(dys, g + 8, WP16, 2 * c, ady[1]);
+        st_pair(dys, g, WP16, 8 + 2 * c, 0u);
+        st_pair(dys, g + 8, WP16, 8 + 2 * c, 0u);
+        // ---- dZ2 = (dY W3) * [Z2 > 0]
+        float acc[8][4];
+        const uint32_t ady1[1][4] = {{ady[0], ady[1], ady[2], ady[3]}};
+        mlp_layer64<1, WP16>(ady1, S.w.w3t, nullptr, acc);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (!((m2 >> (4 * nt + e)) & 1u)) acc[nt][e] = 0.f;
+            db2[nt][0] += acc[nt][0] + acc[nt][2];
+            db2[nt][1] += acc[nt][1] + acc[nt][3];
+            const uint32_t lo = pack_bf16(acc[nt][0], acc[nt][1]), hi = pack_bf16(acc[nt][2], acc[nt][3]);
+            a[nt >> 1][(nt & 1) * 2] = lo;
+            a[nt >> 1][(nt & 1) * 2 + 1] = hi;
+            st_pair(dz2, g, WP64, 8 * nt + 2 * c, lo);
+            st_pair(dz2, g + 8, WP64, 8 * nt + 2 * c, hi);
+        }
+        // ---- dZ1 = (dZ2 W2) * [Z1 > 0]
+        mlp_layer64<4, WP64>(a, S.w.w2t, nullptr, acc);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (!((m1 >> (4 * nt + e)) & 1u)) acc[nt][e] = 0.f;
+            db1[nt][0] += acc[nt][0] + acc[nt][2];
+            db1[nt][1] += acc[nt][1] + acc[nt][3];
+            st_pair(dz1, g, WP64, 8 * nt + 2 * c, pack_bf16(acc[nt][0], acc[nt][1]));
+            st_pair(dz1, g + 8, WP64, 8 * nt + 2 * c, pack_bf16(acc[nt][2], acc[nt][3]));
+        }
+        __syncthreads();
+        // ---- weight gradients over the tile's 128 rows: dW = dZ^T H (K = rows)
+        // warp w: dW2 rows 16 (w/2).. (4 n-tiles from 32 (w%2)), dW1 rows 16 (w/2).. (n-tile w%2),
+        // dW3 (outputs padded to 16) n-tile w
+        const int mt = warp >> 1, i4 = lane >> 3, r8 = lane & 7;
+#pragma unroll 2
+        for (int ks = 0; ks < MLP_TILE / 16; ++ks) {
+            const int rA = 16 * ks + (i4 >> 1) * 8 + r8;  // rows of the transposed A operand
+            uint32_t af[4];
+            // dW2
+            ldsm_x4_t(af, S.dz2 + rA * WP64 + 16 * mt + (i4 & 1) * 8);
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) {
+                uint32_t bf[4];
+                const int n0 = 32 * (warp & 1) + 16 * jj;
+                ldsm_x4_t(bf, S.h1 + (16 * ks + (i4 & 1) * 8 + r8) * WP64 + n0 + (i4 >> 1) * 8);
+                mma_bf16(gw2[2 * jj], af, bf[0], bf[1]);
+                mma_bf16(gw2[2 * jj + 1], af, bf[2], bf[3]);
+            }
+            // dW1
+            ldsm_x4_t(af, S.dz1 + rA * WP64 + 16 * mt + (i4 & 1) * 8);
+            {
+                uint32_t b0, b1;
+                ldsm_x2_t(b0, b1, S.xs + (16 * ks + (i4 & 1) * 8 + r8) * WP16 + 8 * (warp & 1));
+                mma_bf16(gw1, af, b0, b1);
+            }
+            // dW3
+            ldsm_x4_t(af, S.dy + rA * WP16 + (i4 & 1) * 8);
+            {
+                uint32_t b0, b1;
+                ldsm_x2_t(b0, b1, S.h2 + (16 * ks + (i4 & 1) * 8 + r8) * WP64 + 8 * warp);
+                mma_bf16(gw3, af, b0, b1);
+            }
+        }
+        __syncthreads();
+    }
+    // ---- write this CTA's partials
+    float *out = part + (int64_t)blockIdx.x * PC_MLP_NPARAMS;
+    {
+        // dW2 tile (mt, nt): rows 16 mt + g (+8), columns 8 nt + 2c (+1)
+        const int mt = warp >> 1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int nt = 4 * (warp & 1) + j;
+            const int r0 = 16 * mt + g, col = 8 * nt + 2 * c;
+            out[OFF_W2 + r0 * MLP_HID + col] = gw2[j][0];
+            out[OFF_W2 + r0 * MLP_HID + col + 1] = gw2[j][1];
+            out[OFF_W2 + (r0 + 8) * MLP_HID + col] = gw2[j][2];
+            out[OFF_W2 + (r0 + 8) * MLP_HID + col + 1] = gw2[j][3];
+        }
+        // dW1 tile: rows 16 mt + g (+8), input columns 8 (w%2) + 2c (+1), only inputs < 12
+        const int col1 = 8 * (warp & 1) + 2 * c;
+        const int r1 = 16 * mt + g;
+        for (int e = 0; e < 2; ++e) {
+            if (col1 + e < MLP_IN) {
+                out[OFF_W1 + r1 * MLP_IN + col1 + e] = gw1[e];
+                out[OFF_W1 + (r1 + 8) * MLP_IN + col1 + e] = gw1[2 + e];
+            }
+        }
+        // dW3 tile: outputs g (< 3), hidden columns 8 w + 2c (+1)
+        if (g < MLP_OUT) {
+            out[OFF_W3 + g * MLP_HID + 8 * warp + 2 * c] = gw3[0];
+            out[OFF_W3 + g * MLP_HID + 8 * warp + 2 * c + 1] = gw3[1];
+        }
+    }
+    // bias gradients: columns summed over the rows held by lanes of equal c, then warps in order
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+#pragma unroll
+            for (int o = 4; o < 32; o <<= 1) {
+                db1[nt][e] += __shfl_xor_sync(0xffffffffu, db1[nt][e], o);
+                db2[nt][e] += __shfl_xor_sync(0xffffffffu, db2[nt][e], o);
+            }
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) db3[e] += __shfl_xor_sync(0xffffffffu, db3[e], o);
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    if (lane < 4) {
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+            for (int e = 0; e < 2; ++e) {
+                S.db[warp][8 * nt + 2 * lane + e] = db1[nt][e];
+                S.db[warp][MLP_HID + 8 * nt + 2 * lane + e] = db2[nt][e];
+            }
+        S.db[warp][2 * MLP_HID + 2 * lane] = db3[0];
+        S.db[warp][2 * MLP_HID + 2 * lane + 1] = db3[1];
+    }
+    if (lane == 0) S.loss[warp] = loss;
+    __syncthreads();
+    for (int j = threadIdx.x; j < 2 * MLP_HID + MLP_OUT; j += blockDim.x) {
+        float t = 0.f;
+        for (int w = 0; w < MLP_WARPS; ++w) t += S.db[w][j];
+        const int dst = j < MLP_HID ? OFF_B1 + j : j < 2 * MLP_HID ? OFF_B2 + (j - MLP_HID) : OFF_B3 + (j - 2 * MLP_HID);
+        out[dst] = t;
+    }
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < MLP_WARPS; ++w) t += S.loss[w];
+        loss_part[blockIdx.x] = t;
+    }
+}
+
+// grad = sum of the CTA partials in CTA order (FP64 accumulation); with adam != 0 also the
+// Adam update of the FP32 master weights: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+// p -= lr (m / bc1) / (sqrt(v / bc2) + eps) with bc = 1 - beta^t.
+__global__ void mlp_reduce_adam_kernel(int nparts, const float *part, float *grad, int adam, float *params, float *m,
+                                       float *v, float lr, float beta1, float beta2, float eps, float bc1, float bc2)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= PC_MLP_NPARAMS) return;
+    double acc = 0.0;
+    for (int c = 0; c < nparts; ++c) acc += (double)part[(int64_t)c * PC_MLP_NPARAMS + p];
+    const float gr = (float)acc;
+    if (grad) grad[p] = gr;
+    if (adam) {
+        const float mm = beta1 * m[p] + (1.f - beta1) * gr;
+        const float vv = beta2 * v[p] + (1.f - beta2) * gr * gr;
+        m[p] = mm;
+        v[p] = vv;
+        params[p] -= lr * (mm / bc1) / (sqrtf(vv / bc2) + eps);
+    }
+}
+
+__global__ void mlp_loss_sum_kernel(int nparts, const double *loss_part, double *loss)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double t = 0.0;
+    for (int c = 0; c < nparts; ++c) t += loss_part[c];
+    *loss = t;
+}
+
+// ------------------------------------------------------------------------- statistics
+
+#define ST_COLS (MLP_IN + MLP_OUT)
+
+// per-block FP64 sums of each column and of its square (rows grid-strided, fixed order)
+__global__ void __launch_bounds__(256) mlp_stats_partial_kernel(int64_t n, const float *feat, const float *target,
+                                                                double *part)
+{
+    __shared__ double s[2 * ST_COLS][8];
+    double acc[2 * ST_COLS];
+#pragma unroll
+    for (int j = 0; j < 2 * ST_COLS; ++j) acc[j] = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int j = 0; j < ST_COLS; ++j) {
+            const double x = j < MLP_IN ? (double)feat[MLP_IN * r + j]
+                                        : (double)target[MLP_OUT * r + j - MLP_IN] - (double)feat[MLP_IN * r + 3 + j - MLP_IN];
+            acc[j] += x;
+            acc[ST_COLS + j] += x * x;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < 2 * ST_COLS; ++j) {
+        double w = acc[j];
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (lane == 0) s[j][warp] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * ST_COLS) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[threadIdx.x][w];
+        part[(int64_t)blockIdx.x * 2 * ST_COLS + threadIdx.x] = t;
+    }
+}
+
+__global__ void mlp_stats_final_kernel(int nparts, int64_t n, const double *part, float *stats)
+{
+    const int j = threadIdx.x;
+    if (j >= ST_COLS) return;
+    double s1 = 0.0, s2 = 0.0;
+    for (int b = 0; b < nparts; ++b) {
+        s1 += part[(int64_t)b * 2 * ST_COLS + j];
+        s2 += part[(int64_t)b * 2 * ST_COLS + ST_COLS + j];
+    }
+    const double mean = s1 / (double)n;
+    const double var = fmax(s2 / (double)n - mean * mean, 0.0);
+    const double sd = fmax(sqrt(var), 1e-12);
+    if (j < MLP_IN) {
+        stats[j] = (float)mean;
+        stats[MLP_IN + j] = (float)sd;
+    } else {
+        stats[2 * MLP_IN + (j - MLP_IN)] = (float)mean;
+        stats[2 * MLP_IN + MLP_OUT + (j - MLP_IN)] = (float)sd;
+    }
+}
+
+// ------------------------------------------------------------------------- features
+
+__global__ void mlp_features_kernel(int V, const float *v, const float *dv_prev, const float *b, const float *mass,
+                                    float inv_h, float g0, float g1, float g2, const int32_t *erp,
+                                    const int32_t *ecol, float *feat)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= V) return;
+    float *f = feat + (int64_t)MLP_IN * i;
+    const float m = mass[i];
+    const float inv_m = m > 0.f ? 1.f / m : 0.f;
+    const float g[3] = {g0, g1, g2};
+    float ring[3] = {0.f, 0.f, 0.f};
+    const int e0 = erp[i], e1 = erp[i + 1];
+    for (int e = e0; e < e1; ++e) {
+        const int j = ecol[e];
+        for (int d = 0; d < 3; ++d) ring[d] += dv_prev[3ll * j + d];
+    }
+    const float inv_deg = e1 > e0 ? 1.f / (float)(e1 - e0) : 0.f;
+    for (int d = 0; d < 3; ++d) {
+        f[d] = v[3ll * i + d];
+        f[3 + d] = dv_prev[3ll * i + d];
+        f[6 + d] = (b[3ll * i + d] * inv_h - m * g[d]) * inv_m;
+        f[9 + d] = ring[d] * inv_deg;
+    }
+}
+
+// ------------------------------------------------------------------------- host side
+
+struct pc_mlp {
+    int device = 0;
+    int num_sms = 0;
+    int max_parts = 0;
+    float *part = nullptr;     // [max_parts][NPARAMS]
+    double *loss_part = nullptr;
+    double *loss = nullptr;    // device scalar
+    double *h_loss = nullptr;  // pinned mirror
+    double *stat_part = nullptr;
+    float *m = nullptr, *v = nullptr;  // Adam moments
+    int64_t t = 0;                     // Adam steps taken
+};
+
+static size_t train_smem_bytes() { return sizeof(MlpTrainSmem); }
+
+extern "C" pc_status pc_mlp_create(pc_mlp **out)
+{
+    if (!out) return PC_ERR_ARG;
+    *out = nullptr;
+    pc_mlp *M = new pc_mlp();
+    auto fail = [&](cudaError_t e, const char *what) {
+        pc_note_cuda_error(e, what, __FILE__, __LINE__);
+        pc_mlp_destroy(M);
+        return PC_ERR_CUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaGetDevice(&M->device)) != cudaSuccess) return fail(e, "cudaGetDevice");
+    if ((e = cudaDeviceGetAttribute(&M->num_sms, cudaDevAttrMultiProcessorCount, M->device)) != cudaSuccess)
+        return fail(e, "cudaDeviceGetAttribute");
+    M->max_parts = 2 * M->num_sms;
+    if ((e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)train_smem_bytes())) != cudaSuccess)
+        return fail(e, "cudaFuncSetAttribute");
+    if ((e = cudaMalloc(&M->part, sizeof(float) * PC_MLP_NPARAMS * (size_t)M->max_parts)) != cudaSuccess)
+        return fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&M->loss_part, sizeof(double) * (size_t)M->max_parts)) != cudaSuccess)
+        return fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&M->loss, sizeof(double))) != cudaSuccess) return fail(e, "cudaMalloc");
+    if ((e = cudaMallocHost(&M->h_loss, sizeof(double))) != cudaSuccess) return fail(e, "cudaMallocHost");
+    if ((e = cudaMalloc(&M->stat_part, sizeof(double) * 2 * ST_COLS * (size_t)M->max_parts)) != cudaSuccess)
+        return fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&M->m, sizeof(float) * PC_MLP_NPARAMS)) != cudaSuccess) return fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&M->v, sizeof(float) * PC_MLP_NPARAMS)) != cudaSuccess) return fail(e, "cudaMalloc");
+    if ((e = cudaMemset(M->m, 0, sizeof(float) * PC_MLP_NPARAMS)) != cudaSuccess) return fail(e, "cudaMemset");
+    if ((e = cudaMemset(M->v, 0, sizeof(float) * PC_MLP_NPARAMS)) != cudaSuccess) return fail(e, "cudaMemset");
+    *out = M;
+    return PC_OK;
+}
+
+extern "C" pc_status pc_mlp_destroy(pc_mlp *M)
+{
+    if (!M) return PC_OK;
+    cudaFree(M->part);
+    cudaFree(M->loss_part);
+    cudaFree(M->loss);
+    if (M->h_loss) cudaFreeHost(M->h_loss);
+    cudaFree(M->stat_part);
+    cudaFree(M->m);
+    cudaFree(M->v);
+    delete M;
+    return PC_OK;
+}
+
+extern "C" pc_status pc_mlp_reset(pc_mlp *M, void *stream)
+{
+    if (!M) return PC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    PC_CUDA_TRY(cudaMemsetAsync(M->m, 0, sizeof(float) * PC_MLP_NPARAMS, st));
+    PC_CUDA_TRY(cudaMemsetAsync(M->v, 0, sizeof(float) * PC_MLP_NPARAMS, st));
+    M->t = 0;
+    return PC_OK;
+}
+
+#define MLP_LAUNCH(kernel, grid, block, smem, stream, ...)                           \
+    do {                                                                           \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                \
+        cudaError_t _le = cudaGetLastError();                                      \
+        if (_le != cudaSuccess) {                                                  \
+            pc_note_cuda_error(_le, #kernel, __FILE__, __LINE__);                  \
+            return PC_ERR_CUDA;                                                    \
+        }                                                                          \
+    } while (0)
+
+extern "C" pc_status pc_mlp_stats(pc_mlp *M, int64_t n, const float *feat, const float *target, float *stats,
+                                  void *stream)
+{
+    if (!M || n <= 0 || !feat || !target || !stats) return PC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int grid = (int)std::min<int64_t>(M->max_parts, (n + 255) / 256);
+    MLP_LAUNCH(mlp_stats_partial_kernel, grid, 256, 0, st, n, feat, target, M->stat_part);
+    MLP_LAUNCH(mlp_stats_final_kernel, 1, 32, 0, st, grid, n, M->stat_part, stats);
+    return PC_OK;
+}
+
+extern "C" pc_status pc_mlp_infer(int64_t n, const float *params, const float *stats, const float *feat,
+                                  const float *dv_prev, const uint8_t *fixed, float *dv0, void *stream)
+{
+    if (n < 0 || !params || !stats || !feat || !dv0) return PC_ERR_ARG;
+    if (n == 0) return PC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    PC_CUDA_TRY(cudaGetDevice(&dev));
+    PC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t tiles = (n + MLP_TILE - 1) / MLP_TILE;
+    const int grid = (int)std::min<int64_t>(tiles, 4ll * sms);
+    MLP_LAUNCH(mlp_infer_kernel, grid, MLP_THREADS, 0, st, n, params, stats, feat, dv_prev, fixed, dv0);
+    return PC_OK;
+}
+
+static pc_status mlp_grad_impl(pc_mlp *M, int64_t n, const int32_t *rows, const float *params, const float *stats,
+                               const float *feat, const float *target, float *grad, bool adam,
+                               const pc_adam_opts *o, double *loss, cudaStream_t st)
+{
+    if (!M || n <= 0 || !params || !stats || !feat || !target) return PC_ERR_ARG;
+    const int64_t tiles = (n + MLP_TILE - 1) / MLP_TILE;
+    const int grid = (int)std::min<int64_t>(tiles, M->max_parts);
+    MLP_LAUNCH(mlp_train_kernel, grid, MLP_THREADS, train_smem_bytes(), st, n, rows, params, stats, feat, target,
+               M->part, M->loss_part);
+    float lr = 0.f, b1 = 0.f, b2 = 0.f, eps = 0.f, bc1 = 1.f, bc2 = 1.f;
+    if (adam) {
+        M->t += 1;
+        lr = o->lr;
+        b1 = o->beta1;
+        b2 = o->beta2;
+        eps = o->eps;
+        bc1 = (float)(1.0 - pow((double)b1, (double)M->t));
+        bc2 = (float)(1.0 - pow((double)b2, (double)M->t));
+    }
+    MLP_LAUNCH(mlp_reduce_adam_kernel, (PC_MLP_NPARAMS + 255) / 256, 256, 0, st, grid, M->part, grad, adam ? 1 : 0,
+               (float *)params, M->m, M->v, lr, b1, b2, eps, bc1, bc2);
+    if (loss) {
+        MLP_LAUNCH(mlp_loss_sum_kernel, 1, 32, 0, st, grid, M->loss_part, M->loss);
+        PC_CUDA_TRY(cudaMemcpyAsync(M->h_loss, M->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+        PC_CUDA_TRY(cudaStreamSynchronize(st));
+        *loss = 0.5 * *M->h_loss / (double)n;
+    }
+    return PC_OK;
+}
+
+extern "C" pc_status pc_mlp_grad(pc_mlp *M, int64_t n, const int32_t *rows, const float *params, const float *stats,
+                                 const float *feat, const float *target, float *grad, double *loss, void *stream)
+{
+    if (!grad) return PC_ERR_ARG;
+    return mlp_grad_impl(M, n, rows, params, stats, feat, target, grad, false, nullptr, loss, (cudaStream_t)stream);
+}
+
+extern "C" pc_status pc_mlp_train_step(pc_mlp *M, int64_t n, const int32_t *rows, float *params, const float *stats,
+                                       const float *feat, const float *target, const pc_adam_opts *o, double *loss,
+                                       void *stream)
+{
+    if (!o || !(o->lr > 0.f) || !(o->beta1 >= 0.f && o->beta1 < 1.f) || !(o->beta2 >= 0.f && o->beta2 < 1.f) ||
+        !(o->eps > 0.f))
+        return PC_ERR_ARG;
+    return mlp_grad_impl(M, n, rows, params, stats, feat, target, nullptr, true, o, loss, (cudaStream_t)stream);
+}
+
+extern "C" pc_status pc_mlp_adam_apply(pc_mlp *M, float *params, const float *grad, const pc_adam_opts *o,
+                                       void *stream)
+{
+    if (!M || !params || !grad || !o) return PC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the gradient goes through the partial-sum path as a single "CTA"
+    PC_CUDA_TRY(cudaMemcpyAsync(M->part, grad, sizeof(float) * PC_MLP_NPARAMS, cudaMemcpyDeviceToDevice, st));
+    M->t += 1;
+    const float bc1 = (float)(1.0 - pow((double)o->beta1, (double)M->t));
+    const float bc2 = (float)(1.0 - pow((double)o->beta2, (double)M->t));
+    MLP_LAUNCH(mlp_reduce_adam_kernel, (PC_MLP_NPARAMS + 255) / 256, 256, 0, st, 1, M->part, (float *)nullptr, 1,
+               params, M->m, M->v, o->lr, o->beta1, o->beta2, o->eps, bc1, bc2);
+    return PC_OK;
+}
+
+extern "C" pc_status pc_mlp_features(pc_ctx *ctx, const float *v, const float *dv_prev, const float *b, float h,
+                                     float *feat, void *stream)
+{
+    if (!ctx || !v || !dv_prev || !b || !feat || !(h > 0.f)) return PC_ERR_ARG;
+    PC_LAUNCH(ctx, mlp_features_kernel, pc_blocks(ctx->V, 256), 256, 0, (cudaStream_t)stream, ctx->V, v, dv_prev, b,
+              ctx->mass, 1.f / h, ctx->mat.gravity[0], ctx->mat.gravity[1], ctx->mat.gravity[2], ctx->erp, ctx->ecol,
+              feat);
+    return PC_OK;
+}
+
+extern "C" pc_status pc_set_warm_mlp(pc_ctx *ctx, const float *params, const float *stats)
+{
+    if (!ctx || (params == nullptr) != (stats == nullptr)) return PC_ERR_ARG;
+    if (params && !ctx->mlp_feat) {
+        PC_CUDA_TRY(cudaMalloc(&ctx->mlp_feat, sizeof(float) * MLP_IN * (size_t)ctx->V));
+        PC_CUDA_TRY(cudaMalloc(&ctx->mlp_dv, sizeof(float) * 3 * (size_t)ctx->V));
+    }
+    ctx->mlp_params = params;
+    ctx->mlp_stats = stats;
+    return PC_OK;
+}
+
+void pc_mlp_ctx_free(pc_ctx *c)
+{
+    cudaFree(c->mlp_feat);
+    cudaFree(c->mlp_dv);
+    c->mlp_feat = nullptr;
+    c->mlp_dv = nullptr;
+}
+
+// The step's initial guess (ctx->A_dv holds the previous step's dv, or zeros). Features
+// are written to feat_out when given. PC_WARM_MLP evaluates the zero, previous and
+// learned guesses g in FP64 and keeps the one with the lowest CG energy
+// 1/2 g.A g - b.g, which differs from the energy of the solution by half the squared
+// A-norm of the guess's error: the error measure that CG's convergence is bounded by.
+// Their relative residuals |b - A g| / |b| are reported too.
+pc_status pc_warm_guess(pc_ctx *c, const pc_bsr *A, const float *v, float h, int32_t mode, float *feat_out,
+                        int32_t *guess, double *guess_res, double *guess_energy, cudaStream_t st)
+{
+    const size_t vb = sizeof(float) * 3 * (size_t)c->V;
+    for (int k = 0; k < 3; ++k) {
+        guess_res[k] = -1.0;
+        guess_energy[k] = 0.0;
+    }
+    float *feat = feat_out ? feat_out : c->mlp_feat;
+    if (mode == PC_WARM_MLP && (!c->mlp_params || !c->mlp_feat)) return PC_ERR_ARG;
+    if (feat) PC_TRY(pc_mlp_features(c, v, c->A_dv, c->A_b, h, feat, st));
+    if (mode == PC_WARM_PREV) {
+        *guess = c->has_prev_dv ? PC_WARM_PREV : PC_WARM_ZERO;
+        return PC_OK;
+    }
+    if (mode != PC_WARM_MLP) {
+        *guess = PC_WARM_ZERO;
+        PC_CUDA_TRY(cudaMemsetAsync(c->A_dv, 0, vb, st));
+        return PC_OK;
+    }
+    PC_TRY(pc_mlp_infer(c->V, c->mlp_params, c->mlp_stats, feat, c->A_dv, c->pinned, c->mlp_dv, st));
+    double rr_prev = 0.0, rr_mlp = 0.0, bb = 0.0, e_prev = 0.0, e_mlp = 0.0;
+    PC_TRY(pc_guess_eval(c, A, c->A_vals, c->A_dres, c->A_b, c->A_dv, &rr_prev, &bb, &e_prev, st));
+    PC_TRY(pc_guess_eval(c, A, c->A_vals, c->A_dres, c->A_b, c->mlp_dv, &rr_mlp, &bb, &e_mlp, st));
+    const double nb = sqrt(bb);
+    guess_res[0] = bb > 0 ? 1.0 : 0.0;
+    guess_res[1] = bb > 0 ? sqrt(rr_prev) / nb : 0.0;
+    guess_res[2] = bb > 0 ? sqrt(rr_mlp) / nb : 0.0;
+    guess_energy[1] = e_prev;
+    guess_energy[2] = e_mlp;
+    int best = 0;
+    if (c->has_prev_dv && e_prev < guess_energy[best]) best = 1;
+    if (std::isfinite(e_mlp) && e_mlp < guess_energy[best]) best = 2;
+    if (best == 0) {
+        *guess = PC_WARM_ZERO;
+        PC_CUDA_TRY(cudaMemsetAsync(c->A_dv, 0, vb, st));
+    } else if (best == 1) {
+        *guess = PC_WARM_PREV;
+    } else {
+        *guess = PC_WARM_MLP;
+        PC_CUDA_TRY(cudaMemcpyAsync(c->A_dv, c->mlp_dv, vb, cudaMemcpyDeviceToDevice, st));
+    }
+    return PC_OK;
+}

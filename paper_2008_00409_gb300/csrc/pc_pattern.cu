@@ -233,6 +233,16 @@ __global__ void static_keys_kernel(int V, int T, int H, const int32_t *tri, cons
     }
 }
 
+// ordered vertex pairs (a, b), a != b, of every triangle: key a * V + b (6 per triangle)
+__global__ void edge_keys_kernel(int T, int V, const int32_t *tri, uint64_t *keys)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 6ll * T) return;
+    const int t = (int)(i / 6), k = (int)(i % 6);
+    const int a = k >> 1, b = (a + 1 + (k & 1)) % 3;  // (0,1) (0,2) (1,2) (1,0) (2,0) (2,1)
+    keys[i] = (uint64_t)tri[3 * t + a] * (uint64_t)V + (uint64_t)tri[3 * t + b];
+}
+
 __global__ void unique_flag_kernel(int64_t n, const uint64_t *keys, int32_t *flag)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -264,8 +274,9 @@ static void free_ctx(pc_ctx *c)
 {
     if (!c) return;
     pc_batched_free(c);
+    pc_mlp_ctx_free(c);
     void *ptrs[] = {c->tri, c->rest, c->tri_dmi, c->tri_area, c->tri_rgram, c->mass, c->pinned, c->hinge, c->hcoef,
-                    c->hrest, c->srp, c->scol, c->vinc_ptr, c->vinc, c->dkeys, c->dnew, c->dflag, c->dscan, c->ckeys,
+                    c->hrest, c->srp, c->scol, c->erp, c->ecol, c->vinc_ptr, c->vinc, c->dkeys, c->dnew, c->dflag, c->dscan, c->ckeys,
                     c->cinc, c->cinc_ptr, c->tri_buf, c->hinge_buf, c->cont_buf, c->r, c->z, c->p0, c->p1, c->q,
                     c->dinv, c->dtmp, c->rhs32, c->x64, c->r64, c->partials, c->sc, c->A_rp, c->A_ci, c->A_vals, c->A_dres,
                     c->A_b, c->A_dv, c->h_state, c->h_pairs, c->h_w, c->sort.keys_alt, c->sort.vals_alt, c->sort.hist,
@@ -407,6 +418,30 @@ static pc_status create_impl(pc_ctx *c, const int32_t *tris, const float *rest, 
         compact_cols_kernel<<<pc_blocks(nkeys, 256), 256, 0, st>>>(nkeys, keys, flag, pos, V, c->scol, ukeys);
         c->launches++;
         rowptr_from_keys_kernel<<<pc_blocks(V + 1ll, 256), 256, 0, st>>>(V, ukeys, c->snnz, c->srp);
+        c->launches++;
+        // edge one-rings (mesh edge neighbours of each vertex, sorted): the neighbourhood
+        // of the learned warm start's features
+        const int64_t nek = 6ll * T;
+        if ((s = dalloc(&c->erp, V + 1ll)) != PC_OK) break;
+        if (nek > 0) {
+            edge_keys_kernel<<<pc_blocks(nek, 256), 256, 0, st>>>(T, V, c->tri, keys);
+            c->launches++;
+            if ((s = pc_radix_sort(c, keys, nullptr, nek, kbits, st)) != PC_OK) break;
+            unique_flag_kernel<<<pc_blocks(nek, 256), 256, 0, st>>>(nek, keys, flag);
+            c->launches++;
+            if ((s = pc_exclusive_scan(c, flag, pos, nek, st)) != PC_OK) break;
+            PC_CUDA_TRY(cudaMemcpyAsync(c->h_count, pos + nek, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            PC_CUDA_TRY(cudaStreamSynchronize(st));
+            c->enn = *(int32_t *)c->h_count;
+        } else {
+            c->enn = 0;
+        }
+        if ((s = dalloc(&c->ecol, c->enn)) != PC_OK) break;
+        if (nek > 0) {
+            compact_cols_kernel<<<pc_blocks(nek, 256), 256, 0, st>>>(nek, keys, flag, pos, V, c->ecol, ukeys);
+            c->launches++;
+        }
+        rowptr_from_keys_kernel<<<pc_blocks(V + 1ll, 256), 256, 0, st>>>(V, ukeys, c->enn, c->erp);
         c->launches++;
         if ((s = pc_read_errors(c, st, &bits)) != PC_OK) break;
         if (bits) { s = errors_to_status(bits); break; }

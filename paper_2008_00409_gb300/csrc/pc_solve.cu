@@ -710,6 +710,57 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
     return status;
 }
 
+// FP64 measures of an FP32 guess x of A x = b: |b - A x|^2, |b|^2, x.(A x) and b.x (so
+// the CG energy 1/2 x.A x - b.x); the last block leaves them in the scalars' rr, bb, pq
+// and rz slots (before any solve initialises them).
+template <bool DIFF>
+__global__ void __launch_bounds__(EW_THREADS) guess_eval_kernel(int V, const int32_t *__restrict__ rp,
+                                                                const int32_t *__restrict__ ci,
+                                                                const float *__restrict__ vals,
+                                                                const float *__restrict__ dres,
+                                                                const float *__restrict__ b,
+                                                                const float *__restrict__ x, double *partials,
+                                                                pc_scalars *sc)
+{
+    double rr = 0.0, bb = 0.0, xax = 0.0, bx = 0.0;
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
+        double acc[3];
+        row_product64<float, DIFF>(row, rp, ci, vals, dres, x, acc);
+        for (int a2 = 0; a2 < 3; ++a2) {
+            const double bv = (double)b[3ll * row + a2], xv = (double)x[3ll * row + a2];
+            const double rv = bv - acc[a2];
+            rr += rv * rv;
+            bb += bv * bv;
+            xax += xv * acc[a2];
+            bx += bv * xv;
+        }
+    }
+    double v[4] = {rr, bb, xax, bx};
+    if (last_block_reduce(v, 4, partials, &sc->counter) && threadIdx.x == 0) {
+        sc->rr = v[0];
+        sc->bb = v[1];
+        sc->pq = v[2];
+        sc->rz = v[3];
+    }
+}
+
+// Residual and CG energy of an FP32 guess (host results; synchronizes):
+// rr = |b - A x|^2, bb = |b|^2, energy = 1/2 x.(A x) - b.x.
+pc_status pc_guess_eval(pc_ctx *c, const pc_bsr *A, const float *vals, const float *dres, const float *b,
+                        const float *x, double *rr, double *bb, double *energy, cudaStream_t st)
+{
+    const int V = c->V;
+    if (dres) PC_LAUNCH(c, guess_eval_kernel<true>, ew_grid(c, V), EW_THREADS, 0, st, V, A->row_ptr, A->col_idx,
+                        vals, dres, b, x, c->partials, c->sc);
+    else PC_LAUNCH(c, guess_eval_kernel<false>, ew_grid(c, V), EW_THREADS, 0, st, V, A->row_ptr, A->col_idx, vals,
+                   dres, b, x, c->partials, c->sc);
+    PC_TRY(read_scalars(c, st));
+    *rr = c->sc_host->rr;
+    *bb = c->sc_host->bb;
+    *energy = 0.5 * c->sc_host->pq - c->sc_host->rz;
+    return PC_OK;
+}
+
 pc_status pc_update_state(pc_ctx *c, float *x, float *v, const float *dv, float h, cudaStream_t st)
 {
     const int64_t n = 3ll * c->V;

@@ -20,7 +20,8 @@ c_int32, c_int64, c_float, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, 
 PC_OK, PC_ERR_ARG, PC_ERR_CAPACITY, PC_ERR_NOT_CONVERGED, PC_ERR_NONFINITE, PC_ERR_TIMEOUT, PC_ERR_CUDA, PC_ERR_MESH = range(8)
 PC_PREC_FP32, PC_PREC_MIXED = 0, 1
 PC_PRECOND_JACOBI, PC_PRECOND_BLOCK = 0, 1
-PC_WARM_ZERO, PC_WARM_PREV = 0, 1
+PC_WARM_ZERO, PC_WARM_PREV, PC_WARM_GIVEN, PC_WARM_MLP = 0, 1, 2, 3
+PC_MLP_IN, PC_MLP_HIDDEN, PC_MLP_OUT, PC_MLP_NPARAMS, PC_MLP_NSTATS = 12, 64, 3, 5187, 30
 
 
 class pc_material(ctypes.Structure):
@@ -49,11 +50,16 @@ class pc_solve_info(ctypes.Structure):
 
 
 class pc_step_opts(ctypes.Structure):
-    _fields_ = [("h", c_float), ("solve", pc_solve_opts), ("warm_start", c_int32)]
+    _fields_ = [("h", c_float), ("solve", pc_solve_opts), ("warm_start", c_int32), ("feat_out", c_void_p)]
 
 
 class pc_step_info(ctypes.Structure):
-    _fields_ = [("nnzb", c_int64), ("solve", pc_solve_info)]
+    _fields_ = [("nnzb", c_int64), ("solve", pc_solve_info), ("guess", c_int32), ("pad", c_int32),
+                ("guess_res", c_double * 3), ("guess_energy", c_double * 3)]
+
+
+class pc_adam_opts(ctypes.Structure):
+    _fields_ = [("lr", c_float), ("beta1", c_float), ("beta2", c_float), ("eps", c_float)]
 
 
 class PcError(RuntimeError):
@@ -100,13 +106,27 @@ def _load():
     L.pc_batched_config.argtypes = [c_void_p, P(c_int32), c_void_p]
     L.pc_step_host.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, P(pc_step_opts),
                                P(pc_step_info), c_void_p]
+    L.pc_mlp_features.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_void_p, c_void_p]
+    L.pc_mlp_create.argtypes = [P(c_void_p)]
+    L.pc_mlp_destroy.argtypes = [c_void_p]
+    L.pc_mlp_reset.argtypes = [c_void_p, c_void_p]
+    L.pc_mlp_stats.argtypes = [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]
+    L.pc_mlp_infer.argtypes = [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    L.pc_mlp_grad.argtypes = [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                              P(c_double), c_void_p]
+    L.pc_mlp_train_step.argtypes = [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    P(pc_adam_opts), P(c_double), c_void_p]
+    L.pc_mlp_adam_apply.argtypes = [c_void_p, c_void_p, c_void_p, P(pc_adam_opts), c_void_p]
+    L.pc_set_warm_mlp.argtypes = [c_void_p, c_void_p, c_void_p]
     L.pc_launch_count.restype = c_int64
     L.pc_launch_count.argtypes = [c_void_p]
     L.pc_set_profiling.argtypes = [c_void_p, c_int32]
     L.pc_spmv_stats.argtypes = [c_void_p, P(c_int64), P(c_double), P(c_int64)]
     for name in ("pc_create", "pc_destroy", "pc_get_sizes", "pc_get_rest", "pc_assemble_pattern",
                  "pc_assemble_values", "pc_bsr_spmv", "pc_pcg_solve", "pc_pcg_solve_static", "pc_step", "pc_step_host",
-                 "pc_pcg_solve_batched", "pc_step_batched", "pc_batched_config",
+                 "pc_pcg_solve_batched", "pc_step_batched", "pc_batched_config", "pc_mlp_features", "pc_mlp_create",
+                 "pc_mlp_destroy", "pc_mlp_reset", "pc_mlp_stats", "pc_mlp_infer", "pc_mlp_grad", "pc_mlp_train_step",
+                 "pc_mlp_adam_apply", "pc_set_warm_mlp",
                  "pc_set_profiling", "pc_spmv_stats"):
         getattr(L, name).restype = c_int32
     return L
@@ -316,6 +336,64 @@ def pc_step_host(ctx, x: np.ndarray, v: np.ndarray, pairs: np.ndarray, w: np.nda
     return info, st
 
 
+# --------------------------------------------------------------------------- learned warm start
+
+
+def adam_opts(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8) -> pc_adam_opts:
+    return pc_adam_opts(lr, beta1, beta2, eps)
+
+
+def pc_mlp_features(ctx, v, dv_prev, b, h, feat, stream=None):
+    _check(_lib.pc_mlp_features(ctx, _ptr(v), _ptr(dv_prev), _ptr(b), float(h), _ptr(feat), _stream(stream)),
+           "pc_mlp_features")
+
+
+def pc_mlp_create():
+    m = c_void_p()
+    _check(_lib.pc_mlp_create(ctypes.byref(m)), "pc_mlp_create")
+    return m
+
+
+def pc_mlp_destroy(m):
+    _check(_lib.pc_mlp_destroy(m), "pc_mlp_destroy")
+
+
+def pc_mlp_reset(m, stream=None):
+    _check(_lib.pc_mlp_reset(m, _stream(stream)), "pc_mlp_reset")
+
+
+def pc_mlp_stats(m, n, feat, target, stats, stream=None):
+    _check(_lib.pc_mlp_stats(m, int(n), _ptr(feat), _ptr(target), _ptr(stats), _stream(stream)), "pc_mlp_stats")
+
+
+def pc_mlp_infer(n, params, stats, feat, dv_prev, fixed, dv0, stream=None):
+    _check(_lib.pc_mlp_infer(int(n), _ptr(params), _ptr(stats), _ptr(feat), _ptr(dv_prev), _ptr(fixed), _ptr(dv0),
+                             _stream(stream)), "pc_mlp_infer")
+
+
+def pc_mlp_grad(m, n, rows, params, stats, feat, target, grad, with_loss=True, stream=None):
+    loss = c_double(float("nan"))
+    _check(_lib.pc_mlp_grad(m, int(n), _ptr(rows), _ptr(params), _ptr(stats), _ptr(feat), _ptr(target), _ptr(grad),
+                            ctypes.byref(loss) if with_loss else None, _stream(stream)), "pc_mlp_grad")
+    return loss.value
+
+
+def pc_mlp_train_step(m, n, rows, params, stats, feat, target, opts: pc_adam_opts, with_loss=False, stream=None):
+    loss = c_double(float("nan"))
+    _check(_lib.pc_mlp_train_step(m, int(n), _ptr(rows), _ptr(params), _ptr(stats), _ptr(feat), _ptr(target),
+                                  ctypes.byref(opts), ctypes.byref(loss) if with_loss else None, _stream(stream)),
+           "pc_mlp_train_step")
+    return loss.value
+
+
+def pc_mlp_adam_apply(m, params, grad, opts: pc_adam_opts, stream=None):
+    _check(_lib.pc_mlp_adam_apply(m, _ptr(params), _ptr(grad), ctypes.byref(opts), _stream(stream)), "pc_mlp_adam_apply")
+
+
+def pc_set_warm_mlp(ctx, params, stats):
+    _check(_lib.pc_set_warm_mlp(ctx, _ptr(params), _ptr(stats)), "pc_set_warm_mlp")
+
+
 def pc_launch_count(ctx) -> int:
     return int(_lib.pc_launch_count(ctx))
 
@@ -388,10 +466,11 @@ class Cloth:
         return s
 
     def step(self, pairs=None, w=None, tol=1e-6, precision=PC_PREC_FP32, warm_start=PC_WARM_ZERO, max_iter=20000,
-             dv_out=None, precond=PC_PRECOND_JACOBI, allow_not_converged=False):
+             dv_out=None, precond=PC_PRECOND_JACOBI, allow_not_converged=False, feat_out=None):
         o = pc_step_opts()
         o.h = self.h
         o.solve = solve_opts(tol=tol, max_iter=max_iter, precision=precision, precond=precond)
         o.warm_start = warm_start
+        o.feat_out = _ptr(feat_out)
         info, st = pc_step(self.ctx, self.x, self.v, pairs, w, o, dv_out, allow_not_converged=allow_not_converged)
         return info, st

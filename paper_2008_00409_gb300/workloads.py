@@ -248,6 +248,18 @@ def square_cloth(n: int, *, seed: int, z_jitter: float = 1e-4, size: float = 1.0
                     steps=steps)
 
 
+def training_cloth(n: int, *, seed: int, contact_frac: float = 0.02, steps: int = 250) -> Workload:
+    """n x n square cloth with 1 to 4 pins drawn on its boundary and grid contacts: the
+    trajectories that train the learned warm start."""
+    wl = square_cloth(n, seed=seed, contact_frac=contact_frac, steps=steps, name=f"train{n}-{seed}")
+    ring = np.concatenate([np.arange(n), (n - 1) * n + np.arange(n), n * np.arange(1, n - 1),
+                           n * np.arange(1, n - 1) + n - 1])  # bottom, top, left, right edges
+    k = int(randint(seed, 600, 1, 1, 4)[0])
+    keys = splitmix64(_counters_at(seed, 601, np.arange(ring.size, dtype=np.uint64)))
+    wl.pins = np.sort(ring[np.argsort(keys, kind="stable")[:k]]).astype(np.int32)
+    return wl
+
+
 def stacked_sheets(n: int = 526, layers: int = 3, *, seed: int, gap: float = 5e-4, size: float = 1.0,
                    jitter: float = 0.2, flip_prob: float = 0.1, contact_frac: float = 0.05,
                    steps: int = 10, name: str | None = None) -> Workload:
@@ -445,6 +457,17 @@ def dynamic_square(n: int = 512) -> Workload:
 def paper_scale(n: int = 526, layers: int = 3) -> Workload:
     """Three stacked 526 x 526 sheets (about 1.65M triangles), 5% inter-layer contacts."""
     return stacked_sheets(n, layers, seed=SEED_BASE + 3, steps=10, name=f"stack{layers}x{n}")
+
+
+def warm_start_eval(n: int = 708) -> Workload:
+    """708 x 708 cloth (about 1M triangles), 2% contacts: the learned warm start's test cloth."""
+    return square_cloth(n, seed=SEED_BASE + 5, contact_frac=0.02, steps=10, name=f"square{n}-contacts")
+
+
+def warm_start_training(n: int = 256, count: int = 8, steps: int = 250):
+    """`count` n x n cloths with random boundary pins and 2% contacts, `steps` steps each
+    (8 x 250 = 2,000 integrator steps on 256 x 256 cloths by default)."""
+    return [training_cloth(n, seed=SEED_BASE + 5 + 1000 * (k + 1), steps=steps) for k in range(count)]
 
 
 WORKLOADS = {
