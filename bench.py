@@ -10,6 +10,13 @@ contact pairs) are resident on the device before timing starts.
 Prints one JSON line. With N > 1 (torchrun) every rank runs an independent replica of
 the workload ("replicas only": the path does not shard) and rank 0 reports the
 aggregate over ranks with the slowest rank's time.
+
+Two further forms of the integrator have their own lines (one GPU):
+  --form batched    64 garments (log-uniform 2k..200k triangles) stepped together: one
+                    CUDA graph per step with one persistent batched PCG launch
+  --form warmstart  learned warm start: train on 2,000 integrator steps of 256 x 256
+                    cloths, then step a 708 x 708 cloth with the zero, previous-step and
+                    learned initial guesses (and plain FP32 PCG for comparison)
 """
 from __future__ import annotations
 
@@ -32,7 +39,10 @@ METRIC = "steps/s at 1.65M tris (assemble+PCG to 1e-6); BSR SpMV GB/s vs 8 TB/s"
 FALLBACK_HBM_GBS = 6800.0
 # PCG iterations per step of the paper-scale workload, measured by the CUDA path on
 # GB300 (mixed precision, tol 1e-6); the CPU baseline scales its per-iteration time by it.
-REF_ITERS_PER_STEP = 1500
+REF_ITERS_PER_STEP = 7230
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the PCG SpMV,
+# from one ncu capture of the current kernel on that workload (mean of 3 launches).
+SPMV_DRAM_BYTES = {"stack3x526": 496.2e6 + 11.6e6}
 
 
 def parse():
@@ -48,6 +58,10 @@ def parse():
     ap.add_argument("--precond", default="jacobi", choices=["jacobi", "block"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--form", default="step", choices=["step", "batched", "warmstart"])
+    ap.add_argument("--no-sequential", action="store_true", help="batched form: skip the one-garment-at-a-time comparison")
+    ap.add_argument("--train-steps", type=int, default=2000, help="warmstart form: Adam steps")
+    ap.add_argument("--garments", type=int, default=64, help="batched form: number of garments")
     return ap.parse_args()
 
 
@@ -242,6 +256,7 @@ def run_ours(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = pc.pc_launch_count(cl.ctx)
     pc.pc_spmv_stats(cl.ctx)  # reset
+    pc.pc_assembly_stats(cl.ctx)
     pc.pc_set_profiling(cl.ctx, True)
     iters, rels = [], []
     if world > 1:
@@ -259,6 +274,7 @@ def run_ours(args):
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = pc.pc_launch_count(cl.ctx) - launches0
     n_spmv, spmv_ms, nnzb = pc.pc_spmv_stats(cl.ctx)
+    n_asm, asm_ms = pc.pc_assembly_stats(cl.ctx)
     elapsed = max_over_ranks(elapsed, world)
     value = aggregate_steps_per_s(world, args.steps, elapsed)
 
@@ -314,9 +330,11 @@ def run_ours(args):
                        "contacts_per_step": wl.n_contacts, "precision": args.precision, "tol": args.tol,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (matrix about 440 MB per SpMV)",
-                       "pcg_iters_per_step": float(np.mean(iters)), "max_rel_res": float(np.max(rels))},
+                       "pcg_iters_per_step": float(np.mean(iters)), "max_rel_res": float(np.max(rels)),
+                       "assembly_ms_per_step": asm_ms / max(n_asm, 1)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "frac": (achieved / peak) if achieved else None,
+                         "traffic": SPMV_DRAM_BYTES.get(wl.name),
                          "kernel": "spmv_kernel<true,true> (q = A p, difference form, with p.q)",
                          "bytes_per_launch": spmv_bytes, "peak_source": peak_src,
                          "avg_launch_us": avg_spmv_s * 1e6, "timed_launches": n_spmv},
@@ -328,10 +346,134 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------------------- other forms
+
+
+def _setup_single():
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2008_00409_gb300 import build as cuda_build
+    cuda_build.build()
+    from paper_2008_00409_gb300 import pcloth as pc
+    return torch, pc
+
+
+def run_batched(args):
+    """Batched form: every step advances all garments (pc_step_batched)."""
+    torch, pc = _setup_single()
+    from paper_2008_00409_gb300 import workloads as wk
+    u = wk.garment_batch_union(args.garments)
+    cl = pc.Cloth(u)
+    o = pc.pc_step_opts()
+    o.h = u.h
+    o.solve = pc.solve_opts(tol=args.tol, max_iter=args.max_iter)
+    o.warm_start = pc.PC_WARM_PREV
+    nsteps = args.warmup + args.steps
+    contacts = [cl.contacts_device(k) for k in range(nsteps)]
+    for k in range(args.warmup):
+        pc.pc_step_batched(cl.ctx, cl.x, cl.v, *contacts[k], u.inst_rows, o, allow_not_converged=True)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = pc.pc_launch_count(cl.ctx)
+    its, rels = [], []
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        ev0.record(stream)
+        for k in range(args.warmup, nsteps):
+            infos, _ = pc.pc_step_batched(cl.ctx, cl.x, cl.v, *contacts[k], u.inst_rows, o, allow_not_converged=True)
+            its.append([i.iters for i in infos])
+            rels.append(max(i.rel_res for i in infos))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = pc.pc_launch_count(cl.ctx) - launches0
+    bps, tune_ms = pc.pc_batched_config(cl.ctx)
+    its = np.array(its)
+    seq = None
+    if not args.no_sequential:
+        parts = [pc.Cloth(p) for p in u.parts]
+        pcont = [[pp.contacts_device(k) for k in range(3)] for pp in parts]
+        for pp, cc in zip(parts, pcont):
+            pp.step(*cc[0], tol=args.tol, precision=pc.PC_PREC_MIXED, warm_start=pc.PC_WARM_PREV,
+                    allow_not_converged=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in (1, 2):
+            for pp, cc in zip(parts, pcont):
+                pp.step(*cc[k], tol=args.tol, precision=pc.PC_PREC_MIXED, warm_start=pc.PC_WARM_PREV,
+                        allow_not_converged=True)
+        torch.cuda.synchronize()
+        seq = 2 / (time.perf_counter() - t0)
+        for pp in parts:
+            pp.close()
+    out = {"metric": f"batched steps/s: {len(u.parts)} garments ({u.T / 1e6:.2f}M tris), one persistent PCG launch "
+                     "per step, 1e-6 per garment",
+           "value": args.steps / elapsed, "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": u.name, "garments": len(u.parts), "V": u.V, "T": u.T,
+                      "contacts_per_step": u.n_contacts, "tol": args.tol,
+                      "l2": f"matrix {len(u.tris) * 13 * 40 / 1e6 / 2:.0f} MB (L2 is 129 MB)",
+                      "iters_per_garment_min": int(its.min()), "iters_per_garment_mean": float(its.mean()),
+                      "iters_per_garment_max": int(its.max()), "max_rel_res": float(max(rels)),
+                      "autotuned_ctas_per_sm": bps, "autotune_ms": tune_ms},
+           "sequential_steps_per_s": seq, "gpu_launches": int(launches), "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+
+
+def run_warmstart(args):
+    """Learned warm start: train, then compare initial guesses on the 708 x 708 cloth."""
+    torch, pc = _setup_single()
+    from paper_2008_00409_gb300 import warmstart as ws
+    from paper_2008_00409_gb300 import workloads as wk
+    t0 = time.perf_counter()
+    feat, dv = ws.collect(wk.warm_start_training(), tol=args.tol)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    params, stats, losses = ws.train(feat, dv, steps=args.train_steps, batch=65536, lr=1e-3, seed=0,
+                                     log_every=max(1, args.train_steps // 4))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    rows = int(feat.shape[0])
+    del feat, dv
+    wl = wk.warm_start_eval()
+    nsteps = args.warmup + args.steps
+    with ClockSampler(0) as clk:
+        res = ws.evaluate(wl, params, stats, steps=nsteps, tol=args.tol)
+        fp32 = ws.evaluate(wl, params, stats, steps=nsteps, tol=args.tol, precision=pc.PC_PREC_FP32,
+                           modes=(pc.PC_WARM_ZERO,))[pc.PC_WARM_ZERO]
+    names = {pc.PC_WARM_ZERO: "zero", pc.PC_WARM_PREV: "prev", pc.PC_WARM_MLP: "mlp"}
+
+    def summary(rec):
+        w = slice(args.warmup, nsteps)
+        return {"steps_per_s": len(rec["sec"][w]) / sum(rec["sec"][w]), "iters_mean": float(np.mean(rec["iters"][w])),
+                "max_rel_res": float(np.max(rec["rel_res"][w]))}
+
+    modes = {names[m]: summary(r) for m, r in res.items()}
+    mlp = res[pc.PC_WARM_MLP]
+    modes["mlp"]["guess_used"] = [int(g) for g in mlp["guess"][args.warmup:]]
+    modes["fp32_zero"] = summary(fp32)
+    out = {"metric": "steps/s at 1M tris (708^2 cloth, 2% contacts) to 1e-6 with the learned warm start",
+           "value": modes["mlp"]["steps_per_s"], "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 / modes["mlp"]["steps_per_s"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+           "config": {"workload": wl.name, "V": wl.V, "T": wl.T, "contacts_per_step": wl.n_contacts, "tol": args.tol,
+                      "precision": "mixed", "train_rows": rows, "train_steps": args.train_steps,
+                      "train_batch": 65536, "data_seconds": t_gen, "train_seconds": t_train,
+                      "loss_curve": losses},
+           "modes": modes, "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.form == "batched":
+        run_batched(args)
+    elif args.form == "warmstart":
+        run_warmstart(args)
     else:
         run_ours(args)
 

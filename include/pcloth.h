@@ -365,10 +365,14 @@ PC_API pc_status pc_set_warm_mlp(pc_ctx *ctx, const float *params, const float *
 PC_API int64_t pc_launch_count(const pc_ctx *ctx);
 
 /* When enabled, the PCG loop brackets every SpMV launch with CUDA events on its stream
- * and accumulates their durations; pc_spmv_stats returns (launches, total ms, block
- * count of the last matrix) and resets the counters. */
+ * and accumulates their durations, and pc_step brackets its assembly the same way;
+ * pc_spmv_stats returns (launches, total ms, block count of the last matrix) and resets
+ * the counters. */
 PC_API pc_status pc_set_profiling(pc_ctx *ctx, int32_t enable);
 PC_API pc_status pc_spmv_stats(pc_ctx *ctx, int64_t *launches, double *total_ms, int64_t *nnzb);
+/* Likewise for pc_step's assembly (pattern and values, Sec. 3.2.2): (steps timed, total
+ * ms), then reset. */
+PC_API pc_status pc_assembly_stats(pc_ctx *ctx, int64_t *steps, double *total_ms);
 
 #ifdef __cplusplus
 }

@@ -37,6 +37,16 @@ extern "C" pc_status pc_spmv_stats(pc_ctx *ctx, int64_t *launches, double *total
     return PC_OK;
 }
 
+extern "C" pc_status pc_assembly_stats(pc_ctx *ctx, int64_t *steps, double *total_ms)
+{
+    if (!ctx) return PC_ERR_ARG;
+    if (steps) *steps = ctx->asm_steps;
+    if (total_ms) *total_ms = ctx->asm_ms;
+    ctx->asm_steps = 0;
+    ctx->asm_ms = 0.0;
+    return PC_OK;
+}
+
 extern "C" pc_status pc_step(pc_ctx *ctx, float *x, float *v, const pc_contacts *contacts, const pc_step_opts *opts,
                              float *dv_out, pc_step_info *info, void *stream)
 {
@@ -44,8 +54,17 @@ extern "C" pc_status pc_step(pc_ctx *ctx, float *x, float *v, const pc_contacts 
     if (!(opts->h > 0.0f)) return PC_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     pc_bsr A{ctx->A_rp, ctx->A_ci, ctx->A_cap, 0};
+    if (ctx->profiling) PC_CUDA_TRY(cudaEventRecord(ctx->ev[2], st));
     PC_TRY(pc_assemble_pattern(ctx, contacts, &A, stream));
     PC_TRY(pc_assemble_values(ctx, &A, x, v, contacts, opts->h, ctx->A_vals, ctx->A_b, ctx->A_dres, stream));
+    if (ctx->profiling) {
+        PC_CUDA_TRY(cudaEventRecord(ctx->ev[3], st));
+        PC_CUDA_TRY(cudaEventSynchronize(ctx->ev[3]));
+        float ms = 0.f;
+        PC_CUDA_TRY(cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]));
+        ctx->asm_ms += ms;
+        ctx->asm_steps += 1;
+    }
     // A_dv holds the previous step's dv (zeros before the first step); choose the guess
     if (!ctx->has_prev_dv) PC_CUDA_TRY(cudaMemsetAsync(ctx->A_dv, 0, sizeof(float) * 3 * (size_t)ctx->V, st));
     int32_t guess = PC_WARM_ZERO;

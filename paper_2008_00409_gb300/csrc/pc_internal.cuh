@@ -169,6 +169,8 @@ struct pc_ctx {
     int64_t spmv_launches = 0;
     double spmv_ms = 0.0;
     int64_t spmv_nnzb = 0;
+    int64_t asm_steps = 0;         // pc_step calls timed (assembly: pattern + values)
+    double asm_ms = 0.0;
     cudaEvent_t ev[2 * 64] = {};
     int ev_used = 0;
 };

@@ -428,8 +428,8 @@ pc_status pc_solver_alloc(pc_ctx *c)
     PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM_BYTES));
     PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM_BYTES));
     PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM_BYTES));
-    for (int i = 0; i < 2; ++i) PC_CUDA_TRY(cudaEventCreate(&c->ev[i]));
-    c->ev_used = 2;
+    for (int i = 0; i < 4; ++i) PC_CUDA_TRY(cudaEventCreate(&c->ev[i]));
+    c->ev_used = 4;
     return PC_OK;
 }
 

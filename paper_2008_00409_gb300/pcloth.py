@@ -122,12 +122,13 @@ def _load():
     L.pc_launch_count.argtypes = [c_void_p]
     L.pc_set_profiling.argtypes = [c_void_p, c_int32]
     L.pc_spmv_stats.argtypes = [c_void_p, P(c_int64), P(c_double), P(c_int64)]
+    L.pc_assembly_stats.argtypes = [c_void_p, P(c_int64), P(c_double)]
     for name in ("pc_create", "pc_destroy", "pc_get_sizes", "pc_get_rest", "pc_assemble_pattern",
                  "pc_assemble_values", "pc_bsr_spmv", "pc_pcg_solve", "pc_pcg_solve_static", "pc_step", "pc_step_host",
                  "pc_pcg_solve_batched", "pc_step_batched", "pc_batched_config", "pc_mlp_features", "pc_mlp_create",
                  "pc_mlp_destroy", "pc_mlp_reset", "pc_mlp_stats", "pc_mlp_infer", "pc_mlp_grad", "pc_mlp_train_step",
                  "pc_mlp_adam_apply", "pc_set_warm_mlp",
-                 "pc_set_profiling", "pc_spmv_stats"):
+                 "pc_set_profiling", "pc_spmv_stats", "pc_assembly_stats"):
         getattr(L, name).restype = c_int32
     return L
 
@@ -400,6 +401,12 @@ def pc_launch_count(ctx) -> int:
 
 def pc_set_profiling(ctx, enable: bool):
     _check(_lib.pc_set_profiling(ctx, int(bool(enable))), "pc_set_profiling")
+
+
+def pc_assembly_stats(ctx):
+    n, ms = c_int64(), c_double()
+    _check(_lib.pc_assembly_stats(ctx, ctypes.byref(n), ctypes.byref(ms)), "pc_assembly_stats")
+    return n.value, ms.value
 
 
 def pc_spmv_stats(ctx):
