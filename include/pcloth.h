@@ -223,6 +223,14 @@ PC_API pc_status pc_bsr_spmv(pc_ctx *ctx, const pc_bsr *A, const float *vals, co
 PC_API pc_status pc_pcg_solve(pc_ctx *ctx, const pc_bsr *A, const float *vals, const float *dres, const float *b,
                        float *dv, const pc_solve_opts *opts, pc_solve_info *info, void *stream);
 
+/* After a PC_PREC_MIXED pc_pcg_solve or pc_step on this context: copy the solve's FP64
+ * solution accumulator -- the iterate whose FP64 residual the stop test measured; the
+ * returned dv is its rounding to FP32 -- into dv64 (device double[V][3]). On stiff
+ * systems (|A| |dv| much larger than |b|) the FP32 rounding alone can raise the relative
+ * residual far above tol, so this is the solution to check a tolerance against.
+ * Does not synchronize. */
+PC_API pc_status pc_get_solution64(pc_ctx *ctx, double *dv64, void *stream);
+
 /* Batched solve of many independent systems (garments) in ONE persistent PCG launch.
  * The context holds the union of the garments' meshes; instance k owns the contiguous
  * rows inst_rows[k] .. inst_rows[k+1]-1 (host array of n_inst + 1 entries, first 0, last

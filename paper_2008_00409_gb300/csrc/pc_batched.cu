@@ -28,7 +28,7 @@
 #define RED_SLOTS 4
 #define BT_TILE 32  // rows per tile in every phase
 
-// local copies of the reduction helpers used by pc_spmv.cuh's kernel (not launched here)
+// local copy of the block reduction used by pc_spmv.cuh's kernel (not launched here)
 __device__ __forceinline__ double bt_warp_sum(double v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -51,30 +51,6 @@ __device__ __forceinline__ void block_sum_d(double *v, int n)
     }
     __syncthreads();
 }
-static __device__ bool last_block_reduce(double *v, int n, double *partials, uint32_t *counter)
-{
-    __shared__ bool s_last;
-    block_sum_d(v, n);
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < n; ++k) partials[(int64_t)blockIdx.x * RED_SLOTS + k] = v[k];
-        __threadfence();
-        uint32_t t = atomicAdd(counter, 1u);
-        s_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return false;
-    __threadfence();
-    double acc[RED_SLOTS] = {0.0, 0.0, 0.0, 0.0};
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
-        for (int k = 0; k < n; ++k) acc[k] += __ldcg(partials + (int64_t)i * RED_SLOTS + k);
-    block_sum_d(acc, n);
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < n; ++k) v[k] = acc[k];
-        *counter = 0u;
-    }
-    return true;
-}
-
 #include "pc_spmv.cuh"
 
 // ------------------------------------------------------------------------- device state

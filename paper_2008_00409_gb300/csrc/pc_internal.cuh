@@ -173,6 +173,7 @@ struct pc_ctx {
     double asm_ms = 0.0;
     cudaEvent_t ev[2 * 64] = {};
     int ev_used = 0;
+    int ev_pending = 0;            // SpMV events recorded, not yet read
 };
 
 // launch bookkeeping: every kernel launch in the library goes through this
@@ -186,6 +187,33 @@ struct pc_ctx {
             return PC_ERR_CUDA;                                                       \
         }                                                                             \
     } while (0)
+
+// Programmatic dependent launch: the kernel may be scheduled while its predecessor in the
+// stream is still running; it must call pdl_wait() before reading anything the
+// predecessor writes (the wait returns once that grid has completed and its memory is
+// visible), and calls pdl_trigger() to let its own successor be scheduled early.
+#define PC_LAUNCH_PDL(ctx, kernel, grid, block, smem, strm, ...)                        \
+    do {                                                                              \
+        cudaLaunchConfig_t _cfg = {};                                                 \
+        _cfg.gridDim = dim3(grid);                                                    \
+        _cfg.blockDim = dim3(block);                                                  \
+        _cfg.dynamicSmemBytes = (smem);                                               \
+        _cfg.stream = (strm);                                                         \
+        cudaLaunchAttribute _attr[1];                                                 \
+        _attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;             \
+        _attr[0].val.programmaticStreamSerializationAllowed = 1;                      \
+        _cfg.attrs = _attr;                                                           \
+        _cfg.numAttrs = 1;                                                            \
+        cudaError_t _le = cudaLaunchKernelEx(&_cfg, kernel, __VA_ARGS__);             \
+        (ctx)->launches++;                                                            \
+        if (_le != cudaSuccess) {                                                     \
+            pc_note_cuda_error(_le, #kernel, __FILE__, __LINE__);                     \
+            return PC_ERR_CUDA;                                                       \
+        }                                                                             \
+    } while (0)
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 inline unsigned pc_blocks(int64_t n, int threads)
 {

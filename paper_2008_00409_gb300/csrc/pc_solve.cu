@@ -142,6 +142,29 @@ __global__ void dinv_kernel(int V, const int32_t *__restrict__ rp, const int32_t
 // per row and array. Each thread sums its rows' dot-product terms in FP32; the sums
 // across threads and blocks are FP64 (last_block_reduce).
 
+// alpha = r.z / p.q with p.q the sum, in CTA order, of the n_pq partials the SpMV left in
+// slot 3 (every CTA computes the same value; block 0 records pq and alpha). A
+// non-positive or non-finite p.q gives alpha = 0; the last block then reports it.
+__device__ __forceinline__ float pcg_alpha(const double *partials, int n_pq, pc_scalars *sc)
+{
+    __shared__ float s_alpha;
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < n_pq; i += blockDim.x) v[0] += __ldcg(partials + (int64_t)i * RED_SLOTS + 3);
+    block_sum_d(v, 1);
+    if (threadIdx.x == 0) {
+        const double pq = v[0];
+        double alpha = sc->rz / pq;
+        if (!(pq > 0.0) || !isfinite(alpha)) alpha = 0.0;
+        if (blockIdx.x == 0) {
+            sc->pq = pq;
+            sc->alpha = alpha;
+        }
+        s_alpha = (float)alpha;
+    }
+    __syncthreads();
+    return s_alpha;
+}
+
 // Per row: x += alpha p; r -= alpha q; z = D^-1 r; partial (r.z, r.r); the last block
 // computes beta and applies the stop tests.
 template <bool BLOCK>
@@ -151,14 +174,28 @@ __global__ void __launch_bounds__(EW_THREADS) pcg_update_kernel(int V, float4 *_
                                                                  const float4 *__restrict__ q4,
                                                                  const float4 *__restrict__ dinv4,
                                                                  float4 *__restrict__ z4, double *partials,
-                                                                 pc_scalars *sc)
+                                                                 int n_pq, pc_scalars *sc)
 {
+    pdl_wait();
     if (sc->done) return;
-    const float alpha = (float)sc->alpha;
+    // the first row's loads are issued before alpha's reduction, so their latencies overlap
+    int row = blockIdx.x * blockDim.x + threadIdx.x;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f), q = p, x = p, r = p;
+    if (row < V) {
+        p = p4[row];
+        q = q4[row];
+        x = x4[row];
+        r = r4[row];
+    }
+    const float alpha = pcg_alpha(partials, n_pq, sc);
     float rz = 0.f, rr = 0.f;
-    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
-        const float4 p = p4[row], q = q4[row];
-        float4 x = x4[row], r = r4[row];
+    for (; row < V; row += gridDim.x * blockDim.x) {
+        if (row != (int)(blockIdx.x * blockDim.x + threadIdx.x)) {
+            p = p4[row];
+            q = q4[row];
+            x = x4[row];
+            r = r4[row];
+        }
         x.x = fmaf(alpha, p.x, x.x);
         x.y = fmaf(alpha, p.y, x.y);
         x.z = fmaf(alpha, p.z, x.z);
@@ -172,14 +209,19 @@ __global__ void __launch_bounds__(EW_THREADS) pcg_update_kernel(int V, float4 *_
         rz += dot3(r, z);
         rr += dot3(r, r);
     }
+    pdl_trigger();
     double v[2] = {(double)rz, (double)rr};
     if (last_block_reduce(v, 2, partials, &sc->counter) && threadIdx.x == 0) {
         double rz_new = v[0];
+        const double pq = sc->pq;
         sc->beta = rz_new / sc->rz;
         sc->rz = rz_new;
         sc->rr = v[1];
         sc->iter += 1;
-        if (!isfinite(v[1]) || !isfinite(sc->beta)) {
+        if (!(pq > 0.0) || !isfinite(sc->alpha)) {
+            sc->status = PC_ERR_NONFINITE;
+            sc->done = 1;
+        } else if (!isfinite(v[1]) || !isfinite(sc->beta)) {
             sc->status = PC_ERR_NONFINITE;
             sc->done = 1;
         } else if (v[1] <= sc->tol2) {
@@ -444,9 +486,9 @@ static pc_status check_bsr(const pc_bsr *A, const float *vals)
 static pc_status launch_spmv(pc_ctx *c, const SpmvArgs &a, bool diff, bool pcg, cudaStream_t st)
 {
     const int g = spmv_grid(c);
-    if (diff && pcg) PC_LAUNCH(c, (spmv_kernel<true, true>), g, SP_THREADS, SP_SMEM_BYTES, st, a);
+    if (diff && pcg) PC_LAUNCH_PDL(c, (spmv_kernel<true, true>), g, SP_THREADS, SP_SMEM_BYTES, st, a);
     else if (diff) PC_LAUNCH(c, (spmv_kernel<true, false>), g, SP_THREADS, SP_SMEM_BYTES, st, a);
-    else if (pcg) PC_LAUNCH(c, (spmv_kernel<false, true>), g, SP_THREADS, SP_SMEM_BYTES, st, a);
+    else if (pcg) PC_LAUNCH_PDL(c, (spmv_kernel<false, true>), g, SP_THREADS, SP_SMEM_BYTES, st, a);
     else PC_LAUNCH(c, (spmv_kernel<false, false>), g, SP_THREADS, SP_SMEM_BYTES, st, a);
     return PC_OK;
 }
@@ -519,12 +561,14 @@ static pc_status replace_residual(const SolveCtx &s, float *x32, int first, doub
 __global__ void __launch_bounds__(EW_THREADS) pcg_direction_kernel(int V, const float4 *__restrict__ z4,
                                                                     float4 *__restrict__ p4, const pc_scalars *sc)
 {
+    pdl_wait();
     if (sc->done) return;
     const float beta = (float)sc->beta;
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
         const float4 z = z4[row], p = p4[row];
         p4[row] = make_float4(fmaf(beta, p.x, z.x), fmaf(beta, p.y, z.y), fmaf(beta, p.z, z.z), 0.f);
     }
+    pdl_trigger();
 }
 
 // `count` PCG iterations: p = z + beta p; q = A p (and p.q -> alpha); x, r, z update
@@ -543,30 +587,40 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
     a.partials = c->partials;
     a.sc = c->sc;
     a.err = c->d_err;
+    const int n_pq = spmv_grid(c);
     for (int k = 0; k < count; ++k) {
         bool timed = c->profiling && k == 0;
-        PC_LAUNCH(c, pcg_direction_kernel, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (const float4 *)c->z,
-                  (float4 *)c->p0, c->sc);
+        PC_LAUNCH_PDL(c, pcg_direction_kernel, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (const float4 *)c->z,
+                      (float4 *)c->p0, (const pc_scalars *)c->sc);
         if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[0], s.st));
         PC_TRY(launch_spmv(c, a, s.diff, true, s.st));
         if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[1], s.st));
         if (s.block)
-            PC_LAUNCH(c, pcg_update_kernel<true>, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (float4 *)x,
+            PC_LAUNCH_PDL(c, pcg_update_kernel<true>, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (float4 *)x,
                       (const float4 *)c->p0, (float4 *)c->r, (const float4 *)c->q, (const float4 *)c->dinv,
-                      (float4 *)c->z, c->partials, c->sc);
+                      (float4 *)c->z, c->partials, n_pq, c->sc);
         else
-            PC_LAUNCH(c, pcg_update_kernel<false>, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (float4 *)x,
+            PC_LAUNCH_PDL(c, pcg_update_kernel<false>, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (float4 *)x,
                       (const float4 *)c->p0, (float4 *)c->r, (const float4 *)c->q, (const float4 *)c->dinv,
-                      (float4 *)c->z, c->partials, c->sc);
+                      (float4 *)c->z, c->partials, n_pq, c->sc);
         if (timed) {
-            float ms = 0.f;
-            PC_CUDA_TRY(cudaEventSynchronize(c->ev[1]));
-            PC_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
-            c->spmv_ms += ms;
-            c->spmv_launches += 1;
+            c->ev_pending = 1;  // read after the chunk's synchronisation (no stall here)
             c->spmv_nnzb = s.A->nnzb;
         }
     }
+    return PC_OK;
+}
+
+// Fold a pending SpMV timing (events recorded by launch_iterations) into the stats; the
+// caller has synchronised the stream.
+static pc_status collect_spmv_timing(pc_ctx *c)
+{
+    if (!c->ev_pending) return PC_OK;
+    c->ev_pending = 0;
+    float ms = 0.f;
+    PC_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+    c->spmv_ms += ms;
+    c->spmv_launches += 1;
     return PC_OK;
 }
 
@@ -671,6 +725,7 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
         PC_TRY(launch_iterations(s, x, chunk));
         launched += chunk;
         PC_TRY(read_scalars(ctx, st));
+        PC_TRY(collect_spmv_timing(ctx));
     }
     const pc_scalars fin = *ctx->sc_host;
     if (fin.status == PC_ERR_TIMEOUT) return PC_ERR_TIMEOUT;
@@ -708,6 +763,14 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
     if (info) *info = inf;
     PC_CUDA_TRY(cudaStreamSynchronize(st));
     return status;
+}
+
+extern "C" pc_status pc_get_solution64(pc_ctx *ctx, double *dv64, void *stream)
+{
+    if (!ctx || !dv64) return PC_ERR_ARG;
+    PC_CUDA_TRY(cudaMemcpyAsync(dv64, ctx->x64, sizeof(double) * 3 * (size_t)ctx->V, cudaMemcpyDeviceToDevice,
+                                (cudaStream_t)stream));
+    return PC_OK;
 }
 
 // FP64 measures of an FP32 guess x of A x = b: |b - A x|^2, |b|^2, x.(A x) and b.x (so

@@ -10,8 +10,10 @@
 // neighbours' vector entries. Tiles whose blocks exceed a stage (rows with many contacts)
 // are read directly from global memory.
 //
-// PCG mode computes q = A p and its p.q partial, with p stored as float4 per vertex so
-// that each gather is one 16-byte load.
+// PCG mode computes q = A p and this CTA's p.q partial (slot 3 of the CTA's entry in the
+// partials array; the update kernel that follows sums the partials in CTA order and forms
+// alpha, so the SpMV ends without a grid-wide reduction tail), with p stored as float4 per
+// vertex so that each gather is one 16-byte load.
 // Difference form (dres given): y_j = D_j x_j + sum_i A_ji (x_i - x_j); the diagonal
 // block then multiplies x_j - x_j = 0 and needs no special case.
 #pragma once
@@ -103,7 +105,10 @@ __global__ void __launch_bounds__(SP_THREADS, SP_CTAS_PER_SM) spmv_kernel(SpmvAr
     __shared__ uint64_t full_bar[SP_STAGES], empty_bar[SP_STAGES];
     __shared__ int stage_info[SP_STAGES][4];  // b0, value offset, column offset, staged
     __shared__ int s_timeout;
-    if (PCG && a.sc->done) return;
+    if (PCG) {  // launched programmatically after the direction kernel
+        pdl_wait();
+        if (a.sc->done) return;
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < SP_STAGES; ++s) {
@@ -253,20 +258,9 @@ __global__ void __launch_bounds__(SP_THREADS, SP_CTAS_PER_SM) spmv_kernel(SpmvAr
         }
     }
     if (PCG) {
+        pdl_trigger();
         double v[1] = {(double)dot_acc - (double)dot_c};
-        if (last_block_reduce(v, 1, a.partials, &a.sc->counter) && threadIdx.x == 0) {
-            pc_scalars *s = a.sc;
-            double pq = v[0];
-            s->pq = pq;
-            double alpha = s->rz / pq;
-            if (s->status == PC_ERR_TIMEOUT) {
-                alpha = 0.0;
-            } else if (!(pq > 0.0) || !isfinite(alpha)) {
-                s->status = PC_ERR_NONFINITE;
-                s->done = 1;
-                alpha = 0.0;
-            }
-            s->alpha = alpha;
-        }
+        block_sum_d(v, 1);
+        if (threadIdx.x == 0) a.partials[(int64_t)blockIdx.x * RED_SLOTS + 3] = v[0];
     }
 }

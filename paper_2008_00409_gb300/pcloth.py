@@ -123,12 +123,13 @@ def _load():
     L.pc_set_profiling.argtypes = [c_void_p, c_int32]
     L.pc_spmv_stats.argtypes = [c_void_p, P(c_int64), P(c_double), P(c_int64)]
     L.pc_assembly_stats.argtypes = [c_void_p, P(c_int64), P(c_double)]
+    L.pc_get_solution64.argtypes = [c_void_p, c_void_p, c_void_p]
     for name in ("pc_create", "pc_destroy", "pc_get_sizes", "pc_get_rest", "pc_assemble_pattern",
                  "pc_assemble_values", "pc_bsr_spmv", "pc_pcg_solve", "pc_pcg_solve_static", "pc_step", "pc_step_host",
                  "pc_pcg_solve_batched", "pc_step_batched", "pc_batched_config", "pc_mlp_features", "pc_mlp_create",
                  "pc_mlp_destroy", "pc_mlp_reset", "pc_mlp_stats", "pc_mlp_infer", "pc_mlp_grad", "pc_mlp_train_step",
                  "pc_mlp_adam_apply", "pc_set_warm_mlp",
-                 "pc_set_profiling", "pc_spmv_stats", "pc_assembly_stats"):
+                 "pc_set_profiling", "pc_spmv_stats", "pc_assembly_stats", "pc_get_solution64"):
         getattr(L, name).restype = c_int32
     return L
 
@@ -401,6 +402,10 @@ def pc_launch_count(ctx) -> int:
 
 def pc_set_profiling(ctx, enable: bool):
     _check(_lib.pc_set_profiling(ctx, int(bool(enable))), "pc_set_profiling")
+
+
+def pc_get_solution64(ctx, dv64, stream=None):
+    _check(_lib.pc_get_solution64(ctx, _ptr(dv64), _stream(stream)), "pc_get_solution64")
 
 
 def pc_assembly_stats(ctx):

@@ -1,0 +1,80 @@
+"""Parity at full size, in the configuration the bench times (mixed-precision Jacobi-PCG
+to 1e-6, difference form): the 512 x 512 cloth with 2% contacts and the paper-scale
+3 x 526^2 stack. The pattern is compared bit for bit and every block and right-hand
+side entry against the oracle's full FP64 assembly; the oracle's exact solve is too
+slow at these sizes, so the solution is checked by a property that holds at any size:
+the FP64 residual of the solver's FP64 solution on the assembled system, recomputed
+here independently, meets the tolerance, and the returned dv is exactly that solution
+rounded to FP32."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2008_00409_gb300 import workloads as wk
+from tests import _helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pc():
+    from paper_2008_00409_gb300 import build
+    build.build()
+    from paper_2008_00409_gb300 import pcloth
+    return pcloth
+
+
+def diff_form_product(rp, ci, vals, dres, p):
+    """(A p)_i = D_i p_i + sum_{j != i} A_ij (p_j - p_i) in FP64 (the form whose rows are
+    exact for this model: every element Hessian's rows sum to zero)."""
+    V = len(rp) - 1
+    rows = np.repeat(np.arange(V), np.diff(rp))
+    off = ci != rows
+    A = vals[off]
+    d = p[ci[off]] - p[rows[off]]
+    contrib = np.einsum("bij,bj->bi", A, d)
+    y = np.einsum("vij,vj->vi", dres, p)
+    for k in range(3):
+        y[:, k] += np.bincount(rows[off], weights=contrib[:, k], minlength=V)
+    return y
+
+
+@pytest.mark.parametrize("name", ["square512-contacts", "stack3x526"])
+def test_full_size_pattern_values_and_solve(pc, name):
+    wl = wk.WORKLOADS[name]()
+    cl = pc.Cloth(wl)
+    step = 1
+    pairs, w = wl.contacts(step)
+    pd, wd = cl.contacts_device(step)
+    s = cl.assemble(pd, wd)
+    nnzb = s["nnzb"]
+    mesh = oracle.Mesh.from_workload(wl)
+    rp_o, ci_o = mesh.pattern(pairs)
+    rp = s["row_ptr"].cpu().numpy()
+    ci = s["col_idx"][:nnzb].cpu().numpy()
+    np.testing.assert_array_equal(rp, rp_o)
+    np.testing.assert_array_equal(ci, ci_o)
+    _, _, vals_ref, b_ref = mesh.assemble(wl.x0.astype(np.float64), wl.v0.astype(np.float64), pairs, w, wl.h,
+                                          pattern=(rp_o, ci_o))
+    vals = s["vals"][: 9 * nnzb].cpu().numpy().astype(np.float64).reshape(-1, 3, 3)
+    excess = H.block_errors(rp_o, ci_o, vals, vals_ref)
+    assert excess.max() <= 0, f"worst block excess {excess.max():.3e}"
+    del vals_ref, excess
+    b = s["b"].cpu().numpy().astype(np.float64).reshape(-1, 3)
+    assert H.rel_l2(b, b_ref) <= 1e-5
+    dv = torch.zeros(wl.V * 3, device="cuda")
+    info, st = pc.pc_pcg_solve(cl.ctx, s["row_ptr"], s["col_idx"], nnzb, s["vals"], s["dres"], s["b"], dv,
+                               pc.solve_opts(tol=1e-6, precision=pc.PC_PREC_MIXED, max_iter=20000))
+    assert st == pc.PC_OK and info.rel_res <= 1e-6
+    dv64 = torch.empty(wl.V * 3, dtype=torch.float64, device="cuda")
+    pc.pc_get_solution64(cl.ctx, dv64)
+    x64 = dv64.cpu().numpy().reshape(-1, 3)
+    np.testing.assert_array_equal(dv.cpu().numpy().reshape(-1, 3), x64.astype(np.float32))
+    dres = s["dres"].cpu().numpy().astype(np.float64).reshape(-1, 3, 3)
+    r = b - diff_form_product(rp, ci, vals, dres, x64)
+    rel = np.linalg.norm(r) / np.linalg.norm(b)
+    assert rel <= 1.05e-6, rel
+    assert abs(rel - info.rel_res) <= 1e-3 * info.rel_res + 1e-12
+    # pinned vertices do not move
+    assert np.all(x64[wl.pins] == 0.0)
