@@ -23,6 +23,7 @@
 #include <cmath>
 
 #include "pc_internal.cuh"
+#include "pc_tc.cuh"
 #include "pc_tma.cuh"
 
 #define MLP_IN 12
@@ -224,39 +225,175 @@ __device__ __forceinline__ void mlp_forward(const MlpW &s, const uint32_t (&ax)[
     for (int kk = 0; kk < 4; ++kk) mma_bf16(y, a2[kk], row[8 * kk + c], row[8 * kk + 4 + c]);
 }
 
-// ------------------------------------------------------------------------- inference
+// ------------------------------------------------------------------------- inference (tcgen05)
+
+// One CTA of four warps per 128-row tile (persistent over tiles): the three layers are
+// tcgen05 MMAs (M = 128, K = 16 per instruction, BF16 operands from shared memory, FP32
+// accumulators in tensor memory), issued by one thread and committed to an mbarrier;
+// warp w reads tensor-memory lanes 32w.. (its 32 rows), adds the bias, applies the ReLU
+// and writes the BF16 activations back to shared memory as the next layer's A operand.
+#define TC_ROWS 128
+#define TC_THREADS 128
+#define TC_TMEM_COLS 128  // D1 at column 0, D2 at 64, D3 at 0 again
+#define TC_OFF_W1 0       // 64 x 16 BF16 (2 KB)
+#define TC_OFF_W2 2048    // 64 x 64 (8 KB)
+#define TC_OFF_W3 10240   // 16 x 64, outputs 3..15 zero (2 KB)
+#define TC_OFF_X 12288    // 128 x 16 (4 KB)
+#define TC_OFF_H 16384    // 128 x 64 (16 KB)
+// padded so that at most two CTAs share an SM: their 2 x 128 tensor-memory columns
+// always fit in the SM's 512, so an allocation never waits
+#define TC_SMEM_BYTES (100 * 1024)
+#define TC_WAIT_BUDGET (1ll << 31)  // cycles (about a second) before an MMA wait gives up
+
+// byte offset of element (row, k) of a K-major operand with K columns (no swizzle)
+__device__ __forceinline__ uint32_t tc_off(int row, int k, int K)
+{
+    return (uint32_t)((row >> 3) * (K * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ void tc_put(unsigned char *base, int row, int k, int K, float v)
+{
+    *reinterpret_cast<__nv_bfloat16 *>(base + tc_off(row, k, K)) = __float2bfloat16_rn(v);
+}
+
+// Bias + ReLU of 64 accumulator columns (tensor memory, this thread's row) into the BF16
+// A operand (row t, K = 64).
+__device__ __forceinline__ void tc_hidden(uint32_t taddr, const float *bias, unsigned char *H, int t)
+{
+#pragma unroll
+    for (int c = 0; c < 64; c += 16) {
+        float v[16];
+        tc_ld16(taddr + c, v);
+        uint32_t q[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            q[i] = pack_bf16(fmaxf(v[2 * i] + bias[c + 2 * i], 0.f), fmaxf(v[2 * i + 1] + bias[c + 2 * i + 1], 0.f));
+        *reinterpret_cast<uint4 *>(H + tc_off(t, c, 64)) = make_uint4(q[0], q[1], q[2], q[3]);
+        *reinterpret_cast<uint4 *>(H + tc_off(t, c + 8, 64)) = make_uint4(q[4], q[5], q[6], q[7]);
+    }
+}
 
 // dv0 = dv_prev + sd_y * net(standardised feat) + mu_y; rows with fixed[r] != 0 get 0.
-__global__ void __launch_bounds__(MLP_THREADS) mlp_infer_kernel(int64_t n, const float *params, const float *stats,
-                                                                const float *feat, const float *dv_prev,
-                                                                const uint8_t *fixed, float *dv0)
+__global__ void __launch_bounds__(TC_THREADS) mlp_infer_kernel(int64_t n, const float *params, const float *stats,
+                                                               const float *feat, const float *dv_prev,
+                                                               const uint8_t *fixed, float *dv0, uint32_t *err)
 {
-    __shared__ MlpW s;
-    mlp_stage(s, params, stats, false);
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_fail;
+    __shared__ float b1[MLP_HID], b2[MLP_HID], b3[4], mx[MLP_IN], sx[MLP_IN], my[4], sy[4];
+    const int t = threadIdx.x, warp = t >> 5;
+    // weights as BF16 operands (B = W, N x K, K-major)
+    for (int i = t; i < MLP_HID * 16; i += TC_THREADS) {
+        const int r = i >> 4, k = i & 15;
+        tc_put(tsm + TC_OFF_W1, r, k, 16, k < MLP_IN ? params[OFF_W1 + r * MLP_IN + k] : 0.f);
+    }
+    for (int i = t; i < MLP_HID * MLP_HID; i += TC_THREADS) {
+        const int r = i >> 6, k = i & 63;
+        tc_put(tsm + TC_OFF_W2, r, k, 64, params[OFF_W2 + r * MLP_HID + k]);
+    }
+    for (int i = t; i < 16 * MLP_HID; i += TC_THREADS) {
+        const int r = i >> 6, k = i & 63;
+        tc_put(tsm + TC_OFF_W3, r, k, 64, r < MLP_OUT ? params[OFF_W3 + r * MLP_HID + k] : 0.f);
+    }
+    if (t < MLP_HID) {
+        b1[t] = params[OFF_B1 + t];
+        b2[t] = params[OFF_B2 + t];
+    }
+    if (t < MLP_IN) {
+        mx[t] = stats[t];
+        sx[t] = stats[MLP_IN + t];
+    }
+    if (t < 4) {
+        b3[t] = t < MLP_OUT ? params[OFF_B3 + t] : 0.f;
+        my[t] = t < MLP_OUT ? stats[2 * MLP_IN + t] : 0.f;
+        sy[t] = t < MLP_OUT ? stats[2 * MLP_IN + MLP_OUT + t] : 1.f;
+    }
+    if (t == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+        s_fail = 0;
+    }
+    if (warp == 0) tc_alloc(&tmem_slot, TC_TMEM_COLS);
+    fence_async_smem();
+    tc_fence_before();
     __syncthreads();
-    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
-    const int64_t nwarps = (int64_t)gridDim.x * MLP_WARPS;
-    for (int64_t t = (int64_t)blockIdx.x * MLP_WARPS + (threadIdx.x >> 5); t * 16 < n; t += nwarps) {
-        const int64_t base = 16 * t;
-        uint32_t ax[4], a2[4][4], m1, m2;
-        float y[4];
-        mlp_load_x(s, feat, nullptr, n, base, ax);
-        mlp_forward(s, ax, y, m1, m2, a2, nullptr, nullptr);
-        if (c < 2) {  // lanes c = 0 hold outputs 0, 1; c = 1 holds output 2
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t lanes = (uint32_t)(32 * warp) << 16;
+    const uint32_t idesc64 = tc_idesc_bf16(TC_ROWS, 64), idesc16 = tc_idesc_bf16(TC_ROWS, 16);
+    unsigned char *X = tsm + TC_OFF_X, *H = tsm + TC_OFF_H;
+    uint32_t phase = 0;
+    const int64_t ntiles = (n + TC_ROWS - 1) / TC_ROWS;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r = tile * TC_ROWS + t;
+        // ---- standardised inputs of row t as the BF16 A operand (K = 16, inputs 12..15 zero)
+        {
+            float v[16];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int64_t r = base + g + 8 * h;
-                if (r >= n) continue;
-                const bool fx = fixed && fixed[r];
-                for (int e = 0; e < 2; ++e) {
-                    const int o = 2 * c + e;
-                    if (o >= MLP_OUT) break;
-                    const float d = dv_prev ? dv_prev[3 * r + o] : 0.f;
-                    dv0[3 * r + o] = fx ? 0.f : fmaf(y[2 * h + e], s.sy[o], s.my[o]) + d;
+            for (int k = 0; k < 16; ++k) v[k] = 0.f;
+            if (r < n) {
+                const float *x = feat + MLP_IN * r;
+#pragma unroll
+                for (int k = 0; k < MLP_IN; ++k) v[k] = (x[k] - mx[k]) / sx[k];
+            }
+            uint32_t q[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) q[i] = pack_bf16(v[2 * i], v[2 * i + 1]);
+            *reinterpret_cast<uint4 *>(X + tc_off(t, 0, 16)) = make_uint4(q[0], q[1], q[2], q[3]);
+            *reinterpret_cast<uint4 *>(X + tc_off(t, 8, 16)) = make_uint4(q[4], q[5], q[6], q[7]);
+        }
+        // three layers: MMA(s) by thread 0, wait on the commit, epilogue by every thread
+        for (int layer = 0; layer < 3; ++layer) {
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (t == 0) {
+                if (layer == 0) {
+                    tc_mma_bf16(tmem, tc_smem_desc(X, 128, 256), tc_smem_desc(tsm + TC_OFF_W1, 128, 256), idesc64,
+                                false);
+                } else {
+                    const unsigned char *W = tsm + (layer == 1 ? TC_OFF_W2 : TC_OFF_W3);
+                    const uint32_t d = tmem + (layer == 1 ? 64u : 0u);
+                    for (int kk = 0; kk < 4; ++kk)
+                        tc_mma_bf16(d, tc_smem_desc(H + 256 * kk, 128, 1024), tc_smem_desc(W + 256 * kk, 128, 1024),
+                                    layer == 1 ? idesc64 : idesc16, kk > 0);
+                }
+                tc_commit(&bar);
+            }
+            const bool ok = mbar_wait_bounded(&bar, phase, TC_WAIT_BUDGET);
+            phase ^= 1u;
+            if (!ok) s_fail = 1;
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (s_fail) break;
+            if (layer == 0) {
+                tc_hidden(tmem + lanes, b1, H, t);
+            } else if (layer == 1) {
+                tc_hidden(tmem + lanes + 64, b2, H, t);
+            } else {
+                float y[16];
+                tc_ld16(tmem + lanes, y);
+                if (r < n) {
+                    const bool fx = fixed && fixed[r];
+#pragma unroll
+                    for (int o = 0; o < MLP_OUT; ++o) {
+                        const float d = dv_prev ? dv_prev[3 * r + o] : 0.f;
+                        dv0[3 * r + o] = fx ? 0.f : fmaf(y[o] + b3[o], sy[o], my[o]) + d;
+                    }
                 }
             }
         }
+        if (s_fail) break;
     }
+    // every tensor-memory read of this CTA is complete before the columns are released
+    tc_fence_before();
+    __syncthreads();
+    if (s_fail && t == 0) pc_set_err(err, PC_DERR_TIMEOUT);
+    if (warp == 0) tc_dealloc(tmem, TC_TMEM_COLS);
 }
 
 // ------------------------------------------------------------------------- training
@@ -684,10 +821,22 @@ extern "C" pc_status pc_mlp_infer(int64_t n, const float *params, const float *s
     int dev = 0, sms = 0;
     PC_CUDA_TRY(cudaGetDevice(&dev));
     PC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t tiles = (n + MLP_TILE - 1) / MLP_TILE;
-    const int grid = (int)std::min<int64_t>(tiles, 4ll * sms);
-    MLP_LAUNCH(mlp_infer_kernel, grid, MLP_THREADS, 0, st, n, params, stats, feat, dv_prev, fixed, dv0);
-    return PC_OK;
+    PC_CUDA_TRY(cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES));
+    static thread_local uint32_t *d_err = nullptr;  // timeout flag of this host thread's launches
+    static thread_local int err_dev = -1;
+    if (!d_err || err_dev != dev) {
+        PC_CUDA_TRY(cudaMalloc(&d_err, sizeof(uint32_t)));
+        err_dev = dev;
+    }
+    PC_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(uint32_t), st));
+    const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
+    const int grid = (int)std::min<int64_t>(tiles, 2ll * sms);
+    MLP_LAUNCH(mlp_infer_kernel, grid, TC_THREADS, TC_SMEM_BYTES, st, n, params, stats, feat, dv_prev, fixed, dv0,
+               d_err);
+    uint32_t h_err = 0;
+    PC_CUDA_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    PC_CUDA_TRY(cudaStreamSynchronize(st));
+    return h_err ? PC_ERR_TIMEOUT : PC_OK;
 }
 
 static pc_status mlp_grad_impl(pc_mlp *M, int64_t n, const int32_t *rows, const float *params, const float *stats,
