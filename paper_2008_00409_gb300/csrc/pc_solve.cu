@@ -165,8 +165,27 @@ __device__ __forceinline__ float pcg_alpha(const double *partials, int n_pq, pc_
     return s_alpha;
 }
 
+// Launch shape of the update kernel (measured at paper scale: 4 rows in flight per thread
+// and 2 CTAs per SM beat 1 x 8 by 14 us per iteration -- fewer CTAs also means fewer
+// copies of alpha's reduction)
+#ifndef UPD_UNROLL
+#define UPD_UNROLL 4      // rows per thread in flight
+#endif
+#ifndef UPD_CTAS_PER_SM
+#define UPD_CTAS_PER_SM 2
+#endif
+// the direction kernel is fastest in the plain shape (1 row per thread, 8 CTAs per SM)
+#ifndef DIR_UNROLL
+#define DIR_UNROLL 1
+#endif
+#ifndef DIR_CTAS_PER_SM
+#define DIR_CTAS_PER_SM 8
+#endif
+
 // Per row: x += alpha p; r -= alpha q; z = D^-1 r; partial (r.z, r.r); the last block
-// computes beta and applies the stop tests.
+// computes beta and applies the stop tests. Each thread keeps UPD_UNROLL rows in flight
+// (all loads issued before any use), and the first rows' loads are issued before
+// alpha's reduction so that their latencies overlap.
 template <bool BLOCK>
 __global__ void __launch_bounds__(EW_THREADS) pcg_update_kernel(int V, float4 *__restrict__ x4,
                                                                  const float4 *__restrict__ p4,
@@ -178,36 +197,44 @@ __global__ void __launch_bounds__(EW_THREADS) pcg_update_kernel(int V, float4 *_
 {
     pdl_wait();
     if (sc->done) return;
-    // the first row's loads are issued before alpha's reduction, so their latencies overlap
-    int row = blockIdx.x * blockDim.x + threadIdx.x;
-    float4 p = make_float4(0.f, 0.f, 0.f, 0.f), q = p, x = p, r = p;
-    if (row < V) {
-        p = p4[row];
-        q = q4[row];
-        x = x4[row];
-        r = r4[row];
-    }
+    const int stride = gridDim.x * blockDim.x;
+    const int first = blockIdx.x * blockDim.x + threadIdx.x;
+    float4 p[UPD_UNROLL], q[UPD_UNROLL], x[UPD_UNROLL], r[UPD_UNROLL];
+    auto load = [&](int base) {
+#pragma unroll
+        for (int u = 0; u < UPD_UNROLL; ++u) {
+            const int row = base + u * stride;
+            if (row < V) {
+                p[u] = p4[row];
+                q[u] = q4[row];
+                x[u] = x4[row];
+                r[u] = r4[row];
+            }
+        }
+    };
+    load(first);
     const float alpha = pcg_alpha(partials, n_pq, sc);
     float rz = 0.f, rr = 0.f;
-    for (; row < V; row += gridDim.x * blockDim.x) {
-        if (row != (int)(blockIdx.x * blockDim.x + threadIdx.x)) {
-            p = p4[row];
-            q = q4[row];
-            x = x4[row];
-            r = r4[row];
+    for (int base = first; base < V; base += UPD_UNROLL * stride) {
+        if (base != first) load(base);
+#pragma unroll
+        for (int u = 0; u < UPD_UNROLL; ++u) {
+            const int row = base + u * stride;
+            if (row >= V) break;
+            float4 xx = x[u], rv = r[u];
+            xx.x = fmaf(alpha, p[u].x, xx.x);
+            xx.y = fmaf(alpha, p[u].y, xx.y);
+            xx.z = fmaf(alpha, p[u].z, xx.z);
+            rv.x = fmaf(-alpha, q[u].x, rv.x);
+            rv.y = fmaf(-alpha, q[u].y, rv.y);
+            rv.z = fmaf(-alpha, q[u].z, rv.z);
+            const float4 z = apply_precond<BLOCK>(dinv4, row, rv);
+            x4[row] = xx;
+            r4[row] = rv;
+            z4[row] = z;
+            rz += dot3(rv, z);
+            rr += dot3(rv, rv);
         }
-        x.x = fmaf(alpha, p.x, x.x);
-        x.y = fmaf(alpha, p.y, x.y);
-        x.z = fmaf(alpha, p.z, x.z);
-        r.x = fmaf(-alpha, q.x, r.x);
-        r.y = fmaf(-alpha, q.y, r.y);
-        r.z = fmaf(-alpha, q.z, r.z);
-        const float4 z = apply_precond<BLOCK>(dinv4, row, r);
-        x4[row] = x;
-        r4[row] = r;
-        z4[row] = z;
-        rz += dot3(r, z);
-        rr += dot3(r, r);
     }
     pdl_trigger();
     double v[2] = {(double)rz, (double)rr};
@@ -441,6 +468,14 @@ static int spmv_grid(const pc_ctx *c)
     int g = c->num_sms * SP_CTAS_PER_SM;
     return tiles < g ? (tiles > 0 ? tiles : 1) : g;
 }
+static int shaped_grid(const pc_ctx *c, int64_t n, int ctas_per_sm)
+{
+    int64_t b = (n + EW_THREADS - 1) / EW_THREADS;
+    int64_t g = (int64_t)c->num_sms * ctas_per_sm;
+    return (int)(b < g ? (b > 0 ? b : 1) : g);
+}
+static int upd_grid(const pc_ctx *c, int64_t n) { return shaped_grid(c, n, UPD_CTAS_PER_SM); }
+static int dir_grid(const pc_ctx *c, int64_t n) { return shaped_grid(c, n, DIR_CTAS_PER_SM); }
 static int ew_grid(const pc_ctx *c, int64_t n)
 {
     int64_t b = (n + EW_THREADS - 1) / EW_THREADS;
@@ -564,9 +599,24 @@ __global__ void __launch_bounds__(EW_THREADS) pcg_direction_kernel(int V, const 
     pdl_wait();
     if (sc->done) return;
     const float beta = (float)sc->beta;
-    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
-        const float4 z = z4[row], p = p4[row];
-        p4[row] = make_float4(fmaf(beta, p.x, z.x), fmaf(beta, p.y, z.y), fmaf(beta, p.z, z.z), 0.f);
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x + threadIdx.x; base < V; base += DIR_UNROLL * stride) {
+        float4 z[DIR_UNROLL], p[DIR_UNROLL];
+#pragma unroll
+        for (int u = 0; u < DIR_UNROLL; ++u) {
+            const int row = base + u * stride;
+            if (row < V) {
+                z[u] = z4[row];
+                p[u] = p4[row];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < DIR_UNROLL; ++u) {
+            const int row = base + u * stride;
+            if (row < V)
+                p4[row] = make_float4(fmaf(beta, p[u].x, z[u].x), fmaf(beta, p[u].y, z[u].y),
+                                      fmaf(beta, p[u].z, z[u].z), 0.f);
+        }
     }
     pdl_trigger();
 }
@@ -590,17 +640,17 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
     const int n_pq = spmv_grid(c);
     for (int k = 0; k < count; ++k) {
         bool timed = c->profiling && k == 0;
-        PC_LAUNCH_PDL(c, pcg_direction_kernel, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (const float4 *)c->z,
+        PC_LAUNCH_PDL(c, pcg_direction_kernel, dir_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (const float4 *)c->z,
                       (float4 *)c->p0, (const pc_scalars *)c->sc);
         if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[0], s.st));
         PC_TRY(launch_spmv(c, a, s.diff, true, s.st));
         if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[1], s.st));
         if (s.block)
-            PC_LAUNCH_PDL(c, pcg_update_kernel<true>, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (float4 *)x,
+            PC_LAUNCH_PDL(c, pcg_update_kernel<true>, upd_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (float4 *)x,
                       (const float4 *)c->p0, (float4 *)c->r, (const float4 *)c->q, (const float4 *)c->dinv,
                       (float4 *)c->z, c->partials, n_pq, c->sc);
         else
-            PC_LAUNCH_PDL(c, pcg_update_kernel<false>, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (float4 *)x,
+            PC_LAUNCH_PDL(c, pcg_update_kernel<false>, upd_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (float4 *)x,
                       (const float4 *)c->p0, (float4 *)c->r, (const float4 *)c->q, (const float4 *)c->dinv,
                       (float4 *)c->z, c->partials, n_pq, c->sc);
         if (timed) {
