@@ -4,10 +4,10 @@
 // tiles of the matrix (the tile's contiguous run of 36-byte blocks and of column
 // indices) into a 2-stage shared-memory ring with 1-D bulk copies (cp.async.bulk)
 // completing on mbarriers, while 4 consumer warps compute the current tile with four
-// threads per row. Row pointers, the row's own vector entries and the difference-form
-// diagonal of the next tile are prefetched into registers before the current tile is
-// computed, so the only latency left on a tile's critical path is the gather of the
-// neighbours' vector entries. Tiles whose blocks exceed a stage (rows with many contacts)
+// threads per row, up to four gathers in flight per thread. Row pointers, the row's own
+// vector entries and the difference-form diagonal of the next tile are prefetched into
+// registers before the current tile is computed, so the only latency left on a tile's
+// critical path is the gather of the neighbours' vector entries. Tiles whose blocks exceed a stage (rows with many contacts)
 // are read directly from global memory.
 //
 // PCG mode computes q = A p and this CTA's p.q partial (slot 3 of the CTA's entry in the
@@ -191,35 +191,25 @@ __global__ void __launch_bounds__(SP_THREADS, SP_CTAS_PER_SM) spmv_kernel(SpmvAr
             const int32_t *s_cols = reinterpret_cast<const int32_t *>(smem_raw + s * SP_STAGE_BYTES + SP_VAL_BYTES) + co;
             float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
             const float4 xj = cur.xj;
-            int b = cur.rb + j;
-            for (; b + SP_TPR < cur.re; b += 2 * SP_TPR) {
-                int cA, cB;
-                const float *BA, *BB;
-                if (staged) {
-                    cA = s_cols[b - b0];
-                    cB = s_cols[b + SP_TPR - b0];
-                    BA = s_vals + 9 * (b - b0);
-                    BB = s_vals + 9 * (b + SP_TPR - b0);
-                } else {
-                    cA = a.ci[b];
-                    cB = a.ci[b + SP_TPR];
-                    BA = a.vals + 9ll * b;
-                    BB = a.vals + 9ll * (b + SP_TPR);
+            // up to four blocks per thread in flight (rows average about 13 blocks, so one
+            // round covers most rows): all gathers are issued before the first FMA
+            for (int b = cur.rb + j; b < cur.re; b += 4 * SP_TPR) {
+                float4 u[4];
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const int bw = b + w * SP_TPR;
+                    if (bw < cur.re) u[w] = spmv_gather<PCG>(a, staged ? s_cols[bw - b0] : a.ci[bw]);
                 }
-                float4 uA = spmv_gather<PCG>(a, cA), uB = spmv_gather<PCG>(a, cB);
-                if (DIFF) {
-                    uA.x -= xj.x; uA.y -= xj.y; uA.z -= xj.z;
-                    uB.x -= xj.x; uB.y -= xj.y; uB.z -= xj.z;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const int bw = b + w * SP_TPR;
+                    if (bw < cur.re) {
+                        const float *B = staged ? s_vals + 9 * (bw - b0) : a.vals + 9ll * bw;
+                        float4 uw = u[w];
+                        if (DIFF) { uw.x -= xj.x; uw.y -= xj.y; uw.z -= xj.z; }
+                        spmv_fma(B, uw, acc0, acc1, acc2);
+                    }
                 }
-                spmv_fma(BA, uA, acc0, acc1, acc2);
-                spmv_fma(BB, uB, acc0, acc1, acc2);
-            }
-            if (b < cur.re) {
-                const int c = staged ? s_cols[b - b0] : a.ci[b];
-                const float *B = staged ? s_vals + 9 * (b - b0) : a.vals + 9ll * b;
-                float4 u = spmv_gather<PCG>(a, c);
-                if (DIFF) { u.x -= xj.x; u.y -= xj.y; u.z -= xj.z; }
-                spmv_fma(B, u, acc0, acc1, acc2);
             }
             // the stage is no longer read by this warp: release it before the epilogue
             __syncwarp();
