@@ -32,7 +32,12 @@
 #ifndef SP_CTAS_PER_SM
 #define SP_CTAS_PER_SM 4
 #endif
+#ifndef SP_TPR
 #define SP_TPR 4                           // threads per row
+#endif
+#ifndef SP_WIN
+#define SP_WIN 4                           // gathers in flight per thread
+#endif
 #define SP_CWARPS (SP_ROWS * SP_TPR / 32)  // consumer warps
 #define SP_THREADS (32 * (SP_CWARPS + 1))  // + 1 producer warp
 #define SP_CAP (SP_ROWS * SP_CAP_PER_ROW)  // blocks per stage
@@ -193,15 +198,15 @@ __global__ void __launch_bounds__(SP_THREADS, SP_CTAS_PER_SM) spmv_kernel(SpmvAr
             const float4 xj = cur.xj;
             // up to four blocks per thread in flight (rows average about 13 blocks, so one
             // round covers most rows): all gathers are issued before the first FMA
-            for (int b = cur.rb + j; b < cur.re; b += 4 * SP_TPR) {
-                float4 u[4];
+            for (int b = cur.rb + j; b < cur.re; b += SP_WIN * SP_TPR) {
+                float4 u[SP_WIN];
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
+                for (int w = 0; w < SP_WIN; ++w) {
                     const int bw = b + w * SP_TPR;
                     if (bw < cur.re) u[w] = spmv_gather<PCG>(a, staged ? s_cols[bw - b0] : a.ci[bw]);
                 }
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
+                for (int w = 0; w < SP_WIN; ++w) {
                     const int bw = b + w * SP_TPR;
                     if (bw < cur.re) {
                         const float *B = staged ? s_vals + 9 * (bw - b0) : a.vals + 9ll * bw;
