@@ -106,8 +106,20 @@ typedef struct {
     int32_t refresh_every; /* PC_PREC_MIXED: ... or after this many iterations (default 1000) */
     int32_t check_every; /* iterations between convergence checks on the host (default 32) */
     int32_t precond;     /* PC_PRECOND_JACOBI (default) or PC_PRECOND_BLOCK */
-    int32_t reserved;
+    int32_t storage;     /* PC_STORAGE_FULL (default) or PC_STORAGE_SYM: matrix layout the PCG
+                            products read (the result is the same up to summation order) */
 } pc_solve_opts;
+
+/* PC_STORAGE_FULL: the products read the full BSR matrix.
+ * PC_STORAGE_SYM: at the start of each pc_pcg_solve / pc_step the (bitwise symmetric)
+ * matrix is rewritten into its upper blocks plus, per row, the list of lower blocks as
+ * references to the transposed upper blocks, and the products read that: a third less
+ * DRAM traffic per product, but the gathered lower blocks put a second round of
+ * dependent loads on each row's critical path, and on GB300 the product is slower
+ * (about 1.7x at 512^2). It falls back to the full matrix when the system is larger than
+ * the context's step-system capacity or its pattern is not symmetric. */
+#define PC_STORAGE_SYM 0
+#define PC_STORAGE_FULL 1
 
 typedef struct {
     int32_t iters;      /* PCG iterations (all inner solves) */

@@ -324,7 +324,12 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 
 // ------------------------------------------------------------------------- phases
 
+#ifndef BT_U
 #define BT_U 2  // rows per thread in flight in the vector phases
+#endif
+#ifndef BT_MIN_CTAS
+#define BT_MIN_CTAS 4  // register budget: four co-resident CTAs per SM
+#endif
 
 // Direction p = z + beta p over the listed rows; rows of an instance that has just
 // taken an FP64 residual first fold the FP32 increment into the FP64 accumulator.
@@ -779,7 +784,7 @@ __device__ void bt_phase_residual(const BtArgs &a, const bt_list &L, bool start)
 // ------------------------------------------------------------------------- the persistent kernel
 
 template <bool DIFF>
-__global__ void __launch_bounds__(SP_THREADS, 4) batched_pcg_kernel(BtArgs a)
+__global__ void __launch_bounds__(SP_THREADS, BT_MIN_CTAS) batched_pcg_kernel(BtArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t full_bar[SP_STAGES], empty_bar[SP_STAGES];

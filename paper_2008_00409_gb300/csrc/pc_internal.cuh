@@ -134,6 +134,14 @@ struct pc_ctx {
     pc_scalars *sc_host = nullptr; // pinned host mirror
     int32_t max_red_blocks = 0;
 
+    // symmetric storage of the system being solved (built per solve from the full BSR)
+    int64_t sym_cap = 0;
+    int32_t *sym_urp = nullptr, *sym_lrp = nullptr;  // [V+1]
+    int32_t *sym_dpos = nullptr;                     // [V] diagonal position in the full row
+    int32_t *sym_ucnt = nullptr, *sym_lcnt = nullptr;  // [V+1]
+    int32_t *sym_uci = nullptr, *sym_lcol = nullptr, *sym_lsrc = nullptr;  // [sym_cap + 4]
+    float *sym_uvals = nullptr;                      // [9 sym_cap + 16]
+
     // context-owned step system
     int32_t *A_rp = nullptr, *A_ci = nullptr;
     int64_t A_cap = 0;

@@ -82,6 +82,7 @@ static __device__ bool last_block_reduce(double *v, int n, double *partials, uin
 }
 
 #include "pc_spmv.cuh"
+#include "pc_spmv_sym.cuh"
 
 // ------------------------------------------------------------------------- preconditioner
 
@@ -505,6 +506,24 @@ pc_status pc_solver_alloc(pc_ctx *c)
     PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM_BYTES));
     PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM_BYTES));
     PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM_BYTES));
+    PC_CUDA_TRY(cudaFuncSetAttribute(spmv_sym_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SY_SMEM_BYTES));
+    PC_CUDA_TRY(cudaFuncSetAttribute(spmv_sym_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SY_SMEM_BYTES));
+    if (c->A_cap > 0) {  // symmetric storage for systems up to the step-system capacity
+        c->sym_cap = c->A_cap;
+        PC_CUDA_TRY(cudaMalloc(&c->sym_urp, sizeof(int32_t) * (c->V + 2ll)));
+        PC_CUDA_TRY(cudaMalloc(&c->sym_lrp, sizeof(int32_t) * (c->V + 2ll)));
+        PC_CUDA_TRY(cudaMalloc(&c->sym_dpos, sizeof(int32_t) * (size_t)c->V));
+        PC_CUDA_TRY(cudaMalloc(&c->sym_ucnt, sizeof(int32_t) * (c->V + 1ll)));
+        PC_CUDA_TRY(cudaMalloc(&c->sym_lcnt, sizeof(int32_t) * (c->V + 1ll)));
+        PC_CUDA_TRY(cudaMalloc(&c->sym_uci, sizeof(int32_t) * (size_t)(c->sym_cap + 4)));
+        PC_CUDA_TRY(cudaMalloc(&c->sym_lcol, sizeof(int32_t) * (size_t)(c->sym_cap + 4)));
+        PC_CUDA_TRY(cudaMalloc(&c->sym_lsrc, sizeof(int32_t) * (size_t)(c->sym_cap + 4)));
+        PC_CUDA_TRY(cudaMalloc(&c->sym_uvals, sizeof(float) * (size_t)(9 * c->sym_cap + 16)));
+        PC_CUDA_TRY(cudaMemset(c->sym_uvals, 0, sizeof(float) * (size_t)(9 * c->sym_cap + 16)));
+        PC_CUDA_TRY(cudaMemset(c->sym_uci, 0, sizeof(int32_t) * (size_t)(c->sym_cap + 4)));
+        PC_CUDA_TRY(cudaMemset(c->sym_lcol, 0, sizeof(int32_t) * (size_t)(c->sym_cap + 4)));
+        PC_CUDA_TRY(cudaMemset(c->sym_lsrc, 0, sizeof(int32_t) * (size_t)(c->sym_cap + 4)));
+    }
     for (int i = 0; i < 4; ++i) PC_CUDA_TRY(cudaEventCreate(&c->ev[i]));
     c->ev_used = 4;
     return PC_OK;
@@ -555,7 +574,7 @@ extern "C" void pc_default_solve_opts(pc_solve_opts *o)
     o->refresh_every = 1000;
     o->check_every = 32;
     o->precond = PC_PRECOND_JACOBI;
-    o->reserved = 0;
+    o->storage = PC_STORAGE_FULL;
 }
 
 struct SolveCtx {
@@ -564,7 +583,107 @@ struct SolveCtx {
     const float *vals, *dres, *b;
     bool diff, block;
     cudaStream_t st;
+    bool sym;  // the products read the symmetric storage
 };
+
+// ------------------------------------------------------------------------- symmetric storage
+
+// Per row: the diagonal's position in the full row (binary search; missing -> error bit),
+// the counts of upper (col >= row) and lower blocks.
+__global__ void sym_count_kernel(int V, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                 int32_t *dpos, int32_t *ucnt, int32_t *lcnt, uint32_t *err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > V) return;
+    if (i == V) {
+        ucnt[V] = 0;
+        lcnt[V] = 0;
+        return;
+    }
+    int lo = rp[i], hi = rp[i + 1];
+    const int end = hi;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (ci[mid] < i) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo >= end || ci[lo] != i) {
+        pc_set_err(err, PC_DERR_INDEX);
+        lo = rp[i];
+    }
+    dpos[i] = lo;
+    ucnt[i] = end - lo;
+    lcnt[i] = lo - rp[i];
+}
+
+// Upper blocks copied in row order; each lower block (i, j) refers to block (j, i) of
+// row j's upper part (binary search in row j; missing -> error bit: not symmetric).
+__global__ void sym_fill_kernel(int V, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                const float *__restrict__ vals, const int32_t *__restrict__ dpos,
+                                const int32_t *__restrict__ urp, const int32_t *__restrict__ lrp, int64_t cap,
+                                int32_t *uci, float *uvals, int32_t *lcol, int32_t *lsrc, uint32_t *err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= V) return;
+    const int d = dpos[i];
+    if (urp[i + 1] > cap || lrp[i + 1] > cap) {
+        pc_set_err(err, PC_DERR_INDEX);
+        return;
+    }
+    for (int k = d; k < rp[i + 1]; ++k) {
+        const int o = urp[i] + (k - d);
+        uci[o] = ci[k];
+        for (int e = 0; e < 9; ++e) uvals[9ll * o + e] = vals[9ll * k + e];
+    }
+    for (int k = rp[i]; k < d; ++k) {
+        const int jj = ci[k];
+        int lo = rp[jj], hi = rp[jj + 1];
+        const int end = hi;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (ci[mid] < i) lo = mid + 1;
+            else hi = mid;
+        }
+        const int o = lrp[i] + (k - rp[i]);
+        if (lo >= end || ci[lo] != i || lo < dpos[jj]) {
+            pc_set_err(err, PC_DERR_INDEX);
+            lcol[o] = jj;
+            lsrc[o] = urp[jj];
+            continue;
+        }
+        lcol[o] = jj;
+        lsrc[o] = urp[jj] + (lo - dpos[jj]);
+    }
+}
+
+// Build the symmetric storage of A (returns false, leaving the error bits clear, when
+// the pattern has no diagonal somewhere or is not symmetric).
+static pc_status build_sym(pc_ctx *c, const pc_bsr *A, const float *vals, bool *ok, cudaStream_t st)
+{
+    *ok = false;
+    const int V = c->V;
+    if (c->sym_cap <= 0 || A->nnzb > c->sym_cap) return PC_OK;
+    PC_LAUNCH(c, sym_count_kernel, pc_blocks(V + 1ll, 256), 256, 0, st, V, A->row_ptr, A->col_idx, c->sym_dpos,
+              c->sym_ucnt, c->sym_lcnt, c->d_err);
+    PC_TRY(pc_exclusive_scan(c, c->sym_ucnt, c->sym_urp, V, st));
+    PC_TRY(pc_exclusive_scan(c, c->sym_lcnt, c->sym_lrp, V, st));
+    PC_LAUNCH(c, sym_fill_kernel, pc_blocks(V, 128), 128, 0, st, V, A->row_ptr, A->col_idx, vals, c->sym_dpos,
+              c->sym_urp, c->sym_lrp, c->sym_cap, c->sym_uci, c->sym_uvals, c->sym_lcol, c->sym_lsrc, c->d_err);
+    // every lower block found its mirror (checked in the fill); equal counts of lower and
+    // off-diagonal upper blocks make that map a bijection: the pattern is symmetric
+    PC_CUDA_TRY(cudaMemcpyAsync(c->h_count, c->sym_urp + V, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PC_CUDA_TRY(cudaMemcpyAsync(reinterpret_cast<int32_t *>(c->h_count) + 1, c->sym_lrp + V, sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, st));
+    uint32_t bits = 0;
+    PC_TRY(pc_read_errors(c, st, &bits));
+    const int32_t n_up = reinterpret_cast<int32_t *>(c->h_count)[0], n_lo = reinterpret_cast<int32_t *>(c->h_count)[1];
+    if (bits || n_up - V != n_lo) {
+        PC_CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), st));
+        return PC_OK;
+    }
+    *ok = true;
+    return PC_OK;
+}
 
 static pc_status read_scalars(pc_ctx *c, cudaStream_t st)
 {
@@ -643,7 +762,26 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
         PC_LAUNCH_PDL(c, pcg_direction_kernel, dir_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (const float4 *)c->z,
                       (float4 *)c->p0, (const pc_scalars *)c->sc);
         if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[0], s.st));
-        PC_TRY(launch_spmv(c, a, s.diff, true, s.st));
+        if (s.sym) {
+            SymArgs y{};
+            y.V = c->V;
+            y.urp = c->sym_urp;
+            y.uci = c->sym_uci;
+            y.uvals = c->sym_uvals;
+            y.lrp = c->sym_lrp;
+            y.lcol = c->sym_lcol;
+            y.lsrc = c->sym_lsrc;
+            y.dres = s.dres;
+            y.x4 = (const float4 *)c->p0;
+            y.y4 = (float4 *)c->q;
+            y.partials = c->partials;
+            y.sc = c->sc;
+            y.err = c->d_err;
+            if (s.diff) PC_LAUNCH_PDL(c, spmv_sym_kernel<true>, n_pq, SP_THREADS, SY_SMEM_BYTES, s.st, y);
+            else PC_LAUNCH_PDL(c, spmv_sym_kernel<false>, n_pq, SP_THREADS, SY_SMEM_BYTES, s.st, y);
+        } else {
+            PC_TRY(launch_spmv(c, a, s.diff, true, s.st));
+        }
         if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[1], s.st));
         if (s.block)
             PC_LAUNCH_PDL(c, pcg_update_kernel<true>, upd_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (float4 *)x,
@@ -701,8 +839,9 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
     cudaStream_t st = (cudaStream_t)stream;
     const int V = ctx->V;
     const int64_t n = 3ll * V;
-    SolveCtx s{ctx, A, vals, dres, b, dres != nullptr, o.precond == PC_PRECOND_BLOCK, st};
+    SolveCtx s{ctx, A, vals, dres, b, dres != nullptr, o.precond == PC_PRECOND_BLOCK, st, false};
     PC_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), st));
+    if (o.storage == PC_STORAGE_SYM) PC_TRY(build_sym(ctx, A, vals, &s.sym, st));
     if (s.block)
         PC_LAUNCH(ctx, dinv_kernel<true>, pc_blocks(V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals,
                   (float4 *)ctx->dinv, ctx->d_err);

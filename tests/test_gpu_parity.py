@@ -311,3 +311,60 @@ def test_deterministic_repeat(pc):
         outs.append((_np(s["vals"]).copy(), _np(s["b"]).copy(), _np(dv).copy()))
     for u, v in zip(outs[0], outs[1]):
         np.testing.assert_array_equal(u, v)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_symmetric_and_full_storage_agree_with_oracle(pc, case):
+    wl = CASES[case]()
+    cl, om, pairs, w, pd, wd = _setup(pc, wl)
+    s = cl.assemble(pd, wd)
+    rp, ci, vals_ref, b_ref = om.assemble(wl.x0.astype(np.float64), wl.v0.astype(np.float64), pairs, w, wl.h)
+    dv_ref, _, _ = oracle.pcg(rp, ci, vals_ref, b_ref, tol=1e-12)
+    out = {}
+    for storage in (pc.PC_STORAGE_SYM, pc.PC_STORAGE_FULL):
+        dv = torch.zeros(cl.V * 3, device="cuda")
+        info, st = pc.pc_pcg_solve(cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"], s["dres"], s["b"], dv,
+                                   pc.solve_opts(tol=1e-9, precision=pc.PC_PREC_MIXED, max_iter=50000,
+                                                 storage=storage))
+        assert st == pc.PC_OK and info.rel_res <= 2e-9
+        assert H.rel_l2(_np(dv), dv_ref) <= H.DV_RTOL
+        out[storage] = (info.iters, _np(dv))
+    # same method, products summed in another order: nearly the same iteration count
+    assert abs(out[pc.PC_STORAGE_SYM][0] - out[pc.PC_STORAGE_FULL][0]) <= 0.05 * out[pc.PC_STORAGE_FULL][0] + 5
+
+
+def test_asymmetric_pattern_falls_back_to_full_storage(pc):
+    wl = CASES["ragged37x29-contacts"]()
+    cl, om, pairs, w, pd, wd = _setup(pc, wl)
+    s = cl.assemble(pd, wd)
+    nnzb = s["nnzb"]
+    rp = _np(s["row_ptr"]).astype(np.int64)
+    ci = _np(s["col_idx"])[:nnzb]
+    vals = _np(s["vals"])[: 9 * nnzb].reshape(-1, 9)
+    # add an explicit zero block (i, j) to row i only: the matrix is unchanged, the
+    # pattern is no longer symmetric
+    i, j = 100, cl.V - 1
+    assert j not in ci[rp[i]:rp[i + 1]]
+    k = rp[i] + int(np.searchsorted(ci[rp[i]:rp[i + 1]], j))
+    ci2 = np.insert(ci, k, j).astype(np.int32)
+    v2 = np.insert(vals, k, np.zeros(9, np.float32), axis=0)
+    rp2 = rp.copy()
+    rp2[i + 1:] += 1
+    n2 = nnzb + 1
+    cap = (n2 + 3) // 4 * 4
+    ci_p = np.zeros(cap, np.int32)
+    ci_p[:n2] = ci2
+    v_p = np.zeros((cap, 9), np.float32)
+    v_p[:n2] = v2
+    args = [torch.from_numpy(rp2.astype(np.int32)).cuda(), torch.from_numpy(ci_p).cuda(), n2,
+            torch.from_numpy(v_p.reshape(-1)).cuda(), s["dres"], s["b"]]
+    res = {}
+    for storage in (pc.PC_STORAGE_SYM, pc.PC_STORAGE_FULL):
+        dv = torch.zeros(cl.V * 3, device="cuda")
+        info, st = pc.pc_pcg_solve(cl.ctx, *args, dv, pc.solve_opts(tol=1e-9, precision=pc.PC_PREC_MIXED,
+                                                                      max_iter=50000, storage=storage))
+        res[storage] = (st, info.iters, _np(dv))
+    assert res[pc.PC_STORAGE_FULL][0] == pc.PC_OK
+    # the symmetric layout is refused and the full matrix gives the identical solve
+    assert res[pc.PC_STORAGE_SYM][1] == res[pc.PC_STORAGE_FULL][1]
+    assert np.array_equal(res[pc.PC_STORAGE_SYM][2], res[pc.PC_STORAGE_FULL][2])

@@ -30,7 +30,9 @@ def test_static_solve_matches_context_solve_on_two_calls(pc, precision):
     cl = pc.Cloth(wl)
     s = cl.assemble()
     prec = pc.PC_PREC_MIXED if precision == "mixed" else pc.PC_PREC_FP32
-    opts = pc.solve_opts(tol=1e-9 if precision == "mixed" else 1e-6, precision=prec, max_iter=50000)
+    # the static entry point reads the full matrix; compare with the context solve on the same layout
+    opts = pc.solve_opts(tol=1e-9 if precision == "mixed" else 1e-6, precision=prec, max_iter=50000,
+                         storage=pc.PC_STORAGE_FULL)
     ref = torch.zeros(cl.V * 3, device="cuda")
     info_ref, _ = pc.pc_pcg_solve(cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"], s["dres"], s["b"], ref,
                                   opts)
