@@ -78,3 +78,62 @@ def test_full_size_pattern_values_and_solve(pc, name):
     assert abs(rel - info.rel_res) <= 1e-3 * info.rel_res + 1e-12
     # pinned vertices do not move
     assert np.all(x64[wl.pins] == 0.0)
+
+
+def test_full_size_batched_solve(pc):
+    """The 64-garment union through the persistent batched solver (autotuned launch):
+    every garment's dv against a tight single-system solve of the same union."""
+    u = wk.garment_batch_union()
+    cl = pc.Cloth(u)
+    s = cl.assemble(*cl.contacts_device(0))
+    dv = torch.zeros(cl.V * 3, device="cuda")
+    infos, st = pc.pc_pcg_solve_batched(cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"], s["dres"], s["b"],
+                                        dv, u.inst_rows, pc.solve_opts(tol=1e-8, max_iter=50000))
+    assert st == pc.PC_OK
+    assert all(i.rel_res <= 2e-8 for i in infos)
+    ref = torch.zeros_like(dv)
+    info, st = pc.pc_pcg_solve(cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"], s["dres"], s["b"], ref,
+                               pc.solve_opts(tol=1e-11, precision=pc.PC_PREC_MIXED, max_iter=200000))
+    assert st == pc.PC_OK
+    got = dv.cpu().numpy().reshape(-1, 3)
+    want = ref.cpu().numpy().reshape(-1, 3)
+    for k in range(len(u.parts)):
+        r0, r1 = u.inst_rows[k], u.inst_rows[k + 1]
+        assert H.rel_l2(got[r0:r1], want[r0:r1]) <= H.DV_RTOL, k
+
+
+def test_full_size_learned_guess(pc):
+    """Features and the tensor-core inference on the 708 x 708 cloth against the oracle
+    on a random sample of rows."""
+    from oracle import mlp as om
+    wl = wk.warm_start_eval()
+    cl = pc.Cloth(wl)
+    pairs, w = wl.contacts(0)
+    pd, wd = cl.contacts_device(0)
+    rng = np.random.default_rng(31)
+    v = (0.05 * rng.normal(size=(wl.V, 3))).astype(np.float32)
+    dvp = (1e-3 * rng.normal(size=(wl.V, 3))).astype(np.float32)
+    vt, dvpt = torch.from_numpy(v).cuda(), torch.from_numpy(dvp).cuda()
+    s = cl.assemble(pd, wd, v=vt)
+    feat = torch.empty(wl.V, 12, device="cuda")
+    pc.pc_mlp_features(cl.ctx, vt, dvpt, s["b"], wl.h, feat)
+    mesh = oracle.Mesh.from_workload(wl)
+    sample = rng.choice(wl.V, 20000, replace=False)
+    g = wl.material.as_array()[5:8]
+    want = om.features(v, dvp, s["b"].cpu().numpy().astype(np.float64), mesh.mass, wl.h, g,
+                       om.edges_of(wl.tris))[sample]
+    got = feat.cpu().numpy().astype(np.float64)[sample]
+    assert np.all(np.abs(got - want) <= 2e-6 * np.abs(want).max(axis=0) + 1e-12)
+    params = om.init_params(4).astype(np.float32)
+    F = feat.cpu().numpy().astype(np.float64)
+    stats = om.compute_stats(F, 1e-3 * rng.normal(size=(wl.V, 3))).astype(np.float32)
+    out = torch.empty(wl.V, 3, device="cuda")
+    pinned = np.zeros(wl.V, np.uint8)
+    pinned[wl.pins] = 1
+    pc.pc_mlp_infer(wl.V, torch.from_numpy(params).cuda(), torch.from_numpy(stats).cuda(), feat, dvpt,
+                    torch.from_numpy(pinned).cuda(), out)
+    pred = om.predict(params.astype(np.float64), stats.astype(np.float64), F[sample], dvp[sample],
+                      pinned[sample].astype(bool), bf16=True)
+    o = out.cpu().numpy().astype(np.float64)[sample]
+    assert np.linalg.norm((o - dvp[sample]) - (pred - dvp[sample])) <= 2e-3 * np.linalg.norm(pred - dvp[sample])
+    assert np.all(out.cpu().numpy()[wl.pins] == 0.0)
