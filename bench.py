@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--max-iter", type=int, default=20000, help="PCG iteration cap per step (short profiling runs)")
     ap.add_argument("--precond", default="jacobi", choices=["jacobi", "block"])
+    ap.add_argument("--storage", default="full", choices=["full", "sym"], help="matrix layout of the PCG products")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--form", default="step", choices=["step", "batched", "warmstart"])
@@ -240,6 +241,7 @@ def run_ours(args):
     cl = pc.Cloth(wl)
     prec = pc.PC_PREC_MIXED if args.precision == "mixed" else pc.PC_PREC_FP32
     precond = pc.PC_PRECOND_BLOCK if args.precond == "block" else pc.PC_PRECOND_JACOBI
+    storage = pc.PC_STORAGE_SYM if args.storage == "sym" else pc.PC_STORAGE_FULL
     nsteps = args.warmup + args.steps
     contacts = [cl.contacts_device(k % max(wl.steps, 1)) for k in range(nsteps)]
     torch.cuda.synchronize()
@@ -247,7 +249,7 @@ def run_ours(args):
     def one_step(k):
         pd, wd = contacts[k]
         info, st = cl.step(pd, wd, tol=args.tol, precision=prec, warm_start=pc.PC_WARM_PREV,
-                           max_iter=args.max_iter, precond=precond, allow_not_converged=True)
+                           max_iter=args.max_iter, precond=precond, storage=storage, allow_not_converged=True)
         return info
 
     for k in range(args.warmup):
@@ -299,7 +301,8 @@ def run_ours(args):
         cl_e = pc.Cloth(wl)
         o = pc.pc_step_opts()
         o.h = wl.h
-        o.solve = pc.solve_opts(tol=args.tol, precision=prec, max_iter=args.max_iter, precond=precond)
+        o.solve = pc.solve_opts(tol=args.tol, precision=prec, max_iter=args.max_iter, precond=precond,
+                                storage=storage)
         o.warm_start = pc.PC_WARM_PREV
         for k in range(args.warmup):
             pc.pc_step_host(cl_e.ctx, xh, vh, host_contacts[k][0], host_contacts[k][1], o, allow_not_converged=True)
