@@ -390,7 +390,7 @@ def run_batched(args):
         torch.cuda.synchronize()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = pc.pc_launch_count(cl.ctx) - launches0
-    bps, tune_ms = pc.pc_batched_config(cl.ctx)
+    bps, order, tune_ms = pc.pc_batched_config(cl.ctx)
     its = np.array(its)
     seq = None
     if not args.no_sequential:
@@ -419,7 +419,8 @@ def run_batched(args):
                       "l2": f"matrix {len(u.tris) * 13 * 40 / 1e6 / 2:.0f} MB (L2 is 129 MB)",
                       "iters_per_garment_min": int(its.min()), "iters_per_garment_mean": float(its.mean()),
                       "iters_per_garment_max": int(its.max()), "max_rel_res": float(max(rels)),
-                      "autotuned_ctas_per_sm": bps, "autotune_ms": tune_ms},
+                      "autotuned_ctas_per_sm": bps, "autotuned_spmv_order": ["strided", "chunked"][order],
+                      "autotune_ms": {"strided": tune_ms[0], "chunked": tune_ms[1]}},
            "sequential_steps_per_s": seq, "gpu_launches": int(launches), "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
 

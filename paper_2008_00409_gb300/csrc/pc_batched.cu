@@ -90,6 +90,7 @@ struct BtArgs {
     uint32_t *err;
     double tol, refresh;
     int max_iter, refresh_every;
+    int spmv_chunked;          // SpMV entry order: 0 strided, 1 contiguous chunks (autotuned)
 };
 
 // The work list of one phase: the listed instances in order, each contributing one entry
@@ -411,27 +412,44 @@ __device__ __forceinline__ void bt_cursor_load(const BtArgs &a, const bt_list &L
     cu.tb = cu.r0 / BT_TILE;
 }
 
-// Entries this CTA takes in the strided order (b, b+G, b+2G, ... below the total).
-__device__ __forceinline__ int bt_strided_count(const bt_list &L)
+// Entries this CTA takes in the SpMV phase: first entry, step and count. Strided order:
+// b, b+G, b+2G, ... (all CTAs on one band of rows at a time); chunked order: the CTA's
+// contiguous chunk. Either way a CTA meets each instance in one run of its entries.
+struct bt_sched {
+    int j0, step, n;
+};
+
+__device__ __forceinline__ bt_sched bt_spmv_sched(const BtArgs &a, const bt_list &L)
 {
-    return (int)blockIdx.x < L.total ? (L.total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    bt_sched s;
+    if (a.spmv_chunked) {
+        s.j0 = (int)blockIdx.x * L.chunk;
+        s.step = 1;
+        s.n = max(0, min(L.total, s.j0 + L.chunk) - s.j0);
+    } else {
+        s.j0 = blockIdx.x;
+        s.step = gridDim.x;
+        s.n = (int)blockIdx.x < L.total ? (L.total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    }
+    return s;
 }
 
-// q = A p over the listed rows with the bulk-copy stage ring. Entries are taken in the
-// strided order (CTA b: b, b+G, b+2G, ...), so that at any time the CTAs work on one
-// narrow band of rows. A CTA still meets each instance in one run of consecutive entries
-// (an instance's entries are contiguous), beginning at p0 + ((b - p0) mod G); each
-// consumer warp stores its p.q over the run in that entry's slot, so the instance's
-// slots are entries p0 .. p0 + min(G, p1 - p0) - 1, one per CTA taking part, and they
-// are summed where alpha is needed (bt_alpha). `kbase` continues the mbarrier phase
-// count across calls.
+// q = A p over the listed rows with the bulk-copy stage ring, entries in the order the
+// autotuner chose (bt_spmv_sched). A CTA meets each instance in one run of its entries
+// (an instance's entries are contiguous); each consumer warp stores its p.q over the run
+// in the slot of the run's first entry, and the slots are summed where alpha is needed
+// (bt_alpha). Strided order: the run starts at p0 + ((b - p0) mod G), so the instance's
+// slots are entries p0 .. p0 + min(G, p1 - p0) - 1; chunked order: max(b * chunk, p0)
+// for the CTAs b whose chunk meets [p0, p1). `kbase` continues the mbarrier phase count
+// across calls.
 template <bool DIFF>
 __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *smem_raw, uint64_t *full_bar,
                               uint64_t *empty_bar, int (*stage_info)[4], int kbase, int par)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int G = gridDim.x, j0 = blockIdx.x;
-    const int nent = bt_strided_count(L);
+    const bt_sched sched = bt_spmv_sched(a, L);
+    const int G = sched.step, j0 = sched.j0;
+    const int nent = sched.n;
     // the refresh counter of the previous iteration has been read by every CTA
     if (blockIdx.x == 0 && threadIdx.x == 0) a.g->n_refresh[par ^ 1] = 0u;
     bool timed_out = false;
@@ -596,16 +614,20 @@ __device__ float bt_alpha(const BtArgs &a, const bt_list &L, const bt_seg &sg)
     __shared__ float s_alpha;
     const int p0 = L.pref[sg.m], p1 = L.pref[sg.m + 1];
     static_assert(SP_CWARPS == 4, "a p.q slot is four doubles (two double2)");
-    const int n = min((int)gridDim.x, p1 - p0);
-    const double2 *slots = reinterpret_cast<const double2 *>(a.part_pq + (int64_t)SP_CWARPS * p0);
+    const int c = L.chunk;
+    const int n = a.spmv_chunked ? (p1 - 1) / c - p0 / c + 1 : min((int)gridDim.x, p1 - p0);
+    auto slot = [&](int i) -> int64_t { return a.spmv_chunked ? max((p0 / c + i) * c, p0) : p0 + i; };
+    const double2 *slots = reinterpret_cast<const double2 *>(a.part_pq);
     double acc0 = 0.0, acc1 = 0.0;
     for (int i = threadIdx.x; i < n; i += 2 * blockDim.x) {
         const int i2 = i + blockDim.x;
-        const double2 x0 = __ldcg(slots + 2 * i), x1 = __ldcg(slots + 2 * i + 1);
+        const int64_t s0 = 2 * slot(i);
+        const double2 x0 = __ldcg(slots + s0), x1 = __ldcg(slots + s0 + 1);
         double2 y0 = make_double2(0.0, 0.0), y1 = make_double2(0.0, 0.0);
         if (i2 < n) {
-            y0 = __ldcg(slots + 2 * i2);
-            y1 = __ldcg(slots + 2 * i2 + 1);
+            const int64_t s1 = 2 * slot(i2);
+            y0 = __ldcg(slots + s1);
+            y1 = __ldcg(slots + s1 + 1);
         }
         acc0 += (x0.x + x0.y) + (x1.x + x1.y);
         acc1 += (y0.x + y0.y) + (y1.x + y1.y);
@@ -822,7 +844,7 @@ __global__ void __launch_bounds__(SP_THREADS, BT_MIN_CTAS) batched_pcg_kernel(Bt
         bt_phase_direction(a, L);
         if (!bt_grid_sync(a.g)) return;
         bt_phase_spmv<DIFF>(a, L, smem_raw, full_bar, empty_bar, stage_info, kbase, par);
-        kbase += bt_strided_count(L);
+        kbase += bt_spmv_sched(a, L).n;
         if (!bt_grid_sync(a.g)) return;
         bt_phase_update(a, L, par);
         if (!bt_grid_sync(a.g)) return;
@@ -901,9 +923,10 @@ struct pc_batched_state {
     int32_t *inst_rows = nullptr;  // [max_inst + 1]
     int max_inst = 0;
     int blocks_per_sm = 0;         // autotuned launch shape (0 = not tuned yet)
+    int spmv_order = 0;            // autotuned SpMV entry order: 0 strided, 1 chunked
     int64_t tuned_nnzb = -1;
     int tuned_inst = -1;
-    float tune_ms[5] = {0, 0, 0, 0, 0};
+    float tune_ms[2][5] = {};       // [order][CTAs per SM] timings of the tuning runs
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream the step graph is captured on
 };
@@ -952,7 +975,7 @@ static int bt_max_blocks_per_sm(bool diff)
 // host synchronisation, so it can be captured).
 static pc_status bt_enqueue(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, const float *vals, const float *dres,
                             const float *b, float *dv, int n_inst, const pc_solve_opts &o, int blocks_per_sm,
-                            cudaStream_t st)
+                            int spmv_order, cudaStream_t st)
 {
     const int V = c->V;
     PC_LAUNCH(c, bt_dinv_kernel, pc_blocks(V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals,
@@ -984,6 +1007,7 @@ static pc_status bt_enqueue(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, con
     a.refresh = o.refresh;
     a.max_iter = o.max_iter;
     a.refresh_every = o.refresh_every;
+    a.spmv_chunked = spmv_order;
     return bt_launch(c, B, a, dres != nullptr, blocks_per_sm, st);
 }
 
@@ -1006,7 +1030,8 @@ static pc_status bt_setup_instances(pc_ctx *c, pc_batched_state *B, const pc_bsr
 }
 
 // Autotuner: on the first solve of a given shape, time a short solve (fixed iteration
-// budget) for each feasible number of co-resident CTAs per SM and keep the fastest.
+// budget) for each schedule -- SpMV entry order (strided or chunked) x co-resident CTAs
+// per SM (1..4, as far as they fit) -- and keep the fastest.
 static pc_status bt_autotune(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, const float *vals, const float *dres,
                              const float *b, int n_inst, const pc_solve_opts &o, cudaStream_t st)
 {
@@ -1017,26 +1042,28 @@ static pc_status bt_autotune(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, co
     t.max_iter = std::min(o.max_iter, 60);
     t.tol = 1e-30;  // run the whole budget
     float best = 1e30f;
-    int best_b = maxb;
+    int best_b = maxb, best_order = 0;
     cudaEvent_t e0, e1;
     PC_CUDA_TRY(cudaEventCreate(&e0));
     PC_CUDA_TRY(cudaEventCreate(&e1));
     float *scratch_dv = c->rhs32;  // float[V][3], a zero guess
-    for (int nb = 1; nb <= maxb; ++nb) {
-        PC_CUDA_TRY(cudaMemsetAsync(scratch_dv, 0, sizeof(float) * 3 * (size_t)c->V, st));
-        PC_CUDA_TRY(cudaEventRecord(e0, st));
-        pc_status s = bt_enqueue(c, B, A, vals, dres, b, scratch_dv, n_inst, t, nb, st);
-        PC_CUDA_TRY(cudaEventRecord(e1, st));
-        if (s != PC_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
-        PC_CUDA_TRY(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        PC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-        B->tune_ms[nb] = ms;
-        if (ms < best) { best = ms; best_b = nb; }
-    }
+    for (int order = 0; order < 2; ++order)
+        for (int nb = 1; nb <= maxb; ++nb) {
+            PC_CUDA_TRY(cudaMemsetAsync(scratch_dv, 0, sizeof(float) * 3 * (size_t)c->V, st));
+            PC_CUDA_TRY(cudaEventRecord(e0, st));
+            pc_status s = bt_enqueue(c, B, A, vals, dres, b, scratch_dv, n_inst, t, nb, order, st);
+            PC_CUDA_TRY(cudaEventRecord(e1, st));
+            if (s != PC_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
+            PC_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            PC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            B->tune_ms[order][nb] = ms;
+            if (ms < best) { best = ms; best_b = nb; best_order = order; }
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     B->blocks_per_sm = best_b;
+    B->spmv_order = best_order;
     B->tuned_nnzb = A->nnzb;
     B->tuned_inst = n_inst;
     return PC_OK;
@@ -1083,18 +1110,21 @@ extern "C" pc_status pc_pcg_solve_batched(pc_ctx *ctx, const pc_bsr *A, const fl
     PC_TRY(bt_setup_instances(ctx, B, A, n_inst, inst_rows, st));
     PC_TRY(bt_autotune(ctx, B, A, vals, dres, b, n_inst, o, st));
     PC_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), st));
-    PC_TRY(bt_enqueue(ctx, B, A, vals, dres, b, dv, n_inst, o, B->blocks_per_sm, st));
+    PC_TRY(bt_enqueue(ctx, B, A, vals, dres, b, dv, n_inst, o, B->blocks_per_sm, B->spmv_order, st));
     return bt_collect(ctx, B, n_inst, info, st);
 }
 
-extern "C" pc_status pc_batched_config(pc_ctx *ctx, int32_t *blocks_per_sm, float *tune_ms /*[4]*/)
+extern "C" pc_status pc_batched_config(pc_ctx *ctx, int32_t *blocks_per_sm, int32_t *spmv_order,
+                                       float *tune_ms /*[8]*/)
 {
     if (!ctx) return PC_ERR_ARG;
     pc_batched_state *B = bt_state(ctx);
     if (!B) return PC_ERR_CUDA;
     if (blocks_per_sm) *blocks_per_sm = B->blocks_per_sm;
+    if (spmv_order) *spmv_order = B->spmv_order;
     if (tune_ms)
-        for (int i = 0; i < 4; ++i) tune_ms[i] = B->tune_ms[i + 1];
+        for (int order = 0; order < 2; ++order)
+            for (int i = 0; i < 4; ++i) tune_ms[4 * order + i] = B->tune_ms[order][i + 1];
     return PC_OK;
 }
 
@@ -1130,7 +1160,8 @@ extern "C" pc_status pc_step_batched(pc_ctx *ctx, float *x, float *v, const pc_c
     PC_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     pc_status s = pc_assemble_values(ctx, &A, x, v, contacts, opts->h, ctx->A_vals, ctx->A_b, ctx->A_dres, (void *)cs);
     if (s == PC_OK)
-        s = bt_enqueue(ctx, B, &A, ctx->A_vals, ctx->A_dres, ctx->A_b, ctx->A_dv, n_inst, o, B->blocks_per_sm, cs);
+        s = bt_enqueue(ctx, B, &A, ctx->A_vals, ctx->A_dres, ctx->A_b, ctx->A_dv, n_inst, o, B->blocks_per_sm,
+                       B->spmv_order, cs);
     if (s == PC_OK) s = pc_update_state(ctx, x, v, ctx->A_dv, opts->h, cs);
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     if (s != PC_OK) {

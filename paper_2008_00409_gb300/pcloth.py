@@ -104,7 +104,7 @@ def _load():
                                        c_void_p, P(pc_solve_opts), c_void_p, c_void_p]
     L.pc_step_batched.argtypes = [c_void_p, c_void_p, c_void_p, P(pc_contacts), c_int32, c_void_p, P(pc_step_opts),
                                   c_void_p, c_void_p]
-    L.pc_batched_config.argtypes = [c_void_p, P(c_int32), c_void_p]
+    L.pc_batched_config.argtypes = [c_void_p, P(c_int32), P(c_int32), c_void_p]
     L.pc_step_host.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, P(pc_step_opts),
                                P(pc_step_info), c_void_p]
     L.pc_mlp_features.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_void_p, c_void_p]
@@ -308,10 +308,12 @@ def pc_step_batched(ctx, x, v, pairs, w, inst_rows, opts: pc_step_opts, stream=N
 
 
 def pc_batched_config(ctx):
-    bps = c_int32()
-    ms = (c_float * 4)()
-    _check(_lib.pc_batched_config(ctx, ctypes.byref(bps), ctypes.cast(ms, c_void_p)), "pc_batched_config")
-    return bps.value, list(ms)
+    """(CTAs per SM, SpMV entry order 0 strided / 1 chunked, timings [order][CTAs-1] ms)."""
+    bps, order = c_int32(), c_int32()
+    ms = (c_float * 8)()
+    _check(_lib.pc_batched_config(ctx, ctypes.byref(bps), ctypes.byref(order), ctypes.cast(ms, c_void_p)),
+           "pc_batched_config")
+    return bps.value, order.value, [list(ms[0:4]), list(ms[4:8])]
 
 
 def pc_step(ctx, x, v, pairs, w, opts: pc_step_opts, dv_out=None, stream=None, allow_not_converged=False):
