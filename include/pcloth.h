@@ -267,10 +267,21 @@ PC_API pc_status pc_pcg_solve_batched(pc_ctx *ctx, const pc_bsr *A, const float 
  * not tried). Host pointers, may be NULL. */
 PC_API pc_status pc_batched_config(pc_ctx *ctx, int32_t *blocks_per_sm, int32_t *spmv_order, float *tune_ms);
 
+/* Cycle budget of each grid-barrier wait in the persistent batched solver (the solver's
+ * software barrier spins on a generation word; a wait longer than the budget aborts the
+ * launch: every CTA leaves at its next barrier, no result is written back, dv keeps its
+ * initial guess, and pc_pcg_solve_batched / pc_step_batched return PC_ERR_TIMEOUT with
+ * the context still usable). cycles <= 0 restores the default of 2^31 SM cycles (about
+ * a second at 2 GHz). A budget of a few cycles makes every solve time out: that is how the
+ * timeout path is exercised without a hang. Host-only; takes effect at the next launch. */
+PC_API pc_status pc_set_barrier_wait(pc_ctx *ctx, int64_t cycles);
+
 /* One batched time step: the dynamic pattern of the whole union (synchronous), then a
  * CUDA graph holding value assembly, the persistent batched solve and v += dv,
  * x += h v, replayed (updated in place) from step to step. Instances as for
- * pc_pcg_solve_batched; info receives one result per instance. */
+ * pc_pcg_solve_batched; info receives one result per instance. The update applies to
+ * the instances whose solve ended PC_OK or PC_ERR_NOT_CONVERGED; an instance that failed
+ * (PC_ERR_NONFINITE) keeps its x and v, and after PC_ERR_TIMEOUT no instance moves. */
 PC_API pc_status pc_step_batched(pc_ctx *ctx, float *x, float *v, const pc_contacts *contacts, int32_t n_inst,
                                  const int32_t *inst_rows, const pc_step_opts *opts, pc_solve_info *info,
                                  void *stream);

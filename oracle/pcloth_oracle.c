@@ -65,6 +65,8 @@ typedef struct {
     double mu, lam;
 } om_mesh;
 
+void om_spmv(int V, const int *row_ptr, const int *col_idx, const double *vals, const double *x, double *y);
+
 /* ------------------------------------------------------------------ small vector helpers */
 
 static void sub3(const double *a, const double *b, double *o) { o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2]; }

@@ -91,6 +91,7 @@ struct BtArgs {
     double tol, refresh;
     int max_iter, refresh_every;
     int spmv_chunked;          // SpMV entry order: 0 strided, 1 contiguous chunks (autotuned)
+    long long bar_wait;        // cycles a grid-barrier wait may take before the launch aborts
 };
 
 // The work list of one phase: the listed instances in order, each contributing one entry
@@ -205,7 +206,7 @@ __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p)
 
 // All CTAs of the (co-resident) grid meet; returns false everywhere once any CTA gave
 // up waiting (the launch then unwinds without further waits).
-__device__ bool bt_grid_sync(bt_global *g)
+__device__ bool bt_grid_sync(bt_global *g, long long budget)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -223,7 +224,7 @@ __device__ bool bt_grid_sync(bt_global *g)
                 const long long t0 = clock64();
                 while (ld_acquire_gpu(&g->bar_gen) == gen) {
                     if (ld_acquire_gpu(&g->abort) != 0u) { ok = 0; break; }
-                    if (clock64() - t0 > SP_WAIT_BUDGET) {
+                    if (clock64() - t0 > budget) {
                         atomicExch(&g->abort, 1u);
                         ok = 0;
                         break;
@@ -826,7 +827,7 @@ __global__ void __launch_bounds__(SP_THREADS, BT_MIN_CTAS) batched_pcg_kernel(Bt
     // ---- start: x64 = dv0 and x = 0 (set before launch); r = b - A x64, z, p = 0
     bt_build_list(a, BT_LIST_ALL, L);
     bt_phase_residual<DIFF>(a, L, true);
-    if (!bt_grid_sync(a.g)) return;
+    if (!bt_grid_sync(a.g, a.bar_wait)) return;
 
     uint32_t my_gen = 0xffffffffu;
     bool stale = true;
@@ -842,19 +843,19 @@ __global__ void __launch_bounds__(SP_THREADS, BT_MIN_CTAS) batched_pcg_kernel(Bt
         if (L.n == 0) break;
 
         bt_phase_direction(a, L);
-        if (!bt_grid_sync(a.g)) return;
+        if (!bt_grid_sync(a.g, a.bar_wait)) return;
         bt_phase_spmv<DIFF>(a, L, smem_raw, full_bar, empty_bar, stage_info, kbase, par);
         kbase += bt_spmv_sched(a, L).n;
-        if (!bt_grid_sync(a.g)) return;
+        if (!bt_grid_sync(a.g, a.bar_wait)) return;
         bt_phase_update(a, L, par);
-        if (!bt_grid_sync(a.g)) return;
+        if (!bt_grid_sync(a.g, a.bar_wait)) return;
         if (threadIdx.x == 0) s_ref = ld_acquire_gpu(&a.g->n_refresh[par]);
         __syncthreads();
         if (s_ref > 0) {
             bt_build_list(a, BT_LIST_REFRESH, L);
             stale = true;
             bt_phase_residual<DIFF>(a, L, false);
-            if (!bt_grid_sync(a.g)) return;
+            if (!bt_grid_sync(a.g, a.bar_wait)) return;
         }
     }
     // ---- finish: dv = x64 + x (FP32)
@@ -909,6 +910,24 @@ __global__ void bt_start_kernel(int V, const float *dv, double *x64, float4 *x4)
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
         for (int q = 0; q < 3; ++q) x64[3ll * row + q] = (double)dv[3ll * row + q];
         x4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// v += dv, x += h v for the rows of every instance whose solve ended with PC_OK or
+// PC_ERR_NOT_CONVERGED; an instance that failed keeps its state, and after an aborted
+// launch no row moves.
+__global__ void bt_state_update_kernel(int V, const int32_t *row_inst, const bt_inst *inst, const bt_global *g,
+                                       float *x, float *v, const float *dv, float h)
+{
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= V || g->abort != 0u) return;
+    const int32_t st = inst[row_inst[row]].status;
+    if (st != PC_OK && st != PC_ERR_NOT_CONVERGED) return;
+    for (int q = 0; q < 3; ++q) {
+        const int64_t i = 3ll * row + q;
+        const float vi = v[i] + dv[i];
+        v[i] = vi;
+        x[i] = fmaf(h, vi, x[i]);
     }
 }
 
@@ -1008,6 +1027,7 @@ static pc_status bt_enqueue(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, con
     a.max_iter = o.max_iter;
     a.refresh_every = o.refresh_every;
     a.spmv_chunked = spmv_order;
+    a.bar_wait = c->bar_wait_cycles > 0 ? (long long)c->bar_wait_cycles : SP_WAIT_BUDGET;
     return bt_launch(c, B, a, dres != nullptr, blocks_per_sm, st);
 }
 
@@ -1055,6 +1075,9 @@ static pc_status bt_autotune(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, co
             PC_CUDA_TRY(cudaEventRecord(e1, st));
             if (s != PC_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
             PC_CUDA_TRY(cudaEventSynchronize(e1));
+            uint32_t aborted = 0;
+            PC_CUDA_TRY(cudaMemcpy(&aborted, &B->g->abort, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+            if (aborted) { cudaEventDestroy(e0); cudaEventDestroy(e1); return PC_ERR_TIMEOUT; }
             float ms = 0.f;
             PC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
             B->tune_ms[order][nb] = ms;
@@ -1114,6 +1137,13 @@ extern "C" pc_status pc_pcg_solve_batched(pc_ctx *ctx, const pc_bsr *A, const fl
     return bt_collect(ctx, B, n_inst, info, st);
 }
 
+extern "C" pc_status pc_set_barrier_wait(pc_ctx *ctx, int64_t cycles)
+{
+    if (!ctx) return PC_ERR_ARG;
+    ctx->bar_wait_cycles = cycles > 0 ? cycles : 0;
+    return PC_OK;
+}
+
 extern "C" pc_status pc_batched_config(pc_ctx *ctx, int32_t *blocks_per_sm, int32_t *spmv_order,
                                        float *tune_ms /*[8]*/)
 {
@@ -1125,6 +1155,13 @@ extern "C" pc_status pc_batched_config(pc_ctx *ctx, int32_t *blocks_per_sm, int3
     if (tune_ms)
         for (int order = 0; order < 2; ++order)
             for (int i = 0; i < 4; ++i) tune_ms[4 * order + i] = B->tune_ms[order][i + 1];
+    return PC_OK;
+}
+
+static pc_status bt_update_state(pc_ctx *c, pc_batched_state *B, float *x, float *v, float h, cudaStream_t st)
+{
+    PC_LAUNCH(c, bt_state_update_kernel, pc_blocks(c->V, 256), 256, 0, st, c->V, B->row_inst, B->inst, B->g, x, v,
+              c->A_dv, h);
     return PC_OK;
 }
 
@@ -1162,7 +1199,7 @@ extern "C" pc_status pc_step_batched(pc_ctx *ctx, float *x, float *v, const pc_c
     if (s == PC_OK)
         s = bt_enqueue(ctx, B, &A, ctx->A_vals, ctx->A_dres, ctx->A_b, ctx->A_dv, n_inst, o, B->blocks_per_sm,
                        B->spmv_order, cs);
-    if (s == PC_OK) s = pc_update_state(ctx, x, v, ctx->A_dv, opts->h, cs);
+    if (s == PC_OK) s = bt_update_state(ctx, B, x, v, opts->h, cs);
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     if (s != PC_OK) {
         if (graph) cudaGraphDestroy(graph);

@@ -84,6 +84,7 @@ struct pc_ctx {
     pc_material mat{};
     float mu = 0, lam = 0;
     int num_sms = 0;
+    int64_t bar_wait_cycles = 0;   // grid-barrier wait budget of the persistent solver (0: default)
 
     // rest data
     int32_t *tri = nullptr;        // [T][3]

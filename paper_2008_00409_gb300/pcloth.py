@@ -105,6 +105,7 @@ def _load():
     L.pc_step_batched.argtypes = [c_void_p, c_void_p, c_void_p, P(pc_contacts), c_int32, c_void_p, P(pc_step_opts),
                                   c_void_p, c_void_p]
     L.pc_batched_config.argtypes = [c_void_p, P(c_int32), P(c_int32), c_void_p]
+    L.pc_set_barrier_wait.argtypes = [c_void_p, c_int64]
     L.pc_step_host.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, P(pc_step_opts),
                                P(pc_step_info), c_void_p]
     L.pc_mlp_features.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_void_p, c_void_p]
@@ -127,7 +128,7 @@ def _load():
     L.pc_get_solution64.argtypes = [c_void_p, c_void_p, c_void_p]
     for name in ("pc_create", "pc_destroy", "pc_get_sizes", "pc_get_rest", "pc_assemble_pattern",
                  "pc_assemble_values", "pc_bsr_spmv", "pc_pcg_solve", "pc_pcg_solve_static", "pc_step", "pc_step_host",
-                 "pc_pcg_solve_batched", "pc_step_batched", "pc_batched_config", "pc_mlp_features", "pc_mlp_create",
+                 "pc_pcg_solve_batched", "pc_step_batched", "pc_batched_config", "pc_set_barrier_wait", "pc_mlp_features", "pc_mlp_create",
                  "pc_mlp_destroy", "pc_mlp_reset", "pc_mlp_stats", "pc_mlp_infer", "pc_mlp_grad", "pc_mlp_train_step",
                  "pc_mlp_adam_apply", "pc_set_warm_mlp",
                  "pc_set_profiling", "pc_spmv_stats", "pc_assembly_stats", "pc_get_solution64"):
@@ -314,6 +315,12 @@ def pc_batched_config(ctx):
     _check(_lib.pc_batched_config(ctx, ctypes.byref(bps), ctypes.byref(order), ctypes.cast(ms, c_void_p)),
            "pc_batched_config")
     return bps.value, order.value, [list(ms[0:4]), list(ms[4:8])]
+
+
+def pc_set_barrier_wait(ctx, cycles):
+    """Grid-barrier wait budget (SM cycles) of the persistent batched solver; <= 0 restores
+    the default."""
+    _check(_lib.pc_set_barrier_wait(ctx, int(cycles)), "pc_set_barrier_wait")
 
 
 def pc_step(ctx, x, v, pairs, w, opts: pc_step_opts, dv_out=None, stream=None, allow_not_converged=False):
