@@ -63,12 +63,20 @@ def parse():
     ap.add_argument("--no-sequential", action="store_true", help="batched form: skip the one-garment-at-a-time comparison")
     ap.add_argument("--train-steps", type=int, default=2000, help="warmstart form: Adam steps")
     ap.add_argument("--garments", type=int, default=64, help="batched form: number of garments")
+    ap.add_argument("--damp-mass", type=float, default=0.0, help="Rayleigh damping alpha (1/s)")
+    ap.add_argument("--damp-stiff", type=float, default=0.0, help="Rayleigh damping beta (s)")
     return ap.parse_args()
 
 
-def make_workload(name: str):
+def make_workload(name: str, damp_mass: float = 0.0, damp_stiff: float = 0.0):
+    import dataclasses
+
     from paper_2008_00409_gb300 import workloads as wk
-    return wk.WORKLOADS[name]()
+    wl = wk.WORKLOADS[name]()
+    if damp_mass or damp_stiff:
+        wl = dataclasses.replace(wl, material=dataclasses.replace(wl.material, damp_mass=damp_mass,
+                                                                  damp_stiff=damp_stiff))
+    return wl
 
 
 # --------------------------------------------------------------------------- clocks
@@ -175,7 +183,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, args.damp_mass, args.damp_stiff)
     times = []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -237,7 +245,7 @@ def run_ours(args):
         dist.barrier()
     from paper_2008_00409_gb300 import pcloth as pc
 
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, args.damp_mass, args.damp_stiff)
     cl = pc.Cloth(wl)
     prec = pc.PC_PREC_MIXED if args.precision == "mixed" else pc.PC_PREC_FP32
     precond = pc.PC_PRECOND_BLOCK if args.precond == "block" else pc.PC_PRECOND_JACOBI
@@ -334,7 +342,8 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (matrix about 440 MB per SpMV)",
                        "pcg_iters_per_step": float(np.mean(iters)), "max_rel_res": float(np.max(rels)),
-                       "assembly_ms_per_step": asm_ms / max(n_asm, 1)},
+                       "assembly_ms_per_step": asm_ms / max(n_asm, 1),
+                       "rayleigh_damping": [wl.material.damp_mass, wl.material.damp_stiff]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None,
                          "traffic": SPMV_DRAM_BYTES.get(wl.name),

@@ -66,7 +66,12 @@ typedef struct pc_ctx pc_ctx;
 
 /* Material of the cloth (SI units). Membrane: St. Venant-Kirchhoff, plane stress,
  * Young's modulus x thickness `young` (N/m) and `poisson`. Bending: dihedral hinges with
- * stiffness `k_bend` (N m). Contact: hold penalty `k_contact` (N/m). */
+ * stiffness `k_bend` (N m). Contact: hold penalty `k_contact` (N/m). Optional Rayleigh
+ * damping f_d = -(damp_mass M + damp_stiff K) v (an extension; the paper's Eq. 3 has no
+ * velocity derivative): backward Euler then assembles
+ *   A = (1 + h damp_mass) M + h (h + damp_stiff) K,
+ *   b = h (f(x_t) - damp_mass M v_t - (h + damp_stiff) K v_t),
+ * and both zero give Eq. 3 exactly. Pinned rows keep A_ii = m_i I. */
 typedef struct {
     float rho;         /* area density, kg/m^2 */
     float young;       /* N/m */
@@ -74,6 +79,8 @@ typedef struct {
     float k_bend;      /* N m */
     float k_contact;   /* N/m */
     float gravity[3];  /* m/s^2 */
+    float damp_mass;   /* Rayleigh alpha, 1/s (>= 0) */
+    float damp_stiff;  /* Rayleigh beta, s (>= 0) */
 } pc_material;
 
 /* Contact pairs of one step (Sec. 4: proximity forces inside the implicit integrator;

@@ -94,7 +94,9 @@ class Mesh:
     def __init__(self, rest, tris, material, pins=()):
         self.rest = _f64(rest).reshape(-1, 3)
         self.tris = _i32(tris).reshape(-1, 3)
-        self.material = _f64(material)
+        m = _f64(material).reshape(-1)
+        # {rho, E, nu, kb, kc, g[3]} and optionally the Rayleigh damping pair (alpha, beta)
+        self.material = np.concatenate([m, np.zeros(max(0, 10 - m.size))])[:10].copy()
         self.pins = _i32(pins).reshape(-1)
         self.V = self.rest.shape[0]
         self.T = self.tris.shape[0]
@@ -175,7 +177,9 @@ class Mesh:
 
     def assemble(self, x, v, pairs=None, w=None, h=1.0 / 200.0, pins=True, pattern=None):
         """Eq. 3 system: A = M + h^2 K(x_t), b = h (f(x_t) - h K(x_t) v_t) (the first-order
-        expansion of h f(x_t + h v_t), Eq. 2), with the pin rule."""
+        expansion of h f(x_t + h v_t), Eq. 2), with the pin rule. With Rayleigh damping
+        (alpha, beta) in the material: A = (1 + h alpha) M + h (h + beta) K,
+        b = h (f(x_t) - alpha M v_t - (h + beta) K v_t)."""
         pairs, w = self._contacts(pairs, w)
         x = _f64(x).reshape(-1, 3)
         v = _f64(v).reshape(-1, 3)

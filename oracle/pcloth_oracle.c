@@ -35,6 +35,12 @@
  *  - Sec. 3.2.2: the matrix pattern is the set of (row, col) vertex pairs coupled by some
  *    element, duplicates removed, stored as block compressed rows of 3x3 blocks with
  *    columns ascending and the diagonal always present.
+ *  - Rayleigh damping (an extension; the paper's Eq. 3 has no velocity derivative):
+ *    f_d = -(alpha M + beta K) v. Backward Euler keeps the -h df/dv term of the
+ *    linearisation (Baraff and Witkin 1998), so
+ *      A = (1 + h alpha) M + h (h + beta) K,
+ *      b = h (f(x_t) - alpha M v_t - (h + beta) K v_t);
+ *    alpha = beta = 0 gives the system above.
  *  - Pinned vertices keep their pattern entries; their rows and columns are zero except
  *    A_ii = m_i I, and b_i = 0, so dv_i = 0.
  *  - Sec. 2.5: the system is solved with preconditioned conjugate gradients (Jacobi:
@@ -62,6 +68,7 @@ typedef struct {
     double *hrest;       /* [H] rest dihedral angle */
     unsigned char *pinned; /* [V] */
     double rho, E, nu, kb, kc, g[3];
+    double alpha, beta;  /* Rayleigh damping: mass (1/s) and stiffness (s) coefficients */
     double mu, lam;
 } om_mesh;
 
@@ -302,7 +309,7 @@ void om_mesh_destroy(om_mesh *M)
     free(M);
 }
 
-/* mat = {rho, E, nu, kb, kc, gx, gy, gz}. Returns NULL on invalid input (index out of
+/* mat = {rho, E, nu, kb, kc, gx, gy, gz, alpha, beta}. Returns NULL on invalid input (index out of
  * range, degenerate triangle, an edge shared by more than two triangles). */
 om_mesh *om_mesh_create(int V, int T, const int *tri, const double *rest, const double *mat, int npin, const int *pins)
 {
@@ -311,6 +318,7 @@ om_mesh *om_mesh_create(int V, int T, const int *tri, const double *rest, const 
     M->V = V; M->T = T; M->npin = npin;
     M->rho = mat[0]; M->E = mat[1]; M->nu = mat[2]; M->kb = mat[3]; M->kc = mat[4];
     M->g[0] = mat[5]; M->g[1] = mat[6]; M->g[2] = mat[7];
+    M->alpha = mat[8]; M->beta = mat[9];
     M->mu = M->E / (2.0 * (1.0 + M->nu));
     M->lam = M->E * M->nu / (1.0 - M->nu * M->nu);
     M->tri = malloc(sizeof(int) * 3 * (size_t)(T > 0 ? T : 1));
@@ -551,8 +559,11 @@ int om_hessian(const om_mesh *M, const double *x, int P, const int *pairs, const
 /* Eq. 3 with its right-hand side taken to first order, as Eq. 2 prescribes:
  *   f(x_t + h v_t) ~= f(x_t) + J h v_t,  J = -K(x_t),
  * so A = M + h^2 K(x_t) and b = h (f(x_t) - h K(x_t) v_t), K the same sum of element
- * Hessians in both. Then the pin rule if `apply_pins` is nonzero (pinned rows/cols zero,
- * A_ii = m_i I, b_i = 0). */
+ * Hessians in both. With Rayleigh damping f_d = -(alpha M + beta K) v the velocity
+ * derivative adds h (alpha M + beta K) to A and the damping force at v_t to the
+ * right-hand side: A = (1 + h alpha) M + h (h + beta) K,
+ * b = h (f(x_t) - alpha M v_t - (h + beta) K v_t). Then the pin rule if `apply_pins` is
+ * nonzero (pinned rows/cols zero, A_ii = m_i I, b_i = 0). */
 int om_assemble(const om_mesh *M, const double *x, const double *v, int P, const int *pairs, const double *w,
                 double h, int apply_pins, const int *row_ptr, const int *col_idx, double *vals, double *b)
 {
@@ -563,14 +574,18 @@ int om_assemble(const om_mesh *M, const double *x, const double *v, int P, const
     om_spmv(V, row_ptr, col_idx, vals, v, Kv);
     st = om_forces(M, x, P, pairs, w, x, b);
     if (st != OM_OK) { free(Kv); return st; }
-    for (long k = 0; k < 3L * V; ++k) b[k] = h * (b[k] - h * Kv[k]);
+    for (int i = 0; i < V; ++i)
+        for (int a = 0; a < 3; ++a) {
+            long k = 3L * i + a;
+            b[k] = h * (b[k] - M->alpha * M->mass[i] * v[k] - (h + M->beta) * Kv[k]);
+        }
     free(Kv);
     long nnzb = row_ptr[V];
-    for (long s = 0; s < 9 * nnzb; ++s) vals[s] *= h * h;
+    for (long s = 0; s < 9 * nnzb; ++s) vals[s] *= h * (h + M->beta);
     for (int i = 0; i < V; ++i) {
         long s = find_slot(row_ptr, col_idx, i, i);
         if (s < 0) return OM_ERR_PATTERN;
-        for (int a = 0; a < 3; ++a) vals[9 * s + 4 * a] += M->mass[i];
+        for (int a = 0; a < 3; ++a) vals[9 * s + 4 * a] += (1.0 + h * M->alpha) * M->mass[i];
     }
     if (apply_pins) {
         for (int r = 0; r < V; ++r)
@@ -587,14 +602,15 @@ int om_assemble(const om_mesh *M, const double *x, const double *v, int P, const
     return OM_OK;
 }
 
-/* y = M p + h^2 sum_e H_e p_e, element by element with no matrix (no pins). */
+/* y = (1 + h alpha) M p + h (h + beta) sum_e H_e p_e, element by element with no
+ * matrix (no pins). */
 int om_matfree_apply(const om_mesh *M, const double *x, int P, const int *pairs, const double *w, double h,
                      const double *p, double *y)
 {
     if (!check_pairs(M, P, pairs)) return OM_ERR_ARG;
     double He[144];
     for (int i = 0; i < M->V; ++i)
-        for (int a = 0; a < 3; ++a) y[3 * i + a] = M->mass[i] * p[3 * i + a];
+        for (int a = 0; a < 3; ++a) y[3 * i + a] = (1.0 + h * M->alpha) * M->mass[i] * p[3 * i + a];
     for (int t = 0; t < M->T + M->H + P; ++t) {
         const int *v;
         int nv;
@@ -619,7 +635,7 @@ int om_matfree_apply(const om_mesh *M, const double *x, int P, const int *pairs,
             for (int l = 0; l < nv; ++l)
                 for (int a = 0; a < 3; ++a)
                     for (int b = 0; b < 3; ++b)
-                        y[3 * v[k] + a] += h * h * He[(k * nv + l) * 9 + a * 3 + b] * p[3 * v[l] + b];
+                        y[3 * v[k] + a] += h * (h + M->beta) * He[(k * nv + l) * 9 + a * 3 + b] * p[3 * v[l] + b];
     }
     return OM_OK;
 }

@@ -495,7 +495,8 @@ extern "C" pc_status pc_create(pc_ctx **out, int32_t V, int32_t T, const int32_t
     if (3ll * T >= (1ll << 28) || (int64_t)V * (int64_t)V >= (1ll << 62) || 6ll * max_contacts >= (1ll << 30))
         return PC_ERR_ARG;
     if (!(mat->rho > 0.0f) || !(mat->young > 0.0f) || !(mat->poisson > -1.0f && mat->poisson < 0.5f) ||
-        mat->k_bend < 0.0f || mat->k_contact < 0.0f)
+        mat->k_bend < 0.0f || mat->k_contact < 0.0f || !(mat->damp_mass >= 0.0f && mat->damp_mass < 1e30f) ||
+        !(mat->damp_stiff >= 0.0f && mat->damp_stiff < 1e30f))
         return PC_ERR_ARG;
     pc_ctx *c = new pc_ctx();
     c->V = V;

@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(128) tri_eval_kernel(int T, const int32_t *__r
                                                        const float *__restrict__ x, const float *__restrict__ v,
                                                        const float *__restrict__ dmi_all,
                                                        const float *__restrict__ area, const float *__restrict__ rgram,
-                                                       float mu, float lam, float h, float *__restrict__ out)
+                                                       float mu, float lam, float h, float hk,
+                                                       float *__restrict__ out)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(128) tri_eval_kernel(int T, const int32_t *__r
         for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int b = a; b < 3; ++b) FFt[a][b] = F[a][0] * F[b][0] + F[a][1] * F[b][1];
-        const float c = h * h * A0;
+        const float c = hk * A0;
         float *o = out + (int64_t)PC_TRI_STRIDE * t + 9;
 #pragma unroll
         for (int k = 0; k < 3; ++k)
@@ -266,7 +267,7 @@ __device__ __forceinline__ float hinge_angle_grad(float3 a1, float3 a2, float3 a
 __global__ void __launch_bounds__(128) hinge_eval_kernel(int H, const int32_t *__restrict__ hinge,
                                                          const float *__restrict__ x, const float *__restrict__ v,
                                                          const float *__restrict__ hcoef,
-                                                         const float *__restrict__ hrest, float h,
+                                                         const float *__restrict__ hrest, float h, float hk,
                                                          float *__restrict__ out)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(128) hinge_eval_kernel(int H, const int32_t *_
     float3 a1 = sub(X[0], X[2]), a2 = sub(X[1], X[2]), a4 = sub(X[3], X[2]);
     float th = hinge_angle_grad(a1, a2, a4, grad);
     float s = -kc * (th - hrest[i]);  // f_k = s grad_k
-    float sc = h * sqrtf(kc);
+    float sc = sqrtf(hk * kc);
     float3 q[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) q[k] = mul(sc, grad[k]);
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(128) hinge_eval_kernel(int H, const int32_t *_
 // the Hessian block (k, l) is h^2 kc s_k s_l n n^T. The penalty is zero at x_t (d = d0)
 // and linear in x, so its contribution h (f - h K v) is -h^2 kc (n . sum_l s_l v_l) s_k n.
 __global__ void contact_eval_kernel(int P, const int32_t *__restrict__ pairs, const float *__restrict__ wts,
-                                    const float *__restrict__ x, const float *__restrict__ v, float kc, float h,
+                                    const float *__restrict__ x, const float *__restrict__ v, float kc, float hk,
                                     float *__restrict__ out)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -319,18 +320,18 @@ __global__ void contact_eval_kernel(int P, const int32_t *__restrict__ pairs, co
     float3 rv = make_float3(0.f, 0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < 4; ++k) rv = add(rv, mul(s[k], ld3(v, vid[k])));
-    float dd = h * dot(n, rv);  // h n . sum_l s_l v_l
+    float dd = dot(n, rv);  // n . sum_l s_l v_l
     float *o = out + (int64_t)PC_CONTACT_STRIDE * i;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        float fk = -h * kc * dd * s[k];
+        float fk = -hk * kc * dd * s[k];
         o[3 * k] = fk * n.x;
         o[3 * k + 1] = fk * n.y;
         o[3 * k + 2] = fk * n.z;
     }
     o[12] = n.x; o[13] = n.y; o[14] = n.z;
     o[15] = w[0]; o[16] = w[1]; o[17] = w[2];
-    o[18] = h * h * kc;
+    o[18] = hk * kc;
     o[19] = 0.0f;
 }
 
@@ -402,7 +403,8 @@ __global__ void __launch_bounds__(32 * RR_WARPS) row_reduce_kernel(
     const int32_t *__restrict__ tri, const int32_t *__restrict__ hinge, const int32_t *__restrict__ pairs,
     const float *__restrict__ tri_buf, const float *__restrict__ hinge_buf, const float *__restrict__ cont_buf,
     const float *__restrict__ mass, const uint8_t *__restrict__ pinned, float gx, float gy, float gz, float h,
-    float *__restrict__ vals, float *__restrict__ b, float *__restrict__ dres)
+    float md, float ha, const float *__restrict__ v, float *__restrict__ vals, float *__restrict__ b,
+    float *__restrict__ dres)
 {
     __shared__ float s_blk[RR_WARPS][RR_ENTRIES][9];
     __shared__ int s_col[RR_WARPS][RR_ENTRIES];
@@ -415,6 +417,7 @@ __global__ void __launch_bounds__(32 * RR_WARPS) row_reduce_kernel(
     const int c0 = cinc_ptr[row], nc = cinc_ptr[row + 1] - c0;
     const int nref = ni + nc;
     const float m = mass[row];
+    const float mA = md * m;  // diagonal mass term (1 + h alpha) m of an unpinned row
     const bool prow = pinned[row] != 0;
     float fsum[3] = {0.f, 0.f, 0.f};
     float dsum[9];
@@ -479,9 +482,9 @@ __global__ void __launch_bounds__(32 * RR_WARPS) row_reduce_kernel(
 #pragma unroll
                 for (int q = 0; q < 9; ++q) outv[q] = acc[q];
                 if (col == row) {
-                    outv[0] += m;
-                    outv[4] += m;
-                    outv[8] += m;
+                    outv[0] += mA;
+                    outv[4] += mA;
+                    outv[8] += mA;
                 }
             }
             float *dst = vals + 9ll * slot;
@@ -498,17 +501,20 @@ __global__ void __launch_bounds__(32 * RR_WARPS) row_reduce_kernel(
             float *d = dres + 9ll * row;
 #pragma unroll
             for (int q = 0; q < 9; ++q) d[q] = prow ? 0.f : -dsum[q];
-            d[0] += m;
-            d[4] += m;
-            d[8] += m;
+            const float md_row = prow ? m : mA;
+            d[0] += md_row;
+            d[4] += md_row;
+            d[8] += md_row;
         }
         float *bb = b + 3ll * row;
         if (prow) {
             bb[0] = bb[1] = bb[2] = 0.f;
         } else {
-            bb[0] = fsum[0] + h * m * gx;
-            bb[1] = fsum[1] + h * m * gy;
-            bb[2] = fsum[2] + h * m * gz;
+            // gravity and the mass-damping force at v_t, both times h
+            const float hm = h * m, ham = ha * m;
+            bb[0] = fsum[0] + hm * gx - ham * v[3ll * row];
+            bb[1] = fsum[1] + hm * gy - ham * v[3ll * row + 1];
+            bb[2] = fsum[2] + hm * gz - ham * v[3ll * row + 2];
         }
     }
 }
@@ -524,18 +530,22 @@ extern "C" pc_status pc_assemble_values(pc_ctx *ctx, const pc_bsr *A, const floa
     if (!(h > 0.0f)) return PC_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const int V = ctx->V, T = ctx->T, H = ctx->H;
+    // Rayleigh damping: element Hessians enter A as h (h + beta) K, the mass as
+    // (1 + h alpha) M (beta = alpha = 0: h^2 K and M)
+    const float hk = h * (h + ctx->mat.damp_stiff);
+    const float md = 1.0f + h * ctx->mat.damp_mass, ha = h * ctx->mat.damp_mass;
     if (T > 0)
         PC_LAUNCH(ctx, tri_eval_kernel, pc_blocks(T, 128), 128, 0, st, T, ctx->tri, x, v, ctx->tri_dmi, ctx->tri_area,
-                  ctx->tri_rgram, ctx->mu, ctx->lam, h, ctx->tri_buf);
+                  ctx->tri_rgram, ctx->mu, ctx->lam, h, hk, ctx->tri_buf);
     if (H > 0)
         PC_LAUNCH(ctx, hinge_eval_kernel, pc_blocks(H, 128), 128, 0, st, H, ctx->hinge, x, v, ctx->hcoef, ctx->hrest, h,
-                  ctx->hinge_buf);
+                  hk, ctx->hinge_buf);
     if (P > 0)
         PC_LAUNCH(ctx, contact_eval_kernel, pc_blocks(P, 128), 128, 0, st, P, contacts->pairs, contacts->w, x, v,
-                  ctx->mat.k_contact, h, ctx->cont_buf);
+                  ctx->mat.k_contact, hk, ctx->cont_buf);
     PC_LAUNCH(ctx, row_reduce_kernel, pc_blocks(V, RR_WARPS), 32 * RR_WARPS, 0, st, V, A->row_ptr, A->col_idx,
               ctx->vinc_ptr, ctx->vinc, ctx->cinc_ptr, ctx->cinc, ctx->tri, ctx->hinge,
               P > 0 ? contacts->pairs : nullptr, ctx->tri_buf, ctx->hinge_buf, ctx->cont_buf, ctx->mass, ctx->pinned,
-              ctx->mat.gravity[0], ctx->mat.gravity[1], ctx->mat.gravity[2], h, vals, b, dres);
+              ctx->mat.gravity[0], ctx->mat.gravity[1], ctx->mat.gravity[2], h, md, ha, v, vals, b, dres);
     return PC_OK;
 }

@@ -27,7 +27,7 @@ PC_MLP_IN, PC_MLP_HIDDEN, PC_MLP_OUT, PC_MLP_NPARAMS, PC_MLP_NSTATS = 12, 64, 3,
 
 class pc_material(ctypes.Structure):
     _fields_ = [("rho", c_float), ("young", c_float), ("poisson", c_float), ("k_bend", c_float),
-                ("k_contact", c_float), ("gravity", c_float * 3)]
+                ("k_contact", c_float), ("gravity", c_float * 3), ("damp_mass", c_float), ("damp_stiff", c_float)]
 
 
 class pc_contacts(ctypes.Structure):
@@ -171,6 +171,8 @@ def material_struct(m) -> pc_material:
     s.rho, s.young, s.poisson, s.k_bend, s.k_contact = m.rho, m.young, m.poisson, m.k_bend, m.k_contact
     for i in range(3):
         s.gravity[i] = m.gravity[i]
+    s.damp_mass = getattr(m, "damp_mass", 0.0)
+    s.damp_stiff = getattr(m, "damp_stiff", 0.0)
     return s
 
 

@@ -87,10 +87,12 @@ class Material:
     k_bend: float = 1e-4      # dihedral bending stiffness, N*m
     k_contact: float = 1e3    # contact penalty stiffness, N/m
     gravity: tuple = (0.0, 0.0, -9.81)
+    damp_mass: float = 0.0    # Rayleigh damping alpha (1/s): f_d = -(alpha M + beta K) v
+    damp_stiff: float = 0.0   # Rayleigh damping beta (s)
 
     def as_array(self) -> np.ndarray:
         return np.array([self.rho, self.young, self.poisson, self.k_bend, self.k_contact,
-                         *self.gravity], dtype=np.float64)
+                         *self.gravity, self.damp_mass, self.damp_stiff], dtype=np.float64)
 
 
 # --------------------------------------------------------------------------- meshes

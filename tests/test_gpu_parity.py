@@ -4,6 +4,8 @@ Pattern (row_ptr, col_idx): bit-exact. Block values: within the per-block tolera
 _helpers. dv: within 1e-5 relative L2 of the oracle solved to 1e-12. The oracle is fed
 the GPU's own FP32 state cast exactly to FP64 (Sec. 2.5 Eq. 3 at the same x_t, v_t).
 """
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -35,10 +37,16 @@ def _setup(pc, wl, step=0):
     return cl, om, pairs, w, pd, wd
 
 
+def _damped(wl):
+    """The same workload with Rayleigh damping (alpha = 2 / s, beta = 0.01 s)."""
+    return dataclasses.replace(wl, material=dataclasses.replace(wl.material, damp_mass=2.0, damp_stiff=0.01))
+
+
 CASES = {
     "square64": lambda: wk.small_square(),
     "ragged37x29-contacts": lambda: H.small_contact_cloth(),
     "stack3x21-interlayer": lambda: H.small_stack(),
+    "ragged37x29-contacts-damped": lambda: _damped(H.small_contact_cloth()),
 }
 
 
@@ -107,8 +115,10 @@ def test_difference_diagonal_and_spmv(pc, case):
     v = wl.v0.astype(np.float64)
     rp, ci, vals_ref, _ = om.assemble(x, v, pairs, w, wl.h)
     _, _, vals_nopin, _ = om.assemble(x, v, pairs, w, wl.h, pins=False)
-    # D_i = m_i I - sum over pinned neighbours j of the unzeroed block A_ij
-    D_ref = np.tile(np.eye(3), (cl.V, 1, 1)) * om.mass[:, None, None]
+    # D_i = (1 + h alpha) m_i I - sum over pinned neighbours j of the unzeroed block A_ij
+    # (alpha the Rayleigh mass damping; a pinned row keeps m_i I)
+    md = np.where(om.pinned, 1.0, 1.0 + wl.h * wl.material.damp_mass)
+    D_ref = np.tile(np.eye(3), (cl.V, 1, 1)) * (md * om.mass)[:, None, None]
     rows = np.repeat(np.arange(cl.V), np.diff(rp))
     for sl in np.nonzero(om.pinned[ci] & (ci != rows) & ~om.pinned[rows])[0]:
         D_ref[rows[sl]] -= vals_nopin[sl]

@@ -241,3 +241,72 @@ def test_batch_union_keeps_garments_disjoint():
     assert (pi == pi[:, :1]).all() and len(pairs) == u.n_contacts
     M = oracle.Mesh.from_workload(u)
     assert M.H == sum(oracle.Mesh.from_workload(p).H for p in parts)
+
+
+# ------------------------------------------------------------------ Rayleigh damping
+
+
+def _damped(alpha, beta):
+    m = MAT.copy()
+    m[8], m[9] = alpha, beta
+    return m
+
+
+@pytest.mark.parametrize("alpha,beta", [(2.0, 0.0), (0.0, 0.02), (3.5, 0.01)])
+def test_damped_translation_closed_form(alpha, beta):
+    # rest shape, uniform velocity u, no pins: K u = 0, so stiffness damping does nothing
+    # and mass damping gives the scalar backward Euler dv = h (g - alpha u) / (1 + h alpha)
+    rest, tris, _ = wk.grid_piece(9, 7, 0.2, 0.15, jitter=0.2, flip_prob=0.2, seed=9)
+    M = oracle.Mesh(rest, tris, _damped(alpha, beta))
+    u = np.array([0.4, -0.1, 0.2])
+    x = rest.astype(np.float64)
+    v = np.tile(u, (M.V, 1))
+    dv, x1, v1, info = M.step(x, v, h=H_STEP, tol=1e-13)
+    want = H_STEP * (MAT[5:8] - alpha * u) / (1.0 + H_STEP * alpha)
+    np.testing.assert_allclose(dv, np.tile(want, (M.V, 1)), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("alpha,beta", [(0.0, 0.0), (1.5, 0.0), (0.0, 0.03), (2.0, 0.01)])
+def test_damped_free_vertex_matches_fd_backward_euler(alpha, beta):
+    # one free vertex of a triangle in biaxial tension, the other two pinned at rest
+    # velocity: the damped backward Euler step of that vertex, written out with the 3x3
+    # stiffness taken as the central-difference Jacobian of the forces, must match the
+    # assembled and solved system
+    rest = np.array([[0.0, 0.0, 0.0], [0.1, 0.0, 0.0], [0.02, 0.09, 0.0]])
+    tris = np.array([[0, 1, 2]], np.int32)
+    M = oracle.Mesh(rest, tris, _damped(alpha, beta), pins=[1, 2])
+    x = rest * np.array([1.04, 1.06, 1.0])
+    x[0] += np.array([0.001, -0.002, 0.0005])
+    v = np.zeros((3, 3))
+    v[0] = [0.3, -0.2, 0.5]
+    f0 = M.forces(x)[0]
+    eps = 1e-7
+    K = np.zeros((3, 3))
+    for j in range(3):
+        xp, xm = x.copy(), x.copy()
+        xp[0, j] += eps
+        xm[0, j] -= eps
+        K[:, j] = -(M.forces(xp, xt=xp)[0] - M.forces(xm, xt=xm)[0]) / (2 * eps)
+    h, m = H_STEP, M.mass[0]
+    A = (1 + h * alpha) * m * np.eye(3) + h * (h + beta) * K
+    b = h * (f0 - alpha * m * v[0] - (h + beta) * K @ v[0])
+    want = np.linalg.solve(A, b)
+    rp, ci, vals, bb = M.assemble(x, v, h=h)
+    got = np.linalg.solve(oracle.dense(rp, ci, vals), bb.reshape(-1)).reshape(-1, 3)
+    np.testing.assert_allclose(got[0], want, rtol=1e-6, atol=1e-9 * np.abs(want).max())
+    assert np.all(got[1:] == 0.0)
+
+
+def test_damped_matrix_free_identity_and_dissipation():
+    M0, rest, tris, x, v, pairs, w = tiny_cloth(pins=())
+    M = oracle.Mesh(rest, tris, _damped(1.0, 0.02))
+    rp, ci, vals, b = M.assemble(x, v, pairs, w, H_STEP, pins=False)
+    rng = np.random.default_rng(12)
+    p = rng.normal(size=(M.V, 3))
+    y_free = M.matfree_apply(x, p, pairs, w, H_STEP)
+    np.testing.assert_allclose(oracle.spmv(rp, ci, vals, p), y_free, rtol=1e-12, atol=1e-14 * np.abs(y_free).max())
+    # the damping force -(alpha M + beta K) v does negative work: the damped system's
+    # right-hand side differs from the undamped one by -h (alpha M + beta K) v, whose dot
+    # product with v is negative for any v
+    _, _, _, b0 = M0.assemble(x, v, pairs, w, H_STEP, pins=False)
+    assert np.sum((b - b0) * v) < 0.0
