@@ -42,7 +42,8 @@ FALLBACK_HBM_GBS = 6800.0
 REF_ITERS_PER_STEP = 7230
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the PCG SpMV,
 # from one ncu capture of the current kernel on that workload (mean of 3 launches).
-SPMV_DRAM_BYTES = {"stack3x526": 496.1e6 + 11.7e6}
+# ncu DRAM read + write bytes per launch of the PCG product, by (workload, storage)
+SPMV_DRAM_BYTES = {("stack3x526", "full"): 496.1e6 + 11.7e6, ("stack3x526", "offdiag"): 462.9e6 + 11.1e6}
 
 
 def parse():
@@ -56,7 +57,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--max-iter", type=int, default=20000, help="PCG iteration cap per step (short profiling runs)")
     ap.add_argument("--precond", default="jacobi", choices=["jacobi", "block"])
-    ap.add_argument("--storage", default="full", choices=["full", "sym"], help="matrix layout of the PCG products")
+    ap.add_argument("--storage", default="offdiag", choices=["full", "sym", "sell", "offdiag"],
+                    help="matrix layout of the PCG products")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--form", default="step", choices=["step", "batched", "warmstart"])
@@ -249,7 +251,8 @@ def run_ours(args):
     cl = pc.Cloth(wl)
     prec = pc.PC_PREC_MIXED if args.precision == "mixed" else pc.PC_PREC_FP32
     precond = pc.PC_PRECOND_BLOCK if args.precond == "block" else pc.PC_PRECOND_JACOBI
-    storage = pc.PC_STORAGE_SYM if args.storage == "sym" else pc.PC_STORAGE_FULL
+    storage = {"sym": pc.PC_STORAGE_SYM, "sell": pc.PC_STORAGE_SELL,
+               "offdiag": pc.PC_STORAGE_OFFDIAG}.get(args.storage, pc.PC_STORAGE_FULL)
     nsteps = args.warmup + args.steps
     contacts = [cl.contacts_device(k % max(wl.steps, 1)) for k in range(nsteps)]
     torch.cuda.synchronize()
@@ -268,7 +271,7 @@ def run_ours(args):
     pc.pc_spmv_stats(cl.ctx)  # reset
     pc.pc_assembly_stats(cl.ctx)
     pc.pc_set_profiling(cl.ctx, True)
-    iters, rels = [], []
+    iters, rels, nnzbs = [], [], []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -278,22 +281,25 @@ def run_ours(args):
             info = one_step(k)
             iters.append(info.solve.iters)
             rels.append(info.solve.rel_res)
+            nnzbs.append(info.nnzb)
         ev1.record(stream)
         torch.cuda.synchronize()
     pc.pc_set_profiling(cl.ctx, False)
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = pc.pc_launch_count(cl.ctx) - launches0
-    n_spmv, spmv_ms, nnzb = pc.pc_spmv_stats(cl.ctx)
+    n_spmv, spmv_ms, spmv_blocks = pc.pc_spmv_stats(cl.ctx)
+    nnzb = int(nnzbs[-1]) if nnzbs else 0
     n_asm, asm_ms = pc.pc_assembly_stats(cl.ctx)
     elapsed = max_over_ranks(elapsed, world)
     value = aggregate_steps_per_s(world, args.steps, elapsed)
 
     # roofline of the dominant kernel: the PCG SpMV q = A p in the difference form.
-    # Algorithmic bytes per launch: blocks and column indices (40 per block), row
-    # pointers (4 (V+1)), difference diagonal (36 V), p read once and q written (float4,
-    # 16 V each)
+    # Algorithmic bytes per launch: the blocks the product reads and their column indices
+    # (40 per block: the off-diagonal blocks with the default storage, whose diagonal
+    # blocks would multiply p_i - p_i = 0; all blocks with the full matrix), row pointers
+    # (4 (V+1)), difference diagonal (36 V), p read once and q written (float4, 16 V each)
     V = wl.V
-    spmv_bytes = 40 * nnzb + 4 * (V + 1) + 36 * V + 16 * V + 16 * V
+    spmv_bytes = 40 * spmv_blocks + 4 * (V + 1) + 36 * V + 16 * V + 16 * V
     avg_spmv_s = (spmv_ms / 1e3) / max(n_spmv, 1)
     achieved = spmv_bytes / avg_spmv_s / 1e9 if n_spmv else None
     peak, peak_src = measured_hbm()
@@ -337,7 +343,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl.name, "V": V, "T": wl.T, "H": cl.H, "nnzb": int(nnzb),
+            "config": {"workload": wl.name, "V": V, "T": wl.T, "H": cl.H, "nnzb": int(nnzb), "storage": args.storage,
                        "contacts_per_step": wl.n_contacts, "precision": args.precision, "tol": args.tol,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (matrix about 440 MB per SpMV)",
@@ -346,8 +352,11 @@ def run_ours(args):
                        "rayleigh_damping": [wl.material.damp_mass, wl.material.damp_stiff]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None,
-                         "traffic": SPMV_DRAM_BYTES.get(wl.name),
-                         "kernel": "spmv_kernel<true,true> (q = A p, difference form, with p.q)",
+                         "traffic": SPMV_DRAM_BYTES.get((wl.name, args.storage)),
+                         "kernel": {"sell": "spmv_sell_kernel<true>", "sym": "spmv_sym_kernel<true>"}.get(
+                             args.storage, "spmv_kernel<true,true>") + " (q = A p, difference form, with p.q; "
+                             + args.storage + " storage)",
+                         "blocks_per_launch": int(spmv_blocks),
                          "bytes_per_launch": spmv_bytes, "peak_source": peak_src,
                          "avg_launch_us": avg_spmv_s * 1e6, "timed_launches": n_spmv},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),

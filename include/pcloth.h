@@ -113,8 +113,9 @@ typedef struct {
     int32_t refresh_every; /* PC_PREC_MIXED: ... or after this many iterations (default 1000) */
     int32_t check_every; /* iterations between convergence checks on the host (default 32) */
     int32_t precond;     /* PC_PRECOND_JACOBI (default) or PC_PRECOND_BLOCK */
-    int32_t storage;     /* PC_STORAGE_FULL (default) or PC_STORAGE_SYM: matrix layout the PCG
-                            products read (the result is the same up to summation order) */
+    int32_t storage;     /* PC_STORAGE_OFFDIAG (default), PC_STORAGE_FULL, PC_STORAGE_SYM or
+                            PC_STORAGE_SELL: matrix layout the PCG products read (the
+                            result is the same up to summation order) */
 } pc_solve_opts;
 
 /* PC_STORAGE_FULL: the products read the full BSR matrix.
@@ -125,8 +126,21 @@ typedef struct {
  * dependent loads on each row's critical path, and on GB300 the product is slower
  * (about 1.7x at 512^2). It falls back to the full matrix when the system is larger than
  * the context's step-system capacity or its pattern is not symmetric. */
+/* PC_STORAGE_SELL: at the start of each solve the off-diagonal blocks are rewritten into
+ * sliced ELL (the ELL family of Sec. 3.2): slices of 32 rows, rows sorted by length inside
+ * windows of 1024 rows, each 3x3 block stored as 10 words (column, 9 values) in structure
+ * of arrays so that a warp reads every word with coalesced loads; the diagonal blocks are
+ * not in the stream (the difference form does not need them). It falls back to the full
+ * matrix when the layout exceeds the context's capacity. */
+/* PC_STORAGE_OFFDIAG: with the difference-form diagonal given (dres), the products read a
+ * copy of the BSR matrix without its diagonal blocks, made at the start of each solve (in
+ * the difference form the diagonal block multiplies p_i - p_i = 0, so the copy gives the
+ * same product with one block per row fewer to stream). Without dres, or when the copy
+ * exceeds the context's capacity, the products read the matrix itself. */
 #define PC_STORAGE_SYM 0
 #define PC_STORAGE_FULL 1
+#define PC_STORAGE_SELL 2
+#define PC_STORAGE_OFFDIAG 3
 
 typedef struct {
     int32_t iters;      /* PCG iterations (all inner solves) */

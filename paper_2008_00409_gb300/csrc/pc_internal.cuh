@@ -142,6 +142,21 @@ struct pc_ctx {
     int32_t *sym_ucnt = nullptr, *sym_lcnt = nullptr;  // [V+1]
     int32_t *sym_uci = nullptr, *sym_lcol = nullptr, *sym_lsrc = nullptr;  // [sym_cap + 4]
     float *sym_uvals = nullptr;                      // [9 sym_cap + 16]
+    // sliced-ELL storage (PC_STORAGE_SELL), rebuilt per solve
+    int64_t sell_cap = 0;                            // block positions available
+    int32_t sell_nslices = 0;
+    int32_t *sell_perm = nullptr;                    // [32 sell_nslices]
+    int32_t *sell_width = nullptr, *sell_base = nullptr;  // [sell_nslices + 1]
+    int32_t *sell_dpos = nullptr;                    // [V]
+    uint32_t *sell_data = nullptr;                   // [320 sell_cap]
+    float *sell_diag = nullptr;                      // [V][9]
+    // off-diagonal BSR (PC_STORAGE_OFFDIAG): the matrix without its diagonal blocks
+    int64_t od_cap = 0;
+    int32_t *od_rp = nullptr, *od_cnt = nullptr;     // [V+1]
+    int32_t *od_dpos = nullptr;                      // [V]
+    int32_t *od_ci = nullptr;                        // [od_cap + 4]
+    float *od_vals = nullptr;                        // [9 od_cap + 16]
+    int64_t od_nnzb = 0;                             // blocks of the last copy
 
     // context-owned step system
     int32_t *A_rp = nullptr, *A_ci = nullptr;

@@ -281,7 +281,9 @@ static void free_ctx(pc_ctx *c)
                     c->dinv, c->dtmp, c->rhs32, c->x64, c->r64, c->partials, c->sc, c->A_rp, c->A_ci, c->A_vals, c->A_dres,
                     c->A_b, c->A_dv, c->h_state, c->h_pairs, c->h_w, c->sort.keys_alt, c->sort.vals_alt, c->sort.hist,
                     c->d_err, c->d_count, c->scan_tmp, c->sym_urp, c->sym_lrp, c->sym_dpos, c->sym_ucnt, c->sym_lcnt,
-                    c->sym_uci, c->sym_lcol, c->sym_lsrc, c->sym_uvals};
+                    c->sym_uci, c->sym_lcol, c->sym_lsrc, c->sym_uvals, c->sell_perm, c->sell_width,
+                    c->sell_base, c->sell_dpos, c->sell_data, c->sell_diag, c->od_rp, c->od_cnt, c->od_dpos,
+                    c->od_ci, c->od_vals};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->sc_host) cudaFreeHost(c->sc_host);

@@ -83,6 +83,7 @@ static __device__ bool last_block_reduce(double *v, int n, double *partials, uin
 
 #include "pc_spmv.cuh"
 #include "pc_spmv_sym.cuh"
+#include "pc_spmv_sell.cuh"
 
 // ------------------------------------------------------------------------- preconditioner
 
@@ -523,6 +524,28 @@ pc_status pc_solver_alloc(pc_ctx *c)
         PC_CUDA_TRY(cudaMemset(c->sym_uci, 0, sizeof(int32_t) * (size_t)(c->sym_cap + 4)));
         PC_CUDA_TRY(cudaMemset(c->sym_lcol, 0, sizeof(int32_t) * (size_t)(c->sym_cap + 4)));
         PC_CUDA_TRY(cudaMemset(c->sym_lsrc, 0, sizeof(int32_t) * (size_t)(c->sym_cap + 4)));
+        // sliced ELL: in a window sorted by descending length each slice is at most as wide
+        // as the mean row of the slice before it, so a window needs at most its blocks / 32
+        // positions plus the width of its first slice; the capacity allows 64 for that
+        // (longer rows in the first slice of a window make the solve fall back to BSR)
+        const int64_t nwin = (c->V + SL_SIGMA - 1) / SL_SIGMA;
+        c->sell_nslices = (int32_t)(nwin * (SL_SIGMA / SL_C));
+        c->sell_cap = c->A_cap / SL_C + 64 * nwin + c->sell_nslices;
+        PC_CUDA_TRY(cudaMalloc(&c->sell_perm, sizeof(int32_t) * (size_t)nwin * SL_SIGMA));
+        PC_CUDA_TRY(cudaMalloc(&c->sell_width, sizeof(int32_t) * (c->sell_nslices + 1ll)));
+        PC_CUDA_TRY(cudaMalloc(&c->sell_base, sizeof(int32_t) * (c->sell_nslices + 1ll)));
+        PC_CUDA_TRY(cudaMalloc(&c->sell_dpos, sizeof(int32_t) * (size_t)c->V));
+        PC_CUDA_TRY(cudaMalloc(&c->sell_data, sizeof(uint32_t) * SL_WORDS * (size_t)c->sell_cap));
+        PC_CUDA_TRY(cudaMalloc(&c->sell_diag, sizeof(float) * 9 * (size_t)c->V));
+        // off-diagonal BSR: at most the step system's blocks
+        c->od_cap = c->A_cap;
+        PC_CUDA_TRY(cudaMalloc(&c->od_rp, sizeof(int32_t) * (c->V + 1ll)));
+        PC_CUDA_TRY(cudaMalloc(&c->od_cnt, sizeof(int32_t) * (c->V + 1ll)));
+        PC_CUDA_TRY(cudaMalloc(&c->od_dpos, sizeof(int32_t) * (size_t)c->V));
+        PC_CUDA_TRY(cudaMalloc(&c->od_ci, sizeof(int32_t) * (size_t)(c->od_cap + 4)));
+        PC_CUDA_TRY(cudaMalloc(&c->od_vals, sizeof(float) * (size_t)(9 * c->od_cap + 16)));
+        PC_CUDA_TRY(cudaMemset(c->od_ci, 0, sizeof(int32_t) * (size_t)(c->od_cap + 4)));
+        PC_CUDA_TRY(cudaMemset(c->od_vals, 0, sizeof(float) * (size_t)(9 * c->od_cap + 16)));
     }
     for (int i = 0; i < 4; ++i) PC_CUDA_TRY(cudaEventCreate(&c->ev[i]));
     c->ev_used = 4;
@@ -574,7 +597,7 @@ extern "C" void pc_default_solve_opts(pc_solve_opts *o)
     o->refresh_every = 1000;
     o->check_every = 32;
     o->precond = PC_PRECOND_JACOBI;
-    o->storage = PC_STORAGE_FULL;
+    o->storage = PC_STORAGE_OFFDIAG;
 }
 
 struct SolveCtx {
@@ -583,7 +606,9 @@ struct SolveCtx {
     const float *vals, *dres, *b;
     bool diff, block;
     cudaStream_t st;
-    bool sym;  // the products read the symmetric storage
+    bool sym;   // the products read the symmetric storage
+    bool sell;  // the products read the sliced-ELL storage
+    bool offdiag;  // the products read the BSR copy without diagonal blocks
 };
 
 // ------------------------------------------------------------------------- symmetric storage
@@ -685,6 +710,110 @@ static pc_status build_sym(pc_ctx *c, const pc_bsr *A, const float *vals, bool *
     return PC_OK;
 }
 
+// ------------------------------------------------------------------------- sliced ELL
+
+// Build the sliced-ELL storage of A (returns false, error bits clear, when it does not
+// fit the context's capacity; the solve then reads the BSR matrix).
+static pc_status build_sell(pc_ctx *c, const pc_bsr *A, const float *vals, bool *ok, cudaStream_t st)
+{
+    *ok = false;
+    const int V = c->V;
+    if (c->sell_cap <= 0 || !c->sell_data) return PC_OK;
+    const int nwin = c->sell_nslices / (SL_SIGMA / SL_C);
+    PC_LAUNCH(c, sell_sort_kernel, nwin, SL_SIGMA, 0, st, V, A->row_ptr, A->col_idx, c->sell_perm, c->sell_width,
+              c->sell_dpos);
+    PC_TRY(pc_exclusive_scan(c, c->sell_width, c->sell_base, c->sell_nslices, st));
+    PC_CUDA_TRY(cudaMemcpyAsync(c->h_count, c->sell_base + c->sell_nslices, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                st));
+    PC_CUDA_TRY(cudaStreamSynchronize(st));
+    const int32_t total = reinterpret_cast<int32_t *>(c->h_count)[0];
+    if (total < 0 || total > c->sell_cap) return PC_OK;
+    PC_LAUNCH(c, sell_fill_kernel, pc_blocks((int64_t)c->sell_nslices * 32, 256), 256, 0, st, V, c->sell_nslices,
+              A->row_ptr, A->col_idx, vals, c->sell_perm, c->sell_width, c->sell_base, c->sell_dpos, c->sell_cap,
+              c->sell_data, c->sell_diag, c->d_err);
+    uint32_t bits = 0;
+    PC_TRY(pc_read_errors(c, st, &bits));
+    if (bits) {
+        PC_CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), st));
+        return PC_OK;
+    }
+    *ok = true;
+    return PC_OK;
+}
+
+// ------------------------------------------------------------------------- off-diagonal BSR
+
+// Per row: the diagonal block's position (-1 if absent) and the count of the others.
+__global__ void od_count_kernel(int V, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                int32_t *dpos, int32_t *cnt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > V) return;
+    if (i == V) {
+        cnt[V] = 0;
+        return;
+    }
+    int d;
+    cnt[i] = sell_row_length(rp, ci, i, &d);
+    dpos[i] = d;
+}
+
+// One warp per row: the row's blocks except the diagonal, in column order.
+__global__ void od_fill_kernel(int V, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                               const float *__restrict__ vals, const int32_t *__restrict__ dpos,
+                               const int32_t *__restrict__ od_rp, int64_t cap, int32_t *od_ci, float *od_vals,
+                               uint32_t *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (row >= V) return;
+    if (od_rp[row + 1] > cap) {
+        if (lane == 0) pc_set_err(err, PC_DERR_INDEX);
+        return;
+    }
+    const int r0 = rp[row], r1 = rp[row + 1], d = dpos[row], o0 = od_rp[row];
+    for (int k = r0 + lane; k < r1; k += 32) {
+        if (k == d) continue;
+        const int o = o0 + (k - r0) - ((d >= 0 && k > d) ? 1 : 0);
+        od_ci[o] = ci[k];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) od_vals[9ll * o + e] = vals[9ll * k + e];
+    }
+}
+
+// Copy A without its diagonal blocks for the difference-form products (returns false,
+// error bits clear, when there is no room; the solve then reads A itself).
+static pc_status build_offdiag(pc_ctx *c, const pc_bsr *A, const float *vals, bool *ok, cudaStream_t st)
+{
+    *ok = false;
+    const int V = c->V;
+    if (c->od_cap <= 0 || !c->od_vals) return PC_OK;
+    PC_LAUNCH(c, od_count_kernel, pc_blocks(V + 1ll, 256), 256, 0, st, V, A->row_ptr, A->col_idx, c->od_dpos,
+              c->od_cnt);
+    PC_TRY(pc_exclusive_scan(c, c->od_cnt, c->od_rp, V, st));
+    PC_CUDA_TRY(cudaMemcpyAsync(c->h_count, c->od_rp + V, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PC_CUDA_TRY(cudaStreamSynchronize(st));
+    const int32_t total = reinterpret_cast<int32_t *>(c->h_count)[0];
+    if (total < 0 || total > c->od_cap) return PC_OK;
+    PC_LAUNCH(c, od_fill_kernel, pc_blocks(32ll * V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals, c->od_dpos,
+              c->od_rp, c->od_cap, c->od_ci, c->od_vals, c->d_err);
+    uint32_t bits = 0;
+    PC_TRY(pc_read_errors(c, st, &bits));
+    if (bits) {
+        PC_CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), st));
+        return PC_OK;
+    }
+    c->od_nnzb = total;
+    *ok = true;
+    return PC_OK;
+}
+
+static int sell_grid(const pc_ctx *c)
+{
+    const int g = c->num_sms * SL_CTAS_PER_SM;
+    return g < c->max_red_blocks ? g : c->max_red_blocks;
+}
+
 static pc_status read_scalars(pc_ctx *c, cudaStream_t st)
 {
     PC_CUDA_TRY(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(pc_scalars), cudaMemcpyDeviceToHost, st));
@@ -747,16 +876,16 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
     pc_ctx *c = s.c;
     SpmvArgs a{};
     a.V = c->V;
-    a.rp = s.A->row_ptr;
-    a.ci = s.A->col_idx;
-    a.vals = s.vals;
+    a.rp = s.offdiag ? c->od_rp : s.A->row_ptr;
+    a.ci = s.offdiag ? c->od_ci : s.A->col_idx;
+    a.vals = s.offdiag ? c->od_vals : s.vals;
     a.dres = s.dres;
     a.x4 = (const float4 *)c->p0;
     a.y4 = (float4 *)c->q;
     a.partials = c->partials;
     a.sc = c->sc;
     a.err = c->d_err;
-    const int n_pq = spmv_grid(c);
+    const int n_pq = s.sell ? sell_grid(c) : spmv_grid(c);
     for (int k = 0; k < count; ++k) {
         bool timed = c->profiling && k == 0;
         PC_LAUNCH_PDL(c, pcg_direction_kernel, dir_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (const float4 *)c->z,
@@ -779,6 +908,20 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
             y.err = c->d_err;
             if (s.diff) PC_LAUNCH_PDL(c, spmv_sym_kernel<true>, n_pq, SP_THREADS, SY_SMEM_BYTES, s.st, y);
             else PC_LAUNCH_PDL(c, spmv_sym_kernel<false>, n_pq, SP_THREADS, SY_SMEM_BYTES, s.st, y);
+        } else if (s.sell) {
+            SellArgs y{};
+            y.nslices = c->sell_nslices;
+            y.perm = c->sell_perm;
+            y.width = c->sell_width;
+            y.base = c->sell_base;
+            y.data = c->sell_data;
+            y.diag = s.diff ? s.dres : c->sell_diag;
+            y.x4 = (const float4 *)c->p0;
+            y.y4 = (float4 *)c->q;
+            y.partials = c->partials;
+            y.sc = c->sc;
+            if (s.diff) PC_LAUNCH_PDL(c, spmv_sell_kernel<true>, n_pq, SL_THREADS, 0, s.st, y);
+            else PC_LAUNCH_PDL(c, spmv_sell_kernel<false>, n_pq, SL_THREADS, 0, s.st, y);
         } else {
             PC_TRY(launch_spmv(c, a, s.diff, true, s.st));
         }
@@ -793,7 +936,7 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
                       (float4 *)c->z, c->partials, n_pq, c->sc);
         if (timed) {
             c->ev_pending = 1;  // read after the chunk's synchronisation (no stall here)
-            c->spmv_nnzb = s.A->nnzb;
+            c->spmv_nnzb = s.offdiag ? c->od_nnzb : s.A->nnzb;
         }
     }
     return PC_OK;
@@ -839,9 +982,12 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
     cudaStream_t st = (cudaStream_t)stream;
     const int V = ctx->V;
     const int64_t n = 3ll * V;
-    SolveCtx s{ctx, A, vals, dres, b, dres != nullptr, o.precond == PC_PRECOND_BLOCK, st, false};
+    SolveCtx s{ctx, A, vals, dres, b, dres != nullptr, o.precond == PC_PRECOND_BLOCK, st, false, false, false};
     PC_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), st));
     if (o.storage == PC_STORAGE_SYM) PC_TRY(build_sym(ctx, A, vals, &s.sym, st));
+    if (o.storage == PC_STORAGE_SELL) PC_TRY(build_sell(ctx, A, vals, &s.sell, st));
+    // the diagonal blocks multiply p_i - p_i = 0 in the difference form only
+    if (o.storage == PC_STORAGE_OFFDIAG && s.diff) PC_TRY(build_offdiag(ctx, A, vals, &s.offdiag, st));
     if (s.block)
         PC_LAUNCH(ctx, dinv_kernel<true>, pc_blocks(V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals,
                   (float4 *)ctx->dinv, ctx->d_err);

@@ -20,7 +20,7 @@ c_int32, c_int64, c_float, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, 
 PC_OK, PC_ERR_ARG, PC_ERR_CAPACITY, PC_ERR_NOT_CONVERGED, PC_ERR_NONFINITE, PC_ERR_TIMEOUT, PC_ERR_CUDA, PC_ERR_MESH = range(8)
 PC_PREC_FP32, PC_PREC_MIXED = 0, 1
 PC_PRECOND_JACOBI, PC_PRECOND_BLOCK = 0, 1
-PC_STORAGE_SYM, PC_STORAGE_FULL = 0, 1
+PC_STORAGE_SYM, PC_STORAGE_FULL, PC_STORAGE_SELL, PC_STORAGE_OFFDIAG = 0, 1, 2, 3
 PC_WARM_ZERO, PC_WARM_PREV, PC_WARM_GIVEN, PC_WARM_MLP = 0, 1, 2, 3
 PC_MLP_IN, PC_MLP_HIDDEN, PC_MLP_OUT, PC_MLP_NPARAMS, PC_MLP_NSTATS = 12, 64, 3, 5187, 30
 
@@ -201,7 +201,7 @@ def solve_opts(tol=1e-6, max_iter=20000, precision=PC_PREC_FP32, refresh=1e-2, r
     o = pc_solve_opts()
     o.tol, o.max_iter, o.precision, o.refresh, o.refresh_every, o.check_every, o.precond = (
         tol, max_iter, precision, refresh, refresh_every, check_every, precond)
-    o.storage = PC_STORAGE_FULL if storage is None else storage
+    o.storage = PC_STORAGE_OFFDIAG if storage is None else storage
     return o
 
 
