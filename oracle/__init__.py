@@ -95,8 +95,9 @@ class Mesh:
         self.rest = _f64(rest).reshape(-1, 3)
         self.tris = _i32(tris).reshape(-1, 3)
         m = _f64(material).reshape(-1)
-        # {rho, E, nu, kb, kc, g[3]} and optionally the Rayleigh damping pair (alpha, beta)
-        self.material = np.concatenate([m, np.zeros(max(0, 10 - m.size))])[:10].copy()
+        # {rho, E, nu, kb, kc, g[3]}, optionally the Rayleigh damping pair (alpha, beta) and
+        # the contact thickness delta (zeros when absent)
+        self.material = np.concatenate([m, np.zeros(max(0, 11 - m.size))])[:11].copy()
         self.pins = _i32(pins).reshape(-1)
         self.V = self.rest.shape[0]
         self.T = self.tris.shape[0]

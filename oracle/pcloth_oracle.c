@@ -30,7 +30,10 @@
  *                c_h = 3 |e|^2 / (A1 + A2) at rest, angle gradient of Bridson, Marino
  *                and Fedkiw 2003, Gauss-Newton Hessian 2 kb c_h grad(theta) grad(theta)^T;
  *      contact:  hold penalty E = kc/2 (d - d0)^2, d = n . (x_p - sum w_k x_k), n the
- *                unit normal of the partner triangle at x_t (frozen), d0 = d(x_t);
+ *                unit normal of the partner triangle at x_t (frozen), d0 = d(x_t); or,
+ *                with a contact thickness delta > 0 (an extension), the one-sided
+ *                penalty E = kc/2 (delta - d)^2 while d(x_t) < delta, n turned towards
+ *                the vertex's side at x_t;
  *      gravity:  f_i = m_i g.
  *  - Sec. 3.2.2: the matrix pattern is the set of (row, col) vertex pairs coupled by some
  *    element, duplicates removed, stored as block compressed rows of 3x3 blocks with
@@ -69,6 +72,7 @@ typedef struct {
     unsigned char *pinned; /* [V] */
     double rho, E, nu, kb, kc, g[3];
     double alpha, beta;  /* Rayleigh damping: mass (1/s) and stiffness (s) coefficients */
+    double thick;        /* contact thickness delta (m): 0 = hold penalty, > 0 = one-sided */
     double mu, lam;
 } om_mesh;
 
@@ -264,6 +268,30 @@ static void contact_frame(const double *xt, const int *pr, const double *w, doub
     *d0 = dot3(n, r);
 }
 
+/* The frame of contact c for the mesh's contact model, from the state x_t:
+ *  - hold penalty (thickness 0): n the unit normal of (a, b, c), d0 = n . (x_p - sum w x)
+ *    at x_t, so E = kc/2 (d - d0)^2 is zero with zero force at x_t;
+ *  - one-sided thickness delta > 0: n oriented towards p's side (d(x_t) >= 0) and
+ *    E = kc/2 (delta - d)^2, active when d(x_t) < delta and zero otherwise; the active set
+ *    and n are frozen over the step, so E is the hold penalty with d0 = delta.
+ * Returns the stiffness of the contact (kc, or 0 when inactive). */
+static double contact_setup(const om_mesh *M, const double *xt, const int *pr, const double *w, double n[3],
+                            double *d0)
+{
+    double dt;
+    contact_frame(xt, pr, w, n, &dt);
+    if (M->thick <= 0.0) {
+        *d0 = dt;
+        return M->kc;
+    }
+    if (dt < 0.0) {
+        for (int k = 0; k < 3; ++k) n[k] = -n[k];
+        dt = -dt;
+    }
+    *d0 = M->thick;
+    return dt < M->thick ? M->kc : 0.0;
+}
+
 /* Hold-penalty contact (p; a, b, c) with frozen n, d0. Vertex order p, a, b, c. */
 static void contact(const double *x, const int *pr, const double *w, const double *n, double d0, double kc,
                     double *E, double *f, double *H)
@@ -309,7 +337,7 @@ void om_mesh_destroy(om_mesh *M)
     free(M);
 }
 
-/* mat = {rho, E, nu, kb, kc, gx, gy, gz, alpha, beta}. Returns NULL on invalid input (index out of
+/* mat = {rho, E, nu, kb, kc, gx, gy, gz, alpha, beta, delta}. Returns NULL on invalid input (index out of
  * range, degenerate triangle, an edge shared by more than two triangles). */
 om_mesh *om_mesh_create(int V, int T, const int *tri, const double *rest, const double *mat, int npin, const int *pins)
 {
@@ -318,7 +346,7 @@ om_mesh *om_mesh_create(int V, int T, const int *tri, const double *rest, const 
     M->V = V; M->T = T; M->npin = npin;
     M->rho = mat[0]; M->E = mat[1]; M->nu = mat[2]; M->kb = mat[3]; M->kc = mat[4];
     M->g[0] = mat[5]; M->g[1] = mat[6]; M->g[2] = mat[7];
-    M->alpha = mat[8]; M->beta = mat[9];
+    M->alpha = mat[8]; M->beta = mat[9]; M->thick = mat[10];
     M->mu = M->E / (2.0 * (1.0 + M->nu));
     M->lam = M->E * M->nu / (1.0 - M->nu * M->nu);
     M->tri = malloc(sizeof(int) * 3 * (size_t)(T > 0 ? T : 1));
@@ -431,8 +459,8 @@ double om_energy(const om_mesh *M, const double *x, int P, const int *pairs, con
     }
     for (int c = 0; c < P; ++c) {
         double n[3], d0;
-        contact_frame(xt, pairs + 4 * c, w + 3 * c, n, &d0);
-        contact(x, pairs + 4 * c, w + 3 * c, n, d0, M->kc, &e, NULL, NULL);
+        const double kc = contact_setup(M, xt, pairs + 4 * c, w + 3 * c, n, &d0);
+        contact(x, pairs + 4 * c, w + 3 * c, n, d0, kc, &e, NULL, NULL);
         E += e;
     }
     for (int i = 0; i < M->V; ++i) E -= M->mass[i] * dot3(M->g, x + 3 * i);
@@ -461,8 +489,8 @@ int om_forces(const om_mesh *M, const double *x, int P, const int *pairs, const 
     for (int c = 0; c < P; ++c) {
         double n[3], d0;
         const int *v = pairs + 4 * c;
-        contact_frame(xt, v, w + 3 * c, n, &d0);
-        contact(x, v, w + 3 * c, n, d0, M->kc, NULL, fe, NULL);
+        const double kc = contact_setup(M, xt, v, w + 3 * c, n, &d0);
+        contact(x, v, w + 3 * c, n, d0, kc, NULL, fe, NULL);
         for (int k = 0; k < 4; ++k)
             for (int a = 0; a < 3; ++a) f[3 * v[k] + a] += fe[3 * k + a];
     }
@@ -549,8 +577,8 @@ int om_hessian(const om_mesh *M, const double *x, int P, const int *pairs, const
     }
     for (int c = 0; c < P; ++c) {
         double n[3], d0;
-        contact_frame(xt, pairs + 4 * c, w + 3 * c, n, &d0);
-        contact(x, pairs + 4 * c, w + 3 * c, n, d0, M->kc, NULL, NULL, He);
+        const double kc = contact_setup(M, xt, pairs + 4 * c, w + 3 * c, n, &d0);
+        contact(x, pairs + 4 * c, w + 3 * c, n, d0, kc, NULL, NULL, He);
         if (!add_blocks(row_ptr, col_idx, vals, pairs + 4 * c, 4, He, 1.0)) return OM_ERR_PATTERN;
     }
     return OM_OK;
@@ -628,8 +656,8 @@ int om_matfree_apply(const om_mesh *M, const double *x, int P, const int *pairs,
             double n[3], d0;
             v = pairs + 4 * c;
             nv = 4;
-            contact_frame(x, v, w + 3 * c, n, &d0);
-            contact(x, v, w + 3 * c, n, d0, M->kc, NULL, NULL, He);
+            const double kc = contact_setup(M, x, v, w + 3 * c, n, &d0);
+            contact(x, v, w + 3 * c, n, d0, kc, NULL, NULL, He);
         }
         for (int k = 0; k < nv; ++k)
             for (int l = 0; l < nv; ++l)
@@ -653,8 +681,8 @@ double om_element(const om_mesh *M, int kind, const double *x, const double *xt,
     } else {
         int pr[4] = {0, 1, 2, 3};
         double n[3], d0;
-        contact_frame(xt, pr, aux, n, &d0);
-        contact(x, pr, aux, n, d0, M->kc, &E, f, H);
+        const double kc = contact_setup(M, xt, pr, aux, n, &d0);
+        contact(x, pr, aux, n, d0, kc, &E, f, H);
     }
     return E;
 }

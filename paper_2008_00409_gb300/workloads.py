@@ -89,10 +89,12 @@ class Material:
     gravity: tuple = (0.0, 0.0, -9.81)
     damp_mass: float = 0.0    # Rayleigh damping alpha (1/s): f_d = -(alpha M + beta K) v
     damp_stiff: float = 0.0   # Rayleigh damping beta (s)
+    contact_thickness: float = 0.0  # m: 0 = hold penalty, > 0 = one-sided thickness penalty
 
     def as_array(self) -> np.ndarray:
         return np.array([self.rho, self.young, self.poisson, self.k_bend, self.k_contact,
-                         *self.gravity, self.damp_mass, self.damp_stiff], dtype=np.float64)
+                         *self.gravity, self.damp_mass, self.damp_stiff, self.contact_thickness],
+                        dtype=np.float64)
 
 
 # --------------------------------------------------------------------------- meshes
