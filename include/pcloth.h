@@ -64,7 +64,13 @@ typedef int32_t pc_status;
 
 typedef struct pc_ctx pc_ctx;
 
-/* Material of the cloth (SI units). Membrane: St. Venant-Kirchhoff, plane stress,
+/* Contact models (k = k_contact; pair (p; a, b, c) with weights w, s = (1, -w), n the unit
+ * normal of (a, b, c) at x_t, d = n . (x_p - sum w_k x_k)):
+ *  - contact_thickness = 0: hold penalty E = k/2 (d - d(x_t))^2, zero force at x_t;
+ *  - contact_thickness = delta > 0 (an extension: one-sided thickness contact): n turned
+ *    towards p's side at x_t and E = k/2 (delta - d)^2 while d(x_t) < delta, zero (and no
+ *    stiffness) otherwise; the active set and n are frozen over the step.
+ * Material of the cloth (SI units). Membrane: St. Venant-Kirchhoff, plane stress,
  * Young's modulus x thickness `young` (N/m) and `poisson`. Bending: dihedral hinges with
  * stiffness `k_bend` (N m). Contact: hold penalty `k_contact` (N/m). Optional Rayleigh
  * damping f_d = -(damp_mass M + damp_stiff K) v (an extension; the paper's Eq. 3 has no
@@ -81,6 +87,7 @@ typedef struct {
     float gravity[3];  /* m/s^2 */
     float damp_mass;   /* Rayleigh alpha, 1/s (>= 0) */
     float damp_stiff;  /* Rayleigh beta, s (>= 0) */
+    float contact_thickness; /* m (>= 0): 0 = hold penalty; > 0 = one-sided thickness penalty */
 } pc_material;
 
 /* Contact pairs of one step (Sec. 4: proximity forces inside the implicit integrator;
@@ -296,6 +303,20 @@ PC_API pc_status pc_batched_config(pc_ctx *ctx, int32_t *blocks_per_sm, int32_t 
  * a second at 2 GHz). A budget of a few cycles makes every solve time out: that is how the
  * timeout path is exercised without a hang. Host-only; takes effect at the next launch. */
 PC_API pc_status pc_set_barrier_wait(pc_ctx *ctx, int64_t cycles);
+
+/* Proximity query for the one-sided thickness contact model: every pair of a vertex p
+ * and a triangle t = (a, b, c) of the context's mesh whose distance at positions x (device
+ * float[V][3]) is below delta, t touching neither p nor a mesh-edge neighbour of p,
+ * written as pairs (device int32[cap][4]: p, a, b, c) and the barycentric weights of the
+ * point of t closest to p (device float[cap][3]), ordered by p, then by triangle index.
+ * The closest point and the test d^2 < delta^2 are evaluated in FP32 with one rounding
+ * per operation in a fixed order, so the result is reproducible bit for bit. *n_out
+ * (host) receives the pair count; PC_ERR_CAPACITY when it exceeds cap (nothing written),
+ * PC_ERR_ARG when delta <= 0 or a position is too far from the origin for the cell grid
+ * (|x| / cell size >= 2^20). Synchronizes `stream`. Feed the result to pc_step /
+ * pc_assemble_pattern as the step's contacts (at most the context's max_contacts). */
+PC_API pc_status pc_proximity_query(pc_ctx *ctx, const float *x, float delta, int32_t cap, int32_t *pairs, float *w,
+                                    int32_t *n_out, void *stream);
 
 /* One batched time step: the dynamic pattern of the whole union (synchronous), then a
  * CUDA graph holding value assembly, the persistent batched solve and v += dv,

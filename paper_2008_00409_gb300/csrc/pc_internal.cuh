@@ -157,6 +157,13 @@ struct pc_ctx {
     int32_t *od_ci = nullptr;                        // [od_cap + 4]
     float *od_vals = nullptr;                        // [9 od_cap + 16]
     int64_t od_nnzb = 0;                             // blocks of the last copy
+    // proximity query: cell list (8 entries per triangle) and counts
+    int64_t px_cap = 0;
+    uint64_t *px_keys = nullptr;
+    uint32_t *px_vals = nullptr;
+    int32_t *px_cnt = nullptr, *px_off = nullptr;    // [T+1]
+    int32_t *px_vcnt = nullptr, *px_voff = nullptr;  // [V+1]
+    uint32_t *px_max = nullptr;
 
     // context-owned step system
     int32_t *A_rp = nullptr, *A_ci = nullptr;
@@ -251,6 +258,7 @@ inline bool pc_aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 // ------------------------------------------------------------------------- shared helpers (host side)
 pc_status pc_radix_sort(pc_ctx *ctx, uint64_t *keys, uint32_t *vals, int64_t n, int bits, cudaStream_t st);
+pc_status pc_proximity_alloc(pc_ctx *ctx);
 pc_status pc_exclusive_scan(pc_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, cudaStream_t st);
 pc_status pc_sort_reserve(pc_ctx *ctx, int64_t n);
 pc_status pc_read_errors(pc_ctx *ctx, cudaStream_t st, uint32_t *bits);

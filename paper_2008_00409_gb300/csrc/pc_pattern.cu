@@ -283,7 +283,8 @@ static void free_ctx(pc_ctx *c)
                     c->d_err, c->d_count, c->scan_tmp, c->sym_urp, c->sym_lrp, c->sym_dpos, c->sym_ucnt, c->sym_lcnt,
                     c->sym_uci, c->sym_lcol, c->sym_lsrc, c->sym_uvals, c->sell_perm, c->sell_width,
                     c->sell_base, c->sell_dpos, c->sell_data, c->sell_diag, c->od_rp, c->od_cnt, c->od_dpos,
-                    c->od_ci, c->od_vals};
+                    c->od_ci, c->od_vals, c->px_keys, c->px_vals, c->px_cnt, c->px_off, c->px_vcnt, c->px_voff,
+                    c->px_max};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->sc_host) cudaFreeHost(c->sc_host);
@@ -481,6 +482,7 @@ static pc_status create_impl(pc_ctx *c, const int32_t *tris, const float *rest, 
     PC_CUDA_TRY(cudaMemsetAsync(c->A_dv, 0, sizeof(float) * 3 * (size_t)V, st));
     PC_TRY(pc_solver_alloc(c));
     PC_TRY(pc_batched_alloc(c));
+    PC_TRY(pc_proximity_alloc(c));
     PC_CUDA_TRY(cudaStreamSynchronize(st));
     return PC_OK;
 }
@@ -498,7 +500,8 @@ extern "C" pc_status pc_create(pc_ctx **out, int32_t V, int32_t T, const int32_t
         return PC_ERR_ARG;
     if (!(mat->rho > 0.0f) || !(mat->young > 0.0f) || !(mat->poisson > -1.0f && mat->poisson < 0.5f) ||
         mat->k_bend < 0.0f || mat->k_contact < 0.0f || !(mat->damp_mass >= 0.0f && mat->damp_mass < 1e30f) ||
-        !(mat->damp_stiff >= 0.0f && mat->damp_stiff < 1e30f))
+        !(mat->damp_stiff >= 0.0f && mat->damp_stiff < 1e30f) ||
+        !(mat->contact_thickness >= 0.0f && mat->contact_thickness < 1e30f))
         return PC_ERR_ARG;
     pc_ctx *c = new pc_ctx();
     c->V = V;

@@ -302,12 +302,14 @@ __global__ void __launch_bounds__(128) hinge_eval_kernel(int H, const int32_t *_
 // ------------------------------------------------------------------------- contacts
 
 // One thread per pair (p; a, b, c). Record: right-hand-side contributions (12), unit
-// normal n of (a, b, c) at x (3), weights (3), h^2 kc (1). With s = (1, -w_a, -w_b, -w_c)
-// the Hessian block (k, l) is h^2 kc s_k s_l n n^T. The penalty is zero at x_t (d = d0)
-// and linear in x, so its contribution h (f - h K v) is -h^2 kc (n . sum_l s_l v_l) s_k n.
+// normal n of (a, b, c) at x (3), weights (3), h^2 kc (1) (h (h + beta) kc with Rayleigh
+// damping; 0 for an inactive thickness contact). With s = (1, -w_a, -w_b, -w_c) the
+// Hessian block (k, l) is h^2 kc s_k s_l n n^T. The hold penalty is zero at x_t (d = d0)
+// and linear in x, so its contribution h (f - h K v) is -h^2 kc (n . sum_l s_l v_l) s_k n;
+// the thickness penalty adds its force at x_t, h kc (delta - d) s_k n.
 __global__ void contact_eval_kernel(int P, const int32_t *__restrict__ pairs, const float *__restrict__ wts,
-                                    const float *__restrict__ x, const float *__restrict__ v, float kc, float hk,
-                                    float *__restrict__ out)
+                                    const float *__restrict__ x, const float *__restrict__ v, float kc, float h,
+                                    float hk, float thick, float *__restrict__ out)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
@@ -317,6 +319,21 @@ __global__ void contact_eval_kernel(int P, const int32_t *__restrict__ pairs, co
     float3 n = cross(sub(ld3(x, vid[2]), xa), sub(ld3(x, vid[3]), xa));
     n = mul(rsqrtf(dot(n, n)), n);
     float s[4] = {1.0f, -w[0], -w[1], -w[2]};
+    // one-sided thickness model: n turned towards p at x_t, force h kc (delta - d) at x_t
+    // while d < delta, no stiffness otherwise; hold penalty (delta = 0): no force at x_t
+    float kc_eff = kc, fd = 0.f;
+    if (thick > 0.f) {
+        float3 r = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) r = add(r, mul(s[k], ld3(x, vid[k])));
+        float dt = dot(n, r);
+        if (dt < 0.f) {
+            n = mul(-1.0f, n);
+            dt = -dt;
+        }
+        if (dt < thick) fd = h * kc * (thick - dt);
+        else kc_eff = 0.f;
+    }
     float3 rv = make_float3(0.f, 0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < 4; ++k) rv = add(rv, mul(s[k], ld3(v, vid[k])));
@@ -324,14 +341,14 @@ __global__ void contact_eval_kernel(int P, const int32_t *__restrict__ pairs, co
     float *o = out + (int64_t)PC_CONTACT_STRIDE * i;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        float fk = -hk * kc * dd * s[k];
+        float fk = (fd - hk * kc_eff * dd) * s[k];
         o[3 * k] = fk * n.x;
         o[3 * k + 1] = fk * n.y;
         o[3 * k + 2] = fk * n.z;
     }
     o[12] = n.x; o[13] = n.y; o[14] = n.z;
     o[15] = w[0]; o[16] = w[1]; o[17] = w[2];
-    o[18] = hk * kc;
+    o[18] = hk * kc_eff;
     o[19] = 0.0f;
 }
 
@@ -542,7 +559,7 @@ extern "C" pc_status pc_assemble_values(pc_ctx *ctx, const pc_bsr *A, const floa
                   hk, ctx->hinge_buf);
     if (P > 0)
         PC_LAUNCH(ctx, contact_eval_kernel, pc_blocks(P, 128), 128, 0, st, P, contacts->pairs, contacts->w, x, v,
-                  ctx->mat.k_contact, hk, ctx->cont_buf);
+                  ctx->mat.k_contact, h, hk, ctx->mat.contact_thickness, ctx->cont_buf);
     PC_LAUNCH(ctx, row_reduce_kernel, pc_blocks(V, RR_WARPS), 32 * RR_WARPS, 0, st, V, A->row_ptr, A->col_idx,
               ctx->vinc_ptr, ctx->vinc, ctx->cinc_ptr, ctx->cinc, ctx->tri, ctx->hinge,
               P > 0 ? contacts->pairs : nullptr, ctx->tri_buf, ctx->hinge_buf, ctx->cont_buf, ctx->mass, ctx->pinned,

@@ -27,7 +27,8 @@ PC_MLP_IN, PC_MLP_HIDDEN, PC_MLP_OUT, PC_MLP_NPARAMS, PC_MLP_NSTATS = 12, 64, 3,
 
 class pc_material(ctypes.Structure):
     _fields_ = [("rho", c_float), ("young", c_float), ("poisson", c_float), ("k_bend", c_float),
-                ("k_contact", c_float), ("gravity", c_float * 3), ("damp_mass", c_float), ("damp_stiff", c_float)]
+                ("k_contact", c_float), ("gravity", c_float * 3), ("damp_mass", c_float), ("damp_stiff", c_float),
+                ("contact_thickness", c_float)]
 
 
 class pc_contacts(ctypes.Structure):
@@ -106,6 +107,7 @@ def _load():
                                   c_void_p, c_void_p]
     L.pc_batched_config.argtypes = [c_void_p, P(c_int32), P(c_int32), c_void_p]
     L.pc_set_barrier_wait.argtypes = [c_void_p, c_int64]
+    L.pc_proximity_query.argtypes = [c_void_p, c_void_p, c_float, c_int32, c_void_p, c_void_p, P(c_int32), c_void_p]
     L.pc_step_host.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, P(pc_step_opts),
                                P(pc_step_info), c_void_p]
     L.pc_mlp_features.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_void_p, c_void_p]
@@ -128,7 +130,7 @@ def _load():
     L.pc_get_solution64.argtypes = [c_void_p, c_void_p, c_void_p]
     for name in ("pc_create", "pc_destroy", "pc_get_sizes", "pc_get_rest", "pc_assemble_pattern",
                  "pc_assemble_values", "pc_bsr_spmv", "pc_pcg_solve", "pc_pcg_solve_static", "pc_step", "pc_step_host",
-                 "pc_pcg_solve_batched", "pc_step_batched", "pc_batched_config", "pc_set_barrier_wait", "pc_mlp_features", "pc_mlp_create",
+                 "pc_pcg_solve_batched", "pc_step_batched", "pc_batched_config", "pc_set_barrier_wait", "pc_proximity_query", "pc_mlp_features", "pc_mlp_create",
                  "pc_mlp_destroy", "pc_mlp_reset", "pc_mlp_stats", "pc_mlp_infer", "pc_mlp_grad", "pc_mlp_train_step",
                  "pc_mlp_adam_apply", "pc_set_warm_mlp",
                  "pc_set_profiling", "pc_spmv_stats", "pc_assembly_stats", "pc_get_solution64"):
@@ -173,6 +175,7 @@ def material_struct(m) -> pc_material:
         s.gravity[i] = m.gravity[i]
     s.damp_mass = getattr(m, "damp_mass", 0.0)
     s.damp_stiff = getattr(m, "damp_stiff", 0.0)
+    s.contact_thickness = getattr(m, "contact_thickness", 0.0)
     return s
 
 
@@ -319,6 +322,18 @@ def pc_batched_config(ctx):
     return bps.value, order.value, [list(ms[0:4]), list(ms[4:8])]
 
 
+def pc_proximity_query(ctx, x, delta, pairs, w, stream=None):
+    """Contact pairs within `delta` of the positions x into the device buffers pairs
+    (int32[cap, 4]) and w (float32[cap, 3]); returns the pair count."""
+    cap = pairs.shape[0] if pairs is not None else 0
+    if w is not None and w.shape[0] < cap:
+        raise ValueError("w holds fewer rows than pairs")
+    n = c_int32()
+    _check(_lib.pc_proximity_query(ctx, _ptr(x), float(delta), int(cap), _ptr(pairs), _ptr(w), ctypes.byref(n),
+                                   _stream(stream)), "pc_proximity_query", required=n.value)
+    return n.value
+
+
 def pc_set_barrier_wait(ctx, cycles):
     """Grid-barrier wait budget (SM cycles) of the persistent batched solver; <= 0 restores
     the default."""
@@ -463,7 +478,22 @@ class Cloth:
         except Exception:
             pass
 
+    def proximity(self, delta: float | None = None, x=None):
+        """Contacts of the one-sided thickness model at positions x (the cloth's own by
+        default): (pairs, w) views of context-sized device buffers."""
+        if getattr(self, "_px_pairs", None) is None:
+            self._px_pairs = torch.zeros((max(self.max_contacts, 1), 4), dtype=torch.int32, device=self.device)
+            self._px_w = torch.zeros((max(self.max_contacts, 1), 3), dtype=torch.float32, device=self.device)
+        d = self.wl.material.contact_thickness if delta is None else delta
+        n = pc_proximity_query(self.ctx, self.x if x is None else x, d, self._px_pairs[: self.max_contacts],
+                               self._px_w[: self.max_contacts])
+        if n == 0:
+            return None, None
+        return self._px_pairs[:n], self._px_w[:n]
+
     def contacts_device(self, step: int):
+        if self.wl.contact_kind == "proximity":
+            return self.proximity()
         pairs, w = self.wl.contacts(step)
         if pairs.shape[0] == 0:
             return None, None

@@ -123,8 +123,8 @@ class Workload:
     material: Material
     sheets: list
     seed: int
-    contact_kind: str = "none"    # none | grid | interlayer | batch
-    contact_frac: float = 0.0
+    contact_kind: str = "none"    # none | grid | interlayer | batch | proximity
+    contact_frac: float = 0.0     # pairs per vertex (proximity: the capacity per vertex)
     contact_radius: int = 8
     steps: int = 1
     parts: list = None            # batch: the garments, in row order
@@ -152,6 +152,8 @@ class Workload:
             return grid_contacts(self, step)
         if self.contact_kind == "interlayer":
             return interlayer_contacts(self, step)
+        if self.contact_kind == "proximity":
+            raise ValueError("proximity contacts come from the query at the current positions")
         if self.contact_kind == "batch":
             ps, ws = [], []
             for part, vb in zip(self.parts, self.inst_rows[:-1]):
@@ -474,8 +476,23 @@ def warm_start_training(n: int = 256, count: int = 8, steps: int = 250):
     return [training_cloth(n, seed=SEED_BASE + 5 + 1000 * (k + 1), steps=steps) for k in range(count)]
 
 
+def proximity_stack(n: int = 526, layers: int = 3, *, delta: float = 5.5e-4, per_vertex: float = 6.0,
+                    seed: int = SEED_BASE + 3, steps: int = 10, name: str | None = None) -> Workload:
+    """The stacked sheets (0.5 mm apart) with the one-sided thickness contact model: the
+    contacts of each step are the vertex-triangle pairs closer than `delta` at the
+    step's positions (found by the proximity query), room for `per_vertex` pairs per
+    vertex."""
+    wl = stacked_sheets(n, layers, seed=seed, contact_frac=0.0, steps=steps,
+                        name=name or f"stack{layers}x{n}-proximity")
+    wl.material = dataclasses.replace(wl.material, contact_thickness=delta)
+    wl.contact_kind = "proximity"
+    wl.contact_frac = per_vertex
+    return wl
+
+
 WORKLOADS = {
     "square64": small_square,
     "square512-contacts": dynamic_square,
     "stack3x526": paper_scale,
+    "stack3x526-proximity": proximity_stack,
 }
