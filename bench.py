@@ -152,30 +152,48 @@ def measured_hbm():
 # --------------------------------------------------------------------------- CPU oracle sample
 
 
+PROXIMITY_SAMPLE = 100  # vertices whose oracle query is timed (proximity workloads)
+
+
 def oracle_sample(wl, step: int, iters: int = 5):
     """Time the FP64 oracle on one step of the same workload: pattern + assembly, then
-    `iters` PCG iterations; returns (t_setup, t_per_iter)."""
+    `iters` PCG iterations; returns (t_setup, t_per_iter). With the proximity query the
+    oracle's brute-force query is timed on PROXIMITY_SAMPLE vertices and scaled to all
+    vertices, and the assembly is timed without contact elements (a full brute-force
+    query does not fit a bounded sample)."""
     import oracle
     om = oracle.Mesh.from_workload(wl)
-    pairs, w = wl.contacts(step)
+    t_query = 0.0
+    if wl.contact_kind == "proximity":
+        from oracle import proximity as px
+        rings = px.one_rings(wl.V, wl.tris)
+        sample = np.linspace(0, wl.V - 1, PROXIMITY_SAMPLE).astype(np.int64)
+        tq = time.perf_counter()
+        px.query(wl.x0, wl.tris, wl.material.contact_thickness, vertices=sample, rings=rings)
+        t_query = (time.perf_counter() - tq) * wl.V / PROXIMITY_SAMPLE
+        pairs, w = np.zeros((0, 4), np.int32), np.zeros((0, 3))
+    else:
+        pairs, w = wl.contacts(step)
     t0 = time.perf_counter()
     rp, ci, vals, b = om.assemble(wl.x0, wl.v0, pairs, w, wl.h)
-    t1 = time.perf_counter()
+    t1 = time.perf_counter() + t_query
     try:
         oracle.pcg(rp, ci, vals, b, tol=1e-30, max_iter=iters)
     except oracle.OracleError:
         pass
-    t2 = time.perf_counter()
+    t2 = time.perf_counter() + t_query
     return t1 - t0, (t2 - t1) / iters
 
 
 def cpu_baseline(wl, iters_per_step: float):
     t_setup, t_iter = oracle_sample(wl, 0)
     per_step = t_setup + iters_per_step * t_iter
+    extra = (f" (the brute-force FP32 proximity query timed on {PROXIMITY_SAMPLE} vertices and scaled to "
+             f"all; assembly without contact elements)") if wl.contact_kind == "proximity" else ""
     return {"value": 1.0 / per_step, "unit": "steps/s", "cores": 1, "kind": "oracle",
             "sample": (f"FP64 C oracle, single thread: pattern+assembly of step 0 of {wl.name} "
-                       f"({t_setup:.1f} s) + 5 Jacobi-PCG iterations ({t_iter * 1e3:.0f} ms each); per-step time "
-                       f"extrapolated to {iters_per_step:.0f} iterations")}
+                       f"({t_setup:.1f} s{extra}) + 5 Jacobi-PCG iterations ({t_iter * 1e3:.0f} ms each); "
+                       f"per-step time extrapolated to {iters_per_step:.0f} iterations")}
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -254,11 +272,21 @@ def run_ours(args):
     storage = {"sym": pc.PC_STORAGE_SYM, "sell": pc.PC_STORAGE_SELL,
                "offdiag": pc.PC_STORAGE_OFFDIAG}.get(args.storage, pc.PC_STORAGE_FULL)
     nsteps = args.warmup + args.steps
-    contacts = [cl.contacts_device(k % max(wl.steps, 1)) for k in range(nsteps)]
+    proximity = wl.contact_kind == "proximity"
+    # random contact sets are inputs (generated before timing); proximity contacts are
+    # found by the GPU query at each step's positions, inside the timed step
+    contacts = None if proximity else [cl.contacts_device(k % max(wl.steps, 1)) for k in range(nsteps)]
+    n_pairs, query_s = [], []
     torch.cuda.synchronize()
 
     def one_step(k):
-        pd, wd = contacts[k]
+        if proximity:
+            tq = time.perf_counter()  # the query synchronizes (it returns the pair count)
+            pd, wd = cl.proximity()
+            query_s.append(time.perf_counter() - tq)
+            n_pairs.append(0 if pd is None else int(pd.shape[0]))
+        else:
+            pd, wd = contacts[k]
         info, st = cl.step(pd, wd, tol=args.tol, precision=prec, warm_start=pc.PC_WARM_PREV,
                            max_iter=args.max_iter, precond=precond, storage=storage, allow_not_converged=True)
         return info
@@ -306,7 +334,35 @@ def run_ours(args):
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and proximity:
+        # host state in pinned memory; per step: state to the device, query, step, state back
+        xh = torch.from_numpy(wl.x0.copy()).pin_memory()
+        vh = torch.from_numpy(wl.v0.copy()).pin_memory()
+        cl_e = pc.Cloth(wl)
+
+        def e2e_step():
+            cl_e.x.copy_(xh, non_blocking=True)
+            cl_e.v.copy_(vh, non_blocking=True)
+            pd, wd = cl_e.proximity()
+            cl_e.step(pd, wd, tol=args.tol, precision=prec, warm_start=pc.PC_WARM_PREV, max_iter=args.max_iter,
+                      precond=precond, storage=storage, allow_not_converged=True)
+            xh.copy_(cl_e.x)
+            vh.copy_(cl_e.v)
+
+        for k in range(args.warmup):
+            e2e_step()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.warmup, nsteps):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": aggregate_steps_per_s(world, args.steps, te), "unit": "steps/s",
+               "h2d_bytes_per_step": 24 * V, "d2h_bytes_per_step": 24 * V}
+        cl_e.close()
+    elif not args.no_e2e:
         xh = torch.from_numpy(wl.x0.copy()).pin_memory().numpy()
         vh = torch.from_numpy(wl.v0.copy()).pin_memory().numpy()
         host_contacts = [wl.contacts(k % max(wl.steps, 1)) for k in range(nsteps)]
@@ -344,9 +400,14 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "V": V, "T": wl.T, "H": cl.H, "nnzb": int(nnzb), "storage": args.storage,
-                       "contacts_per_step": wl.n_contacts, "precision": args.precision, "tol": args.tol,
+                       "contacts_per_step": (float(np.mean(n_pairs[-args.steps:])) if proximity else wl.n_contacts),
+                       "contact_model": (f"one-sided thickness {wl.material.contact_thickness * 1e3:.2f} mm, "
+                                         "pairs from the GPU proximity query each step") if proximity
+                       else "hold penalty, seeded random pairs",
+                       "query_ms_per_step": (1e3 * float(np.mean(query_s[-args.steps:])) if proximity else None),
+                       "precision": args.precision, "tol": args.tol,
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (matrix about 440 MB per SpMV)",
+                       "l2": f"inputs larger than L2 (about {spmv_bytes / 1e6:.0f} MB per SpMV)",
                        "pcg_iters_per_step": float(np.mean(iters)), "max_rel_res": float(np.max(rels)),
                        "assembly_ms_per_step": asm_ms / max(n_asm, 1),
                        "rayleigh_damping": [wl.material.damp_mass, wl.material.damp_stiff]},
