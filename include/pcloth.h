@@ -354,6 +354,14 @@ PC_API pc_status pc_pcg_solve_static(int32_t V, const pc_bsr *A, const float *va
 PC_API pc_status pc_step(pc_ctx *ctx, float *x, float *v, const pc_contacts *contacts, const pc_step_opts *opts,
                   float *dv_out, pc_step_info *info, void *stream);
 
+/* The previous step's dv that PC_WARM_PREV starts from (and the learned guess reads):
+ * get copies it to dv (device float[V][3]; zeros and *valid = 0 before the first step),
+ * set restores it (NULL: forget it, as before the first step). With positions,
+ * velocities and the step index this is the integrator state a checkpoint needs.
+ * Synchronize `stream`. */
+PC_API pc_status pc_get_prev_dv(pc_ctx *ctx, float *dv, int32_t *valid, void *stream);
+PC_API pc_status pc_set_prev_dv(pc_ctx *ctx, const float *dv, void *stream);
+
 /* pc_step on HOST buffers: copies x, v (host float[V][3]) and the contacts (host
  * int32[n][4], float[n][3]) to the device, runs pc_step, and copies x and v back. Host
  * buffers may be pageable or pinned. */
@@ -400,6 +408,10 @@ PC_API pc_status pc_mlp_create(pc_mlp **out);
 PC_API pc_status pc_mlp_destroy(pc_mlp *m);
 /* Zero the Adam moments and the step count. */
 PC_API pc_status pc_mlp_reset(pc_mlp *m, void *stream);
+/* Adam state for checkpoints: the first and second moments (device float[PC_MLP_NPARAMS]
+ * each) and the step count (host). Get copies out, set copies in. Synchronize `stream`. */
+PC_API pc_status pc_mlp_get_state(pc_mlp *m, float *m1, float *m2, int64_t *t, void *stream);
+PC_API pc_status pc_mlp_set_state(pc_mlp *m, const float *m1, const float *m2, int64_t t, void *stream);
 
 /* Training rows: feat float[*][12] as pc_mlp_features writes it and target float[*][3]
  * the solution dv of the same step (pc_step's dv_out); the network's target is

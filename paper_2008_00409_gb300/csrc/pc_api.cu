@@ -117,3 +117,31 @@ extern "C" pc_status pc_step_host(pc_ctx *ctx, float *x_host, float *v_host, int
     PC_CUDA_TRY(cudaStreamSynchronize(st));
     return s;
 }
+
+extern "C" pc_status pc_get_prev_dv(pc_ctx *ctx, float *dv, int32_t *valid, void *stream)
+{
+    if (!ctx || !dv || !valid) return PC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    *valid = ctx->has_prev_dv;
+    if (ctx->has_prev_dv)
+        PC_CUDA_TRY(cudaMemcpyAsync(dv, ctx->A_dv, sizeof(float) * 3 * (size_t)ctx->V, cudaMemcpyDeviceToDevice, st));
+    else
+        PC_CUDA_TRY(cudaMemsetAsync(dv, 0, sizeof(float) * 3 * (size_t)ctx->V, st));
+    PC_CUDA_TRY(cudaStreamSynchronize(st));
+    return PC_OK;
+}
+
+extern "C" pc_status pc_set_prev_dv(pc_ctx *ctx, const float *dv, void *stream)
+{
+    if (!ctx) return PC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dv) {
+        PC_CUDA_TRY(cudaMemcpyAsync(ctx->A_dv, dv, sizeof(float) * 3 * (size_t)ctx->V, cudaMemcpyDeviceToDevice, st));
+        ctx->has_prev_dv = 1;
+    } else {
+        PC_CUDA_TRY(cudaMemsetAsync(ctx->A_dv, 0, sizeof(float) * 3 * (size_t)ctx->V, st));
+        ctx->has_prev_dv = 0;
+    }
+    PC_CUDA_TRY(cudaStreamSynchronize(st));
+    return PC_OK;
+}

@@ -981,3 +981,25 @@ pc_status pc_warm_guess(pc_ctx *c, const pc_bsr *A, const float *v, float h, int
     }
     return PC_OK;
 }
+
+extern "C" pc_status pc_mlp_get_state(pc_mlp *m, float *m1, float *m2, int64_t *t, void *stream)
+{
+    if (!m || !m1 || !m2 || !t) return PC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    PC_CUDA_TRY(cudaMemcpyAsync(m1, m->m, sizeof(float) * PC_MLP_NPARAMS, cudaMemcpyDeviceToDevice, st));
+    PC_CUDA_TRY(cudaMemcpyAsync(m2, m->v, sizeof(float) * PC_MLP_NPARAMS, cudaMemcpyDeviceToDevice, st));
+    PC_CUDA_TRY(cudaStreamSynchronize(st));
+    *t = m->t;
+    return PC_OK;
+}
+
+extern "C" pc_status pc_mlp_set_state(pc_mlp *m, const float *m1, const float *m2, int64_t t, void *stream)
+{
+    if (!m || !m1 || !m2 || t < 0) return PC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    PC_CUDA_TRY(cudaMemcpyAsync(m->m, m1, sizeof(float) * PC_MLP_NPARAMS, cudaMemcpyDeviceToDevice, st));
+    PC_CUDA_TRY(cudaMemcpyAsync(m->v, m2, sizeof(float) * PC_MLP_NPARAMS, cudaMemcpyDeviceToDevice, st));
+    PC_CUDA_TRY(cudaStreamSynchronize(st));
+    m->t = t;
+    return PC_OK;
+}

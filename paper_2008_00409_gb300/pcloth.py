@@ -107,6 +107,10 @@ def _load():
                                   c_void_p, c_void_p]
     L.pc_batched_config.argtypes = [c_void_p, P(c_int32), P(c_int32), c_void_p]
     L.pc_set_barrier_wait.argtypes = [c_void_p, c_int64]
+    L.pc_get_prev_dv.argtypes = [c_void_p, c_void_p, P(c_int32), c_void_p]
+    L.pc_set_prev_dv.argtypes = [c_void_p, c_void_p, c_void_p]
+    L.pc_mlp_get_state.argtypes = [c_void_p, c_void_p, c_void_p, P(c_int64), c_void_p]
+    L.pc_mlp_set_state.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]
     L.pc_proximity_query.argtypes = [c_void_p, c_void_p, c_float, c_int32, c_void_p, c_void_p, P(c_int32), c_void_p]
     L.pc_step_host.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, P(pc_step_opts),
                                P(pc_step_info), c_void_p]
@@ -130,7 +134,8 @@ def _load():
     L.pc_get_solution64.argtypes = [c_void_p, c_void_p, c_void_p]
     for name in ("pc_create", "pc_destroy", "pc_get_sizes", "pc_get_rest", "pc_assemble_pattern",
                  "pc_assemble_values", "pc_bsr_spmv", "pc_pcg_solve", "pc_pcg_solve_static", "pc_step", "pc_step_host",
-                 "pc_pcg_solve_batched", "pc_step_batched", "pc_batched_config", "pc_set_barrier_wait", "pc_proximity_query", "pc_mlp_features", "pc_mlp_create",
+                 "pc_pcg_solve_batched", "pc_step_batched", "pc_batched_config", "pc_set_barrier_wait", "pc_proximity_query", "pc_get_prev_dv", "pc_set_prev_dv",
+                 "pc_mlp_get_state", "pc_mlp_set_state", "pc_mlp_features", "pc_mlp_create",
                  "pc_mlp_destroy", "pc_mlp_reset", "pc_mlp_stats", "pc_mlp_infer", "pc_mlp_grad", "pc_mlp_train_step",
                  "pc_mlp_adam_apply", "pc_set_warm_mlp",
                  "pc_set_profiling", "pc_spmv_stats", "pc_assembly_stats", "pc_get_solution64"):
@@ -332,6 +337,27 @@ def pc_proximity_query(ctx, x, delta, pairs, w, stream=None):
     _check(_lib.pc_proximity_query(ctx, _ptr(x), float(delta), int(cap), _ptr(pairs), _ptr(w), ctypes.byref(n),
                                    _stream(stream)), "pc_proximity_query", required=n.value)
     return n.value
+
+
+def pc_get_prev_dv(ctx, dv, stream=None):
+    """Copy the previous step's dv into dv (device float[V*3]); returns whether one exists."""
+    valid = c_int32()
+    _check(_lib.pc_get_prev_dv(ctx, _ptr(dv), ctypes.byref(valid), _stream(stream)), "pc_get_prev_dv")
+    return bool(valid.value)
+
+
+def pc_set_prev_dv(ctx, dv, stream=None):
+    _check(_lib.pc_set_prev_dv(ctx, _ptr(dv), _stream(stream)), "pc_set_prev_dv")
+
+
+def pc_mlp_get_state(m, m1, m2, stream=None):
+    t = c_int64()
+    _check(_lib.pc_mlp_get_state(m, _ptr(m1), _ptr(m2), ctypes.byref(t), _stream(stream)), "pc_mlp_get_state")
+    return t.value
+
+
+def pc_mlp_set_state(m, m1, m2, t, stream=None):
+    _check(_lib.pc_mlp_set_state(m, _ptr(m1), _ptr(m2), int(t), _stream(stream)), "pc_mlp_set_state")
 
 
 def pc_set_barrier_wait(ctx, cycles):
