@@ -43,7 +43,7 @@ REF_ITERS_PER_STEP = 7230
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the PCG SpMV,
 # from one ncu capture of the current kernel on that workload (mean of 3 launches).
 # ncu DRAM read + write bytes per launch of the PCG product, by (workload, storage)
-SPMV_DRAM_BYTES = {("stack3x526", "full"): 496.1e6 + 11.7e6, ("stack3x526", "offdiag"): 462.9e6 + 11.1e6}
+SPMV_DRAM_BYTES = {}
 
 
 def parse():
@@ -325,9 +325,11 @@ def run_ours(args):
     # Algorithmic bytes per launch: the blocks the product reads and their column indices
     # (40 per block: the off-diagonal blocks with the default storage, whose diagonal
     # blocks would multiply p_i - p_i = 0; all blocks with the full matrix), row pointers
-    # (4 (V+1)), difference diagonal (36 V), p read once and q written (float4, 16 V each)
+    # (4 (V+1)), the difference diagonal (4 V: one scalar per row, m_i I; the few rows next
+    # to pins read 36 more bytes, not counted), p read once and q written (float4, 16 V each)
     V = wl.V
-    spmv_bytes = 40 * spmv_blocks + 4 * (V + 1) + 36 * V + 16 * V + 16 * V
+    diag_bytes = 4 * V if args.storage in ("offdiag", "full") else 36 * V
+    spmv_bytes = 40 * spmv_blocks + 4 * (V + 1) + diag_bytes + 16 * V + 16 * V
     avg_spmv_s = (spmv_ms / 1e3) / max(n_spmv, 1)
     achieved = spmv_bytes / avg_spmv_s / 1e9 if n_spmv else None
     peak, peak_src = measured_hbm()

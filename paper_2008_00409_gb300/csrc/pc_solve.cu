@@ -494,6 +494,7 @@ pc_status pc_solver_alloc(pc_ctx *c)
     PC_CUDA_TRY(cudaMalloc(&c->p0, sizeof(float4) * c->V));
     PC_CUDA_TRY(cudaMalloc(&c->q, sizeof(float4) * c->V));
     PC_CUDA_TRY(cudaMalloc(&c->dinv, sizeof(float4) * 3 * c->V));
+    PC_CUDA_TRY(cudaMalloc(&c->dsc, sizeof(float) * (size_t)(c->V > 0 ? c->V : 1)));
     PC_CUDA_TRY(cudaMalloc(&c->dtmp, sizeof(float4) * c->V));
     PC_CUDA_TRY(cudaMalloc(&c->rhs32, sizeof(float) * n));
     PC_CUDA_TRY(cudaMalloc(&c->x64, sizeof(double) * n));
@@ -741,6 +742,21 @@ static pc_status build_sell(pc_ctx *c, const pc_bsr *A, const float *vals, bool 
     return PC_OK;
 }
 
+// ------------------------------------------------------------------------- scalar diagonals
+
+// dsc[i] = s when the difference-form diagonal of row i is exactly s I with s > 0 (every
+// row away from pins: its lumped mass term), else -1 (the product then reads all nine
+// entries). The product is bitwise the same either way.
+__global__ void dsc_kernel(int V, const float *__restrict__ dres, float *__restrict__ dsc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= V) return;
+    const float *D = dres + 9ll * i;
+    const bool scalar = D[1] == 0.f && D[2] == 0.f && D[3] == 0.f && D[5] == 0.f && D[6] == 0.f && D[7] == 0.f &&
+                        D[0] == D[4] && D[4] == D[8] && D[0] > 0.f;
+    dsc[i] = scalar ? D[0] : -1.f;
+}
+
 // ------------------------------------------------------------------------- off-diagonal BSR
 
 // Per row: the diagonal block's position (-1 if absent) and the count of the others.
@@ -880,6 +896,7 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
     a.ci = s.offdiag ? c->od_ci : s.A->col_idx;
     a.vals = s.offdiag ? c->od_vals : s.vals;
     a.dres = s.dres;
+    a.dsc = (s.dres && c->dsc) ? c->dsc : nullptr;
     a.x4 = (const float4 *)c->p0;
     a.y4 = (float4 *)c->q;
     a.partials = c->partials;
@@ -988,6 +1005,7 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
     if (o.storage == PC_STORAGE_SELL) PC_TRY(build_sell(ctx, A, vals, &s.sell, st));
     // the diagonal blocks multiply p_i - p_i = 0 in the difference form only
     if (o.storage == PC_STORAGE_OFFDIAG && s.diff) PC_TRY(build_offdiag(ctx, A, vals, &s.offdiag, st));
+    if (s.diff && ctx->dsc) PC_LAUNCH(ctx, dsc_kernel, pc_blocks(V, 256), 256, 0, st, V, dres, ctx->dsc);
     if (s.block)
         PC_LAUNCH(ctx, dinv_kernel<true>, pc_blocks(V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals,
                   (float4 *)ctx->dinv, ctx->d_err);
@@ -1183,6 +1201,7 @@ struct pc_static_scratch {
     float4 q[PC_STATIC_MAX_ROWS];
     float4 dinv[3 * PC_STATIC_MAX_ROWS];
     float4 dtmp[PC_STATIC_MAX_ROWS];
+    float dsc[PC_STATIC_MAX_ROWS];
     float rhs32[3 * PC_STATIC_MAX_ROWS];
     double x64[3 * PC_STATIC_MAX_ROWS];
     double partials[RED_SLOTS * PC_STATIC_MAX_BLOCKS];
@@ -1244,6 +1263,7 @@ extern "C" pc_status pc_pcg_solve_static(int32_t V, const pc_bsr *A, const float
     tmp.q = reinterpret_cast<float *>(S->q);
     tmp.dinv = reinterpret_cast<float *>(S->dinv);
     tmp.dtmp = reinterpret_cast<float *>(S->dtmp);
+    tmp.dsc = S->dsc;
     tmp.rhs32 = S->rhs32;
     tmp.x64 = S->x64;
     tmp.partials = S->partials;

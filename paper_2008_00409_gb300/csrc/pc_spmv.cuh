@@ -53,6 +53,7 @@ struct SpmvArgs {
     const int32_t *ci;
     const float *vals;
     const float *dres;    // difference-form diagonal, or null
+    const float *dsc;     // optional: per row the scalar s when dres_i = s I (s > 0), else -1
     const float *xin;     // plain mode: x as float[V][3]
     const float4 *x4;     // PCG mode: the search direction p as float4[V]
     float *y;             // plain mode: result, float[V][3]
@@ -98,7 +99,15 @@ __device__ __forceinline__ void spmv_load_row(const SpmvArgs &a, int tile, int t
         if (DIFF || PCG) r.xj = spmv_gather<PCG>(a, r.row);
         if (DIFF && (t & (SP_TPR - 1)) == 0) {
 #pragma unroll
-            for (int e = 0; e < 9; ++e) r.D[e] = a.dres[9ll * r.row + e];
+            for (int e = 0; e < 9; ++e) r.D[e] = 0.f;
+            // most rows' difference diagonal is m_i I: one float instead of nine
+            const float s = a.dsc ? a.dsc[r.row] : -1.f;
+            if (s > 0.f) {
+                r.D[0] = r.D[4] = r.D[8] = s;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 9; ++e) r.D[e] = a.dres[9ll * r.row + e];
+            }
         }
     }
 }
