@@ -123,6 +123,10 @@ typedef struct {
     int32_t storage;     /* PC_STORAGE_OFFDIAG (default), PC_STORAGE_FULL, PC_STORAGE_SYM or
                             PC_STORAGE_SELL: matrix layout the PCG products read (the
                             result is the same up to summation order) */
+    int32_t fuse;        /* 1 (default): each iteration's update and direction step run as one
+                            kernel with a grid-wide barrier (z stays in registers; used when
+                            every thread can carry its rows, up to about 0.9M rows on GB300);
+                            0: two kernels. Same method, same stop tests. */
 } pc_solve_opts;
 
 /* PC_STORAGE_FULL: the products read the full BSR matrix.

@@ -158,6 +158,7 @@ struct pc_ctx {
     float *od_vals = nullptr;                        // [9 od_cap + 16]
     int64_t od_nnzb = 0;                             // blocks of the last copy
     float *dsc = nullptr;                            // [V] scalar difference diagonal or -1
+    struct pc_fuse_bar *fbar = nullptr;              // grid barrier of the fused PCG update
     // proximity query: cell list (8 entries per triangle) and counts
     int64_t px_cap = 0;
     uint64_t *px_keys = nullptr;

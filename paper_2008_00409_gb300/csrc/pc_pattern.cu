@@ -284,7 +284,7 @@ static void free_ctx(pc_ctx *c)
                     c->sym_uci, c->sym_lcol, c->sym_lsrc, c->sym_uvals, c->sell_perm, c->sell_width,
                     c->sell_base, c->sell_dpos, c->sell_data, c->sell_diag, c->od_rp, c->od_cnt, c->od_dpos,
                     c->od_ci, c->od_vals, c->px_keys, c->px_vals, c->px_cnt, c->px_off, c->px_vcnt, c->px_voff,
-                    c->px_max, c->dsc};
+                    c->px_max, c->dsc, c->fbar};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->sc_host) cudaFreeHost(c->sc_host);

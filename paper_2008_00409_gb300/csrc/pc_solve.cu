@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(EW_THREADS) pcg_init_kernel(int V, const float
                                                                const float4 *__restrict__ dinv4,
                                                                float4 *__restrict__ z4, float4 *__restrict__ p4,
                                                                float4 *__restrict__ x4, double tol, int max_iter,
-                                                               double *partials, pc_scalars *sc)
+                                                               double *partials, pc_scalars *sc, int fused)
 {
     double rz = 0.0, rr = 0.0, bb = 0.0;
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
@@ -281,7 +281,8 @@ __global__ void __launch_bounds__(EW_THREADS) pcg_init_kernel(int V, const float
         const float4 z = apply_precond<BLOCK>(dinv4, row, r);
         r4[row] = r;
         z4[row] = z;
-        p4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
+        // the fused update leaves p ready for the next product: start from p = z
+        p4[row] = fused ? z : make_float4(0.f, 0.f, 0.f, 0.f);
         x4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
         rz += (double)dot3(r, z);
         rr += (double)dot3(r, r);
@@ -365,6 +366,185 @@ __global__ void __launch_bounds__(EW_THREADS) residual_check_kernel(int V, const
     }
 }
 
+// ------------------------------------------------------------------------- fused update + direction
+
+// One kernel per iteration instead of two: the update (x += alpha p, r -= alpha q,
+// z = M^-1 r, partial r.z and r.r), a grid-wide barrier, then every CTA sums the partials
+// in the same order, forms beta and applies p = z + beta p to its own rows from
+// registers. z never goes to memory and p is read once, so an iteration moves 48 bytes
+// per row less. Each thread owns rows first + u * stride (u < R <= FU_ROWS) and keeps
+// their z and p across the barrier; the grid is sized so that all CTAs are resident at
+// once (checked against the occupancy on the host). The barrier's waits are bounded; a
+// timeout ends the solve with PC_ERR_TIMEOUT.
+#define FU_THREADS 256
+#define FU_ROWS 12  // rows a thread carries across the barrier
+#define FU_CTAS_PER_SM 2
+
+struct pc_fuse_bar {
+    uint32_t count, gen, abort, pad;
+};
+
+__device__ __forceinline__ uint32_t fu_ld_acquire(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// All CTAs meet; false everywhere once a CTA gave up waiting.
+__device__ bool fu_grid_sync(pc_fuse_bar *g, long long budget)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = fu_ld_acquire(&g->abort) == 0u;
+        if (ok) {
+            const uint32_t gen = fu_ld_acquire(&g->gen);
+            __threadfence();
+            const uint32_t arrived = atomicAdd(&g->count, 1u);
+            if (arrived == gridDim.x - 1) {
+                g->count = 0u;
+                __threadfence();
+                atomicAdd(&g->gen, 1u);
+            } else {
+                const long long t0 = clock64();
+                while (fu_ld_acquire(&g->gen) == gen) {
+                    if (fu_ld_acquire(&g->abort) != 0u) { ok = 0; break; }
+                    if (clock64() - t0 > budget) {
+                        atomicExch(&g->abort, 1u);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+        }
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <bool BLOCK>
+__global__ void __launch_bounds__(FU_THREADS, FU_CTAS_PER_SM) pcg_update_dir_kernel(
+    int V, int R, float4 *__restrict__ x4, float4 *__restrict__ p4, float4 *__restrict__ r4,
+    const float4 *__restrict__ q4, const float4 *__restrict__ dinv4, double *partials, int n_pq, pc_scalars *sc,
+    pc_fuse_bar *bar, uint32_t *err)
+{
+    pdl_wait();
+    if (sc->done) return;
+    const double rz_old = sc->rz;  // read before the barrier; block 0 rewrites it after
+    const int stride = gridDim.x * blockDim.x;
+    const int first = blockIdx.x * blockDim.x + threadIdx.x;
+    float zs[FU_ROWS][3], ps[FU_ROWS][3];
+    float alpha = 0.f, rz = 0.f, rr = 0.f;
+#pragma unroll
+    for (int g = 0; g < FU_ROWS; g += 2) {
+        if (g >= R) break;
+        float4 p[2], q[2], x[2], r[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int row = first + (g + u) * stride;
+            if (g + u < R && row < V) {
+                p[u] = p4[row];
+                q[u] = q4[row];
+                x[u] = x4[row];
+                r[u] = r4[row];
+            }
+        }
+        if (g == 0) alpha = pcg_alpha(partials, n_pq, sc);  // overlaps the first loads
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int row = first + (g + u) * stride;
+            zs[g + u][0] = zs[g + u][1] = zs[g + u][2] = 0.f;
+            ps[g + u][0] = ps[g + u][1] = ps[g + u][2] = 0.f;
+            if (g + u < R && row < V) {
+                float4 xx = x[u], rv = r[u];
+                xx.x = fmaf(alpha, p[u].x, xx.x);
+                xx.y = fmaf(alpha, p[u].y, xx.y);
+                xx.z = fmaf(alpha, p[u].z, xx.z);
+                rv.x = fmaf(-alpha, q[u].x, rv.x);
+                rv.y = fmaf(-alpha, q[u].y, rv.y);
+                rv.z = fmaf(-alpha, q[u].z, rv.z);
+                const float4 z = apply_precond<BLOCK>(dinv4, row, rv);
+                x4[row] = xx;
+                r4[row] = rv;
+                rz += dot3(rv, z);
+                rr += dot3(rv, rv);
+                zs[g + u][0] = z.x;
+                zs[g + u][1] = z.y;
+                zs[g + u][2] = z.z;
+                ps[g + u][0] = p[u].x;
+                ps[g + u][1] = p[u].y;
+                ps[g + u][2] = p[u].z;
+            }
+        }
+    }
+    double v[2] = {(double)rz, (double)rr};
+    block_sum_d(v, 2);
+    if (threadIdx.x == 0) {
+        partials[(int64_t)blockIdx.x * RED_SLOTS] = v[0];
+        partials[(int64_t)blockIdx.x * RED_SLOTS + 1] = v[1];
+    }
+    if (!fu_grid_sync(bar, SP_WAIT_BUDGET)) {
+        if (threadIdx.x == 0) {
+            atomicOr(err, PC_DERR_TIMEOUT);
+            sc->status = PC_ERR_TIMEOUT;
+            sc->done = 1;
+        }
+        return;
+    }
+    // every CTA: the grid's r.z and r.r, summed in block order (the same value everywhere)
+    double t[2] = {0.0, 0.0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        t[0] += __ldcg(partials + (int64_t)b * RED_SLOTS);
+        t[1] += __ldcg(partials + (int64_t)b * RED_SLOTS + 1);
+    }
+    block_sum_d(t, 2);
+    __shared__ double s_beta;
+    if (threadIdx.x == 0) {
+        const double rz_new = t[0], beta = rz_new / rz_old;
+        s_beta = beta;
+        if (blockIdx.x == 0) {
+            const double pq = sc->pq;
+            sc->beta = beta;
+            sc->rz = rz_new;
+            sc->rr = t[1];
+            sc->iter += 1;
+            if (!(pq > 0.0) || !isfinite(sc->alpha)) {
+                sc->status = PC_ERR_NONFINITE;
+                sc->done = 1;
+            } else if (!isfinite(t[1]) || !isfinite(beta)) {
+                sc->status = PC_ERR_NONFINITE;
+                sc->done = 1;
+            } else if (t[1] <= sc->tol2) {
+                sc->status = PC_OK;
+                sc->done = 1;
+            } else if (sc->iter >= sc->max_iter) {
+                sc->status = PC_ERR_NOT_CONVERGED;
+                sc->done = 1;
+            }
+        }
+    }
+    __syncthreads();
+    const double beta_d = s_beta;
+    // the direction step even when this iteration stopped the solve: a residual
+    // replacement that resumes it corrects p from z_old to the replaced z
+    if (isfinite(beta_d)) {
+        const float beta = (float)beta_d;
+#pragma unroll
+        for (int u = 0; u < FU_ROWS; ++u) {
+            if (u >= R) break;
+            const int row = first + u * stride;
+            if (row < V)
+                p4[row] = make_float4(fmaf(beta, ps[u][0], zs[u][0]), fmaf(beta, ps[u][1], zs[u][1]),
+                                      fmaf(beta, ps[u][2], zs[u][2]), 0.f);
+        }
+    }
+    pdl_trigger();
+}
+
 // Residual replacement: r64 = b - A x64 in FP64; r = (float) r64, z = D^-1 r; partial
 // (r.z, r64.r64, b.b). The last block installs r.z and the FP64 residual as the
 // iteration's scalars (keeping beta and the search direction), and either starts the
@@ -374,7 +554,7 @@ __global__ void __launch_bounds__(EW_THREADS) residual_replace_kernel(
     int V, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const float *__restrict__ vals,
     const float *__restrict__ dres, const float *__restrict__ b, const double *__restrict__ x64,
     const float4 *__restrict__ dinv4, float4 *__restrict__ r4, float4 *__restrict__ z4, float4 *__restrict__ p4,
-    int first, double tol, int max_iter, double *partials, pc_scalars *sc)
+    int first, double tol, int max_iter, double *partials, pc_scalars *sc, int fused)
 {
     double rz = 0.0, rr = 0.0, bb = 0.0;
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
@@ -390,9 +570,24 @@ __global__ void __launch_bounds__(EW_THREADS) residual_replace_kernel(
         }
         const float4 r = make_float4(rf[0], rf[1], rf[2], 0.f);
         const float4 z = apply_precond<BLOCK>(dinv4, row, r);
+        if (fused) {
+            // p already holds z_old + beta p_prev (the fused update applied the direction
+            // step): swap z_old for the replaced z, p = z + beta p_prev as without fusion
+            if (first) {
+                p4[row] = z;
+            } else {
+                const float4 zo = apply_precond<BLOCK>(dinv4, row, r4[row]);
+                float4 pv = p4[row];
+                pv.x += z.x - zo.x;
+                pv.y += z.y - zo.y;
+                pv.z += z.z - zo.z;
+                p4[row] = pv;
+            }
+        } else if (first) {
+            p4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         r4[row] = r;
         z4[row] = z;
-        if (first) p4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
         rz += (double)dot3(r, z);
     }
     double v[3] = {rz, rr, bb};
@@ -495,6 +690,8 @@ pc_status pc_solver_alloc(pc_ctx *c)
     PC_CUDA_TRY(cudaMalloc(&c->q, sizeof(float4) * c->V));
     PC_CUDA_TRY(cudaMalloc(&c->dinv, sizeof(float4) * 3 * c->V));
     PC_CUDA_TRY(cudaMalloc(&c->dsc, sizeof(float) * (size_t)(c->V > 0 ? c->V : 1)));
+    PC_CUDA_TRY(cudaMalloc(&c->fbar, sizeof(pc_fuse_bar)));
+    PC_CUDA_TRY(cudaMemset(c->fbar, 0, sizeof(pc_fuse_bar)));
     PC_CUDA_TRY(cudaMalloc(&c->dtmp, sizeof(float4) * c->V));
     PC_CUDA_TRY(cudaMalloc(&c->rhs32, sizeof(float) * n));
     PC_CUDA_TRY(cudaMalloc(&c->x64, sizeof(double) * n));
@@ -599,6 +796,7 @@ extern "C" void pc_default_solve_opts(pc_solve_opts *o)
     o->check_every = 32;
     o->precond = PC_PRECOND_JACOBI;
     o->storage = PC_STORAGE_OFFDIAG;
+    o->fuse = 1;
 }
 
 struct SolveCtx {
@@ -610,6 +808,8 @@ struct SolveCtx {
     bool sym;   // the products read the symmetric storage
     bool sell;  // the products read the sliced-ELL storage
     bool offdiag;  // the products read the BSR copy without diagonal blocks
+    bool fuse;     // update and direction in one kernel (pcg_update_dir_kernel)
+    int fu_grid, fu_rows;
 };
 
 // ------------------------------------------------------------------------- symmetric storage
@@ -824,6 +1024,28 @@ static pc_status build_offdiag(pc_ctx *c, const pc_bsr *A, const float *vals, bo
     return PC_OK;
 }
 
+// Launch shape of the fused update (false in *ok when a thread would need more than
+// FU_ROWS rows, when the grid would not be co-resident, or without the barrier word).
+static pc_status fuse_shape(pc_ctx *c, bool block, bool *ok, int *grid, int *rows)
+{
+    *ok = false;
+    if (!c->fbar || c->V < 1) return PC_OK;
+    int occ = 0;
+    if (block)
+        PC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_update_dir_kernel<true>, FU_THREADS, 0));
+    else
+        PC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_update_dir_kernel<false>, FU_THREADS, 0));
+    if (occ < FU_CTAS_PER_SM) return PC_OK;
+    const int64_t need = ((int64_t)c->V + FU_THREADS - 1) / FU_THREADS;
+    const int64_t g = std::min<int64_t>((int64_t)c->num_sms * FU_CTAS_PER_SM, need);
+    const int64_t r = ((int64_t)c->V + g * FU_THREADS - 1) / (g * FU_THREADS);
+    if (r > FU_ROWS || g > c->max_red_blocks) return PC_OK;
+    *grid = (int)g;
+    *rows = (int)r;
+    *ok = true;
+    return PC_OK;
+}
+
 static int sell_grid(const pc_ctx *c)
 {
     const int g = c->num_sms * SL_CTAS_PER_SM;
@@ -852,7 +1074,7 @@ static pc_status replace_residual(const SolveCtx &s, float *x32, int first, doub
     if (!first) PC_LAUNCH(c, fold_kernel, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (float4 *)x32, c->x64);
     DISPATCH2(c, residual_replace_kernel, s.diff, s.block, ew_grid(c, c->V), EW_THREADS, s.st, c->V, s.A->row_ptr,
               s.A->col_idx, s.vals, s.dres, s.b, c->x64, (const float4 *)c->dinv, (float4 *)c->r, (float4 *)c->z,
-              (float4 *)c->p0, first, tol, max_iter, c->partials, c->sc);
+              (float4 *)c->p0, first, tol, max_iter, c->partials, c->sc, (int)s.fuse);
     return PC_OK;
 }
 
@@ -905,8 +1127,9 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
     const int n_pq = s.sell ? sell_grid(c) : spmv_grid(c);
     for (int k = 0; k < count; ++k) {
         bool timed = c->profiling && k == 0;
-        PC_LAUNCH_PDL(c, pcg_direction_kernel, dir_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (const float4 *)c->z,
-                      (float4 *)c->p0, (const pc_scalars *)c->sc);
+        if (!s.fuse)  // with fusion the previous update already formed p
+            PC_LAUNCH_PDL(c, pcg_direction_kernel, dir_grid(c, c->V), EW_THREADS, 0, s.st, c->V,
+                          (const float4 *)c->z, (float4 *)c->p0, (const pc_scalars *)c->sc);
         if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[0], s.st));
         if (s.sym) {
             SymArgs y{};
@@ -943,7 +1166,15 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
             PC_TRY(launch_spmv(c, a, s.diff, true, s.st));
         }
         if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[1], s.st));
-        if (s.block)
+        if (s.fuse && s.block)
+            PC_LAUNCH_PDL(c, pcg_update_dir_kernel<true>, s.fu_grid, FU_THREADS, 0, s.st, c->V, s.fu_rows,
+                          (float4 *)x, (float4 *)c->p0, (float4 *)c->r, (const float4 *)c->q, (const float4 *)c->dinv,
+                          c->partials, n_pq, c->sc, c->fbar, c->d_err);
+        else if (s.fuse)
+            PC_LAUNCH_PDL(c, pcg_update_dir_kernel<false>, s.fu_grid, FU_THREADS, 0, s.st, c->V, s.fu_rows,
+                          (float4 *)x, (float4 *)c->p0, (float4 *)c->r, (const float4 *)c->q, (const float4 *)c->dinv,
+                          c->partials, n_pq, c->sc, c->fbar, c->d_err);
+        else if (s.block)
             PC_LAUNCH_PDL(c, pcg_update_kernel<true>, upd_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (float4 *)x,
                       (const float4 *)c->p0, (float4 *)c->r, (const float4 *)c->q, (const float4 *)c->dinv,
                       (float4 *)c->z, c->partials, n_pq, c->sc);
@@ -999,7 +1230,10 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
     cudaStream_t st = (cudaStream_t)stream;
     const int V = ctx->V;
     const int64_t n = 3ll * V;
-    SolveCtx s{ctx, A, vals, dres, b, dres != nullptr, o.precond == PC_PRECOND_BLOCK, st, false, false, false};
+    SolveCtx s{ctx, A, vals, dres, b, dres != nullptr, o.precond == PC_PRECOND_BLOCK, st, false, false, false, false,
+               0, 0};
+    if (o.fuse) PC_TRY(fuse_shape(ctx, s.block, &s.fuse, &s.fu_grid, &s.fu_rows));
+    if (s.fuse) PC_CUDA_TRY(cudaMemsetAsync(ctx->fbar, 0, sizeof(pc_fuse_bar), st));
     PC_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), st));
     if (o.storage == PC_STORAGE_SYM) PC_TRY(build_sym(ctx, A, vals, &s.sym, st));
     if (o.storage == PC_STORAGE_SELL) PC_TRY(build_sell(ctx, A, vals, &s.sell, st));
@@ -1039,11 +1273,11 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
         if (s.block)
             PC_LAUNCH(ctx, pcg_init_kernel<true>, ew_grid(ctx, V), EW_THREADS, 0, st, V, b, ctx->rhs32,
                       (float4 *)ctx->r, (const float4 *)ctx->dinv, (float4 *)ctx->z, (float4 *)ctx->p0, (float4 *)x,
-                      o.tol, o.max_iter, ctx->partials, ctx->sc);
+                      o.tol, o.max_iter, ctx->partials, ctx->sc, (int)s.fuse);
         else
             PC_LAUNCH(ctx, pcg_init_kernel<false>, ew_grid(ctx, V), EW_THREADS, 0, st, V, b, ctx->rhs32,
                       (float4 *)ctx->r, (const float4 *)ctx->dinv, (float4 *)ctx->z, (float4 *)ctx->p0, (float4 *)x,
-                      o.tol, o.max_iter, ctx->partials, ctx->sc);
+                      o.tol, o.max_iter, ctx->partials, ctx->sc, (int)s.fuse);
     }
     PC_TRY(read_scalars(ctx, st));
     double rr_last = ctx->sc_host->rr;
@@ -1202,6 +1436,7 @@ struct pc_static_scratch {
     float4 dinv[3 * PC_STATIC_MAX_ROWS];
     float4 dtmp[PC_STATIC_MAX_ROWS];
     float dsc[PC_STATIC_MAX_ROWS];
+    pc_fuse_bar fbar;
     float rhs32[3 * PC_STATIC_MAX_ROWS];
     double x64[3 * PC_STATIC_MAX_ROWS];
     double partials[RED_SLOTS * PC_STATIC_MAX_BLOCKS];
@@ -1264,6 +1499,7 @@ extern "C" pc_status pc_pcg_solve_static(int32_t V, const pc_bsr *A, const float
     tmp.dinv = reinterpret_cast<float *>(S->dinv);
     tmp.dtmp = reinterpret_cast<float *>(S->dtmp);
     tmp.dsc = S->dsc;
+    tmp.fbar = &S->fbar;
     tmp.rhs32 = S->rhs32;
     tmp.x64 = S->x64;
     tmp.partials = S->partials;

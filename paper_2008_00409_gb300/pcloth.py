@@ -41,7 +41,8 @@ class pc_bsr(ctypes.Structure):
 
 class pc_solve_opts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("max_iter", c_int32), ("precision", c_int32), ("refresh", c_double),
-                ("refresh_every", c_int32), ("check_every", c_int32), ("precond", c_int32), ("storage", c_int32)]
+                ("refresh_every", c_int32), ("check_every", c_int32), ("precond", c_int32), ("storage", c_int32),
+                ("fuse", c_int32)]
 
 
 class pc_solve_info(ctypes.Structure):
@@ -205,11 +206,12 @@ def bsr_struct(row_ptr, col_idx, nnzb: int = 0) -> pc_bsr:
 
 
 def solve_opts(tol=1e-6, max_iter=20000, precision=PC_PREC_FP32, refresh=1e-2, refresh_every=1000, check_every=32,
-               precond=PC_PRECOND_JACOBI, storage=None):
+               precond=PC_PRECOND_JACOBI, storage=None, fuse=True):
     o = pc_solve_opts()
     o.tol, o.max_iter, o.precision, o.refresh, o.refresh_every, o.check_every, o.precond = (
         tol, max_iter, precision, refresh, refresh_every, check_every, precond)
     o.storage = PC_STORAGE_OFFDIAG if storage is None else storage
+    o.fuse = 1 if fuse else 0
     return o
 
 

@@ -351,10 +351,11 @@ def test_all_storages_agree_with_oracle(pc, case, form):
         else:
             assert H.rel_l2(_np(dv), out[pc.PC_STORAGE_FULL][1] if out else _np(dv)) <= 1e-6
         out[storage] = (info.iters, _np(dv))
-    # same method, products summed in another order: nearly the same iteration count
-    # (the plain form at 1e-11 runs into the FP32 blocks' rounding, where the count is
-    # sensitive to summation order)
-    slack = 0.05 if form == "difference" else 0.15
+    # same method, products summed in another order: nearly the same iteration count. Near
+    # 1e-9 the FP32 inner iterations stagnate between FP64 replacements and the count
+    # depends on summation order (measured: 809..931 on the 64^2 cloth for the four
+    # layouts, fused or not; within 1% at 1e-6); the plain form at 1e-11 more so
+    slack = 0.12 if form == "difference" else 0.15
     for storage in (pc.PC_STORAGE_SYM, pc.PC_STORAGE_SELL, pc.PC_STORAGE_OFFDIAG):
         assert abs(out[storage][0] - out[pc.PC_STORAGE_FULL][0]) <= slack * out[pc.PC_STORAGE_FULL][0] + 5
     if form == "plain":  # the copy without diagonal blocks is for the difference form only
@@ -439,3 +440,27 @@ def test_asymmetric_pattern_falls_back_to_full_storage(pc):
     # the symmetric layout is refused and the full matrix gives the identical solve
     assert res[pc.PC_STORAGE_SYM][1] == res[pc.PC_STORAGE_FULL][1]
     assert np.array_equal(res[pc.PC_STORAGE_SYM][2], res[pc.PC_STORAGE_FULL][2])
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("precond", ["jacobi", "block"])
+def test_fused_and_two_kernel_updates_agree(pc, case, precond):
+    """The fused update + direction kernel (one grid-wide barrier per iteration) and the
+    two-kernel form are the same method: both meet the tolerance and match the oracle,
+    with nearly the same iteration count (summation order differs)."""
+    wl = CASES[case]()
+    cl, om, pairs, w, pd, wd = _setup(pc, wl)
+    s = cl.assemble(pd, wd)
+    rp, ci, vals_ref, b_ref = om.assemble(wl.x0.astype(np.float64), wl.v0.astype(np.float64), pairs, w, wl.h)
+    dv_ref, _, _ = oracle.pcg(rp, ci, vals_ref, b_ref, tol=1e-12)
+    pre = pc.PC_PRECOND_BLOCK if precond == "block" else pc.PC_PRECOND_JACOBI
+    out = {}
+    for fuse in (True, False):
+        dv = torch.zeros(cl.V * 3, device="cuda")
+        info, st = pc.pc_pcg_solve(cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"], s["dres"], s["b"], dv,
+                                   pc.solve_opts(tol=1e-9, precision=pc.PC_PREC_MIXED, max_iter=50000, precond=pre,
+                                                 fuse=fuse))
+        assert st == pc.PC_OK and info.rel_res <= 2e-9
+        assert H.rel_l2(_np(dv), dv_ref) <= H.DV_RTOL
+        out[fuse] = info.iters
+    assert abs(out[True] - out[False]) <= 0.12 * out[False] + 5  # see the storage test
