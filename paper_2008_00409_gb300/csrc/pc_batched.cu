@@ -78,6 +78,10 @@ struct BtArgs {
     int V, n_inst;
     const int32_t *rp, *ci;
     const float *vals, *dres, *b;
+    // the SpMV phase's matrix: a copy without diagonal blocks (difference form) or A itself,
+    // and per row the scalar difference diagonal (s when dres_i = s I, else -1; or null)
+    const int32_t *srp, *sci;
+    const float *svals, *dsc;
     const int32_t *inst_rows;  // [n_inst + 1]
     float4 *r4, *z4, *p4, *q4, *x4;
     const float4 *dinv4;
@@ -392,8 +396,8 @@ __device__ __forceinline__ void bt_load_row(const BtArgs &a, int tile, int ra, i
     r.on = r.row >= ra && r.row < rb;
     r.rb = r.re = 0;
     if (r.on) {
-        r.rb = a.rp[r.row];
-        r.re = a.rp[r.row + 1];
+        r.rb = a.srp[r.row];
+        r.re = a.srp[r.row + 1];
     }
 }
 
@@ -471,7 +475,7 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
                     timed_out = true;
                     break;
                 }
-                const int b0 = a.rp[ra], b1 = a.rp[rb];
+                const int b0 = a.srp[ra], b1 = a.srp[rb];
                 unsigned char *base = smem_raw + s * SP_STAGE_BYTES;
                 if (b1 - b0 <= SP_CAP) {
                     const int64_t f0 = 9ll * b0, al0 = f0 & ~3ll, al1 = (9ll * b1 + 3) & ~3ll;
@@ -482,8 +486,8 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
                     stage_info[s][2] = b0 - c0;
                     stage_info[s][3] = 1;
                     mbar_arrive_expect_tx(&full_bar[s], vbytes + cbytes);
-                    bulk_g2s(base, a.vals + al0, vbytes, &full_bar[s]);
-                    bulk_g2s(base + SP_VAL_BYTES, a.ci + c0, cbytes, &full_bar[s]);
+                    bulk_g2s(base, a.svals + al0, vbytes, &full_bar[s]);
+                    bulk_g2s(base + SP_VAL_BYTES, a.sci + c0, cbytes, &full_bar[s]);
                 } else {
                     stage_info[s][0] = b0;
                     stage_info[s][1] = 0;
@@ -538,7 +542,14 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
                 xj = a.p4[cur.row];
                 if (DIFF && jl == 0) {
 #pragma unroll
-                    for (int q = 0; q < 9; ++q) D[q] = a.dres[9ll * cur.row + q];
+                    for (int q = 0; q < 9; ++q) D[q] = 0.f;
+                    const float sd = a.dsc ? a.dsc[cur.row] : -1.f;
+                    if (sd > 0.f) {
+                        D[0] = D[4] = D[8] = sd;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) D[q] = a.dres[9ll * cur.row + q];
+                    }
                 }
             }
             const int kg = kbase + e;
@@ -563,13 +574,13 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
 #pragma unroll
                     for (int w = 0; w < 4; ++w) {
                         const int bw = bb + w * SP_TPR;
-                        if (bw < cur.re) u[w] = a.p4[staged ? s_cols[bw - b0] : a.ci[bw]];
+                        if (bw < cur.re) u[w] = a.p4[staged ? s_cols[bw - b0] : a.sci[bw]];
                     }
 #pragma unroll
                     for (int w = 0; w < 4; ++w) {
                         const int bw = bb + w * SP_TPR;
                         if (bw < cur.re) {
-                            const float *B = staged ? s_vals + 9 * (bw - b0) : a.vals + 9ll * bw;
+                            const float *B = staged ? s_vals + 9 * (bw - b0) : a.svals + 9ll * bw;
                             float4 uw = u[w];
                             if (DIFF) { uw.x -= xj.x; uw.y -= xj.y; uw.z -= xj.z; }
                             spmv_fma(B, uw, acc0, acc1, acc2);
@@ -1008,6 +1019,18 @@ static pc_status bt_enqueue(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, con
     a.vals = vals;
     a.dres = dres;
     a.b = b;
+    a.srp = A->row_ptr;
+    a.sci = A->col_idx;
+    a.svals = vals;
+    a.dsc = nullptr;
+    // difference form: the SpMV phase streams the matrix without its diagonal blocks
+    // (they multiply p_i - p_i = 0) and reads one scalar per row for D_i = m_i I
+    if (dres && pc_build_offdiag_async(c, A, vals, dres, st) == PC_OK) {
+        a.srp = c->od_rp;
+        a.sci = c->od_ci;
+        a.svals = c->od_vals;
+        a.dsc = c->dsc;
+    }
     a.inst_rows = B->inst_rows;
     a.r4 = (float4 *)c->r;
     a.z4 = (float4 *)c->z;

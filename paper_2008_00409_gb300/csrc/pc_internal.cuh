@@ -261,6 +261,7 @@ inline bool pc_aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 // ------------------------------------------------------------------------- shared helpers (host side)
 pc_status pc_radix_sort(pc_ctx *ctx, uint64_t *keys, uint32_t *vals, int64_t n, int bits, cudaStream_t st);
 pc_status pc_proximity_alloc(pc_ctx *ctx);
+pc_status pc_build_offdiag_async(pc_ctx *c, const pc_bsr *A, const float *vals, const float *dres, cudaStream_t st);
 pc_status pc_exclusive_scan(pc_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, cudaStream_t st);
 pc_status pc_sort_reserve(pc_ctx *ctx, int64_t n);
 pc_status pc_read_errors(pc_ctx *ctx, cudaStream_t st, uint32_t *bits);

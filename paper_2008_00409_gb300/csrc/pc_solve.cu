@@ -1046,6 +1046,22 @@ static pc_status fuse_shape(pc_ctx *c, bool block, bool *ok, int *grid, int *row
     return PC_OK;
 }
 
+// The same copy without a host round trip (so it can be captured in a graph): valid
+// whenever the matrix fits the copy's capacity, which the caller checks from nnzb.
+// Also fills the scalar difference diagonals.
+pc_status pc_build_offdiag_async(pc_ctx *c, const pc_bsr *A, const float *vals, const float *dres, cudaStream_t st)
+{
+    const int V = c->V;
+    if (c->od_cap <= 0 || !c->od_vals || A->nnzb > c->od_cap) return PC_ERR_CAPACITY;
+    PC_LAUNCH(c, od_count_kernel, pc_blocks(V + 1ll, 256), 256, 0, st, V, A->row_ptr, A->col_idx, c->od_dpos,
+              c->od_cnt);
+    PC_TRY(pc_exclusive_scan(c, c->od_cnt, c->od_rp, V, st));
+    PC_LAUNCH(c, od_fill_kernel, pc_blocks(32ll * V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals, c->od_dpos,
+              c->od_rp, c->od_cap, c->od_ci, c->od_vals, c->d_err);
+    if (dres && c->dsc) PC_LAUNCH(c, dsc_kernel, pc_blocks(V, 256), 256, 0, st, V, dres, c->dsc);
+    return PC_OK;
+}
+
 static int sell_grid(const pc_ctx *c)
 {
     const int g = c->num_sms * SL_CTAS_PER_SM;
