@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-sequential", action="store_true", help="batched form: skip the one-garment-at-a-time comparison")
     ap.add_argument("--train-steps", type=int, default=2000, help="warmstart form: Adam steps")
     ap.add_argument("--garments", type=int, default=64, help="batched form: number of garments")
+    ap.add_argument("--no-fuse", action="store_true", help="two-kernel PCG update (no fused direction step)")
     ap.add_argument("--damp-mass", type=float, default=0.0, help="Rayleigh damping alpha (1/s)")
     ap.add_argument("--damp-stiff", type=float, default=0.0, help="Rayleigh damping beta (s)")
     return ap.parse_args()
@@ -288,7 +289,7 @@ def run_ours(args):
         else:
             pd, wd = contacts[k]
         info, st = cl.step(pd, wd, tol=args.tol, precision=prec, warm_start=pc.PC_WARM_PREV,
-                           max_iter=args.max_iter, precond=precond, storage=storage, allow_not_converged=True)
+                           max_iter=args.max_iter, precond=precond, storage=storage, fuse=not args.no_fuse, allow_not_converged=True)
         return info
 
     for k in range(args.warmup):
@@ -347,7 +348,7 @@ def run_ours(args):
             cl_e.v.copy_(vh, non_blocking=True)
             pd, wd = cl_e.proximity()
             cl_e.step(pd, wd, tol=args.tol, precision=prec, warm_start=pc.PC_WARM_PREV, max_iter=args.max_iter,
-                      precond=precond, storage=storage, allow_not_converged=True)
+                      precond=precond, storage=storage, fuse=not args.no_fuse, allow_not_converged=True)
             xh.copy_(cl_e.x)
             vh.copy_(cl_e.v)
 
@@ -374,7 +375,7 @@ def run_ours(args):
         o = pc.pc_step_opts()
         o.h = wl.h
         o.solve = pc.solve_opts(tol=args.tol, precision=prec, max_iter=args.max_iter, precond=precond,
-                                storage=storage)
+                                storage=storage, fuse=not args.no_fuse)
         o.warm_start = pc.PC_WARM_PREV
         for k in range(args.warmup):
             pc.pc_step_host(cl_e.ctx, xh, vh, host_contacts[k][0], host_contacts[k][1], o, allow_not_converged=True)
@@ -401,7 +402,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl.name, "V": V, "T": wl.T, "H": cl.H, "nnzb": int(nnzb), "storage": args.storage,
+            "config": {"workload": wl.name, "V": V, "T": wl.T, "H": cl.H, "nnzb": int(nnzb), "storage": args.storage, "fused_update": not args.no_fuse,
                        "contacts_per_step": (float(np.mean(n_pairs[-args.steps:])) if proximity else wl.n_contacts),
                        "contact_model": (f"one-sided thickness {wl.material.contact_thickness * 1e3:.2f} mm, "
                                          "pairs from the GPU proximity query each step") if proximity

@@ -548,10 +548,12 @@ class Cloth:
         return s
 
     def step(self, pairs=None, w=None, tol=1e-6, precision=PC_PREC_FP32, warm_start=PC_WARM_ZERO, max_iter=20000,
-             dv_out=None, precond=PC_PRECOND_JACOBI, allow_not_converged=False, feat_out=None, storage=None):
+             dv_out=None, precond=PC_PRECOND_JACOBI, allow_not_converged=False, feat_out=None, storage=None,
+             fuse=True):
         o = pc_step_opts()
         o.h = self.h
-        o.solve = solve_opts(tol=tol, max_iter=max_iter, precision=precision, precond=precond, storage=storage)
+        o.solve = solve_opts(tol=tol, max_iter=max_iter, precision=precision, precond=precond, storage=storage,
+                             fuse=fuse)
         o.warm_start = warm_start
         o.feat_out = _ptr(feat_out)
         info, st = pc_step(self.ctx, self.x, self.v, pairs, w, o, dv_out, allow_not_converged=allow_not_converged)
