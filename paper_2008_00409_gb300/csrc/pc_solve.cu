@@ -90,23 +90,39 @@ static __device__ bool last_block_reduce(double *v, int n, double *partials, uin
 // z = D^-1 r for one row. Scalar Jacobi: one float4 (three inverses) per row; block
 // Jacobi: three float4 per row (the rows of the inverse 3x3 block).
 template <bool BLOCK>
-__device__ __forceinline__ float4 apply_precond(const float4 *__restrict__ dinv4, int row, float4 r)
+__device__ __forceinline__ float4 apply_precond(const float *__restrict__ dinv4, int row, float4 r)
 {
     if (BLOCK) {
-        const float4 a = dinv4[3ll * row], b = dinv4[3ll * row + 1], c = dinv4[3ll * row + 2];
+        const float4 *d4 = reinterpret_cast<const float4 *>(dinv4);
+        const float4 a = d4[3ll * row], b = d4[3ll * row + 1], c = d4[3ll * row + 2];
         return make_float4(a.x * r.x + a.y * r.y + a.z * r.z, b.x * r.x + b.y * r.y + b.z * r.z,
                            c.x * r.x + c.y * r.y + c.z * r.z, 0.f);
     }
-    const float4 d = dinv4[row];
-    return make_float4(d.x * r.x, d.y * r.y, d.z * r.z, 0.f);
+    const float *d = dinv4 + 3ll * row;
+    return make_float4(d[0] * r.x, d[1] * r.y, d[2] * r.z, 0.f);
 }
 
 __device__ __forceinline__ float dot3(float4 a, float4 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
 
+// The single-system PCG keeps x, r and the Jacobi inverse packed, three floats per row
+// (12 bytes instead of 16: these vectors are never gathered, only streamed).
+__device__ __forceinline__ float4 ld3(const float *__restrict__ a, int row)
+{
+    const float *p = a + 3ll * row;
+    return make_float4(p[0], p[1], p[2], 0.f);
+}
+__device__ __forceinline__ void st3(float *__restrict__ a, int row, float4 v)
+{
+    float *p = a + 3ll * row;
+    p[0] = v.x;
+    p[1] = v.y;
+    p[2] = v.z;
+}
+
 // Inverse of the diagonal (scalar entries, or the whole 3x3 block computed in FP64).
 template <bool BLOCK>
 __global__ void dinv_kernel(int V, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                            const float *__restrict__ vals, float4 *__restrict__ dinv4, uint32_t *err)
+                            const float *__restrict__ vals, float *__restrict__ dinv, uint32_t *err)
 {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= V) return;
@@ -117,9 +133,12 @@ __global__ void dinv_kernel(int V, const int32_t *__restrict__ rp, const int32_t
     for (int e = 0; e < 9; ++e) B[e] = s >= 0 ? (double)vals[9ll * s + e] : 0.0;
     bool ok = s >= 0 && B[0] > 0.0 && B[4] > 0.0 && B[8] > 0.0 && isfinite(B[0] + B[4] + B[8]);
     if (!BLOCK) {
-        dinv4[r] = ok ? make_float4((float)(1.0 / B[0]), (float)(1.0 / B[4]), (float)(1.0 / B[8]), 0.f)
-                      : make_float4(1.f, 1.f, 1.f, 0.f);
+        float *d = dinv + 3ll * r;  // packed: three floats per row
+        d[0] = ok ? (float)(1.0 / B[0]) : 1.f;
+        d[1] = ok ? (float)(1.0 / B[4]) : 1.f;
+        d[2] = ok ? (float)(1.0 / B[8]) : 1.f;
     } else {
+        float4 *dinv4 = reinterpret_cast<float4 *>(dinv);
         double c00 = B[4] * B[8] - B[5] * B[7], c01 = B[2] * B[7] - B[1] * B[8], c02 = B[1] * B[5] - B[2] * B[4];
         double c10 = B[5] * B[6] - B[3] * B[8], c11 = B[0] * B[8] - B[2] * B[6], c12 = B[2] * B[3] - B[0] * B[5];
         double c20 = B[3] * B[7] - B[4] * B[6], c21 = B[1] * B[6] - B[0] * B[7], c22 = B[0] * B[4] - B[1] * B[3];
@@ -189,11 +208,11 @@ __device__ __forceinline__ float pcg_alpha(const double *partials, int n_pq, pc_
 // (all loads issued before any use), and the first rows' loads are issued before
 // alpha's reduction so that their latencies overlap.
 template <bool BLOCK>
-__global__ void __launch_bounds__(EW_THREADS) pcg_update_kernel(int V, float4 *__restrict__ x4,
+__global__ void __launch_bounds__(EW_THREADS) pcg_update_kernel(int V, float *__restrict__ x4,
                                                                  const float4 *__restrict__ p4,
-                                                                 float4 *__restrict__ r4,
+                                                                 float *__restrict__ r4,
                                                                  const float4 *__restrict__ q4,
-                                                                 const float4 *__restrict__ dinv4,
+                                                                 const float *__restrict__ dinv4,
                                                                  float4 *__restrict__ z4, double *partials,
                                                                  int n_pq, pc_scalars *sc)
 {
@@ -209,8 +228,8 @@ __global__ void __launch_bounds__(EW_THREADS) pcg_update_kernel(int V, float4 *_
             if (row < V) {
                 p[u] = p4[row];
                 q[u] = q4[row];
-                x[u] = x4[row];
-                r[u] = r4[row];
+                x[u] = ld3(x4, row);
+                r[u] = ld3(r4, row);
             }
         }
     };
@@ -231,8 +250,8 @@ __global__ void __launch_bounds__(EW_THREADS) pcg_update_kernel(int V, float4 *_
             rv.y = fmaf(-alpha, q[u].y, rv.y);
             rv.z = fmaf(-alpha, q[u].z, rv.z);
             const float4 z = apply_precond<BLOCK>(dinv4, row, rv);
-            x4[row] = xx;
-            r4[row] = rv;
+            st3(x4, row, xx);
+            st3(r4, row, rv);
             z4[row] = z;
             rz += dot3(rv, z);
             rr += dot3(rv, rv);
@@ -268,10 +287,10 @@ __global__ void __launch_bounds__(EW_THREADS) pcg_update_kernel(int V, float4 *_
 template <bool BLOCK>
 __global__ void __launch_bounds__(EW_THREADS) pcg_init_kernel(int V, const float *__restrict__ b,
                                                                const float *__restrict__ q,
-                                                               float4 *__restrict__ r4,
-                                                               const float4 *__restrict__ dinv4,
+                                                               float *__restrict__ r4,
+                                                               const float *__restrict__ dinv4,
                                                                float4 *__restrict__ z4, float4 *__restrict__ p4,
-                                                               float4 *__restrict__ x4, double tol, int max_iter,
+                                                               float *__restrict__ x4, double tol, int max_iter,
                                                                double *partials, pc_scalars *sc, int fused)
 {
     double rz = 0.0, rr = 0.0, bb = 0.0;
@@ -279,11 +298,11 @@ __global__ void __launch_bounds__(EW_THREADS) pcg_init_kernel(int V, const float
         const float b0 = b[3ll * row], b1 = b[3ll * row + 1], b2 = b[3ll * row + 2];
         const float4 r = make_float4(b0 - q[3ll * row], b1 - q[3ll * row + 1], b2 - q[3ll * row + 2], 0.f);
         const float4 z = apply_precond<BLOCK>(dinv4, row, r);
-        r4[row] = r;
+        st3(r4, row, r);
         z4[row] = z;
         // the fused update leaves p ready for the next product: start from p = z
         p4[row] = fused ? z : make_float4(0.f, 0.f, 0.f, 0.f);
-        x4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
+        st3(x4, row, make_float4(0.f, 0.f, 0.f, 0.f));
         rz += (double)dot3(r, z);
         rr += (double)dot3(r, r);
         bb += (double)b0 * b0 + (double)b1 * b1 + (double)b2 * b2;
@@ -428,8 +447,8 @@ __device__ bool fu_grid_sync(pc_fuse_bar *g, long long budget)
 
 template <bool BLOCK>
 __global__ void __launch_bounds__(FU_THREADS, FU_CTAS_PER_SM) pcg_update_dir_kernel(
-    int V, int R, float4 *__restrict__ x4, float4 *__restrict__ p4, float4 *__restrict__ r4,
-    const float4 *__restrict__ q4, const float4 *__restrict__ dinv4, double *partials, int n_pq, pc_scalars *sc,
+    int V, int R, float *__restrict__ x4, float4 *__restrict__ p4, float *__restrict__ r4,
+    const float4 *__restrict__ q4, const float *__restrict__ dinv4, double *partials, int n_pq, pc_scalars *sc,
     pc_fuse_bar *bar, uint32_t *err)
 {
     pdl_wait();
@@ -449,8 +468,8 @@ __global__ void __launch_bounds__(FU_THREADS, FU_CTAS_PER_SM) pcg_update_dir_ker
             if (g + u < R && row < V) {
                 p[u] = p4[row];
                 q[u] = q4[row];
-                x[u] = x4[row];
-                r[u] = r4[row];
+                x[u] = ld3(x4, row);
+                r[u] = ld3(r4, row);
             }
         }
         if (g == 0) alpha = pcg_alpha(partials, n_pq, sc);  // overlaps the first loads
@@ -468,8 +487,8 @@ __global__ void __launch_bounds__(FU_THREADS, FU_CTAS_PER_SM) pcg_update_dir_ker
                 rv.y = fmaf(-alpha, q[u].y, rv.y);
                 rv.z = fmaf(-alpha, q[u].z, rv.z);
                 const float4 z = apply_precond<BLOCK>(dinv4, row, rv);
-                x4[row] = xx;
-                r4[row] = rv;
+                st3(x4, row, xx);
+                st3(r4, row, rv);
                 rz += dot3(rv, z);
                 rr += dot3(rv, rv);
                 zs[g + u][0] = z.x;
@@ -553,7 +572,7 @@ template <bool DIFF, bool BLOCK>
 __global__ void __launch_bounds__(EW_THREADS) residual_replace_kernel(
     int V, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const float *__restrict__ vals,
     const float *__restrict__ dres, const float *__restrict__ b, const double *__restrict__ x64,
-    const float4 *__restrict__ dinv4, float4 *__restrict__ r4, float4 *__restrict__ z4, float4 *__restrict__ p4,
+    const float *__restrict__ dinv4, float *__restrict__ r4, float4 *__restrict__ z4, float4 *__restrict__ p4,
     int first, double tol, int max_iter, double *partials, pc_scalars *sc, int fused)
 {
     double rz = 0.0, rr = 0.0, bb = 0.0;
@@ -576,7 +595,7 @@ __global__ void __launch_bounds__(EW_THREADS) residual_replace_kernel(
             if (first) {
                 p4[row] = z;
             } else {
-                const float4 zo = apply_precond<BLOCK>(dinv4, row, r4[row]);
+                const float4 zo = apply_precond<BLOCK>(dinv4, row, ld3(r4, row));
                 float4 pv = p4[row];
                 pv.x += z.x - zo.x;
                 pv.y += z.y - zo.y;
@@ -586,7 +605,7 @@ __global__ void __launch_bounds__(EW_THREADS) residual_replace_kernel(
         } else if (first) {
             p4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        r4[row] = r;
+        st3(r4, row, r);
         z4[row] = z;
         rz += (double)dot3(r, z);
     }
@@ -618,21 +637,21 @@ __global__ void __launch_bounds__(EW_THREADS) residual_replace_kernel(
 }
 
 // x64 += increment; increment = 0 (per row, float4 increment)
-__global__ void fold_kernel(int V, float4 *x4, double *x64)
+__global__ void fold_kernel(int V, float *x4, double *x64)
 {
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
-        const float4 d = x4[row];
+        const float4 d = ld3(x4, row);
         x64[3ll * row] += (double)d.x;
         x64[3ll * row + 1] += (double)d.y;
         x64[3ll * row + 2] += (double)d.z;
-        x4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
+        st3(x4, row, make_float4(0.f, 0.f, 0.f, 0.f));
     }
 }
 // dv += increment (FP32 solve)
-__global__ void add_increment_kernel(int V, const float4 *x4, float *dv)
+__global__ void add_increment_kernel(int V, const float *x4, float *dv)
 {
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
-        const float4 d = x4[row];
+        const float4 d = ld3(x4, row);
         dv[3ll * row] += d.x;
         dv[3ll * row + 1] += d.y;
         dv[3ll * row + 2] += d.z;
@@ -1087,9 +1106,9 @@ static pc_status read_scalars(pc_ctx *c, cudaStream_t st)
 static pc_status replace_residual(const SolveCtx &s, float *x32, int first, double tol, int max_iter)
 {
     pc_ctx *c = s.c;
-    if (!first) PC_LAUNCH(c, fold_kernel, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (float4 *)x32, c->x64);
+    if (!first) PC_LAUNCH(c, fold_kernel, ew_grid(c, c->V), EW_THREADS, 0, s.st, c->V, x32, c->x64);
     DISPATCH2(c, residual_replace_kernel, s.diff, s.block, ew_grid(c, c->V), EW_THREADS, s.st, c->V, s.A->row_ptr,
-              s.A->col_idx, s.vals, s.dres, s.b, c->x64, (const float4 *)c->dinv, (float4 *)c->r, (float4 *)c->z,
+              s.A->col_idx, s.vals, s.dres, s.b, c->x64, c->dinv, c->r, (float4 *)c->z,
               (float4 *)c->p0, first, tol, max_iter, c->partials, c->sc, (int)s.fuse);
     return PC_OK;
 }
@@ -1184,19 +1203,19 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
         if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[1], s.st));
         if (s.fuse && s.block)
             PC_LAUNCH_PDL(c, pcg_update_dir_kernel<true>, s.fu_grid, FU_THREADS, 0, s.st, c->V, s.fu_rows,
-                          (float4 *)x, (float4 *)c->p0, (float4 *)c->r, (const float4 *)c->q, (const float4 *)c->dinv,
+                          x, (float4 *)c->p0, c->r, (const float4 *)c->q, c->dinv,
                           c->partials, n_pq, c->sc, c->fbar, c->d_err);
         else if (s.fuse)
             PC_LAUNCH_PDL(c, pcg_update_dir_kernel<false>, s.fu_grid, FU_THREADS, 0, s.st, c->V, s.fu_rows,
-                          (float4 *)x, (float4 *)c->p0, (float4 *)c->r, (const float4 *)c->q, (const float4 *)c->dinv,
+                          x, (float4 *)c->p0, c->r, (const float4 *)c->q, c->dinv,
                           c->partials, n_pq, c->sc, c->fbar, c->d_err);
         else if (s.block)
-            PC_LAUNCH_PDL(c, pcg_update_kernel<true>, upd_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (float4 *)x,
-                      (const float4 *)c->p0, (float4 *)c->r, (const float4 *)c->q, (const float4 *)c->dinv,
+            PC_LAUNCH_PDL(c, pcg_update_kernel<true>, upd_grid(c, c->V), EW_THREADS, 0, s.st, c->V, x,
+                      (const float4 *)c->p0, c->r, (const float4 *)c->q, c->dinv,
                       (float4 *)c->z, c->partials, n_pq, c->sc);
         else
-            PC_LAUNCH_PDL(c, pcg_update_kernel<false>, upd_grid(c, c->V), EW_THREADS, 0, s.st, c->V, (float4 *)x,
-                      (const float4 *)c->p0, (float4 *)c->r, (const float4 *)c->q, (const float4 *)c->dinv,
+            PC_LAUNCH_PDL(c, pcg_update_kernel<false>, upd_grid(c, c->V), EW_THREADS, 0, s.st, c->V, x,
+                      (const float4 *)c->p0, c->r, (const float4 *)c->q, c->dinv,
                       (float4 *)c->z, c->partials, n_pq, c->sc);
         if (timed) {
             c->ev_pending = 1;  // read after the chunk's synchronisation (no stall here)
@@ -1258,10 +1277,10 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
     if (s.diff && ctx->dsc) PC_LAUNCH(ctx, dsc_kernel, pc_blocks(V, 256), 256, 0, st, V, dres, ctx->dsc);
     if (s.block)
         PC_LAUNCH(ctx, dinv_kernel<true>, pc_blocks(V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals,
-                  (float4 *)ctx->dinv, ctx->d_err);
+                  ctx->dinv, ctx->d_err);
     else
         PC_LAUNCH(ctx, dinv_kernel<false>, pc_blocks(V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals,
-                  (float4 *)ctx->dinv, ctx->d_err);
+                  ctx->dinv, ctx->d_err);
     uint32_t bits = 0;
     PC_TRY(pc_read_errors(ctx, st, &bits));
     if (bits) return PC_ERR_NONFINITE;
@@ -1288,11 +1307,11 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
         PC_TRY(launch_spmv(ctx, a, s.diff, false, st));
         if (s.block)
             PC_LAUNCH(ctx, pcg_init_kernel<true>, ew_grid(ctx, V), EW_THREADS, 0, st, V, b, ctx->rhs32,
-                      (float4 *)ctx->r, (const float4 *)ctx->dinv, (float4 *)ctx->z, (float4 *)ctx->p0, (float4 *)x,
+                      ctx->r, ctx->dinv, (float4 *)ctx->z, (float4 *)ctx->p0, x,
                       o.tol, o.max_iter, ctx->partials, ctx->sc, (int)s.fuse);
         else
             PC_LAUNCH(ctx, pcg_init_kernel<false>, ew_grid(ctx, V), EW_THREADS, 0, st, V, b, ctx->rhs32,
-                      (float4 *)ctx->r, (const float4 *)ctx->dinv, (float4 *)ctx->z, (float4 *)ctx->p0, (float4 *)x,
+                      ctx->r, ctx->dinv, (float4 *)ctx->z, (float4 *)ctx->p0, x,
                       o.tol, o.max_iter, ctx->partials, ctx->sc, (int)s.fuse);
     }
     PC_TRY(read_scalars(ctx, st));
@@ -1339,7 +1358,7 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
     double rr = fin.rr, bb = fin.bb;
     if (mixed) {
         if (fin.iter > iter_last) {  // stopped early (limit / breakdown): fold what there is
-            PC_LAUNCH(ctx, fold_kernel, ew_grid(ctx, V), EW_THREADS, 0, st, V, (float4 *)x, ctx->x64);
+            PC_LAUNCH(ctx, fold_kernel, ew_grid(ctx, V), EW_THREADS, 0, st, V, x, ctx->x64);
         }
         PC_LAUNCH(ctx, f64_to_f32_kernel, ew_grid(ctx, n), EW_THREADS, 0, st, n, ctx->x64, dv);
         if (fin.iter > iter_last) {
@@ -1352,7 +1371,7 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
             bb = ctx->sc_host->bb;
         }
     } else {
-        PC_LAUNCH(ctx, add_increment_kernel, ew_grid(ctx, V), EW_THREADS, 0, st, V, (const float4 *)x, dv);
+        PC_LAUNCH(ctx, add_increment_kernel, ew_grid(ctx, V), EW_THREADS, 0, st, V, x, dv);
         if (s.diff) PC_LAUNCH(ctx, residual_check_kernel<true>, ew_grid(ctx, V), EW_THREADS, 0, st, V, A->row_ptr,
                               A->col_idx, vals, dres, b, dv, ctx->partials, ctx->sc);
         else PC_LAUNCH(ctx, residual_check_kernel<false>, ew_grid(ctx, V), EW_THREADS, 0, st, V, A->row_ptr,
