@@ -56,12 +56,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 }
 
 // Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from global to
-// this CTA's shared memory, completing on `bar` as transaction bytes.
+// this CTA's shared memory, completing on `bar` as transaction bytes. The copies stream
+// matrix tiles that each product reads once, so they carry an L2 evict-first policy:
+// the stream then does not push the vectors (the gathered direction p, q, x, r, ...,
+// together well under the 129 MB L2) out of L2 between their uses.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
 {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
+        "{\n\t.reg .b64 pol;\n\t"
+        "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], pol;"
+        "\n\t}" ::"r"(smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
