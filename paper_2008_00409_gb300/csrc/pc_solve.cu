@@ -2,16 +2,18 @@
 // equations are solved with a preconditioned conjugate gradient solver; Sec. 3.1: the
 // SpMV is the most expensive operator and vector operations are data parallel).
 //
-// Per iteration three kernels run:
-//   direction: p = z + beta p                                        (in place)
-//   spmv:      q = A p, partial p.q                                  -> alpha = rz / pq
-//   update:    x += alpha p, r -= alpha q, z = D^-1 r, partial r.z, r.r -> beta, stop test
-// (the SpMV kernel, a bulk-copy pipelined stream over the blocks, is in pc_spmv.cuh).
-// Dot products: FP32 within a thread, FP64 across threads; each kernel's last block sums the
-// per-block partials in a fixed order, so every reduction is deterministic. The
-// internal vectors (r, z, p, q, the FP32 increment, Jacobi) are float4 per vertex
-// (padded) so that every access is one coalesced 16-byte load and each SpMV gather is
-// a single load.
+// Per iteration two kernels run by default:
+//   spmv:           q = A p, partial p.q                             -> alpha = rz / pq
+//   update + dir:   x += alpha p, r -= alpha q, z = D^-1 r, partial r.z, r.r; a grid-wide
+//                   barrier; beta, stop test; p = z + beta p        (pcg_update_dir_kernel)
+// or, when the rows do not fit the fused kernel's registers (or fuse = 0), three:
+//   direction: p = z + beta p; spmv; update (z to memory, the last block forms beta).
+// The SpMV kernel, a bulk-copy pipelined stream over the blocks, is in pc_spmv.cuh; it
+// reads by default a per-solve copy of the matrix without its diagonal blocks.
+// Dot products: FP32 within a thread, FP64 across threads; partials are summed in a fixed
+// order, so every reduction is deterministic. p, q and z are float4 per vertex (each SpMV
+// gather is one 16-byte load); x, r and the scalar Jacobi inverse, only ever streamed,
+// are packed float[V][3].
 //
 // Mixed precision (PC_PREC_MIXED): the solution is an FP64 accumulator plus the FP32
 // increment the iterations build; at refresh points the increment is folded into the
@@ -396,8 +398,12 @@ __global__ void __launch_bounds__(EW_THREADS) residual_check_kernel(int V, const
 // once (checked against the occupancy on the host). The barrier's waits are bounded; a
 // timeout ends the solve with PC_ERR_TIMEOUT.
 #define FU_THREADS 256
+#ifndef FU_ROWS
 #define FU_ROWS 12  // rows a thread carries across the barrier
+#endif
+#ifndef FU_CTAS_PER_SM
 #define FU_CTAS_PER_SM 2
+#endif
 
 struct pc_fuse_bar {
     uint32_t count, gen, abort, pad;
