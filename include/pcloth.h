@@ -299,11 +299,12 @@ PC_API pc_status pc_pcg_solve_batched(pc_ctx *ctx, const pc_bsr *A, const float 
  * not tried). Host pointers, may be NULL. */
 PC_API pc_status pc_batched_config(pc_ctx *ctx, int32_t *blocks_per_sm, int32_t *spmv_order, float *tune_ms);
 
-/* Cycle budget of each grid-barrier wait in the persistent batched solver (the solver's
- * software barrier spins on a generation word; a wait longer than the budget aborts the
- * launch: every CTA leaves at its next barrier, no result is written back, dv keeps its
- * initial guess, and pc_pcg_solve_batched / pc_step_batched return PC_ERR_TIMEOUT with
- * the context still usable). cycles <= 0 restores the default of 2^31 SM cycles (about
+/* Cycle budget of each grid-barrier wait in the persistent batched solver and in the
+ * fused PCG update of pc_pcg_solve / pc_step (software barriers spinning on a generation
+ * word). A wait longer than the budget aborts: in the batched solver every CTA leaves at
+ * its next barrier, no result is written back and dv keeps its initial guess; in the
+ * single-system solve the iteration stops; the calls return PC_ERR_TIMEOUT with the
+ * context still usable. cycles <= 0 restores the default of 2^31 SM cycles (about
  * a second at 2 GHz). A budget of a few cycles makes every solve time out: that is how the
  * timeout path is exercised without a hang. Host-only; takes effect at the next launch. */
 PC_API pc_status pc_set_barrier_wait(pc_ctx *ctx, int64_t cycles);

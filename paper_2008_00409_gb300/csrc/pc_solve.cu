@@ -455,7 +455,7 @@ template <bool BLOCK>
 __global__ void __launch_bounds__(FU_THREADS, FU_CTAS_PER_SM) pcg_update_dir_kernel(
     int V, int R, float *__restrict__ x4, float4 *__restrict__ p4, float *__restrict__ r4,
     const float4 *__restrict__ q4, const float *__restrict__ dinv4, double *partials, int n_pq, pc_scalars *sc,
-    pc_fuse_bar *bar, uint32_t *err)
+    pc_fuse_bar *bar, uint32_t *err, long long wait_budget)
 {
     pdl_wait();
     if (sc->done) return;
@@ -512,10 +512,11 @@ __global__ void __launch_bounds__(FU_THREADS, FU_CTAS_PER_SM) pcg_update_dir_ker
         partials[(int64_t)blockIdx.x * RED_SLOTS] = v[0];
         partials[(int64_t)blockIdx.x * RED_SLOTS + 1] = v[1];
     }
-    if (!fu_grid_sync(bar, SP_WAIT_BUDGET)) {
+    if (!fu_grid_sync(bar, wait_budget)) {
+        // a timeout outranks any status block 0 may record in this launch
         if (threadIdx.x == 0) {
             atomicOr(err, PC_DERR_TIMEOUT);
-            sc->status = PC_ERR_TIMEOUT;
+            atomicExch(&sc->status, (int32_t)PC_ERR_TIMEOUT);
             sc->done = 1;
         }
         return;
@@ -537,19 +538,13 @@ __global__ void __launch_bounds__(FU_THREADS, FU_CTAS_PER_SM) pcg_update_dir_ker
             sc->rz = rz_new;
             sc->rr = t[1];
             sc->iter += 1;
-            if (!(pq > 0.0) || !isfinite(sc->alpha)) {
-                sc->status = PC_ERR_NONFINITE;
-                sc->done = 1;
-            } else if (!isfinite(t[1]) || !isfinite(beta)) {
-                sc->status = PC_ERR_NONFINITE;
-                sc->done = 1;
-            } else if (t[1] <= sc->tol2) {
-                sc->status = PC_OK;
-                sc->done = 1;
-            } else if (sc->iter >= sc->max_iter) {
-                sc->status = PC_ERR_NOT_CONVERGED;
-                sc->done = 1;
-            }
+            // status changes only from PC_OK, so a timeout another CTA recorded stays
+            int32_t st = PC_OK;
+            if (!(pq > 0.0) || !isfinite(sc->alpha)) st = PC_ERR_NONFINITE;
+            else if (!isfinite(t[1]) || !isfinite(beta)) st = PC_ERR_NONFINITE;
+            else if (sc->iter >= sc->max_iter && !(t[1] <= sc->tol2)) st = PC_ERR_NOT_CONVERGED;
+            if (st != PC_OK) atomicCAS(&sc->status, (int32_t)PC_OK, st);
+            if (st != PC_OK || t[1] <= sc->tol2) sc->done = 1;
         }
     }
     __syncthreads();
@@ -1210,11 +1205,13 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
         if (s.fuse && s.block)
             PC_LAUNCH_PDL(c, pcg_update_dir_kernel<true>, s.fu_grid, FU_THREADS, 0, s.st, c->V, s.fu_rows,
                           x, (float4 *)c->p0, c->r, (const float4 *)c->q, c->dinv,
-                          c->partials, n_pq, c->sc, c->fbar, c->d_err);
+                          c->partials, n_pq, c->sc, c->fbar, c->d_err,
+                          c->bar_wait_cycles > 0 ? (long long)c->bar_wait_cycles : SP_WAIT_BUDGET);
         else if (s.fuse)
             PC_LAUNCH_PDL(c, pcg_update_dir_kernel<false>, s.fu_grid, FU_THREADS, 0, s.st, c->V, s.fu_rows,
                           x, (float4 *)c->p0, c->r, (const float4 *)c->q, c->dinv,
-                          c->partials, n_pq, c->sc, c->fbar, c->d_err);
+                          c->partials, n_pq, c->sc, c->fbar, c->d_err,
+                          c->bar_wait_cycles > 0 ? (long long)c->bar_wait_cycles : SP_WAIT_BUDGET);
         else if (s.block)
             PC_LAUNCH_PDL(c, pcg_update_kernel<true>, upd_grid(c, c->V), EW_THREADS, 0, s.st, c->V, x,
                       (const float4 *)c->p0, c->r, (const float4 *)c->q, c->dinv,

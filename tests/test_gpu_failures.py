@@ -165,3 +165,26 @@ def test_nonfinite_garment_keeps_its_state_while_the_others_step(pc):
         a, c = int(u.inst_rows[j]), int(u.inst_rows[j + 1])
         assert np.isfinite(dv_bad[a:c]).all()
         assert H.rel_l2(dv_bad[a:c], dv_good[a:c]) <= H.DV_RTOL, j
+
+
+def test_fused_update_barrier_timeout_and_recovery(pc):
+    """The single-system solve's fused update meets at a grid barrier once per iteration:
+    with a one-cycle budget the solve reports PC_ERR_TIMEOUT, and with the default budget
+    the same context gives the identical solve."""
+    wl = H.small_contact_cloth()
+    cl = pc.Cloth(wl)
+    s = cl.assemble(*cl.contacts_device(0))
+    args = (cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"], s["dres"], s["b"])
+    opts = pc.solve_opts(tol=1e-9, precision=pc.PC_PREC_MIXED, max_iter=50000)
+    ref = torch.zeros(cl.V * 3, device="cuda")
+    info_ref, _ = pc.pc_pcg_solve(*args, ref, opts)
+    pc.pc_set_barrier_wait(cl.ctx, 1)
+    dv = torch.zeros(cl.V * 3, device="cuda")
+    with pytest.raises(pc.PcError) as e:
+        pc.pc_pcg_solve(*args, dv, opts)
+    assert e.value.status == pc.PC_ERR_TIMEOUT
+    pc.pc_set_barrier_wait(cl.ctx, 0)
+    dv.zero_()
+    info, st = pc.pc_pcg_solve(*args, dv, opts)
+    assert st == pc.PC_OK and info.iters == info_ref.iters
+    assert torch.equal(dv, ref)
