@@ -404,6 +404,10 @@ __global__ void __launch_bounds__(EW_THREADS) residual_check_kernel(int V, const
 #ifndef FU_CTAS_PER_SM
 #define FU_CTAS_PER_SM 2
 #endif
+#ifndef FU_GROUP
+#define FU_GROUP 2  // rows whose loads are in flight together
+#endif
+static_assert(FU_ROWS % FU_GROUP == 0, "a thread's rows come in whole groups");
 
 struct pc_fuse_bar {
     uint32_t count, gen, abort, pad;
@@ -465,11 +469,11 @@ __global__ void __launch_bounds__(FU_THREADS, FU_CTAS_PER_SM) pcg_update_dir_ker
     float zs[FU_ROWS][3], ps[FU_ROWS][3];
     float alpha = 0.f, rz = 0.f, rr = 0.f;
 #pragma unroll
-    for (int g = 0; g < FU_ROWS; g += 2) {
+    for (int g = 0; g < FU_ROWS; g += FU_GROUP) {
         if (g >= R) break;
-        float4 p[2], q[2], x[2], r[2];
+        float4 p[FU_GROUP], q[FU_GROUP], x[FU_GROUP], r[FU_GROUP];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < FU_GROUP; ++u) {
             const int row = first + (g + u) * stride;
             if (g + u < R && row < V) {
                 p[u] = p4[row];
@@ -480,7 +484,7 @@ __global__ void __launch_bounds__(FU_THREADS, FU_CTAS_PER_SM) pcg_update_dir_ker
         }
         if (g == 0) alpha = pcg_alpha(partials, n_pq, sc);  // overlaps the first loads
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < FU_GROUP; ++u) {
             const int row = first + (g + u) * stride;
             zs[g + u][0] = zs[g + u][1] = zs[g + u][2] = 0.f;
             ps[g + u][0] = ps[g + u][1] = ps[g + u][2] = 0.f;
