@@ -683,12 +683,14 @@ __global__ void state_update_kernel(int64_t n, float *x, float *v, const float *
 
 // ------------------------------------------------------------------------- host side
 
-static int spmv_grid(const pc_ctx *c)
+static int tile_grid(const pc_ctx *c, int ctas_per_sm)
 {
     int tiles = (c->V + SP_ROWS - 1) / SP_ROWS;
-    int g = c->num_sms * SP_CTAS_PER_SM;
+    int g = c->num_sms * ctas_per_sm;
     return tiles < g ? (tiles > 0 ? tiles : 1) : g;
 }
+static int spmv_grid(const pc_ctx *c) { return tile_grid(c, SP_CTAS_PER_SM); }
+static int sym_grid(const pc_ctx *c) { return tile_grid(c, SY_CTAS_PER_SM); }
 static int shaped_grid(const pc_ctx *c, int64_t n, int ctas_per_sm)
 {
     int64_t b = (n + EW_THREADS - 1) / EW_THREADS;
@@ -1164,7 +1166,7 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
     a.partials = c->partials;
     a.sc = c->sc;
     a.err = c->d_err;
-    const int n_pq = s.sell ? sell_grid(c) : spmv_grid(c);
+    const int n_pq = s.sell ? sell_grid(c) : s.sym ? sym_grid(c) : spmv_grid(c);
     for (int k = 0; k < count; ++k) {
         bool timed = c->profiling && k == 0;
         if (!s.fuse)  // with fusion the previous update already formed p

@@ -1,6 +1,6 @@
 // Block-sparse (3x3) matrix-vector product, the dominant operator of the solve (Sec. 3.1).
 //
-// Persistent CTAs, four per SM. In each CTA a producer warp streams the CTA's 32-row
+// Persistent CTAs, five per SM. In each CTA a producer warp streams the CTA's 32-row
 // tiles of the matrix (the tile's contiguous run of 36-byte blocks and of column
 // indices) into a 2-stage shared-memory ring with 1-D bulk copies (cp.async.bulk)
 // completing on mbarriers, while 4 consumer warps compute the current tile with four
@@ -27,10 +27,10 @@
 #define SP_STAGES 2
 #endif
 #ifndef SP_CAP_PER_ROW
-#define SP_CAP_PER_ROW 18                  // stage capacity in blocks per row
+#define SP_CAP_PER_ROW 14                  // stage capacity in blocks per row (rows average about 12)
 #endif
 #ifndef SP_CTAS_PER_SM
-#define SP_CTAS_PER_SM 4
+#define SP_CTAS_PER_SM 5
 #endif
 #ifndef SP_TPR
 #define SP_TPR 4                           // threads per row

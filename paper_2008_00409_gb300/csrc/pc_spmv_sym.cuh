@@ -18,6 +18,7 @@
 #define SY_CAP_PER_ROW 12   // upper blocks per row that a stage holds
 #define SY_LCAP_PER_ROW 12  // lower entries per row that a stage holds
 #define SY_LWIN 2           // lower blocks per thread in flight
+#define SY_CTAS_PER_SM 4    // register budget without spills
 #define SY_CAP (SP_ROWS * SY_CAP_PER_ROW)
 #define SY_LCAP (SP_ROWS * SY_LCAP_PER_ROW)
 #define SY_VAL_BYTES ((SY_CAP * 36 + 32 + 15) / 16 * 16)
@@ -87,7 +88,7 @@ __device__ __forceinline__ void load_block9(const float *vals, int64_t s, float 
 }
 
 template <bool DIFF>
-__global__ void __launch_bounds__(SP_THREADS, SP_CTAS_PER_SM) spmv_sym_kernel(SymArgs a)
+__global__ void __launch_bounds__(SP_THREADS, SY_CTAS_PER_SM) spmv_sym_kernel(SymArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t full_bar[SP_STAGES], empty_bar[SP_STAGES];
