@@ -43,7 +43,7 @@ REF_ITERS_PER_STEP = 7230
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the PCG SpMV,
 # from one ncu capture of the current kernel on that workload (mean of 3 launches).
 # ncu DRAM read + write bytes per launch of the PCG product, by (workload, storage)
-SPMV_DRAM_BYTES = {("stack3x526", "offdiag"): 406.7e6 + 5.5e6}  # steady state (ncu --cache-control none)
+SPMV_DRAM_BYTES = {("stack3x526", "offdiag"): 407.4e6 + 8.3e6}  # steady state (ncu --cache-control none)
 
 
 def parse():
