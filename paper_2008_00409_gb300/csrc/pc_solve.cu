@@ -689,7 +689,41 @@ static int tile_grid(const pc_ctx *c, int ctas_per_sm)
     int g = c->num_sms * ctas_per_sm;
     return tiles < g ? (tiles > 0 ? tiles : 1) : g;
 }
-static int spmv_grid(const pc_ctx *c) { return tile_grid(c, SP_CTAS_PER_SM); }
+// The product's grid for stages of `capr` blocks per row (SP_CAP_PER_ROW or SP_CAPR_WIDE).
+static int spmv_grid(const pc_ctx *c, int capr)
+{
+    return tile_grid(c, capr <= SP_CAP_PER_ROW ? SpShape<SP_CAP_PER_ROW>::ctas_per_sm
+                                               : SpShape<SP_CAPR_WIDE>::ctas_per_sm);
+}
+
+// Dynamic shared memory of every instantiation of the product (set once per device).
+static pc_status spmv_set_smem()
+{
+    const int n = SpShape<SP_CAP_PER_ROW>::smem_bytes, w = SpShape<SP_CAPR_WIDE>::smem_bytes;
+    PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<true, true, SP_CAP_PER_ROW>, cudaFuncAttributeMaxDynamicSharedMemorySize, n));
+    PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<false, true, SP_CAP_PER_ROW>, cudaFuncAttributeMaxDynamicSharedMemorySize, n));
+    PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<true, true, SP_CAPR_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, w));
+    PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<false, true, SP_CAPR_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, w));
+    PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<true, false, SP_CAPR_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, w));
+    PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<false, false, SP_CAPR_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, w));
+    return PC_OK;
+}
+
+// The largest tile (blocks in SP_ROWS consecutive rows) of a BSR pattern, into *out
+// (zeroed by the caller) with one atomicMax per warp.
+__global__ void tile_max_kernel(int V, const int32_t *__restrict__ rp, long long *out)
+{
+    const int ntiles = (V + SP_ROWS - 1) / SP_ROWS;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    long long m = 0;
+    if (t < ntiles) {
+        const int r0 = t * SP_ROWS, r1 = min(r0 + SP_ROWS, V);
+        m = (long long)rp[r1] - rp[r0];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
+}
 static int sym_grid(const pc_ctx *c) { return tile_grid(c, SY_CTAS_PER_SM); }
 static int shaped_grid(const pc_ctx *c, int64_t n, int ctas_per_sm)
 {
@@ -727,10 +761,7 @@ pc_status pc_solver_alloc(pc_ctx *c)
     PC_CUDA_TRY(cudaMalloc(&c->sc, sizeof(pc_scalars)));
     PC_CUDA_TRY(cudaMemset(c->sc, 0, sizeof(pc_scalars)));
     PC_CUDA_TRY(cudaMallocHost(&c->sc_host, sizeof(pc_scalars)));
-    PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM_BYTES));
-    PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM_BYTES));
-    PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM_BYTES));
-    PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM_BYTES));
+    PC_TRY(spmv_set_smem());
     PC_CUDA_TRY(cudaFuncSetAttribute(spmv_sym_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SY_SMEM_BYTES));
     PC_CUDA_TRY(cudaFuncSetAttribute(spmv_sym_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SY_SMEM_BYTES));
     if (c->A_cap > 0) {  // symmetric storage for systems up to the step-system capacity
@@ -784,13 +815,23 @@ static pc_status check_bsr(const pc_bsr *A, const float *vals)
     return PC_OK;
 }
 
-static pc_status launch_spmv(pc_ctx *c, const SpmvArgs &a, bool diff, bool pcg, cudaStream_t st)
+// PCG products take the stage width the solve chose; plain products (y = A x) always
+// the wide stages, which no tile of an assembled system outgrows in practice.
+static pc_status launch_spmv(pc_ctx *c, const SpmvArgs &a, bool diff, bool pcg, cudaStream_t st,
+                             int capr = SP_CAPR_WIDE)
 {
-    const int g = spmv_grid(c);
-    if (diff && pcg) PC_LAUNCH_PDL(c, (spmv_kernel<true, true>), g, SP_THREADS, SP_SMEM_BYTES, st, a);
-    else if (diff) PC_LAUNCH(c, (spmv_kernel<true, false>), g, SP_THREADS, SP_SMEM_BYTES, st, a);
-    else if (pcg) PC_LAUNCH_PDL(c, (spmv_kernel<false, true>), g, SP_THREADS, SP_SMEM_BYTES, st, a);
-    else PC_LAUNCH(c, (spmv_kernel<false, false>), g, SP_THREADS, SP_SMEM_BYTES, st, a);
+    const int g = spmv_grid(c, pcg ? capr : SP_CAPR_WIDE);
+    const int n = SpShape<SP_CAP_PER_ROW>::smem_bytes, w = SpShape<SP_CAPR_WIDE>::smem_bytes;
+    if (pcg && capr <= SP_CAP_PER_ROW) {
+        if (diff) PC_LAUNCH_PDL(c, (spmv_kernel<true, true, SP_CAP_PER_ROW>), g, SP_THREADS, n, st, a);
+        else PC_LAUNCH_PDL(c, (spmv_kernel<false, true, SP_CAP_PER_ROW>), g, SP_THREADS, n, st, a);
+    } else if (pcg) {
+        if (diff) PC_LAUNCH_PDL(c, (spmv_kernel<true, true, SP_CAPR_WIDE>), g, SP_THREADS, w, st, a);
+        else PC_LAUNCH_PDL(c, (spmv_kernel<false, true, SP_CAPR_WIDE>), g, SP_THREADS, w, st, a);
+    } else {
+        if (diff) PC_LAUNCH(c, (spmv_kernel<true, false, SP_CAPR_WIDE>), g, SP_THREADS, w, st, a);
+        else PC_LAUNCH(c, (spmv_kernel<false, false, SP_CAPR_WIDE>), g, SP_THREADS, w, st, a);
+    }
     return PC_OK;
 }
 
@@ -836,6 +877,7 @@ struct SolveCtx {
     bool offdiag;  // the products read the BSR copy without diagonal blocks
     bool fuse;     // update and direction in one kernel (pcg_update_dir_kernel)
     int fu_grid, fu_rows;
+    int capr = SP_CAPR_WIDE;  // the product's stage width (blocks per row)
 };
 
 // ------------------------------------------------------------------------- symmetric storage
@@ -1166,7 +1208,7 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
     a.partials = c->partials;
     a.sc = c->sc;
     a.err = c->d_err;
-    const int n_pq = s.sell ? sell_grid(c) : s.sym ? sym_grid(c) : spmv_grid(c);
+    const int n_pq = s.sell ? sell_grid(c) : s.sym ? sym_grid(c) : spmv_grid(c, s.capr);
     for (int k = 0; k < count; ++k) {
         bool timed = c->profiling && k == 0;
         if (!s.fuse)  // with fusion the previous update already formed p
@@ -1205,7 +1247,7 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
             if (s.diff) PC_LAUNCH_PDL(c, spmv_sell_kernel<true>, n_pq, SL_THREADS, 0, s.st, y);
             else PC_LAUNCH_PDL(c, spmv_sell_kernel<false>, n_pq, SL_THREADS, 0, s.st, y);
         } else {
-            PC_TRY(launch_spmv(c, a, s.diff, true, s.st));
+            PC_TRY(launch_spmv(c, a, s.diff, true, s.st, s.capr));
         }
         if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[1], s.st));
         if (s.fuse && s.block)
@@ -1290,9 +1332,18 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
     else
         PC_LAUNCH(ctx, dinv_kernel<false>, pc_blocks(V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals,
                   ctx->dinv, ctx->d_err);
+    // the narrower stages (more CTAs per SM) when every tile of the streamed matrix fits
+    const bool tmax = !s.sym && !s.sell && ctx->d_count && ctx->h_count;
+    if (tmax) {
+        PC_CUDA_TRY(cudaMemsetAsync(ctx->d_count + 3, 0, sizeof(int64_t), st));
+        PC_LAUNCH(ctx, tile_max_kernel, pc_blocks((V + SP_ROWS - 1) / SP_ROWS, 256), 256, 0, st, V,
+                  s.offdiag ? ctx->od_rp : A->row_ptr, reinterpret_cast<long long *>(ctx->d_count + 3));
+        PC_CUDA_TRY(cudaMemcpyAsync(ctx->h_count + 3, ctx->d_count + 3, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    }
     uint32_t bits = 0;
-    PC_TRY(pc_read_errors(ctx, st, &bits));
+    PC_TRY(pc_read_errors(ctx, st, &bits));  // synchronises the stream
     if (bits) return PC_ERR_NONFINITE;
+    if (tmax && ctx->h_count[3] <= (int64_t)SpShape<SP_CAP_PER_ROW>::cap) s.capr = SP_CAP_PER_ROW;
 
     const bool mixed = o.precision == PC_PREC_MIXED;
     // the iterations build an FP32 increment (float4 per row) on top of the initial dv:
@@ -1505,14 +1556,7 @@ static pc_status static_scratch_address(pc_static_scratch **out, int *device)
     if (!addr[dev]) {
         void *p = nullptr;
         PC_CUDA_TRY(cudaGetSymbolAddress(&p, g_pcg_scratch));
-        PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SP_SMEM_BYTES));
-        PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SP_SMEM_BYTES));
-        PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SP_SMEM_BYTES));
-        PC_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SP_SMEM_BYTES));
+        PC_TRY(spmv_set_smem());
         addr[dev] = p;
     }
     *out = static_cast<pc_static_scratch *>(addr[dev]);

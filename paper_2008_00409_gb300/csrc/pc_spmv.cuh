@@ -1,6 +1,8 @@
 // Block-sparse (3x3) matrix-vector product, the dominant operator of the solve (Sec. 3.1).
 //
-// Persistent CTAs, five per SM. In each CTA a producer warp streams the CTA's 32-row
+// Persistent CTAs, five per SM when every tile fits stages of 14 blocks per row, else
+// four with stages of 18 (the solve picks the shape from the matrix's largest tile). In
+// each CTA a producer warp streams the CTA's 32-row
 // tiles of the matrix (the tile's contiguous run of 36-byte blocks and of column
 // indices) into a 2-stage shared-memory ring with 1-D bulk copies (cp.async.bulk)
 // completing on mbarriers, while 4 consumer warps compute the current tile with four
@@ -46,6 +48,20 @@
 #define SP_STAGE_BYTES (SP_VAL_BYTES + SP_COL_BYTES)
 #define SP_SMEM_BYTES (SP_STAGES * SP_STAGE_BYTES)
 #define SP_WAIT_BUDGET (1ll << 31)         // cycles (about a second) before a wait gives up
+#define SP_CAPR_WIDE 18                    // the wider stages (blocks per row) of the product
+
+// Stage layout and residency of spmv_kernel for stages of CAPR blocks per row: the more
+// tiles in flight per SM, the more gathers of p are in flight, which is what the product
+// waits on; five CTAs fit an SM with 14-block stages, four with 18-block stages.
+template <int CAPR>
+struct SpShape {
+    static constexpr int cap = SP_ROWS * CAPR;
+    static constexpr int val_bytes = (cap * 36 + 32 + 15) / 16 * 16;
+    static constexpr int col_bytes = (cap * 4 + 32 + 15) / 16 * 16;
+    static constexpr int stage_bytes = val_bytes + col_bytes;
+    static constexpr int smem_bytes = SP_STAGES * stage_bytes;
+    static constexpr int ctas_per_sm = CAPR <= SP_CAP_PER_ROW ? SP_CTAS_PER_SM : 4;
+};
 
 struct SpmvArgs {
     int V;
@@ -112,9 +128,10 @@ __device__ __forceinline__ void spmv_load_row(const SpmvArgs &a, int tile, int t
     }
 }
 
-template <bool DIFF, bool PCG>
-__global__ void __launch_bounds__(SP_THREADS, SP_CTAS_PER_SM) spmv_kernel(SpmvArgs a)
+template <bool DIFF, bool PCG, int CAPR>
+__global__ void __launch_bounds__(SP_THREADS, SpShape<CAPR>::ctas_per_sm) spmv_kernel(SpmvArgs a)
 {
+    using Sh = SpShape<CAPR>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t full_bar[SP_STAGES], empty_bar[SP_STAGES];
     __shared__ int stage_info[SP_STAGES][4];  // b0, value offset, column offset, staged
@@ -154,8 +171,8 @@ __global__ void __launch_bounds__(SP_THREADS, SP_CTAS_PER_SM) spmv_kernel(SpmvAr
                 if (*(volatile int *)&s_timeout) break;
                 const int r0 = tile * SP_ROWS, r1 = min(r0 + SP_ROWS, a.V);
                 const int b0 = a.rp[r0], b1 = a.rp[r1];
-                unsigned char *base = smem_raw + s * SP_STAGE_BYTES;
-                if (b1 - b0 <= SP_CAP) {
+                unsigned char *base = smem_raw + s * Sh::stage_bytes;
+                if (b1 - b0 <= Sh::cap) {
                     const int64_t f0 = 9ll * b0, al0 = f0 & ~3ll, al1 = (9ll * b1 + 3) & ~3ll;
                     const int c0 = b0 & ~3, c1 = (b1 + 3) & ~3;
                     const uint32_t vbytes = (uint32_t)((al1 - al0) * 4), cbytes = (uint32_t)((c1 - c0) * 4);
@@ -165,7 +182,7 @@ __global__ void __launch_bounds__(SP_THREADS, SP_CTAS_PER_SM) spmv_kernel(SpmvAr
                     stage_info[s][3] = 1;
                     mbar_arrive_expect_tx(&full_bar[s], vbytes + cbytes);
                     bulk_g2s(base, a.vals + al0, vbytes, &full_bar[s]);
-                    bulk_g2s(base + SP_VAL_BYTES, a.ci + c0, cbytes, &full_bar[s]);
+                    bulk_g2s(base + Sh::val_bytes, a.ci + c0, cbytes, &full_bar[s]);
                 } else {
                     stage_info[s][0] = b0;
                     stage_info[s][1] = 0;
@@ -201,8 +218,8 @@ __global__ void __launch_bounds__(SP_THREADS, SP_CTAS_PER_SM) spmv_kernel(SpmvAr
             }
             const int b0 = stage_info[s][0], vo = stage_info[s][1], co = stage_info[s][2];
             const bool staged = stage_info[s][3] != 0;
-            const float *s_vals = reinterpret_cast<const float *>(smem_raw + s * SP_STAGE_BYTES) + vo;
-            const int32_t *s_cols = reinterpret_cast<const int32_t *>(smem_raw + s * SP_STAGE_BYTES + SP_VAL_BYTES) + co;
+            const float *s_vals = reinterpret_cast<const float *>(smem_raw + s * Sh::stage_bytes) + vo;
+            const int32_t *s_cols = reinterpret_cast<const int32_t *>(smem_raw + s * Sh::stage_bytes + Sh::val_bytes) + co;
             float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
             const float4 xj = cur.xj;
             // up to four blocks per thread in flight (rows average about 13 blocks, so one

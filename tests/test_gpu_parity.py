@@ -464,3 +464,76 @@ def test_fused_and_two_kernel_updates_agree(pc, case, precond):
         assert H.rel_l2(_np(dv), dv_ref) <= H.DV_RTOL
         out[fuse] = info.iters
     assert abs(out[True] - out[False]) <= 0.12 * out[False] + 5  # see the storage test
+
+
+def _banded_spd(V, extra_rows, n_extra, seed):
+    """Symmetric block pattern: a band of +-6 neighbours (13 blocks a row), plus, for the
+    rows in `extra_rows`, `n_extra` couplings to rows 160 q further on (q = 1..n_extra),
+    mirrored; off-diagonal blocks 0.1 x random symmetric 3x3, diagonal blocks the sum of
+    the row's off-diagonal Frobenius norms + 1 times I (block diagonally dominant: SPD)."""
+    rng = np.random.default_rng(seed)
+    cols = [set(range(max(0, i - 6), min(V, i + 7))) for i in range(V)]
+    for r in extra_rows:
+        for q in range(1, n_extra + 1):
+            c = r + 160 * q
+            assert c < V
+            cols[r].add(c)
+            cols[c].add(r)
+    blocks = {}
+    for i in range(V):
+        for j in cols[i]:
+            if j > i:
+                m = rng.uniform(-1.0, 1.0, size=(3, 3))
+                blocks[(i, j)] = 0.1 * (m + m.T)
+                blocks[(j, i)] = blocks[(i, j)].T
+    rp = np.zeros(V + 1, np.int32)
+    rp[1:] = np.cumsum([len(c) for c in cols])
+    ci = np.zeros(int(rp[-1]), np.int32)
+    vals = np.zeros((int(rp[-1]), 3, 3))
+    for i in range(V):
+        row = sorted(cols[i])
+        off = sum(np.linalg.norm(blocks[(i, j)]) for j in row if j != i)
+        for n, j in enumerate(row):
+            ci[rp[i] + n] = j
+            vals[rp[i] + n] = (off + 1.0) * np.eye(3) if j == i else blocks[(i, j)]
+    return rp, ci, vals
+
+
+@pytest.mark.parametrize("shape", ["narrow", "wide", "direct"])
+def test_product_stage_widths(pc, shape):
+    """The solve streams the matrix in stages of 14 blocks per row (five CTAs per SM) when
+    every 32-row tile fits, else of 18 (four CTAs per SM); a tile beyond that is read from
+    global memory. One matrix per case, its largest tile checked here on the CPU; the
+    mixed solve to 1e-10 against FP64 dense LU of the same FP32 blocks."""
+    V = 32 * 40
+    extra = {"narrow": 0, "wide": 3, "direct": 7}[shape]
+    rp, ci, vals = _banded_spd(V, range(32, 64) if extra else [], extra, seed=17)
+    tiles = rp[np.minimum(np.arange(V // 32 + 1) * 32, V)]
+    tmax = int(np.diff(tiles).max())
+    assert {"narrow": tmax <= 32 * 14, "wide": 32 * 14 < tmax <= 32 * 18, "direct": tmax > 32 * 18}[shape]
+    wl = wk.garment(36, seed=91, stream=400)
+    cl = pc.Cloth(wl)
+    assert cl.V >= V
+    # the context's V rows: the matrix above, then identity rows
+    n_id = cl.V - V
+    rp_full = np.concatenate([rp, rp[-1] + np.arange(1, n_id + 1, dtype=np.int32)])
+    ci_full = np.concatenate([ci, np.arange(V, cl.V, dtype=np.int32)])
+    vals_full = np.concatenate([vals, np.tile(np.eye(3), (n_id, 1, 1))])
+    nnzb = int(rp_full[-1])
+    cap = (nnzb + 3) // 4 * 4
+    ci_pad = np.zeros(cap, np.int32)
+    ci_pad[:nnzb] = ci_full
+    vals_pad = np.zeros((cap, 3, 3), np.float32)
+    vals_pad[:nnzb] = vals_full
+    b = np.random.default_rng(3).normal(size=cl.V * 3).astype(np.float32)
+    t = [torch.from_numpy(a).cuda() for a in (rp_full, ci_pad, vals_pad.reshape(-1), b)]
+    dv = torch.zeros(cl.V * 3, device="cuda")
+    info, st = pc.pc_pcg_solve(cl.ctx, t[0], t[1], nnzb, t[2], None, t[3], dv,
+                               pc.solve_opts(tol=1e-10, precision=pc.PC_PREC_MIXED, max_iter=5000,
+                                             storage=pc.PC_STORAGE_FULL))
+    assert st == pc.PC_OK and info.rel_res <= 2e-10
+    # the solve's matrix is the FP32 rounding of these blocks: solve that one in FP64
+    A = oracle.dense(rp, ci, vals.astype(np.float32).astype(np.float64))
+    want = np.linalg.solve(A, b[: 3 * V].astype(np.float64))
+    assert H.rel_l2(_np(dv)[: 3 * V].astype(np.float64), want) <= 1e-8
+    np.testing.assert_allclose(_np(dv)[3 * V:], b[3 * V:], rtol=1e-6)
