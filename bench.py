@@ -43,7 +43,7 @@ REF_ITERS_PER_STEP = 7230
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the PCG SpMV,
 # from one ncu capture of the current kernel on that workload (mean of 3 launches).
 # ncu DRAM read + write bytes per launch of the PCG product, by (workload, storage)
-SPMV_DRAM_BYTES = {("stack3x526", "offdiag"): 407.4e6 + 8.3e6}  # steady state (ncu --cache-control none)
+SPMV_DRAM_BYTES = {("stack3x526", "offdiag"): 407.4e6 + 8.6e6}  # steady state (ncu --cache-control none)
 
 
 def parse():
@@ -418,8 +418,9 @@ def run_ours(args):
                          "frac": (achieved / peak) if achieved else None,
                          "traffic": SPMV_DRAM_BYTES.get((wl.name, args.storage)),
                          "kernel": {"sell": "spmv_sell_kernel<true>", "sym": "spmv_sym_kernel<true>"}.get(
-                             args.storage, "spmv_kernel<true,true>") + " (q = A p, difference form, with p.q; "
-                             + args.storage + " storage)",
+                             args.storage, "spmv_kernel<true,true,CAPR>") + " (q = A p, difference form, with p.q; "
+                             + args.storage + " storage; CAPR = 14 or 18 blocks per row per stage, chosen per "
+                             "solve from the largest tile)",
                          "blocks_per_launch": int(spmv_blocks),
                          "bytes_per_launch": spmv_bytes, "peak_source": peak_src,
                          "avg_launch_us": avg_spmv_s * 1e6, "timed_launches": n_spmv},
