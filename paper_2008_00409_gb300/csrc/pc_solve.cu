@@ -9,7 +9,9 @@
 // or, when the rows do not fit the fused kernel's registers (or fuse = 0), three:
 //   direction: p = z + beta p; spmv; update (z to memory, the last block forms beta).
 // The SpMV kernel, a bulk-copy pipelined stream over the blocks, is in pc_spmv.cuh; it
-// reads by default a per-solve copy of the matrix without its diagonal blocks.
+// reads by default a per-solve copy of the matrix without its diagonal blocks, in stages
+// of 14 blocks per row at five CTAs per SM when the matrix's largest 32-row tile fits
+// them, else of 18 at four (measured per solve by tile_max_kernel).
 // Dot products: FP32 within a thread, FP64 across threads; partials are summed in a fixed
 // order, so every reduction is deterministic. p, q and z are float4 per vertex (each SpMV
 // gather is one 16-byte load); x, r and the scalar Jacobi inverse, only ever streamed,
