@@ -215,3 +215,125 @@ def test_gravity_and_lumped_mass():
     assert corner == pytest.approx(sum(MAT[0] * M.area[t] / 3 for t in inc), rel=1e-12)
     f = M.forces(rest)
     np.testing.assert_allclose(f, M.mass[:, None] * MAT[5:8][None, :], atol=1e-12)
+
+
+# ------------------------------------------------------------------------- membrane clamp, mixed-sign stress
+#
+# Draped cloth is usually stretched one way and compressed the other, so the second
+# Piola-Kirchhoff stress S has one positive and one negative principal value and the
+# clamp keeps only the positive one. The exact Hessian (finite differences of the forces)
+# contains the geometric term A0 (g_k . S g_l) I; the clamped one replaces S by its
+# positive part. So the oracle's Hessian must equal H_fd + A0 (g_k . (S+ - S) g_l) I with
+# S+ from numpy's symmetric eigendecomposition, S from the deformation gradient chosen
+# here, and g the shape gradients of the rest triangle computed here.
+
+def _stvk_stress(Fd):
+    E_, nu = MAT[1], MAT[2]
+    mu, lam = E_ / (2 * (1 + nu)), E_ * nu / (1 - nu * nu)
+    G = 0.5 * (Fd.T @ Fd - np.eye(2))
+    return 2 * mu * G + lam * np.trace(G) * np.eye(2)
+
+
+def _positive_part(S):
+    w, Q = np.linalg.eigh(S)
+    return Q @ np.diag(np.maximum(w, 0.0)) @ Q.T
+
+
+def _rot2(t):
+    return np.array([[math.cos(t), -math.sin(t)], [math.sin(t), math.cos(t)]])
+
+
+def _clamp_case(name):
+    """Rest triangle in the xy plane with its first edge along +x (so the oracle's material
+    frame is the world's x, y), an in-plane deformation Fd (2x2) and a rigid motion."""
+    right = np.array([[0.0, 0.0], [0.012, 0.0], [0.0, 0.010]])
+    general = np.array([[0.0, 0.0], [0.012, 0.0], [0.004, 0.010]])
+    I3, zero = np.eye(3), np.zeros(3)
+    if name == "axes-stretch-x":   # S diagonal (b = 0 exactly), stretch along the first axis: a >= c
+        return right, np.diag([1.06, 0.95]), I3, zero
+    if name == "axes-stretch-y":   # b = 0, stretch along the second axis: a < c
+        return right, np.diag([0.95, 1.06]), I3, zero
+    # principal axes at theta: the positive eigenvector is (cos theta, sin theta), so
+    # |l1 - a| = (l1 - l2) sin^2 theta and |l1 - c| = (l1 - l2) cos^2 theta
+    if name == "rotated-30deg":    # |l1 - a| < |l1 - c|
+        Q = _rot2(math.radians(30))
+        return general, Q @ np.diag([1.05, 0.94]) @ Q.T, _rot([0.3, -0.5, 0.8], 1.1), np.array([0.2, -0.7, 3.0])
+    if name == "rotated-60deg":    # |l1 - a| > |l1 - c|
+        Q = _rot2(math.radians(60))
+        return general, Q @ np.diag([1.05, 0.94]) @ Q.T, _rot([-0.2, 0.9, 0.1], 2.3), np.array([-1.0, 0.4, 0.5])
+    if name == "shear-rotation":   # non-symmetric Fd: a rotation inside the deformation gradient
+        return general, _rot2(0.4) @ np.array([[1.04, 0.03], [-0.02, 0.955]]), _rot([1, 1, 0], 0.5), zero
+    raise KeyError(name)
+
+
+def _clamp_expectation(rest2d, Fd, S_plus):
+    Dm = (rest2d[1:] - rest2d[0]).T                    # columns: the two rest edges
+    g = np.array([[-1.0, -1.0], [1.0, 0.0], [0.0, 1.0]]) @ np.linalg.inv(Dm)
+    A0 = 0.5 * abs(np.linalg.det(Dm))
+    corr = A0 * np.einsum("kc,cd,ld->kl", g, S_plus - _stvk_stress(Fd), g)
+    return corr[:, :, None, None] * np.eye(3)[None, None]
+
+
+def _fd_hessian(M, x, aux, eps=1e-8):
+    Hfd = np.zeros((3, 3, 3, 3))
+    for l in range(3):
+        for b in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[l, b] += eps
+            xm[l, b] -= eps
+            Hfd[:, l, :, b] = -(M.element(0, xp, aux=aux)[1] - M.element(0, xm, aux=aux)[1]) / (2 * eps)
+    return Hfd
+
+
+@pytest.mark.parametrize("name", ["axes-stretch-x", "axes-stretch-y", "rotated-30deg", "rotated-60deg",
+                                  "shear-rotation"])
+def test_membrane_clamp_mixed_sign_matches_eigendecomposition(name):
+    rest2d, Fd, R, t = _clamp_case(name)
+    rest = np.c_[rest2d, np.zeros(3)]
+    M = _mesh_one_triangle(rest)
+    aux = _aux_tri(M)
+    x = np.c_[rest2d @ Fd.T, np.zeros(3)] @ R.T + t
+    S = _stvk_stress(Fd)
+    lam = np.linalg.eigvalsh(S)
+    assert lam[0] < 0.0 < lam[1], "the state must have one stretched and one compressed direction"
+    a, b, c, l1 = S[0, 0], S[0, 1], S[1, 1], lam[1]
+    if name.startswith("axes"):
+        assert b == 0.0 and ((a >= c) == name.endswith("x"))
+    elif name == "rotated-30deg":
+        assert b != 0.0 and abs(l1 - a) < abs(l1 - c)
+    elif name == "rotated-60deg":
+        assert b != 0.0 and abs(l1 - a) > abs(l1 - c)
+    _, _, H = M.element(0, x, aux=aux)
+    Hfd = _fd_hessian(M, x, aux)
+    want = Hfd + _clamp_expectation(rest2d, Fd, _positive_part(S))
+    tol = 1e-6 * np.abs(H).max()
+    np.testing.assert_allclose(H, want, rtol=1e-5, atol=tol)
+    # the check is sensitive to the eigenvector: swapping its components (or keeping the
+    # negative eigenvalue's vector) moves the Hessian by far more than the tolerance
+    w, Q = np.linalg.eigh(S)
+    v = Q[:, 1]
+    for wrong in (np.array([v[1], v[0]]), Q[:, 0]):
+        S_wrong = l1 * np.outer(wrong, wrong)
+        bad = Hfd + _clamp_expectation(rest2d, Fd, S_wrong)
+        assert np.abs(H - bad).max() > 100 * tol
+
+
+def test_membrane_clamp_random_mixed_sign_states():
+    rng = np.random.default_rng(7)
+    rest2d = np.array([[0.0, 0.0], [0.012, 0.0], [0.004, 0.010]])
+    M = _mesh_one_triangle(np.c_[rest2d, np.zeros(3)])
+    aux = _aux_tri(M)
+    done = 0
+    while done < 12:
+        Q = _rot2(rng.uniform(0, math.pi))
+        Fd = _rot2(rng.uniform(-1, 1)) @ Q @ np.diag([rng.uniform(1.01, 1.1), rng.uniform(0.9, 0.99)]) @ Q.T
+        S = _stvk_stress(Fd)
+        lam = np.linalg.eigvalsh(S)
+        if not (lam[0] < 0.0 < lam[1]):
+            continue
+        R = _rot(rng.normal(size=3), rng.normal())
+        x = np.c_[rest2d @ Fd.T, np.zeros(3)] @ R.T + rng.normal(size=3)
+        _, _, H = M.element(0, x, aux=aux)
+        want = _fd_hessian(M, x, aux) + _clamp_expectation(rest2d, Fd, _positive_part(S))
+        np.testing.assert_allclose(H, want, rtol=1e-5, atol=1e-6 * np.abs(H).max())
+        done += 1
