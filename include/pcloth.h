@@ -2,11 +2,13 @@
  * pcloth.h -- C ABI of the GB300 (sm_103a) implicit-integrator hot path of P-Cloth
  * (Li, Tang, Manocha et al., SIGGRAPH Asia 2020).
  *
- * One time step of the method (Sec. 2.5, Eq. 3) solves
+ * One time step of the method (Sec. 2.5, Eq. 2-3) solves
  *
- *     (M - h^2 J) dv = h f(x_t + h v_t),        J = df/dx at x_t,
+ *     (M - h^2 J) dv = h (f(x_t) + h J v_t),     J = df/dx at x_t = -K,
  *
- * for the velocity increment dv, where the matrix is assembled anew each step from the
+ * for the velocity increment dv: Eq. 3's right-hand side h f(x_t + h v_t) taken to first
+ * order around x_t, as Eq. 2 linearises f (the same J as in the matrix; K is the sum of
+ * the positive-semidefinite element Hessians). The matrix is assembled anew each step from the
  * mesh's assembly elements (Sec. 3.2: membrane triangles, bending hinges, contact pairs,
  * gravity) and its sparsity pattern changes with the step's contact pairs (Sec. 3, first
  * paragraph). The system is solved with preconditioned conjugate gradients, whose cost
@@ -24,8 +26,13 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Work is
  *    stream-ordered; calls that return host-visible results (counts, solve info)
  *    synchronize the stream before returning.
- *  - A context (pc_ctx) holds one mesh's rest state and all scratch memory. It is
- *    allocated once by pc_create; no other call allocates device memory.
+ *  - A context (pc_ctx) holds one mesh's rest state and all scratch memory of the
+ *    assembly and solve calls, allocated once by pc_create. The calls that allocate
+ *    device memory are: pc_create; pc_mlp_create (training state); pc_set_warm_mlp
+ *    (the context's feature and guess buffers, on the first attach); pc_mlp_infer (a
+ *    4-byte timeout flag, on its first call in each host thread on each device, kept
+ *    until the process exits); pc_step_batched (the CUDA graph it instantiates on its
+ *    first call for a system shape). pc_pcg_solve_static allocates nothing at all.
  */
 #ifndef PCLOTH_H
 #define PCLOTH_H
@@ -226,10 +233,11 @@ PC_API pc_status pc_get_rest(const pc_ctx *ctx, int32_t *hinges, float *mass, vo
  * Synchronizes `stream`. */
 PC_API pc_status pc_assemble_pattern(pc_ctx *ctx, const pc_contacts *contacts, pc_bsr *A, void *stream);
 
-/* Sec. 3.2.2, value half, and Eq. 3: writes
- *   vals[nnzb][9]  A = M + h^2 sum_e H_e(x_t)   (element Hessians: membrane with its stress
- *                  clamped to the positive part, Gauss-Newton bending, contact penalty)
- *   b[V][3]        b = h f(x_t + h v_t)         (f includes gravity)
+/* Sec. 3.2.2, value half, and Eq. 2-3: writes
+ *   vals[nnzb][9]  A = M + h^2 K,  K = sum_e H_e(x_t)   (element Hessians: membrane with its
+ *                  stress clamped to the positive part, Gauss-Newton bending, contact penalty)
+ *   b[V][3]        b = h (f(x_t) - h K v_t)     (f includes gravity; the first-order
+ *                  expansion of Eq. 3's h f(x_t + h v_t), with the same K as the matrix)
  * on the pattern that pc_assemble_pattern produced for the same contacts. Pinned vertex
  * i: row and column blocks zero except A_ii = m_i I, b_i = 0.
  * dres (optional, float[V][9], may be NULL) receives the "difference-form" diagonal
@@ -262,7 +270,9 @@ PC_API pc_status pc_bsr_spmv(pc_ctx *ctx, const pc_bsr *A, const float *vals, co
  * direction (iterative refinement by residual replacement). The solve stops when the
  * FP64 residual meets tol.
  * info (host, may be NULL) receives iterations and the FP64 true relative residual.
- * Returns PC_ERR_NOT_CONVERGED (dv = last iterate) or PC_ERR_NONFINITE when those occur.
+ * Returns PC_ERR_NOT_CONVERGED (dv = last iterate) or PC_ERR_NONFINITE when those occur,
+ * and PC_ERR_ARG, before any product runs, when the pattern is malformed (row pointers
+ * decreasing or outside [0, A->nnzb], a column index outside [0, V)).
  * Synchronizes `stream`. */
 PC_API pc_status pc_pcg_solve(pc_ctx *ctx, const pc_bsr *A, const float *vals, const float *dres, const float *b,
                        float *dv, const pc_solve_opts *opts, pc_solve_info *info, void *stream);
@@ -334,19 +344,27 @@ PC_API pc_status pc_step_batched(pc_ctx *ctx, float *x, float *v, const pc_conta
                                  void *stream);
 
 /* Allocation-free variant of pc_pcg_solve (the paper has no counterpart): the same
- * solver, options and results, for callers that cannot allocate device memory and so
- * cannot hold a context -- for example a plug-in inside a host application that owns
- * and pre-reserves all GPU memory itself, or a real-time loop that must never call
- * cudaMalloc because an allocation can synchronize the device and stall the frame.
+ * solver, for callers that cannot allocate device memory and so cannot hold a context --
+ * for example a plug-in inside a host application that owns and pre-reserves all GPU
+ * memory itself, or a real-time loop that must never call cudaMalloc because an
+ * allocation can synchronize the device and stall the frame.
  * All scratch (PCG vectors, FP64 accumulator, reduction partials and scalars) lives in
  * one static device array inside the library sized for PC_STATIC_MAX_ROWS rows (about
  * 2.7 MB, held by every GPU that loads the library until the process exits); nothing is
  * allocated. The caller passes the system (V rows, as for pc_pcg_solve) and the output.
- * V > PC_STATIC_MAX_ROWS returns PC_ERR_CAPACITY before any device work.
- * The first call on a device looks up the array's device address and sets the kernels'
- * shared-memory limit for that device (make it before any stream capture). Every call
- * on a device shares the array and clears its scalars on entry; calls that overlap on
- * the GPU (concurrent streams, or several host threads on one device) race and must be
+ * V > PC_STATIC_MAX_ROWS returns PC_ERR_CAPACITY before any device work; a pattern whose
+ * row pointers or column indices do not fit V rows and A->nnzb blocks returns PC_ERR_ARG
+ * before any product runs. Options, stop tests and results are those of pc_pcg_solve,
+ * except opts->storage: there is no room for a second layout of the matrix, so every
+ * storage choice (including the default PC_STORAGE_OFFDIAG) is read as PC_STORAGE_FULL
+ * -- the products stream the caller's matrix; the solution is the same up to summation
+ * order. The stage shape of the product is chosen per solve as in pc_pcg_solve.
+ * Each call looks up the array's device address on the current device and sets the
+ * kernels' shared-memory limit (host-side set-up, no allocation); make the first call on
+ * a device before any stream capture. Every call on a device shares the array, which
+ * keeps the last call's contents; each call clears what must start at zero (scalars,
+ * reduction ticket, barrier word, error bits) on entry. Calls that overlap on the GPU
+ * (concurrent streams, or several host threads on one device) race and must be
  * serialized by the caller. Synchronizes `stream`. */
 #define PC_STATIC_MAX_ROWS 16384
 PC_API pc_status pc_pcg_solve_static(int32_t V, const pc_bsr *A, const float *vals, const float *dres,

@@ -25,7 +25,6 @@
 #include <math.h>
 #include <string.h>
 
-#include <mutex>
 
 #include "pc_internal.cuh"
 
@@ -124,15 +123,26 @@ __device__ __forceinline__ void st3(float *__restrict__ a, int row, float4 v)
 }
 
 // Inverse of the diagonal (scalar entries, or the whole 3x3 block computed in FP64).
+// The same pass validates the caller's pattern before any product reads it: row pointers
+// non-decreasing within [0, nnzb] and every column index in [0, V) (PC_DERR_INDEX, mapped
+// to PC_ERR_ARG; a bad row's entries are not read).
 template <bool BLOCK>
-__global__ void dinv_kernel(int V, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+__global__ void dinv_kernel(int V, int64_t nnzb, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                             const float *__restrict__ vals, float *__restrict__ dinv, uint32_t *err)
 {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= V) return;
+    const int k0 = rp[r], k1 = rp[r + 1];
     int s = -1;
-    for (int k = rp[r]; k < rp[r + 1]; ++k)
-        if (ci[k] == r) { s = k; break; }
+    if (k0 < 0 || k1 < k0 || (int64_t)k1 > nnzb) {
+        pc_set_err(err, PC_DERR_INDEX);
+    } else {
+        for (int k = k0; k < k1; ++k) {
+            const int c = ci[k];
+            if (c < 0 || c >= V) pc_set_err(err, PC_DERR_INDEX);
+            if (c == r && s < 0) s = k;
+        }
+    }
     double B[9];
     for (int e = 0; e < 9; ++e) B[e] = s >= 0 ? (double)vals[9ll * s + e] : 0.0;
     bool ok = s >= 0 && B[0] > 0.0 && B[4] > 0.0 && B[8] > 0.0 && isfinite(B[0] + B[4] + B[8]);
@@ -1323,17 +1333,22 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
     if (o.fuse) PC_TRY(fuse_shape(ctx, s.block, &s.fuse, &s.fu_grid, &s.fu_rows));
     if (s.fuse) PC_CUDA_TRY(cudaMemsetAsync(ctx->fbar, 0, sizeof(pc_fuse_bar), st));
     PC_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), st));
+    // the preconditioner's pass also validates the pattern; nothing else reads it before
+    if (s.block)
+        PC_LAUNCH(ctx, dinv_kernel<true>, pc_blocks(V, 256), 256, 0, st, V, A->nnzb, A->row_ptr, A->col_idx, vals,
+                  ctx->dinv, ctx->d_err);
+    else
+        PC_LAUNCH(ctx, dinv_kernel<false>, pc_blocks(V, 256), 256, 0, st, V, A->nnzb, A->row_ptr, A->col_idx, vals,
+                  ctx->dinv, ctx->d_err);
+    uint32_t bits = 0;
+    PC_TRY(pc_read_errors(ctx, st, &bits));  // synchronises the stream
+    if (bits & PC_DERR_INDEX) return PC_ERR_ARG;
+    if (bits) return PC_ERR_NONFINITE;
     if (o.storage == PC_STORAGE_SYM) PC_TRY(build_sym(ctx, A, vals, &s.sym, st));
     if (o.storage == PC_STORAGE_SELL) PC_TRY(build_sell(ctx, A, vals, &s.sell, st));
     // the diagonal blocks multiply p_i - p_i = 0 in the difference form only
     if (o.storage == PC_STORAGE_OFFDIAG && s.diff) PC_TRY(build_offdiag(ctx, A, vals, &s.offdiag, st));
     if (s.diff && ctx->dsc) PC_LAUNCH(ctx, dsc_kernel, pc_blocks(V, 256), 256, 0, st, V, dres, ctx->dsc);
-    if (s.block)
-        PC_LAUNCH(ctx, dinv_kernel<true>, pc_blocks(V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals,
-                  ctx->dinv, ctx->d_err);
-    else
-        PC_LAUNCH(ctx, dinv_kernel<false>, pc_blocks(V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals,
-                  ctx->dinv, ctx->d_err);
     // the narrower stages (more CTAs per SM) when every tile of the streamed matrix fits
     const bool tmax = !s.sym && !s.sell && ctx->d_count && ctx->h_count;
     if (tmax) {
@@ -1342,8 +1357,7 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
                   s.offdiag ? ctx->od_rp : A->row_ptr, reinterpret_cast<long long *>(ctx->d_count + 3));
         PC_CUDA_TRY(cudaMemcpyAsync(ctx->h_count + 3, ctx->d_count + 3, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     }
-    uint32_t bits = 0;
-    PC_TRY(pc_read_errors(ctx, st, &bits));  // synchronises the stream
+    PC_TRY(pc_read_errors(ctx, st, &bits));
     if (bits) return PC_ERR_NONFINITE;
     if (tmax && ctx->h_count[3] <= (int64_t)SpShape<SP_CAP_PER_ROW>::cap) s.capr = SP_CAP_PER_ROW;
 
@@ -1537,31 +1551,26 @@ struct pc_static_scratch {
     float rhs32[3 * PC_STATIC_MAX_ROWS];
     double x64[3 * PC_STATIC_MAX_ROWS];
     double partials[RED_SLOTS * PC_STATIC_MAX_BLOCKS];
+    int64_t count[4];  // the largest tile of the streamed matrix (slot 3), for the stage shape
     pc_scalars sc;
     uint32_t err;
 };
 
 static __device__ __align__(256) pc_static_scratch g_pcg_scratch;
 
-// Device address of g_pcg_scratch for the current device, looked up once per device
-// (host code may not use the symbol itself as a device pointer). The same set-up also
-// raises the SpMV kernels' dynamic shared-memory limit, which pc_create does for
-// context-based calls.
+// Device address of g_pcg_scratch on the current device (host code may not use the
+// symbol itself as a device pointer), looked up on every call, together with the SpMV
+// kernels' dynamic shared-memory limit, which pc_create sets for context-based calls.
+// Both are host-side set-up without any allocation; redoing them on each call keeps them
+// valid even if the device's context was reset and the module reloaded in between.
 static pc_status static_scratch_address(pc_static_scratch **out, int *device)
 {
-    static std::mutex mu;
-    static void *addr[256] = {};
     int dev = 0;
     PC_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 256) return PC_ERR_ARG;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void *p = nullptr;
-        PC_CUDA_TRY(cudaGetSymbolAddress(&p, g_pcg_scratch));
-        PC_TRY(spmv_set_smem());
-        addr[dev] = p;
-    }
-    *out = static_cast<pc_static_scratch *>(addr[dev]);
+    void *p = nullptr;
+    PC_CUDA_TRY(cudaGetSymbolAddress(&p, g_pcg_scratch));
+    PC_TRY(spmv_set_smem());
+    *out = static_cast<pc_static_scratch *>(p);
     *device = dev;
     return PC_OK;
 }
@@ -1582,6 +1591,7 @@ extern "C" pc_status pc_pcg_solve_static(int32_t V, const pc_bsr *A, const float
     if (8 * tmp.num_sms > PC_STATIC_MAX_BLOCKS) return PC_ERR_CAPACITY;
     pc_scalars host_sc{};
     uint32_t host_err = 0;
+    int64_t host_count[4] = {0, 0, 0, 0};
     tmp.r = reinterpret_cast<float *>(S->r);
     tmp.z = reinterpret_cast<float *>(S->z);
     tmp.p0 = reinterpret_cast<float *>(S->p);
@@ -1598,6 +1608,8 @@ extern "C" pc_status pc_pcg_solve_static(int32_t V, const pc_bsr *A, const float
     tmp.d_err = &S->err;
     tmp.sc_host = &host_sc;
     tmp.h_err = &host_err;
+    tmp.d_count = S->count;
+    tmp.h_count = host_count;
     // the previous call's scalars (and its reduction ticket) must not leak into this one
     PC_CUDA_TRY(cudaMemsetAsync(&S->sc, 0, sizeof(pc_scalars), (cudaStream_t)stream));
     return pcg_solve_impl(&tmp, A, vals, dres, b, dv, opts, info, stream);

@@ -1,5 +1,6 @@
-// Value assembly (Sec. 3.2.2 "value filling", Eq. 3): element kernels evaluate every
-// assembly element once (force at x_t + h v_t, Hessian at x_t) into per-element records;
+// Value assembly (Sec. 3.2.2 "value filling", Eq. 2-3): element kernels evaluate every
+// assembly element once (force and Hessian at x_t) into per-element records, and the
+// right-hand side is Eq. 3's h f(x_t + h v_t) to first order, b = h (f(x_t) - h K v_t);
 // a warp per matrix row then gathers the records of the elements incident to that row
 // and reduces them into the row's blocks in a fixed order. No atomics: the result is
 // deterministic and the matrix is bitwise symmetric.
