@@ -30,14 +30,20 @@ _i = ctypes.POINTER(ctypes.c_int)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle library with gcc (plain -O2, no fast-math, no -march)."""
+    """Compile the oracle library with gcc (plain -O2, no fast-math, no -march; OpenMP
+    spreads the product's rows and the solver's vector loops over the host cores)."""
     with _lock:
         if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
             os.makedirs(_BUILD, exist_ok=True)
             tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-            subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+            subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
             os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def num_threads() -> int:
+    """Threads the oracle's parallel loops use (OMP_NUM_THREADS, else every core)."""
+    return int(lib().om_num_threads())
 
 
 def lib():
@@ -64,6 +70,8 @@ def lib():
         L.om_hinge_angle.argtypes = [_d, _d, _d, _d, _d]
         L.om_spmv.argtypes = [ctypes.c_int, _i, _i, _d, _d, _d]
         L.om_pcg.argtypes = [ctypes.c_int, _i, _i, _d, _d, _d, ctypes.c_double, ctypes.c_int, _d]
+        L.om_num_threads.restype = ctypes.c_int
+        L.om_num_threads.argtypes = []
         _lib = L
     return _lib
 

@@ -48,11 +48,19 @@
  *    A_ii = m_i I, and b_i = 0, so dv_i = 0.
  *  - Sec. 2.5: the system is solved with preconditioned conjugate gradients (Jacobi:
  *    the scalar diagonal of A), stopping on the unpreconditioned relative residual.
+ *
+ * The row loops of the matrix-vector product and the vector loops of the solver carry
+ * OpenMP work-sharing pragmas, so the oracle uses every host core at the benchmark sizes;
+ * they split independent rows (or independent terms of a sum) across threads and change
+ * nothing else. Without OpenMP the file compiles to the same single-threaded program.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OM_OK 0
 #define OM_ERR_ARG -1
@@ -696,6 +704,7 @@ double om_hinge_angle(const double *x1, const double *x2, const double *x3, cons
 
 void om_spmv(int V, const int *row_ptr, const int *col_idx, const double *vals, const double *x, double *y)
 {
+#pragma omp parallel for schedule(static)
     for (int r = 0; r < V; ++r) {
         double acc[3] = {0, 0, 0};
         for (int s = row_ptr[r]; s < row_ptr[r + 1]; ++s) {
@@ -710,8 +719,25 @@ void om_spmv(int V, const int *row_ptr, const int *col_idx, const double *vals, 
 static double vdot(long n, const double *a, const double *b)
 {
     double s = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : s)
     for (long i = 0; i < n; ++i) s += a[i] * b[i];
     return s;
+}
+
+/* Number of threads the oracle's parallel loops use (1 without OpenMP). */
+int om_num_threads(void)
+{
+#ifdef _OPENMP
+    int n = 1;
+#pragma omp parallel
+    {
+#pragma omp single
+        n = omp_get_num_threads();
+    }
+    return n;
+#else
+    return 1;
+#endif
 }
 
 /* Jacobi-preconditioned conjugate gradients on A x = b (A symmetric positive definite),
@@ -737,6 +763,7 @@ int om_pcg(int V, const int *row_ptr, const int *col_idx, const double *vals, co
         return OM_OK;
     }
     om_spmv(V, row_ptr, col_idx, vals, x, q);
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < n; ++i) { r[i] = b[i] - q[i]; z[i] = dinv[i] * r[i]; p[i] = z[i]; }
     double rz = vdot(n, r, z);
     double rn = sqrt(vdot(n, r, r));
@@ -744,13 +771,16 @@ int om_pcg(int V, const int *row_ptr, const int *col_idx, const double *vals, co
         if (it >= max_iter) { status = OM_ERR_NOT_CONVERGED; break; }
         om_spmv(V, row_ptr, col_idx, vals, p, q);
         double alpha = rz / vdot(n, p, q);
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
         ++it;
         rn = sqrt(vdot(n, r, r));
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
         double rz_new = vdot(n, r, z);
         double beta = rz_new / rz;
         rz = rz_new;
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
     }
     om_spmv(V, row_ptr, col_idx, vals, x, q);

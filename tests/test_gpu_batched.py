@@ -83,7 +83,9 @@ def test_batched_steps_follow_the_oracle(pc):
             r0, r1 = u.inst_rows[k], u.inst_rows[k + 1]
             sel = (pairs[:, 0] >= r0) & (pairs[:, 0] < r1)
             dv_ref, _, _, _ = om.step(x[r0:r1], v[r0:r1], pairs[sel] - r0, w[sel], h=u.h, tol=1e-12)
-            assert H.rel_l2(v1[r0:r1] - v[r0:r1], dv_ref) <= 2 * H.DV_RTOL, f"step {step} instance {k}"
+            err = H.rel_l2(v1[r0:r1] - v[r0:r1], dv_ref)
+            print(f"batched step {step} garment {k}: dv rel err {err:.3e}")
+            assert err <= H.DV_RTOL, f"step {step} instance {k}"
 
 
 def test_batched_rejects_coupled_or_tiny_instances(pc):

@@ -1,11 +1,11 @@
 """Parity at full size, in the configuration the bench times (mixed-precision Jacobi-PCG
 to 1e-6, difference form): the 512 x 512 cloth with 2% contacts and the paper-scale
 3 x 526^2 stack. The pattern is compared bit for bit and every block and right-hand
-side entry against the oracle's full FP64 assembly; the oracle's exact solve is too
-slow at these sizes, so the solution is checked by a property that holds at any size:
-the FP64 residual of the solver's FP64 solution on the assembled system, recomputed
-here independently, meets the tolerance, and the returned dv is exactly that solution
-rounded to FP32."""
+side entry against the oracle's full FP64 assembly. The solution is checked by a
+property that holds at any size (the FP64 residual of the solver's FP64 solution on the
+assembled system, recomputed here independently, meets the tolerance, and the returned
+dv is exactly that solution rounded to FP32) and, at 512 x 512, element by element
+against the oracle's FP64 solve to 1e-12 (the oracle's loops run on every host core)."""
 import numpy as np
 import pytest
 import torch
@@ -137,3 +137,61 @@ def test_full_size_learned_guess(pc):
     o = out.cpu().numpy().astype(np.float64)[sample]
     assert np.linalg.norm((o - dvp[sample]) - (pred - dvp[sample])) <= 2e-3 * np.linalg.norm(pred - dvp[sample])
     assert np.all(out.cpu().numpy()[wl.pins] == 0.0)
+
+
+FULL_DV = {
+    # name: (workload, reference tolerance of the oracle's FP64 solve)
+    "square512-contacts": (wk.dynamic_square, 1e-12),
+    "stack3x526": (wk.paper_scale, 1e-11),          # FP64 CG stalls near 2e-9 true residual here
+    "square708-contacts": (wk.warm_start_eval, 1e-11),
+}
+
+
+@pytest.mark.parametrize("name", list(FULL_DV))
+def test_full_size_dv_matches_oracle(pc, name):
+    """dv element by element against the oracle's FP64 solve of its own FP64 assembly, at
+    the benchmark's tolerance (1e-6) and at a tight one (1e-9), at the full sizes of the
+    512 x 512 cloth, the paper-scale stack and the 708 x 708 cloth.
+
+    On the paper-scale stack (flat sheets: the right-hand side is essentially gravity) a
+    1e-6 residual gives dv within 1e-5 of the oracle, as required. On the single sheets
+    with out-of-plane jitter the condition number is about 1e6 and the jitter's elastic
+    and bending forces are thousands of times the gravity load, so two effects of the
+    method (not of this implementation) set the error:
+    - a relative residual of 1e-6 does not bound the dv error by 1e-5: the oracle's own
+      FP64 PCG stopped at 1e-6 is 6e-4 to 8e-4 away from the exact solution; at 1e-6 the
+      GPU is held to twice that plus 1e-5;
+    - element forces evaluated in FP32 (the paper's precision, Sec. 5) carry rounding of
+      about 1e-7 of each element's force before the per-vertex sums cancel it, and this
+      stiff system amplifies the sum's error: the dv error no longer falls below a few
+      1e-5 (512^2) to 2e-4 (708^2) however tight the solve. At 1e-9 the GPU must still
+      have at most half the error the exact method has at 1e-6, and at most 3e-4."""
+    make, ref_tol = FULL_DV[name]
+    wl = make()
+    cl = pc.Cloth(wl)
+    pairs, w = wl.contacts(1)
+    pd, wd = cl.contacts_device(1)
+    s = cl.assemble(pd, wd)
+    mesh = oracle.Mesh.from_workload(wl)
+    rp, ci, vals_ref, b_ref = mesh.assemble(wl.x0.astype(np.float64), wl.v0.astype(np.float64), pairs, w, wl.h)
+    dv_ref, it_ref, res_ref = oracle.pcg(rp, ci, vals_ref, b_ref, tol=ref_tol, max_iter=200000)
+    dv6, it6, _ = oracle.pcg(rp, ci, vals_ref, b_ref, tol=1e-6, max_iter=200000)
+    del vals_ref
+    err_oracle6 = H.rel_l2(dv6, dv_ref)
+    print(f"{name}: oracle ({oracle.num_threads()} threads): {it_ref} iterations to {ref_tol:g} (true residual "
+          f"{res_ref:.2e}), {it6} to 1e-6; its own dv error at 1e-6: {err_oracle6:.3e}")
+    for tol in (1e-6, 1e-9):
+        dv = torch.zeros(wl.V * 3, device="cuda")
+        info, st = pc.pc_pcg_solve(cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"], s["dres"], s["b"], dv,
+                                   pc.solve_opts(tol=tol, precision=pc.PC_PREC_MIXED, max_iter=50000))
+        assert st == pc.PC_OK and info.rel_res <= tol
+        got = dv.cpu().numpy().astype(np.float64).reshape(-1, 3)
+        err = H.rel_l2(got, dv_ref)
+        print(f"{name}: GPU mixed tol {tol:g}: {info.iters} iterations, dv rel err vs oracle {err:.3e}")
+        if err_oracle6 <= 0.1 * H.DV_RTOL:  # the residual bounds the error: the parity bound holds
+            assert err <= H.DV_RTOL
+        elif tol == 1e-6:
+            assert err <= 2 * err_oracle6 + H.DV_RTOL
+        else:
+            assert err <= min(0.5 * err_oracle6, 3e-4)
+        assert np.all(got[wl.pins] == 0.0)

@@ -190,5 +190,7 @@ def test_warm_start_steps(pc):
         x0, v0 = _np(cl.x), _np(cl.v)
         cl.step(pd, wd, tol=1e-9, precision=pc.PC_PREC_MIXED, warm_start=pc.PC_WARM_MLP, dv_out=dvo, max_iter=50000)
         dv_ref, _, _, _ = mesh.step(x0, v0, pairs, w, h=eval_wl.h, tol=1e-12)
-        assert H.rel_l2(_np(dvo), dv_ref) <= 2 * H.DV_RTOL, t
+        err = H.rel_l2(_np(dvo), dv_ref)
+        print(f"warm-started step {t}: dv rel err {err:.3e}")
+        assert err <= H.DV_RTOL, t
     pc.pc_set_warm_mlp(cl.ctx, None, None)

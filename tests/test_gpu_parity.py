@@ -147,8 +147,11 @@ def test_difference_diagonal_and_spmv(pc, case):
 
 
 @pytest.mark.parametrize("case", list(CASES))
-@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+@pytest.mark.parametrize("precision", ["fp32", "mixed", "mixed-bench"])
 def test_pcg_solution_matches_oracle(pc, case, precision):
+    """dv against the oracle solved to 1e-12. "mixed-bench" is the configuration the
+    benchmark times (mixed precision, tol 1e-6): on these small systems a 1e-6 residual
+    already bounds the dv error by 1e-5."""
     wl = CASES[case]()
     cl, om, pairs, w, pd, wd = _setup(pc, wl)
     s = cl.assemble(pd, wd)
@@ -156,12 +159,13 @@ def test_pcg_solution_matches_oracle(pc, case, precision):
     rp, ci, vals_ref, b_ref = om.assemble(x, wl.v0.astype(np.float64), pairs, w, wl.h)
     dv_ref, it_ref, _ = oracle.pcg(rp, ci, vals_ref, b_ref, tol=1e-12)
     prec = pc.PC_PREC_FP32 if precision == "fp32" else pc.PC_PREC_MIXED
-    tol = 1e-6 if precision == "fp32" else 1e-9
+    tol = 1e-9 if precision == "mixed" else 1e-6
     dv = torch.zeros(cl.V * 3, device="cuda")
     info, st = pc.pc_pcg_solve(cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"], s["dres"], s["b"], dv,
                                pc.solve_opts(tol=tol, precision=prec, max_iter=50000))
     err = H.rel_l2(_np(dv), dv_ref)
-    if precision == "mixed":
+    print(f"{case} {precision} tol {tol:g}: {info.iters} iterations, dv rel err {err:.3e}")
+    if precision != "fp32":
         assert info.rel_res <= 2 * tol
         assert err <= H.DV_RTOL, f"dv rel err {err:.3e}"
     else:
@@ -173,8 +177,10 @@ def test_pcg_solution_matches_oracle(pc, case, precision):
     assert (_np(dv).reshape(-1, 3)[wl.pins] == 0).all()
 
 
-def test_twenty_step_trajectory_small_square(pc):
-    """64 x 64 cloth, 20 steps: per-step dv parity with the oracle fed the same state."""
+@pytest.mark.parametrize("tol", [1e-9, 1e-6])
+def test_twenty_step_trajectory_small_square(pc, tol):
+    """64 x 64 cloth, 20 steps: per-step dv parity with the oracle fed the same state, at
+    a tight tolerance and at the benchmark's 1e-6."""
     wl = wk.small_square()
     cl = pc.Cloth(wl)
     om = oracle.Mesh.from_workload(wl)
@@ -183,11 +189,12 @@ def test_twenty_step_trajectory_small_square(pc):
     for step in range(wl.steps):
         x = _np(cl.x).astype(np.float64)
         v = _np(cl.v).astype(np.float64)
-        info, st = cl.step(tol=1e-9, precision=pc.PC_PREC_MIXED, dv_out=dv)
+        info, st = cl.step(tol=tol, precision=pc.PC_PREC_MIXED, dv_out=dv)
         dv_ref, _, _, oinfo = om.step(x, v, h=wl.h, tol=1e-12)
         err = H.rel_l2(_np(dv), dv_ref)
         worst = max(worst, err)
         assert err <= H.DV_RTOL, f"step {step}: rel err {err:.3e}"
+    print(f"square64 trajectory tol {tol:g}: worst dv rel err over {wl.steps} steps {worst:.3e}")
     # the state really moved and stayed finite
     assert np.isfinite(_np(cl.x)).all() and np.abs(_np(cl.x) - wl.x0).max() > 1e-3
 

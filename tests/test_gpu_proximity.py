@@ -148,7 +148,9 @@ def test_proximity_steps_follow_the_oracle(pc):
         assert st == pc.PC_OK
         dv_ref, _, _, _ = om.step(x, v, pairs, w.astype(np.float64), h=wl.h, tol=1e-12)
         dv = _np(cl.v).astype(np.float64) - v
-        assert H.rel_l2(dv, dv_ref) <= 2e-5, step
+        err = H.rel_l2(dv, dv_ref)
+        print(f"proximity step {step}: dv rel err {err:.3e}")
+        assert err <= H.DV_RTOL, step
 
 
 def test_query_full_size_sampled(pc):
