@@ -248,8 +248,9 @@ def spmv(rp, ci, vals, x) -> np.ndarray:
     return y
 
 
-def pcg(rp, ci, vals, b, x0=None, tol=1e-12, max_iter=100000):
-    """Jacobi-PCG; returns (x, iterations, true relative residual). Raises if not converged."""
+def pcg(rp, ci, vals, b, x0=None, tol=1e-12, max_iter=100000, check=True):
+    """Jacobi-PCG; returns (x, iterations, true relative residual). Raises if not
+    converged within max_iter (unless check is False: then the last iterate returns)."""
     rp, ci = _i32(rp), _i32(ci)
     vals = _f64(vals)
     b = _f64(b).reshape(-1, 3)
@@ -257,7 +258,7 @@ def pcg(rp, ci, vals, b, x0=None, tol=1e-12, max_iter=100000):
     x = np.zeros((V, 3)) if x0 is None else _f64(x0).reshape(-1, 3).copy()
     info = np.zeros(2)
     st = lib().om_pcg(V, _pi(rp), _pi(ci), _pd(vals), _pd(b), _pd(x), float(tol), int(max_iter), _pd(info))
-    if st == OM_ERR_NOT_CONVERGED:
+    if st == OM_ERR_NOT_CONVERGED and check:
         raise OracleError(f"om_pcg: not converged after {int(info[0])} iterations (rel res {info[1]:.3e})")
     return x, int(info[0]), float(info[1])
 
