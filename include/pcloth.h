@@ -371,6 +371,81 @@ PC_API pc_status pc_pcg_solve_static(int32_t V, const pc_bsr *A, const float *va
                                      const float *b, float *dv, const pc_solve_opts *opts, pc_solve_info *info,
                                      void *stream);
 
+/* ---------------------------------------------------------------- row-partitioned solve
+ * Sec. 3.1, Eq. 4-5: the system's rows are split into contiguous blocks, one per rank
+ * (one process and GPU each). Each rank holds its rows of A, of the vectors and of b;
+ * vector operations need no communication, and the product needs the "halo": the entries
+ * of the direction owned by other ranks that the rank's blocks reference. The product
+ * runs as an own-column part (started before the halo arrives) plus a halo part, so the
+ * exchange overlaps the multiplication (the paper's pipelined SpMV, with each peer's
+ * column block reduced to the entries actually referenced).
+ * Communication is the caller's: pc_comm holds two callbacks, implemented with NCCL,
+ * MPI, gloo or anything else, that every rank calls in the same order with the same
+ * sizes. Both must leave their results visible to work enqueued later on `stream`
+ * (either enqueue on it, or synchronize it, transfer and return), and return 0 on
+ * success (anything else makes the library call return PC_ERR_CUDA). */
+typedef struct {
+    void *user;
+    /* Sum n doubles over all ranks, in place. vals: DEVICE pointer. */
+    int32_t (*allreduce_sum)(void *user, double *vals, int32_t n, void *stream);
+    /* Point-to-point exchange among all ranks: to every rank j this rank sends
+     * send_bytes[j] bytes starting at send + send_off[j] and receives recv_bytes[j] bytes
+     * from rank j into recv + recv_off[j]. send, recv: DEVICE pointers; the four arrays
+     * are HOST arrays of nranks entries (the rank's own entries are 0). */
+    int32_t (*exchange)(void *user, const void *send, const int64_t *send_off, const int64_t *send_bytes,
+                        void *recv, const int64_t *recv_off, const int64_t *recv_bytes, void *stream);
+} pc_comm;
+
+typedef struct pc_dist pc_dist;
+
+/* Rows per rank: contiguous blocks with boundaries on multiples of 32 rows, balanced by
+ * block count when row_ptr (HOST, V+1 entries) is given, else by rows. row_starts: HOST
+ * int32[nranks + 1] (0 .. V). Host-only; needs no GPU. */
+PC_API pc_status pc_dist_partition(int32_t V, const int32_t *row_ptr, int32_t nranks, int32_t *row_starts);
+
+/* The halo a rank needs, from the remote columns its rows reference (HOST arrays, any
+ * order, repeats allowed): halo (HOST int32[n_remote]) receives the distinct columns in
+ * ascending order, *n_halo their count, counts (HOST int64[nranks]) how many each rank
+ * owns. PC_ERR_ARG when a column is outside [0, V) or is one of the rank's own rows.
+ * Host-only; needs no GPU. */
+PC_API pc_status pc_dist_halo(int32_t nranks, const int32_t *row_starts, int32_t rank, int64_t n_remote,
+                              const int32_t *remote, int32_t *halo, int64_t *n_halo, int64_t *counts);
+
+/* Create rank `rank` of `nranks` on the current device: it owns global rows
+ * [row_starts[rank], row_starts[rank+1]) (HOST int32[nranks+1], from pc_dist_partition or
+ * any non-decreasing split with every rank non-empty). max_blocks: capacity for the rank's
+ * blocks; max_halo: capacity for halo and send entries (0: every remote row).
+ * Allocates the rank's scratch and a second stream for the exchange. */
+PC_API pc_status pc_dist_create(pc_dist **out, int32_t rank, int32_t nranks, const int32_t *row_starts,
+                                int64_t max_blocks, int64_t max_halo);
+PC_API pc_status pc_dist_destroy(pc_dist *d);
+
+/* Plan the rank's part of a new pattern (once per step, as the pattern changes): A->row_ptr
+ * points at the rank's n_own + 1 row pointers (DEVICE; global block positions, e.g. the
+ * full system's row_ptr + row0), A->col_idx at the column indices those positions index
+ * (DEVICE, global columns), A->nnzb the total block count they index. Finds the remote
+ * columns, the halo and its owners, exchanges the requests with the peers (two calls of
+ * comm->exchange), and splits the rows into the own part (local columns) and the halo
+ * part. PC_ERR_ARG for indices out of range, PC_ERR_CAPACITY when the rank's blocks or
+ * halo exceed the capacities. Synchronizes `stream`; collective (every rank calls it). */
+PC_API pc_status pc_dist_plan(pc_dist *d, const pc_bsr *A, const pc_comm *comm, void *stream);
+
+/* Sizes of the last plan (HOST pointers, each may be NULL). */
+PC_API pc_status pc_dist_sizes(const pc_dist *d, int32_t *row0, int32_t *row1, int64_t *n_halo, int64_t *n_send,
+                               int64_t *nnzb_own, int64_t *nnzb_halo);
+
+/* Jacobi-PCG (Sec. 2.5) on the partitioned system, every rank on its rows: vals (DEVICE)
+ * is indexed like the col_idx array the plan was given (the rank reads its own range);
+ * dres (DEVICE float[n_own][9], may be NULL) the difference-form diagonal of its rows;
+ * b and dv (DEVICE float[n_own][3]) its rows of the right-hand side and of the solution
+ * (guess in, solution out). Options as pc_pcg_solve (PC_PREC_FP32 or PC_PREC_MIXED, scalar
+ * Jacobi; storage and fuse are not used). The global dot products are the all-reduced
+ * sums of the ranks' partial sums, so every rank gets the same scalars, iterations and
+ * stop decision; info (HOST, may be NULL) receives the global iteration count and the
+ * FP64 relative residual of the whole system. Collective; synchronizes `stream`. */
+PC_API pc_status pc_dist_pcg_solve(pc_dist *d, const float *vals, const float *dres, const float *b, float *dv,
+                                   const pc_solve_opts *opts, const pc_comm *comm, pc_solve_info *info, void *stream);
+
 /* One time step on device state: pattern, values (with the difference-form diagonal),
  * PCG solve, then v += dv, x += h v. Uses buffers owned by the context. dv_out (device
  * float[V][3], may be NULL) receives dv. Synchronizes `stream`. */
