@@ -12,7 +12,8 @@
 // the instance's scalars, so no separate scalar phase is needed. Phases are separated by
 // a software grid barrier whose waits are bounded; a timeout aborts the launch with
 // PC_ERR_TIMEOUT instead of hanging. Per iteration (three grid barriers):
-//   direction  p = z + beta_k p                   (fold x into x64 after a refresh)
+//   direction  p = z + beta_k p                   (fold x into x64 after a refresh, and
+//                                                  every 32 iterations)
 //   spmv       q = A p, p.q -> alpha_k            (the bulk-copy pipelined SpMV)
 //   update     x += alpha p, r -= alpha q, z = D^-1 r, r.z, r.r -> beta_k, stop tests
 // and, when some instance asks for it, FP64 residual replacement for those instances
@@ -338,7 +339,8 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 #endif
 
 // Direction p = z + beta p over the listed rows; rows of an instance that has just
-// taken an FP64 residual first fold the FP32 increment into the FP64 accumulator.
+// taken an FP64 residual, or has done another 32 iterations, also fold the FP32
+// increment into the FP64 accumulator.
 __device__ void bt_phase_direction(const BtArgs &a, const bt_list &L)
 {
     const int c = L.chunk, j0 = blockIdx.x * c, j1 = min(L.total, j0 + c);
@@ -349,7 +351,10 @@ __device__ void bt_phase_direction(const BtArgs &a, const bt_list &L)
         bt_seg_at(a, L, m, j, j1, sg);
         j = sg.je;
         const float beta = (float)__ldcg(&a.inst[sg.k].beta);
-        const bool fold = __ldcg(&a.inst[sg.k].refresh) != 0;
+        // fold after an FP64 residual, and every 32 iterations so the FP32 increment (and
+        // its rounding, which the stiff matrix amplifies) never grows large
+        const int it_k = __ldcg(&a.inst[sg.k].iter);
+        const bool fold = __ldcg(&a.inst[sg.k].refresh) != 0 || (it_k > 0 && (it_k & 31) == 0);
         for (int base = sg.ra + (int)threadIdx.x; base < sg.rb; base += BT_U * T) {
             float4 z[BT_U], p[BT_U];
 #pragma unroll

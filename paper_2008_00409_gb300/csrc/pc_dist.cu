@@ -943,6 +943,9 @@ extern "C" pc_status pc_dist_pcg_solve(pc_dist *d, const float *vals, const floa
             iter_last = d->sc_host->iter;
             continue;
         }
+        // mixed: the FP32 increment goes into the FP64 accumulator at every check (its
+        // rounding stays far below what a residual replacement measures)
+        if (mixed && launched > 0) DS_LAUNCH(d, ds_fold_kernel, g, DS_THREADS, 0, st, n, d->x, d->x64, dv, 0);
         for (int k = 0; k < o.check_every; ++k) PC_TRY(ds_iteration(d, comm, dres, st));
         launched += o.check_every;
         PC_TRY(ds_read_scalars(d, st));

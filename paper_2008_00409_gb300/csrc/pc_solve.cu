@@ -1420,6 +1420,12 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
         }
         int chunk = o.check_every;
         if (launched == 0 && chunk > 8) chunk = 8;
+        // mixed: move the FP32 increment into the FP64 accumulator at every check, so the
+        // increment never grows large. Its rounding (about 6e-8 of the increment, white
+        // noise that the stiff matrix amplifies) then stays far below what a residual
+        // replacement measures, and replacements do not undo the iterations' progress.
+        if (mixed && launched > 0)
+            PC_LAUNCH(ctx, fold_kernel, ew_grid(ctx, V), EW_THREADS, 0, st, V, x, ctx->x64);
         PC_TRY(launch_iterations(s, x, chunk));
         launched += chunk;
         PC_TRY(read_scalars(ctx, st));

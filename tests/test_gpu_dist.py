@@ -103,8 +103,10 @@ def test_row_partitioned_solve_matches_single_gpu_and_oracle(world, case):
             assert rec["pins_zero"]
             if label != "fp32":
                 assert rec["rel_res"] <= 1e-9 * 1.01
-                assert rec["err_oracle"] <= 1e-5, (label, rec)
-            else:
-                assert rec["err_oracle"] <= 1e-4, (label, rec)
+            # the difference form reaches the oracle within 1e-5; the plain form stores the
+            # diagonal blocks in FP32, whose rounding (6e-8 of the stiffness) is a visible
+            # share of the mass term they contain, and FP32 PCG stops on its recurrence
+            # residual: both are held to 1e-4, as in the single-GPU parity tests
+            assert rec["err_oracle"] <= (1e-5 if label == "mixed" else 1e-4), (label, rec)
     # all ranks made the same collective calls
     assert len({tuple(sorted(out[r]["calls"].items())) for r in range(world)}) == 1
