@@ -555,6 +555,10 @@ def run_warmstart(args):
     modes = {names[m]: summary(r) for m, r in res.items()}
     mlp = res[pc.PC_WARM_MLP]
     modes["mlp"]["guess_used"] = [int(g) for g in mlp["guess"][args.warmup:]]
+    modes["mlp"]["guess_coef"] = [list(c) for c in mlp["guess_coef"][args.warmup:]]
+    # CG energies of the guesses per timed step: zero (0), previous, learned, and the one used
+    modes["mlp"]["energies"] = [list(e[1:]) + [u] for e, u in zip(mlp["guess_energy"][args.warmup:],
+                                                                  mlp["combo_energy"][args.warmup:])]
     modes["fp32_zero"] = summary(fp32)
     out = {"metric": "steps/s at 1M tris (708^2 cloth, 2% contacts) to 1e-6 with the learned warm start",
            "value": modes["mlp"]["steps_per_s"], "unit": "steps/s", "n_gpus": 1, "steps": args.steps,

@@ -65,9 +65,12 @@ typedef int32_t pc_status;
 #define PC_WARM_ZERO 0   /* initial guess dv = 0 */
 #define PC_WARM_PREV 1   /* initial guess = previous step's dv */
 #define PC_WARM_GIVEN 2  /* initial guess = the dv buffer passed in */
-#define PC_WARM_MLP 3    /* learned guess (pc_set_warm_mlp), judged against the previous-step and zero
-                            guesses: the one with the lowest CG energy 1/2 g.A g - b.g (the smallest
-                            A-norm error) starts the solve */
+#define PC_WARM_MLP 3    /* learned guess (pc_set_warm_mlp), combined with the previous-step guess:
+                            the solve starts from the combination c_p g_prev + c_l g_learned with the
+                            lowest CG energy 1/2 g.A g - b.g (the smallest A-norm error), found by a
+                            2x2 Galerkin solve in FP64; the zero, previous and learned guesses are
+                            its special cases, so it is never worse than any of them */
+#define PC_WARM_COMBINED 4 /* pc_step_info.guess only: the solve started from that combination */
 
 typedef struct pc_ctx pc_ctx;
 
@@ -178,11 +181,14 @@ typedef struct {
 typedef struct {
     int64_t nnzb;
     pc_solve_info solve;
-    int32_t guess;         /* initial guess used: PC_WARM_ZERO, PC_WARM_PREV or PC_WARM_MLP */
+    int32_t guess;         /* initial guess used: PC_WARM_ZERO, PC_WARM_PREV, PC_WARM_MLP or
+                              PC_WARM_COMBINED */
     int32_t pad;
     double guess_res[3];   /* PC_WARM_MLP: |b - A g| / |b| of the zero, previous and learned
                               guesses (FP64); -1 when not evaluated */
     double guess_energy[3]; /* PC_WARM_MLP: 1/2 g.A g - b.g of the same guesses (0 for zero) */
+    double guess_coef[2];  /* PC_WARM_MLP: the combination's coefficients (c_p, c_l) */
+    double combo_energy;   /* PC_WARM_MLP: the CG energy of the guess the solve started from */
 } pc_step_info;
 
 /* Text for a status code (static storage). */
@@ -470,9 +476,11 @@ PC_API pc_status pc_step_host(pc_ctx *ctx, float *x_host, float *v_host, int32_t
  * The paper has no learned component; this is an extension built on its integrator. A
  * per-vertex MLP predicts the initial guess of the Eq. 3 solve:
  *   features (PC_MLP_IN = 12 per vertex): v_i; the previous step's dv_i; the internal
- *     force per unit mass at the first-order end-of-step position,
- *     (b_i / h - m_i g) / m_i with b the assembled right-hand side; the mean of the
- *     previous dv over the vertex's mesh-edge neighbours;
+ *     force per unit mass at the first-order end-of-step position times the vertex's mean
+ *     rest edge length l_i, l_i (b_i / h - m_i g) / m_i with b the assembled right-hand
+ *     side (the length scale makes the membrane's share independent of the grid spacing,
+ *     so a network trained on one resolution sees the same inputs on another); the mean
+ *     of the previous dv over the vertex's mesh-edge neighbours;
  *   network: 12 -> 64 -> 64 -> 3 with ReLU, on inputs standardised by stats
  *     (mu_x[12], sd_x[12], mu_y[3], sd_y[3]); it predicts the change of dv from the
  *     previous step: dv0 = dv_prev + sd_y * y + mu_y;
@@ -496,7 +504,8 @@ typedef struct {
 } pc_adam_opts;
 
 /* The 12 raw features of every vertex of a cloth state: v, dv_prev (float[V][3]), b the
- * right-hand side assembled for this state (pc_assemble_values), h the time step.
+ * right-hand side assembled for this state (pc_assemble_values), h the time step (the
+ * rest edge lengths come from the context).
  * feat: float[V][12]. Does not synchronize. */
 PC_API pc_status pc_mlp_features(pc_ctx *ctx, const float *v, const float *dv_prev, const float *b, float h,
                                  float *feat, void *stream);

@@ -9,9 +9,11 @@ the initial guess of the Eq. 3 solve from per-vertex quantities available before
 solve:
 
 * features (12 per vertex): the velocity v_i; the previous step's solution dv_prev_i;
-  the internal force per unit mass at the first-order end-of-step position,
-  (b_i / h - m_i g) / m_i, where b = h (f(x_t) - h K(x_t) v_t) + h M g is the assembled
-  right-hand side (so b_i / h - m_i g = f_int(x_t) - h (K v_t)_i); and the mean of
+  the internal force per unit mass at the first-order end-of-step position times the
+  vertex's mean rest edge length l_i, l_i (b_i / h - m_i g) / m_i, where
+  b = h (f(x_t) - h K(x_t) v_t) + h M g is the assembled right-hand side (so
+  b_i / h - m_i g = f_int(x_t) - h (K v_t)_i; the length makes the membrane force's share
+  independent of the grid spacing: force ~ stress x edge, mass ~ edge^2); and the mean of
   dv_prev over the vertex's edge neighbours (its one-ring).
 * network: 12 -> 64 -> 64 -> 3, ReLU after the two hidden layers; inputs and targets
   are standardised with per-component means and standard deviations from the
@@ -90,7 +92,21 @@ def ring_mean(V: int, edges, q) -> np.ndarray:
     return s / np.maximum(deg, 1.0)[:, None]
 
 
-def features(v, dv_prev, b, mass, h: float, gravity, edges) -> np.ndarray:
+def rest_lengths(rest, edges) -> np.ndarray:
+    """Mean rest length of each vertex's edges (zero for an isolated vertex)."""
+    X = np.asarray(rest, dtype=np.float64).reshape(-1, 3)
+    e = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    L = np.linalg.norm(X[e[:, 1]] - X[e[:, 0]], axis=1)
+    s = np.zeros(X.shape[0])
+    deg = np.zeros(X.shape[0])
+    np.add.at(s, e[:, 0], L)
+    np.add.at(s, e[:, 1], L)
+    np.add.at(deg, e[:, 0], 1.0)
+    np.add.at(deg, e[:, 1], 1.0)
+    return s / np.maximum(deg, 1.0)
+
+
+def features(v, dv_prev, b, mass, h: float, gravity, edges, rest) -> np.ndarray:
     """The 12 raw features per vertex (see the module docstring)."""
     v = np.asarray(v, dtype=np.float64).reshape(-1, 3)
     V = v.shape[0]
@@ -99,7 +115,8 @@ def features(v, dv_prev, b, mass, h: float, gravity, edges) -> np.ndarray:
     m = np.asarray(mass, dtype=np.float64).reshape(V)
     g = np.asarray(gravity, dtype=np.float64).reshape(3)
     f_int = b / h - m[:, None] * g[None, :]
-    return np.concatenate([v, dvp, f_int / m[:, None], ring_mean(V, edges, dvp)], axis=1)
+    ell = rest_lengths(rest, edges)
+    return np.concatenate([v, dvp, ell[:, None] * f_int / m[:, None], ring_mean(V, edges, dvp)], axis=1)
 
 
 # --------------------------------------------------------------------------- statistics

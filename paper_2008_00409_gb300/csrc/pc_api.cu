@@ -68,9 +68,9 @@ extern "C" pc_status pc_step(pc_ctx *ctx, float *x, float *v, const pc_contacts 
     // A_dv holds the previous step's dv (zeros before the first step); choose the guess
     if (!ctx->has_prev_dv) PC_CUDA_TRY(cudaMemsetAsync(ctx->A_dv, 0, sizeof(float) * 3 * (size_t)ctx->V, st));
     int32_t guess = PC_WARM_ZERO;
-    double guess_res[3], guess_energy[3];
+    double guess_res[3], guess_energy[3], guess_coef[2] = {0.0, 0.0}, combo_energy = 0.0;
     PC_TRY(pc_warm_guess(ctx, &A, v, opts->h, opts->warm_start, opts->feat_out, &guess, guess_res, guess_energy,
-                         st));
+                         guess_coef, &combo_energy, st));
     pc_solve_info si{};
     pc_status s = pc_pcg_solve(ctx, &A, ctx->A_vals, ctx->A_dres, ctx->A_b, ctx->A_dv, &opts->solve, &si, stream);
     if (info) {
@@ -82,6 +82,9 @@ extern "C" pc_status pc_step(pc_ctx *ctx, float *x, float *v, const pc_contacts 
             info->guess_res[k] = guess_res[k];
             info->guess_energy[k] = guess_energy[k];
         }
+        info->guess_coef[0] = guess_coef[0];
+        info->guess_coef[1] = guess_coef[1];
+        info->combo_energy = combo_energy;
     }
     if (s != PC_OK && s != PC_ERR_NOT_CONVERGED) return s;
     ctx->has_prev_dv = 1;

@@ -107,6 +107,7 @@ struct pc_ctx {
     int64_t enn = 0;
     int32_t *erp = nullptr;        // [V+1] edge one-rings (CSR)
     int32_t *ecol = nullptr;       // [enn] edge neighbours, sorted per vertex
+    float *rest_len = nullptr;     // [V] mean rest length of the vertex's mesh edges
 
     // per-step contact data
     uint64_t *dkeys = nullptr;     // [6 * maxP] dynamic pattern keys (sorted)
@@ -272,8 +273,13 @@ pc_status pc_batched_alloc(pc_ctx *ctx);
 void pc_batched_free(pc_ctx *ctx);
 pc_status pc_guess_eval(pc_ctx *c, const pc_bsr *A, const float *vals, const float *dres, const float *b,
                         const float *x, double *rr, double *bb, double *energy, cudaStream_t st);
+pc_status pc_guess_cross(pc_ctx *c, const pc_bsr *A, const float *vals, const float *dres, const float *x,
+                         const float *y, double *xay, cudaStream_t st);
+pc_status pc_guess_combine(pc_ctx *c, float *out, const float *x, const float *y, double a, double b,
+                           cudaStream_t st);
 pc_status pc_warm_guess(pc_ctx *c, const pc_bsr *A, const float *v, float h, int32_t mode, float *feat_out,
-                        int32_t *guess, double *guess_res, double *guess_energy, cudaStream_t st);
+                        int32_t *guess, double *guess_res, double *guess_energy, double *guess_coef,
+                        double *combo_energy, cudaStream_t st);
 void pc_mlp_ctx_free(pc_ctx *c);
 
 inline int pc_bits_for(int64_t n)

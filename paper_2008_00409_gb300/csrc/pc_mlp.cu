@@ -692,14 +692,16 @@ __global__ void mlp_stats_final_kernel(int nparts, int64_t n, const double *part
 // ------------------------------------------------------------------------- features
 
 __global__ void mlp_features_kernel(int V, const float *v, const float *dv_prev, const float *b, const float *mass,
-                                    float inv_h, float g0, float g1, float g2, const int32_t *erp,
-                                    const int32_t *ecol, float *feat)
+                                    const float *rest_len, float inv_h, float g0, float g1, float g2,
+                                    const int32_t *erp, const int32_t *ecol, float *feat)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= V) return;
     float *f = feat + (int64_t)MLP_IN * i;
     const float m = mass[i];
-    const float inv_m = m > 0.f ? 1.f / m : 0.f;
+    // force per unit mass times the vertex's rest edge length: the membrane's share does
+    // not change with the grid spacing (force ~ stress x edge, mass ~ edge^2)
+    const float inv_m = m > 0.f ? rest_len[i] / m : 0.f;
     const float g[3] = {g0, g1, g2};
     float ring[3] = {0.f, 0.f, 0.f};
     const int e0 = erp[i], e1 = erp[i + 1];
@@ -906,8 +908,8 @@ extern "C" pc_status pc_mlp_features(pc_ctx *ctx, const float *v, const float *d
 {
     if (!ctx || !v || !dv_prev || !b || !feat || !(h > 0.f)) return PC_ERR_ARG;
     PC_LAUNCH(ctx, mlp_features_kernel, pc_blocks(ctx->V, 256), 256, 0, (cudaStream_t)stream, ctx->V, v, dv_prev, b,
-              ctx->mass, 1.f / h, ctx->mat.gravity[0], ctx->mat.gravity[1], ctx->mat.gravity[2], ctx->erp, ctx->ecol,
-              feat);
+              ctx->mass, ctx->rest_len, 1.f / h, ctx->mat.gravity[0], ctx->mat.gravity[1], ctx->mat.gravity[2],
+              ctx->erp, ctx->ecol, feat);
     return PC_OK;
 }
 
@@ -932,19 +934,28 @@ void pc_mlp_ctx_free(pc_ctx *c)
 }
 
 // The step's initial guess (ctx->A_dv holds the previous step's dv, or zeros). Features
-// are written to feat_out when given. PC_WARM_MLP evaluates the zero, previous and
-// learned guesses g in FP64 and keeps the one with the lowest CG energy
-// 1/2 g.A g - b.g, which differs from the energy of the solution by half the squared
-// A-norm of the guess's error: the error measure that CG's convergence is bounded by.
-// Their relative residuals |b - A g| / |b| are reported too.
+// are written to feat_out when given. PC_WARM_MLP combines the previous-step guess g_p
+// and the learned guess g_l: the combination c_p g_p + c_l g_l with the lowest CG energy
+// phi(g) = 1/2 g.A g - b.g (phi(g) - phi(dv*) is half the squared A-norm of the guess's
+// error, the measure CG's convergence is bounded by) solves the 2x2 Galerkin system
+//   [g_p.A g_p  g_p.A g_l] [c_p]   [b.g_p]
+//   [g_l.A g_p  g_l.A g_l] [c_l] = [b.g_l],
+// formed in FP64 from the matrix the solve uses. The zero, previous and learned guesses
+// are points of the same plane, so the optimum is never worse than any of them; the
+// energy of the FP32 combination actually formed is evaluated again and compared with
+// theirs, and the best of the four starts the solve. Residuals |b - A g| / |b| of the
+// single guesses are reported too.
 pc_status pc_warm_guess(pc_ctx *c, const pc_bsr *A, const float *v, float h, int32_t mode, float *feat_out,
-                        int32_t *guess, double *guess_res, double *guess_energy, cudaStream_t st)
+                        int32_t *guess, double *guess_res, double *guess_energy, double *guess_coef,
+                        double *combo_energy, cudaStream_t st)
 {
     const size_t vb = sizeof(float) * 3 * (size_t)c->V;
     for (int k = 0; k < 3; ++k) {
         guess_res[k] = -1.0;
         guess_energy[k] = 0.0;
     }
+    guess_coef[0] = guess_coef[1] = 0.0;
+    *combo_energy = 0.0;
     float *feat = feat_out ? feat_out : c->mlp_feat;
     if (mode == PC_WARM_MLP && (!c->mlp_params || !c->mlp_feat)) return PC_ERR_ARG;
     if (feat) PC_TRY(pc_mlp_features(c, v, c->A_dv, c->A_b, h, feat, st));
@@ -960,16 +971,54 @@ pc_status pc_warm_guess(pc_ctx *c, const pc_bsr *A, const float *v, float h, int
     PC_TRY(pc_mlp_infer(c->V, c->mlp_params, c->mlp_stats, feat, c->A_dv, c->pinned, c->mlp_dv, st));
     double rr_prev = 0.0, rr_mlp = 0.0, bb = 0.0, e_prev = 0.0, e_mlp = 0.0;
     PC_TRY(pc_guess_eval(c, A, c->A_vals, c->A_dres, c->A_b, c->A_dv, &rr_prev, &bb, &e_prev, st));
+    const double gAg_p = c->sc_host->pq, bg_p = c->sc_host->rz;
     PC_TRY(pc_guess_eval(c, A, c->A_vals, c->A_dres, c->A_b, c->mlp_dv, &rr_mlp, &bb, &e_mlp, st));
+    const double gAg_l = c->sc_host->pq, bg_l = c->sc_host->rz;
     const double nb = sqrt(bb);
     guess_res[0] = bb > 0 ? 1.0 : 0.0;
     guess_res[1] = bb > 0 ? sqrt(rr_prev) / nb : 0.0;
     guess_res[2] = bb > 0 ? sqrt(rr_mlp) / nb : 0.0;
     guess_energy[1] = e_prev;
     guess_energy[2] = e_mlp;
+    // the best single guess, the fallback
     int best = 0;
-    if (c->has_prev_dv && e_prev < guess_energy[best]) best = 1;
-    if (std::isfinite(e_mlp) && e_mlp < guess_energy[best]) best = 2;
+    double e_best = 0.0;
+    if (c->has_prev_dv && e_prev < e_best) { best = 1; e_best = e_prev; }
+    if (std::isfinite(e_mlp) && e_mlp < e_best) { best = 2; e_best = e_mlp; }
+    // the Galerkin combination (one-dimensional on the learned guess before the first step)
+    double cp = 0.0, cl = 0.0;
+    bool combo = false;
+    if (std::isfinite(e_mlp) && gAg_l > 0.0) {
+        if (c->has_prev_dv && gAg_p > 0.0) {
+            double g_pl = 0.0;
+            PC_TRY(pc_guess_cross(c, A, c->A_vals, c->A_dres, c->A_dv, c->mlp_dv, &g_pl, st));
+            const double det = gAg_p * gAg_l - g_pl * g_pl;
+            if (std::isfinite(g_pl) && det > 1e-12 * gAg_p * gAg_l) {
+                cp = (bg_p * gAg_l - bg_l * g_pl) / det;
+                cl = (bg_l * gAg_p - bg_p * g_pl) / det;
+                combo = true;
+            }
+        } else {
+            cl = bg_l / gAg_l;
+            combo = true;
+        }
+    }
+    if (combo && std::isfinite(cp) && std::isfinite(cl)) {
+        // form it in scratch (rhs32 is free until the solve) and measure what was formed
+        float *g = c->rhs32;
+        PC_TRY(pc_guess_combine(c, g, c->A_dv, c->mlp_dv, c->has_prev_dv ? cp : 0.0, cl, st));
+        double rr_c = 0.0, e_c = 0.0;
+        PC_TRY(pc_guess_eval(c, A, c->A_vals, c->A_dres, c->A_b, g, &rr_c, &bb, &e_c, st));
+        if (std::isfinite(e_c) && e_c <= e_best) {
+            *guess = PC_WARM_COMBINED;
+            guess_coef[0] = c->has_prev_dv ? cp : 0.0;
+            guess_coef[1] = cl;
+            *combo_energy = e_c;
+            PC_CUDA_TRY(cudaMemcpyAsync(c->A_dv, g, vb, cudaMemcpyDeviceToDevice, st));
+            return PC_OK;
+        }
+    }
+    *combo_energy = e_best;
     if (best == 0) {
         *guess = PC_WARM_ZERO;
         PC_CUDA_TRY(cudaMemsetAsync(c->A_dv, 0, vb, st));

@@ -268,6 +268,26 @@ __global__ void rowptr_from_keys_kernel(int V, const uint64_t *ukeys, int64_t n,
     rp[r] = (int32_t)pc_lower_bound_u64(ukeys, n, (uint64_t)r * (uint64_t)V);
 }
 
+// Mean rest length of each vertex's mesh edges (0 for an isolated vertex), in FP64.
+__global__ void rest_len_kernel(int V, const int32_t *__restrict__ erp, const int32_t *__restrict__ ecol,
+                                const float *__restrict__ rest, float *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= V) return;
+    double s = 0.0;
+    const int e0 = erp[i], e1 = erp[i + 1];
+    for (int e = e0; e < e1; ++e) {
+        const int j = ecol[e];
+        double d2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double d = (double)rest[3ll * j + a] - (double)rest[3ll * i + a];
+            d2 += d * d;
+        }
+        s += sqrt(d2);
+    }
+    out[i] = e1 > e0 ? (float)(s / (double)(e1 - e0)) : 0.f;
+}
+
 // ------------------------------------------------------------------------- context
 
 static void free_ctx(pc_ctx *c)
@@ -276,7 +296,7 @@ static void free_ctx(pc_ctx *c)
     pc_batched_free(c);
     pc_mlp_ctx_free(c);
     void *ptrs[] = {c->tri, c->rest, c->tri_dmi, c->tri_area, c->tri_rgram, c->mass, c->pinned, c->hinge, c->hcoef,
-                    c->hrest, c->srp, c->scol, c->erp, c->ecol, c->vinc_ptr, c->vinc, c->dkeys, c->dnew, c->dflag, c->dscan, c->ckeys,
+                    c->hrest, c->srp, c->scol, c->erp, c->ecol, c->rest_len, c->vinc_ptr, c->vinc, c->dkeys, c->dnew, c->dflag, c->dscan, c->ckeys,
                     c->cinc, c->cinc_ptr, c->tri_buf, c->hinge_buf, c->cont_buf, c->r, c->z, c->p0, c->p1, c->q,
                     c->dinv, c->dtmp, c->rhs32, c->x64, c->r64, c->partials, c->sc, c->A_rp, c->A_ci, c->A_vals, c->A_dres,
                     c->A_b, c->A_dv, c->h_state, c->h_pairs, c->h_w, c->sort.keys_alt, c->sort.vals_alt, c->sort.hist,
@@ -446,6 +466,10 @@ static pc_status create_impl(pc_ctx *c, const int32_t *tris, const float *rest, 
             c->launches++;
         }
         rowptr_from_keys_kernel<<<pc_blocks(V + 1ll, 256), 256, 0, st>>>(V, ukeys, c->enn, c->erp);
+        c->launches++;
+        // each vertex's mean rest edge length (the learned warm start's length scale)
+        if ((s = dalloc(&c->rest_len, V)) != PC_OK) break;
+        rest_len_kernel<<<pc_blocks(V, 256), 256, 0, st>>>(V, c->erp, c->ecol, c->rest, c->rest_len);
         c->launches++;
         if ((s = pc_read_errors(c, st, &bits)) != PC_OK) break;
         if (bits) { s = errors_to_status(bits); break; }

@@ -1528,6 +1528,55 @@ pc_status pc_guess_eval(pc_ctx *c, const pc_bsr *A, const float *vals, const flo
     return PC_OK;
 }
 
+// The FP64 cross term x.(A y) of two FP32 vectors (A symmetric, so it equals y.(A x)),
+// left in the scalars' pq slot.
+template <bool DIFF>
+__global__ void __launch_bounds__(EW_THREADS) guess_cross_kernel(int V, const int32_t *__restrict__ rp,
+                                                                 const int32_t *__restrict__ ci,
+                                                                 const float *__restrict__ vals,
+                                                                 const float *__restrict__ dres,
+                                                                 const float *__restrict__ x,
+                                                                 const float *__restrict__ y, double *partials,
+                                                                 pc_scalars *sc)
+{
+    double xay = 0.0;
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
+        double acc[3];
+        row_product64<float, DIFF>(row, rp, ci, vals, dres, y, acc);
+        for (int a2 = 0; a2 < 3; ++a2) xay += (double)x[3ll * row + a2] * acc[a2];
+    }
+    double v[1] = {xay};
+    if (last_block_reduce(v, 1, partials, &sc->counter) && threadIdx.x == 0) sc->pq = v[0];
+}
+
+pc_status pc_guess_cross(pc_ctx *c, const pc_bsr *A, const float *vals, const float *dres, const float *x,
+                         const float *y, double *xay, cudaStream_t st)
+{
+    const int V = c->V;
+    if (dres) PC_LAUNCH(c, guess_cross_kernel<true>, ew_grid(c, V), EW_THREADS, 0, st, V, A->row_ptr, A->col_idx,
+                        vals, dres, x, y, c->partials, c->sc);
+    else PC_LAUNCH(c, guess_cross_kernel<false>, ew_grid(c, V), EW_THREADS, 0, st, V, A->row_ptr, A->col_idx, vals,
+                   dres, x, y, c->partials, c->sc);
+    PC_TRY(read_scalars(c, st));
+    *xay = c->sc_host->pq;
+    return PC_OK;
+}
+
+// out = a x + b y (FP32 vectors of 3V entries; a and b rounded from the FP64 coefficients)
+__global__ void combine_kernel(int64_t n, float *out, const float *x, const float *y, float a, float b)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = fmaf(a, x[i], b * y[i]);
+}
+
+pc_status pc_guess_combine(pc_ctx *c, float *out, const float *x, const float *y, double a, double b,
+                           cudaStream_t st)
+{
+    const int64_t n = 3ll * c->V;
+    PC_LAUNCH(c, combine_kernel, ew_grid(c, n), EW_THREADS, 0, st, n, out, x, y, (float)a, (float)b);
+    return PC_OK;
+}
+
 pc_status pc_update_state(pc_ctx *c, float *x, float *v, const float *dv, float h, cudaStream_t st)
 {
     const int64_t n = 3ll * c->V;

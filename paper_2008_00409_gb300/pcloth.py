@@ -21,7 +21,7 @@ PC_OK, PC_ERR_ARG, PC_ERR_CAPACITY, PC_ERR_NOT_CONVERGED, PC_ERR_NONFINITE, PC_E
 PC_PREC_FP32, PC_PREC_MIXED = 0, 1
 PC_PRECOND_JACOBI, PC_PRECOND_BLOCK = 0, 1
 PC_STORAGE_SYM, PC_STORAGE_FULL, PC_STORAGE_SELL, PC_STORAGE_OFFDIAG = 0, 1, 2, 3
-PC_WARM_ZERO, PC_WARM_PREV, PC_WARM_GIVEN, PC_WARM_MLP = 0, 1, 2, 3
+PC_WARM_ZERO, PC_WARM_PREV, PC_WARM_GIVEN, PC_WARM_MLP, PC_WARM_COMBINED = 0, 1, 2, 3, 4
 PC_MLP_IN, PC_MLP_HIDDEN, PC_MLP_OUT, PC_MLP_NPARAMS, PC_MLP_NSTATS = 12, 64, 3, 5187, 30
 
 
@@ -58,7 +58,8 @@ class pc_step_opts(ctypes.Structure):
 
 class pc_step_info(ctypes.Structure):
     _fields_ = [("nnzb", c_int64), ("solve", pc_solve_info), ("guess", c_int32), ("pad", c_int32),
-                ("guess_res", c_double * 3), ("guess_energy", c_double * 3)]
+                ("guess_res", c_double * 3), ("guess_energy", c_double * 3), ("guess_coef", c_double * 2),
+                ("combo_energy", c_double)]
 
 
 class pc_adam_opts(ctypes.Structure):

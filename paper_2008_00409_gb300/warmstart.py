@@ -101,7 +101,8 @@ def evaluate(wl, params, stats, steps: int, tol: float = 1e-6, precision: int = 
             contacts = [cl.contacts_device(t) for t in range(steps)]
         if mode == pc.PC_WARM_MLP:
             pc.pc_set_warm_mlp(cl.ctx, params, stats)
-        rec = {"iters": [], "guess": [], "guess_res": [], "guess_energy": [], "rel_res": [], "sec": []}
+        rec = {"iters": [], "guess": [], "guess_res": [], "guess_energy": [], "guess_coef": [], "combo_energy": [],
+               "rel_res": [], "sec": []}
         for t in range(steps):
             torch.cuda.synchronize(device)
             t0 = time.perf_counter()
@@ -113,6 +114,8 @@ def evaluate(wl, params, stats, steps: int, tol: float = 1e-6, precision: int = 
             rec["guess"].append(info.guess)
             rec["guess_res"].append(list(info.guess_res))
             rec["guess_energy"].append(list(info.guess_energy))
+            rec["guess_coef"].append(list(info.guess_coef))
+            rec["combo_energy"].append(info.combo_energy)
         if mode == pc.PC_WARM_MLP:
             pc.pc_set_warm_mlp(cl.ctx, None, None)
         cl.close()

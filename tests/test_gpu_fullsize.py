@@ -121,7 +121,7 @@ def test_full_size_learned_guess(pc):
     sample = rng.choice(wl.V, 20000, replace=False)
     g = wl.material.as_array()[5:8]
     want = om.features(v, dvp, s["b"].cpu().numpy().astype(np.float64), mesh.mass, wl.h, g,
-                       om.edges_of(wl.tris))[sample]
+                       om.edges_of(wl.tris), wl.rest)[sample]
     got = feat.cpu().numpy().astype(np.float64)[sample]
     assert np.all(np.abs(got - want) <= 2e-6 * np.abs(want).max(axis=0) + 1e-12)
     params = om.init_params(4).astype(np.float32)

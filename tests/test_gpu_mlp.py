@@ -61,7 +61,7 @@ def test_features_match_oracle(pc):
     pc.pc_mlp_features(cl.ctx, vt, dvpt, s["b"], wl.h, feat)
     mesh = oracle.Mesh.from_workload(wl)
     g = wl.material.as_array()[5:8]
-    want = om.features(v, dvp, _np(s["b"]), mesh.mass, wl.h, g, om.edges_of(wl.tris))
+    want = om.features(v, dvp, _np(s["b"]), mesh.mass, wl.h, g, om.edges_of(wl.tris), wl.rest)
     got = _np(feat)
     scale = np.abs(want).max(axis=0)
     assert np.all(np.abs(got - want) <= 2e-6 * scale + 1e-12)
@@ -170,11 +170,19 @@ def test_warm_start_steps(pc):
     for mode, rec in res.items():
         assert max(rec["rel_res"]) <= 1e-7, mode
     en = np.array(mlp["guess_energy"])
-    # the chosen guess is the one with the lowest CG energy (the previous guess is not a
-    # candidate on the first step)
+    # the solve starts from the A-norm-optimal combination of the previous and learned
+    # guesses: its CG energy is at most that of the zero, previous and learned guesses (the
+    # previous guess is not a candidate on the first step)
     for k, used in enumerate(mlp["guess"]):
         cand = en[k] if k > 0 else np.array([en[k, 0], np.inf, en[k, 2]])
-        assert used == [pc.PC_WARM_ZERO, pc.PC_WARM_PREV, pc.PC_WARM_MLP][int(np.argmin(cand))]
+        e_used = mlp["combo_energy"][k]
+        assert e_used <= cand.min() + 1e-9 * np.abs(cand[np.isfinite(cand)]).max(), (k, e_used, cand)
+        assert used in (pc.PC_WARM_COMBINED, pc.PC_WARM_ZERO, pc.PC_WARM_PREV, pc.PC_WARM_MLP)
+        if used == pc.PC_WARM_COMBINED:
+            assert np.all(np.isfinite(mlp["guess_coef"][k]))
+            if k == 0:
+                assert mlp["guess_coef"][k][0] == 0.0
+    assert mlp["guess"].count(pc.PC_WARM_COMBINED) >= len(mlp["guess"]) // 2
     # the trained network's guess has a smaller A-norm error than the zero guess
     assert np.mean(en[2:, 2] < 0.0) >= 0.8
     # and the learned warm start needs fewer PCG iterations than the zero guess in total

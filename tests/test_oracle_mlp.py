@@ -117,13 +117,28 @@ def test_force_feature_is_the_linearised_internal_force():
     h = wl.h
     _, _, _, b = om.assemble(x, v, h=h)
     g = wl.material.as_array()[5:8]
-    F = mlp.features(v, np.zeros_like(v), b, om.mass, h, g, mlp.edges_of(wl.tris))
+    F = mlp.features(v, np.zeros_like(v), b, om.mass, h, g, mlp.edges_of(wl.tris), wl.rest)
     f_int = om.forces(x) - om.mass[:, None] * g                    # element forces at x_t
     hKv = (om.matfree_apply(x, v, h=h) - om.mass[:, None] * v) / h  # h K v (A v = M v + h^2 K v)
     free = ~om.pinned
-    want = (f_int - hKv)[free] / om.mass[free, None]
+    ell = mlp.rest_lengths(wl.rest, mlp.edges_of(wl.tris))
+    want = ell[free, None] * (f_int - hKv)[free] / om.mass[free, None]
     assert np.allclose(F[free, 6:9], want, rtol=1e-9, atol=1e-12)
     assert np.array_equal(F[:, 0:3], v)
+
+
+def test_rest_length_scale_closed_form():
+    # a regular n x n grid of spacing s split along one diagonal: an interior vertex has
+    # four axis neighbours at s and two diagonal ones at s sqrt(2)
+    for n in (5, 9):
+        wl = wk.square_cloth(n, seed=3, z_jitter=0.0)
+        s_ = 1.0 / (n - 1)
+        ell = mlp.rest_lengths(wl.rest, mlp.edges_of(wl.tris))
+        inner = np.array([i * n + j for i in range(1, n - 1) for j in range(1, n - 1)])
+        assert np.allclose(ell[inner], s_ * (4 + 2 * np.sqrt(2)) / 6, rtol=1e-12)
+        # a corner on the diagonal's ends has two axis edges and one diagonal, the others two axis edges
+        corners = ell[[0, n - 1, n * (n - 1), n * n - 1]]
+        assert set(np.round(corners / s_, 9)) <= {1.0, round((2 + np.sqrt(2)) / 3, 9)}
 
 
 def test_predict_of_a_silent_network():
