@@ -300,8 +300,8 @@ PC_API pc_status pc_get_solution64(pc_ctx *ctx, double *dv64, void *stream);
  * PC_PREC_MIXED (refresh, refresh_every); finished instances drop out while the others
  * continue. The launch is cooperative (all CTAs co-resident) with bounded grid-wide
  * waits (PC_ERR_TIMEOUT instead of a hang). On the first call for a matrix shape an
- * autotuner times short solves for each schedule (SpMV entry order x 1..4 CTAs per SM)
- * and keeps the fastest
+ * autotuner times short solves for each tile and schedule (the SpMV phase's stage width
+ * x its entry order x 1..4 CTAs per SM) and keeps the fastest
  * (pc_batched_config reports the choice). info: host array of n_inst results, may be
  * NULL. Returns the first non-OK instance status. Synchronizes `stream`.
  * (The paper solves one garment system per step; batching is this library's extension.) */
@@ -309,11 +309,14 @@ PC_API pc_status pc_pcg_solve_batched(pc_ctx *ctx, const pc_bsr *A, const float 
                                       const float *b, float *dv, int32_t n_inst, const int32_t *inst_rows,
                                       const pc_solve_opts *opts, pc_solve_info *info, void *stream);
 
-/* Schedule chosen by the batched autotuner: CTAs per SM (0 if not tuned yet) and the
- * SpMV entry order (0: strided, CTA b takes entries b, b+G, ...; 1: contiguous chunks),
- * and the timings (ms) of the candidates, tune_ms[4 * order + (CTAs per SM - 1)] (0 where
- * not tried). Host pointers, may be NULL. */
-PC_API pc_status pc_batched_config(pc_ctx *ctx, int32_t *blocks_per_sm, int32_t *spmv_order, float *tune_ms);
+/* Tile and schedule chosen by the batched autotuner: CTAs per SM (0 if not tuned yet),
+ * the SpMV entry order (0: strided, CTA b takes entries b, b+G, ...; 1: contiguous
+ * chunks), the SpMV phase's stage width in blocks per row of a 32-row tile (14 or 18),
+ * and the timings (ms) of every candidate,
+ * tune_ms[8 * (width == 18) + 4 * order + (CTAs per SM - 1)] (0 where not tried: a shape
+ * that does not fit the SM). Host pointers, may be NULL. */
+PC_API pc_status pc_batched_config(pc_ctx *ctx, int32_t *blocks_per_sm, int32_t *spmv_order, int32_t *stage_blocks,
+                                   float *tune_ms);
 
 /* Cycle budget of each grid-barrier wait in the persistent batched solver and in the
  * fused PCG update of pc_pcg_solve / pc_step (software barriers spinning on a generation

@@ -452,7 +452,7 @@ __device__ __forceinline__ bt_sched bt_spmv_sched(const BtArgs &a, const bt_list
 // slots are entries p0 .. p0 + min(G, p1 - p0) - 1; chunked order: max(b * chunk, p0)
 // for the CTAs b whose chunk meets [p0, p1). `kbase` continues the mbarrier phase count
 // across calls.
-template <bool DIFF>
+template <bool DIFF, int CAPR>
 __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *smem_raw, uint64_t *full_bar,
                               uint64_t *empty_bar, int (*stage_info)[4], int kbase, int par)
 {
@@ -481,8 +481,8 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
                     break;
                 }
                 const int b0 = a.srp[ra], b1 = a.srp[rb];
-                unsigned char *base = smem_raw + s * SP_STAGE_BYTES;
-                if (b1 - b0 <= SP_CAP) {
+                unsigned char *base = smem_raw + s * SpShape<CAPR>::stage_bytes;
+                if (b1 - b0 <= SpShape<CAPR>::cap) {
                     const int64_t f0 = 9ll * b0, al0 = f0 & ~3ll, al1 = (9ll * b1 + 3) & ~3ll;
                     const int c0 = b0 & ~3, c1 = (b1 + 3) & ~3;
                     const uint32_t vbytes = (uint32_t)((al1 - al0) * 4), cbytes = (uint32_t)((c1 - c0) * 4);
@@ -492,7 +492,7 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
                     stage_info[s][3] = 1;
                     mbar_arrive_expect_tx(&full_bar[s], vbytes + cbytes);
                     bulk_g2s(base, a.svals + al0, vbytes, &full_bar[s]);
-                    bulk_g2s(base + SP_VAL_BYTES, a.sci + c0, cbytes, &full_bar[s]);
+                    bulk_g2s(base + SpShape<CAPR>::val_bytes, a.sci + c0, cbytes, &full_bar[s]);
                 } else {
                     stage_info[s][0] = b0;
                     stage_info[s][1] = 0;
@@ -567,9 +567,10 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
             } else {
                 const int b0 = stage_info[s][0], vo = stage_info[s][1], co = stage_info[s][2];
                 const bool staged = stage_info[s][3] != 0;
-                const float *s_vals = reinterpret_cast<const float *>(smem_raw + s * SP_STAGE_BYTES) + vo;
+                const float *s_vals = reinterpret_cast<const float *>(smem_raw + s * SpShape<CAPR>::stage_bytes) + vo;
                 const int32_t *s_cols =
-                    reinterpret_cast<const int32_t *>(smem_raw + s * SP_STAGE_BYTES + SP_VAL_BYTES) + co;
+                    reinterpret_cast<const int32_t *>(smem_raw + s * SpShape<CAPR>::stage_bytes +
+                                                      SpShape<CAPR>::val_bytes) + co;
                 float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
                 // up to four blocks per thread in flight; p is not written in this phase, so
                 // the gathers may hit L1 (the grid barrier's acquire orders them after the
@@ -822,7 +823,7 @@ __device__ void bt_phase_residual(const BtArgs &a, const bt_list &L, bool start)
 
 // ------------------------------------------------------------------------- the persistent kernel
 
-template <bool DIFF>
+template <bool DIFF, int CAPR>
 __global__ void __launch_bounds__(SP_THREADS, BT_MIN_CTAS) batched_pcg_kernel(BtArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -860,7 +861,7 @@ __global__ void __launch_bounds__(SP_THREADS, BT_MIN_CTAS) batched_pcg_kernel(Bt
 
         bt_phase_direction(a, L);
         if (!bt_grid_sync(a.g, a.bar_wait)) return;
-        bt_phase_spmv<DIFF>(a, L, smem_raw, full_bar, empty_bar, stage_info, kbase, par);
+        bt_phase_spmv<DIFF, CAPR>(a, L, smem_raw, full_bar, empty_bar, stage_info, kbase, par);
         kbase += bt_spmv_sched(a, L).n;
         if (!bt_grid_sync(a.g, a.bar_wait)) return;
         bt_phase_update(a, L, par);
@@ -959,9 +960,10 @@ struct pc_batched_state {
     int max_inst = 0;
     int blocks_per_sm = 0;         // autotuned launch shape (0 = not tuned yet)
     int spmv_order = 0;            // autotuned SpMV entry order: 0 strided, 1 chunked
+    int capr = SP_CAP_PER_ROW;     // autotuned stage width of the SpMV phase (blocks per row)
     int64_t tuned_nnzb = -1;
     int tuned_inst = -1;
-    float tune_ms[2][5] = {};       // [order][CTAs per SM] timings of the tuning runs
+    float tune_ms[2][2][5] = {};    // [stage width 14 / 18][order][CTAs per SM] timings of the tuning runs
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream the step graph is captured on
 };
@@ -976,13 +978,19 @@ static pc_status bt_prepare(pc_ctx *c, pc_batched_state **out)
     return PC_OK;
 }
 
+// The SpMV phase's stage widths the autotuner chooses between (blocks per row of a
+// 32-row tile): the narrow one leaves more shared memory per SM, the wide one stages
+// more tiles instead of reading them from global memory.
+static int bt_capr(int i) { return i == 0 ? SP_CAP_PER_ROW : SP_CAPR_WIDE; }
+
 static pc_status bt_launch(pc_ctx *c, pc_batched_state *B, const BtArgs &args, bool diff, int blocks_per_sm,
-                           cudaStream_t st)
+                           int capr, cudaStream_t st)
 {
+    const bool wide = capr > SP_CAP_PER_ROW;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(c->num_sms * blocks_per_sm));
     cfg.blockDim = dim3(SP_THREADS);
-    cfg.dynamicSmemBytes = SP_SMEM_BYTES;
+    cfg.dynamicSmemBytes = wide ? SpShape<SP_CAPR_WIDE>::smem_bytes : SpShape<SP_CAP_PER_ROW>::smem_bytes;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -992,17 +1000,25 @@ static pc_status bt_launch(pc_ctx *c, pc_batched_state *B, const BtArgs &args, b
     PC_CUDA_TRY(cudaMemsetAsync(B->g, 0, sizeof(bt_global), st));
     PC_CUDA_TRY(cudaMemsetAsync(B->inst, 0, sizeof(bt_inst) * (size_t)args.n_inst, st));
     BtArgs a = args;
-    if (diff) PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, batched_pcg_kernel<true>, a));
-    else PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, batched_pcg_kernel<false>, a));
+    if (diff && wide) PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, batched_pcg_kernel<true, SP_CAPR_WIDE>, a));
+    else if (diff) PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, batched_pcg_kernel<true, SP_CAP_PER_ROW>, a));
+    else if (wide) PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, batched_pcg_kernel<false, SP_CAPR_WIDE>, a));
+    else PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, batched_pcg_kernel<false, SP_CAP_PER_ROW>, a));
     c->launches++;
     return PC_OK;
 }
 
-static int bt_max_blocks_per_sm(bool diff)
+static int bt_max_blocks_per_sm(bool diff, int capr)
 {
     int n = 0;
-    if (diff) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_pcg_kernel<true>, SP_THREADS, SP_SMEM_BYTES);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_pcg_kernel<false>, SP_THREADS, SP_SMEM_BYTES);
+    const int wb = SpShape<SP_CAPR_WIDE>::smem_bytes, nb = SpShape<SP_CAP_PER_ROW>::smem_bytes;
+    if (capr > SP_CAP_PER_ROW) {
+        if (diff) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_pcg_kernel<true, SP_CAPR_WIDE>, SP_THREADS, wb);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_pcg_kernel<false, SP_CAPR_WIDE>, SP_THREADS, wb);
+    } else {
+        if (diff) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_pcg_kernel<true, SP_CAP_PER_ROW>, SP_THREADS, nb);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_pcg_kernel<false, SP_CAP_PER_ROW>, SP_THREADS, nb);
+    }
     return n;
 }
 
@@ -1010,7 +1026,7 @@ static int bt_max_blocks_per_sm(bool diff)
 // host synchronisation, so it can be captured).
 static pc_status bt_enqueue(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, const float *vals, const float *dres,
                             const float *b, float *dv, int n_inst, const pc_solve_opts &o, int blocks_per_sm,
-                            int spmv_order, cudaStream_t st)
+                            int spmv_order, int capr, cudaStream_t st)
 {
     const int V = c->V;
     PC_LAUNCH(c, bt_dinv_kernel, pc_blocks(V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals,
@@ -1056,7 +1072,7 @@ static pc_status bt_enqueue(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, con
     a.refresh_every = o.refresh_every;
     a.spmv_chunked = spmv_order;
     a.bar_wait = c->bar_wait_cycles > 0 ? (long long)c->bar_wait_cycles : SP_WAIT_BUDGET;
-    return bt_launch(c, B, a, dres != nullptr, blocks_per_sm, st);
+    return bt_launch(c, B, a, dres != nullptr, blocks_per_sm, capr, st);
 }
 
 static pc_status bt_setup_instances(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, int n_inst,
@@ -1078,43 +1094,48 @@ static pc_status bt_setup_instances(pc_ctx *c, pc_batched_state *B, const pc_bsr
 }
 
 // Autotuner: on the first solve of a given shape, time a short solve (fixed iteration
-// budget) for each schedule -- SpMV entry order (strided or chunked) x co-resident CTAs
-// per SM (1..4, as far as they fit) -- and keep the fastest.
+// budget) for each tile and schedule choice -- the SpMV phase's stage width (14 or 18
+// blocks per row of a 32-row tile) x its entry order (strided or chunked) x co-resident
+// CTAs per SM (1..4, as far as they fit) -- and keep the fastest.
 static pc_status bt_autotune(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, const float *vals, const float *dres,
                              const float *b, int n_inst, const pc_solve_opts &o, cudaStream_t st)
 {
     if (B->blocks_per_sm > 0 && B->tuned_nnzb == A->nnzb && B->tuned_inst == n_inst) return PC_OK;
-    const int maxb = std::min(4, bt_max_blocks_per_sm(dres != nullptr));
-    if (maxb < 1) return PC_ERR_CUDA;
     pc_solve_opts t = o;
     t.max_iter = std::min(o.max_iter, 60);
     t.tol = 1e-30;  // run the whole budget
     float best = 1e30f;
-    int best_b = maxb, best_order = 0;
+    int best_b = 0, best_order = 0, best_capr = SP_CAP_PER_ROW;
     cudaEvent_t e0, e1;
     PC_CUDA_TRY(cudaEventCreate(&e0));
     PC_CUDA_TRY(cudaEventCreate(&e1));
     float *scratch_dv = c->rhs32;  // float[V][3], a zero guess
-    for (int order = 0; order < 2; ++order)
-        for (int nb = 1; nb <= maxb; ++nb) {
-            PC_CUDA_TRY(cudaMemsetAsync(scratch_dv, 0, sizeof(float) * 3 * (size_t)c->V, st));
-            PC_CUDA_TRY(cudaEventRecord(e0, st));
-            pc_status s = bt_enqueue(c, B, A, vals, dres, b, scratch_dv, n_inst, t, nb, order, st);
-            PC_CUDA_TRY(cudaEventRecord(e1, st));
-            if (s != PC_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
-            PC_CUDA_TRY(cudaEventSynchronize(e1));
-            uint32_t aborted = 0;
-            PC_CUDA_TRY(cudaMemcpy(&aborted, &B->g->abort, sizeof(uint32_t), cudaMemcpyDeviceToHost));
-            if (aborted) { cudaEventDestroy(e0); cudaEventDestroy(e1); return PC_ERR_TIMEOUT; }
-            float ms = 0.f;
-            PC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            B->tune_ms[order][nb] = ms;
-            if (ms < best) { best = ms; best_b = nb; best_order = order; }
-        }
+    for (int w = 0; w < 2; ++w) {
+        const int capr = bt_capr(w);
+        const int maxb = std::min(4, bt_max_blocks_per_sm(dres != nullptr, capr));
+        for (int order = 0; order < 2; ++order)
+            for (int nb = 1; nb <= maxb; ++nb) {
+                PC_CUDA_TRY(cudaMemsetAsync(scratch_dv, 0, sizeof(float) * 3 * (size_t)c->V, st));
+                PC_CUDA_TRY(cudaEventRecord(e0, st));
+                pc_status s = bt_enqueue(c, B, A, vals, dres, b, scratch_dv, n_inst, t, nb, order, capr, st);
+                PC_CUDA_TRY(cudaEventRecord(e1, st));
+                if (s != PC_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
+                PC_CUDA_TRY(cudaEventSynchronize(e1));
+                uint32_t aborted = 0;
+                PC_CUDA_TRY(cudaMemcpy(&aborted, &B->g->abort, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+                if (aborted) { cudaEventDestroy(e0); cudaEventDestroy(e1); return PC_ERR_TIMEOUT; }
+                float ms = 0.f;
+                PC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                B->tune_ms[w][order][nb] = ms;
+                if (ms < best) { best = ms; best_b = nb; best_order = order; best_capr = capr; }
+            }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (best_b < 1) return PC_ERR_CUDA;  // no launch shape fits an SM
     B->blocks_per_sm = best_b;
     B->spmv_order = best_order;
+    B->capr = best_capr;
     B->tuned_nnzb = A->nnzb;
     B->tuned_inst = n_inst;
     return PC_OK;
@@ -1161,7 +1182,7 @@ extern "C" pc_status pc_pcg_solve_batched(pc_ctx *ctx, const pc_bsr *A, const fl
     PC_TRY(bt_setup_instances(ctx, B, A, n_inst, inst_rows, st));
     PC_TRY(bt_autotune(ctx, B, A, vals, dres, b, n_inst, o, st));
     PC_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), st));
-    PC_TRY(bt_enqueue(ctx, B, A, vals, dres, b, dv, n_inst, o, B->blocks_per_sm, B->spmv_order, st));
+    PC_TRY(bt_enqueue(ctx, B, A, vals, dres, b, dv, n_inst, o, B->blocks_per_sm, B->spmv_order, B->capr, st));
     return bt_collect(ctx, B, n_inst, info, st);
 }
 
@@ -1173,16 +1194,18 @@ extern "C" pc_status pc_set_barrier_wait(pc_ctx *ctx, int64_t cycles)
 }
 
 extern "C" pc_status pc_batched_config(pc_ctx *ctx, int32_t *blocks_per_sm, int32_t *spmv_order,
-                                       float *tune_ms /*[8]*/)
+                                       int32_t *stage_blocks, float *tune_ms /*[16]*/)
 {
     if (!ctx) return PC_ERR_ARG;
     pc_batched_state *B = bt_state(ctx);
     if (!B) return PC_ERR_CUDA;
     if (blocks_per_sm) *blocks_per_sm = B->blocks_per_sm;
     if (spmv_order) *spmv_order = B->spmv_order;
+    if (stage_blocks) *stage_blocks = B->capr;
     if (tune_ms)
-        for (int order = 0; order < 2; ++order)
-            for (int i = 0; i < 4; ++i) tune_ms[4 * order + i] = B->tune_ms[order][i + 1];
+        for (int w = 0; w < 2; ++w)
+            for (int order = 0; order < 2; ++order)
+                for (int i = 0; i < 4; ++i) tune_ms[8 * w + 4 * order + i] = B->tune_ms[w][order][i + 1];
     return PC_OK;
 }
 
@@ -1226,7 +1249,7 @@ extern "C" pc_status pc_step_batched(pc_ctx *ctx, float *x, float *v, const pc_c
     pc_status s = pc_assemble_values(ctx, &A, x, v, contacts, opts->h, ctx->A_vals, ctx->A_b, ctx->A_dres, (void *)cs);
     if (s == PC_OK)
         s = bt_enqueue(ctx, B, &A, ctx->A_vals, ctx->A_dres, ctx->A_b, ctx->A_dv, n_inst, o, B->blocks_per_sm,
-                       B->spmv_order, cs);
+                       B->spmv_order, B->capr, cs);
     if (s == PC_OK) s = bt_update_state(ctx, B, x, v, opts->h, cs);
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     if (s != PC_OK) {
@@ -1281,10 +1304,15 @@ pc_status pc_batched_alloc(pc_ctx *c)
     PC_CUDA_TRY(cudaMalloc(&B->g, sizeof(bt_global)));
     PC_CUDA_TRY(cudaMalloc(&B->inst_rows, sizeof(int32_t) * (BT_MAX_INST + 1)));
     PC_CUDA_TRY(cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking));
-    PC_CUDA_TRY(cudaFuncSetAttribute(batched_pcg_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     SP_SMEM_BYTES));
-    PC_CUDA_TRY(cudaFuncSetAttribute(batched_pcg_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     SP_SMEM_BYTES));
+    const int nbytes = SpShape<SP_CAP_PER_ROW>::smem_bytes, wbytes = SpShape<SP_CAPR_WIDE>::smem_bytes;
+    PC_CUDA_TRY(cudaFuncSetAttribute(batched_pcg_kernel<true, SP_CAP_PER_ROW>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, nbytes));
+    PC_CUDA_TRY(cudaFuncSetAttribute(batched_pcg_kernel<false, SP_CAP_PER_ROW>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, nbytes));
+    PC_CUDA_TRY(cudaFuncSetAttribute(batched_pcg_kernel<true, SP_CAPR_WIDE>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, wbytes));
+    PC_CUDA_TRY(cudaFuncSetAttribute(batched_pcg_kernel<false, SP_CAPR_WIDE>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, wbytes));
     return PC_OK;
 }
 
