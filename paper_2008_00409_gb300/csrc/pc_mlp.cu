@@ -1,21 +1,20 @@
 // Learned warm start: a per-vertex MLP (12 -> 64 -> 64 -> 3, ReLU) that predicts the
 // initial guess of the Eq. 3 solve, its training (forward, back-propagation, Adam) and
-// the step's choice among the learned, previous-step and zero guesses by their residual.
+// the step's initial guess combining the learned and previous-step guesses.
 // The paper has no learned component; this is an extension built on its integrator.
 //
-// Features of vertex i (12): v_i, dv_prev_i, (b_i / h - m_i g) / m_i (the internal force
-// per unit mass at the first-order end-of-step position, from the assembled right-hand
-// side b = h (f(x_t) - h K v_t) + h M g), and the mean of dv_prev over the edge one-ring.
+// Features of vertex i (12): v_i, dv_prev_i, l_i (b_i / h - m_i g) / m_i (the internal
+// force per unit mass at the first-order end-of-step position, from the assembled
+// right-hand side b = h (f(x_t) - h K v_t) + h M g, times the vertex's mean rest edge
+// length l_i), and the mean of dv_prev over the edge one-ring.
 // Inputs and targets are standardised with training-set statistics; the network predicts
 // the change dv - dv_prev, so the guess is dv0 = dv_prev + sd_y * y + mu_y (0 at pins).
 //
-// Every matrix product runs on the tensor cores as warp-level BF16 MMAs (m16n8k16, FP32
-// accumulation): a warp owns 16 rows and carries them through all layers in registers
-// (the accumulator fragment of one layer is the operand fragment of the next). Training
-// stages the tile's BF16 activations and back-propagated signals in shared memory and
-// forms the weight gradients dW = dZ^T H as MMAs over the rows (operands transposed by
-// ldmatrix.trans); per-CTA partial gradients are summed in a fixed order (deterministic)
-// by the kernel that applies Adam to the FP32 master weights.
+// Every matrix product, in inference and in training, runs on the 5th-generation tensor
+// cores (tcgen05.mma, BF16 operands in shared memory, FP32 accumulators in tensor memory).
+// Training forms the weight gradients dW = dZ^T H as products over a tile's rows,
+// accumulated in tensor memory; per-CTA partial gradients are summed in a fixed order
+// (deterministic) by the kernel that applies Adam to the FP32 master weights.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -38,11 +37,6 @@
 static_assert(OFF_B3 + MLP_OUT == PC_MLP_NPARAMS, "parameter layout");
 static_assert(2 * MLP_IN + 2 * MLP_OUT == PC_MLP_NSTATS, "statistics layout");
 
-#define WP16 24  // shared-memory pitch (BF16 elements) of 16-wide rows: conflict-free fragment loads
-#define WP64 72  // pitch of 64-wide rows
-#define MLP_WARPS 8
-#define MLP_THREADS (32 * MLP_WARPS)
-#define MLP_TILE (16 * MLP_WARPS)  // rows per CTA tile
 
 // ------------------------------------------------------------------------- tensor-core helpers
 
@@ -50,179 +44,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x (low half) = lo
     return *reinterpret_cast<uint32_t *>(&v);
-}
-
-// D += A (16x16, row) * B (16x8, col), BF16 inputs, FP32 accumulation
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const __nv_bfloat16 *p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_addr(p)));
-}
-
-__device__ __forceinline__ void ldsm_x2_t(uint32_t &r0, uint32_t &r1, const __nv_bfloat16 *p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
-                 : "=r"(r0), "=r"(r1)
-                 : "r"(smem_addr(p)));
-}
-
-__device__ __forceinline__ void st_pair(__nv_bfloat16 *base, int row, int pitch, int col, uint32_t v)
-{
-    *reinterpret_cast<uint32_t *>(base + row * pitch + col) = v;
-}
-
-// ------------------------------------------------------------------------- weights in shared memory
-
-// BF16 copies of the weights in the layouts the fragments read: W[n][k] rows (forward,
-// B[k][n] = W[n][k]) and transposes (backward, B[k][n] = W[k][n]); zero padding of the
-// 12 inputs to 16 and of the 3 outputs to 8 (forward) or 16 (backward operands).
-struct MlpW {
-    __nv_bfloat16 w1[MLP_HID * WP16];
-    __nv_bfloat16 w2[MLP_HID * WP64];
-    __nv_bfloat16 w3[8 * WP64];
-    __nv_bfloat16 w2t[MLP_HID * WP64];
-    __nv_bfloat16 w3t[MLP_HID * WP16];
-    float b1[MLP_HID], b2[MLP_HID], b3[8];
-    float mx[16], sx[16], my[4], sy[4];
-};
-
-__device__ void mlp_stage(MlpW &s, const float *P, const float *stats, bool backward)
-{
-    const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
-    for (int i = threadIdx.x; i < MLP_HID * WP16; i += blockDim.x) {
-        const int n = i / WP16, k = i % WP16;
-        s.w1[i] = k < MLP_IN ? __float2bfloat16_rn(P[OFF_W1 + n * MLP_IN + k]) : z;
-        if (backward) s.w3t[i] = k < MLP_OUT ? __float2bfloat16_rn(P[OFF_W3 + k * MLP_HID + n]) : z;
-    }
-    for (int i = threadIdx.x; i < MLP_HID * WP64; i += blockDim.x) {
-        const int n = i / WP64, k = i % WP64;
-        s.w2[i] = k < MLP_HID ? __float2bfloat16_rn(P[OFF_W2 + n * MLP_HID + k]) : z;
-        if (backward) s.w2t[i] = k < MLP_HID ? __float2bfloat16_rn(P[OFF_W2 + k * MLP_HID + n]) : z;
-    }
-    for (int i = threadIdx.x; i < 8 * WP64; i += blockDim.x) {
-        const int n = i / WP64, k = i % WP64;
-        s.w3[i] = (n < MLP_OUT && k < MLP_HID) ? __float2bfloat16_rn(P[OFF_W3 + n * MLP_HID + k]) : z;
-    }
-    for (int i = threadIdx.x; i < MLP_HID; i += blockDim.x) {
-        s.b1[i] = P[OFF_B1 + i];
-        s.b2[i] = P[OFF_B2 + i];
-    }
-    if (threadIdx.x < 8) s.b3[threadIdx.x] = threadIdx.x < MLP_OUT ? P[OFF_B3 + threadIdx.x] : 0.f;
-    if (threadIdx.x < 16) {
-        const int j = threadIdx.x;
-        s.mx[j] = j < MLP_IN ? stats[j] : 0.f;
-        s.sx[j] = j < MLP_IN ? stats[MLP_IN + j] : 1.f;
-    }
-    if (threadIdx.x < 4) {
-        const int j = threadIdx.x;
-        s.my[j] = j < MLP_OUT ? stats[2 * MLP_IN + j] : 0.f;
-        s.sy[j] = j < MLP_OUT ? stats[2 * MLP_IN + MLP_OUT + j] : 1.f;
-    }
-}
-
-// ------------------------------------------------------------------------- per-warp network
-
-// Operand fragment of 16 standardised input rows (rows r0 = base + g and r0 + 8, columns
-// 2c, 2c+1 and 2c+8, 2c+9; columns 12..15 are zero padding). Rows at or past n are zero.
-__device__ __forceinline__ void mlp_load_x(const MlpW &s, const float *feat, const int32_t *rows, int64_t n,
-                                           int64_t base, uint32_t (&ax)[4])
-{
-    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int64_t r = base + g + 8 * h;
-        float v[4] = {0.f, 0.f, 0.f, 0.f};
-        if (r < n) {
-            const float *x = feat + (int64_t)MLP_IN * (rows ? (int64_t)rows[r] : r);
-            const int k0 = 2 * c, k1 = 8 + 2 * c;
-            v[0] = (x[k0] - s.mx[k0]) / s.sx[k0];
-            v[1] = (x[k0 + 1] - s.mx[k0 + 1]) / s.sx[k0 + 1];
-            if (k1 < MLP_IN) {
-                v[2] = (x[k1] - s.mx[k1]) / s.sx[k1];
-                v[3] = (x[k1 + 1] - s.mx[k1 + 1]) / s.sx[k1 + 1];
-            }
-        }
-        ax[h] = pack_bf16(v[0], v[1]);      // a0a1 (row g) / a2a3 (row g+8)
-        ax[2 + h] = pack_bf16(v[2], v[3]);  // a4a5 / a6a7
-    }
-}
-
-// bias + ReLU of a 16x64 accumulator, as BF16 operand fragments of the next layer;
-// mask bit (4 nt + e) records Z > 0. With `store`, the BF16 activations are also written
-// to the warp's 16 shared-memory rows.
-__device__ __forceinline__ void mlp_relu_pack(float (&acc)[8][4], uint32_t (&a)[4][4], uint32_t &mask,
-                                              __nv_bfloat16 *store)
-{
-    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
-    mask = 0u;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        float h[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const bool pos = acc[nt][e] > 0.f;
-            mask |= (pos ? 1u : 0u) << (4 * nt + e);
-            h[e] = pos ? acc[nt][e] : 0.f;
-        }
-        const uint32_t lo = pack_bf16(h[0], h[1]), hi = pack_bf16(h[2], h[3]);
-        a[nt >> 1][(nt & 1) * 2] = lo;
-        a[nt >> 1][(nt & 1) * 2 + 1] = hi;
-        if (store) {
-            st_pair(store, g, WP64, 8 * nt + 2 * c, lo);
-            st_pair(store, g + 8, WP64, 8 * nt + 2 * c, hi);
-        }
-    }
-}
-
-// Z = A (16 x 16 kk) * W^T + bias, W as [64][pitch] BF16 rows (B[k][n] = W[n][k])
-template <int KSTEPS, int PITCH>
-__device__ __forceinline__ void mlp_layer64(const uint32_t (&a)[KSTEPS][4], const __nv_bfloat16 *W, const float *bias,
-                                            float (&acc)[8][4])
-{
-    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const float b0 = bias ? bias[8 * nt + 2 * c] : 0.f, b1 = bias ? bias[8 * nt + 2 * c + 1] : 0.f;
-        acc[nt][0] = b0;
-        acc[nt][1] = b1;
-        acc[nt][2] = b0;
-        acc[nt][3] = b1;
-        const uint32_t *row = reinterpret_cast<const uint32_t *>(W + (8 * nt + g) * PITCH);
-#pragma unroll
-        for (int kk = 0; kk < KSTEPS; ++kk) mma_bf16(acc[nt], a[kk], row[8 * kk + c], row[8 * kk + 4 + c]);
-    }
-}
-
-// The forward pass of one warp's 16 rows: y (16 x 8 accumulator, outputs 0..2 real) and
-// the ReLU masks; optionally stores X, H1, H2 (BF16) for the weight gradients.
-__device__ __forceinline__ void mlp_forward(const MlpW &s, const uint32_t (&ax)[4], float (&y)[4], uint32_t &m1,
-                                            uint32_t &m2, uint32_t (&a2)[4][4], __nv_bfloat16 *h1s,
-                                            __nv_bfloat16 *h2s)
-{
-    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
-    float acc[8][4];
-    const uint32_t ax1[1][4] = {{ax[0], ax[1], ax[2], ax[3]}};
-    mlp_layer64<1, WP16>(ax1, s.w1, s.b1, acc);
-    uint32_t a1[4][4];
-    mlp_relu_pack(acc, a1, m1, h1s);
-    mlp_layer64<4, WP64>(a1, s.w2, s.b2, acc);
-    mlp_relu_pack(acc, a2, m2, h2s);
-    y[0] = s.b3[2 * c];
-    y[1] = s.b3[2 * c + 1];
-    y[2] = y[0];
-    y[3] = y[1];
-    const uint32_t *row = reinterpret_cast<const uint32_t *>(s.w3 + g * WP64);
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) mma_bf16(y, a2[kk], row[8 * kk + c], row[8 * kk + 4 + c]);
 }
 
 // ------------------------------------------------------------------------- inference (tcgen05)
@@ -396,211 +217,308 @@ __global__ void __launch_bounds__(TC_THREADS) mlp_infer_kernel(int64_t n, const 
     if (warp == 0) tc_dealloc(tmem, TC_TMEM_COLS);
 }
 
-// ------------------------------------------------------------------------- training
+// ------------------------------------------------------------------------- training (tcgen05)
+//
+// One CTA of four warps per SM (persistent over 128-row tiles; its shared memory keeps a
+// second CTA off the SM, so the CTA owns all 512 tensor-memory columns). Per tile, one
+// thread issues the tensor-core products and every thread handles its own row in the
+// epilogues (warp w reads tensor-memory lanes 32w.., the tile's rows 32w..):
+//   forward   D1 = X W1^T, D2 = H1 W2^T, D3 = H2 W3^T                  (M = 128 rows)
+//   backward  dH2 = dY W3, dH1 = dZ2 W2                                (M = 128 rows)
+//   gradients [dZ2^T ; dZ1^T] [H1^T ; X^T]^T   (M = 128: dW2 and dW1 are its diagonal
+//             blocks, 64 x 64 and 64 x 16), H2^T dY (dW3^T): products over the tile's rows
+//             (K = 128), accumulated in tensor memory across the CTA's tiles.
+// Every operand is a K-major BF16 array in shared memory (the layout the inference kernel
+// uses): the epilogues write each row's activations and back-propagated signals both as a
+// row of the next product's A operand and, transposed, as a column of the gradient
+// products' operands. BF16 rounding happens where the oracle's bfloat16 mode rounds
+// (standardised inputs, weights, hidden activations, dY, dZ2, dZ1); the bias gradients and
+// the loss are summed on the CUDA cores from the unrounded FP32 signals, per warp in a
+// fixed order, so training stays bit-reproducible.
+#define TT_ROWS 128
+#define TT_THREADS 128
+#define TT_TMEM_COLS 512  // D1 / dH2 at 0, D2 / dH1 at 64, D3 at 128, gradients at 256 and 352
+#define TT_GW12 256       // 80 columns: [dW2 | dW1] blocks
+#define TT_GW3 352        // 16 columns: dW3^T
+#define TT_W1 0           // 64 x 16 (forward B: W1[n][k])
+#define TT_W2 2048        // 64 x 64
+#define TT_W3 10240       // 16 x 64 (outputs 3..15 zero)
+#define TT_W3T 12288      // 64 x 16: W3T[n][k] = W3[k][n] (k < 3)
+#define TT_W2T 14336      // 64 x 64: W2T[n][k] = W2[k][n]
+#define TT_X 22528        // 128 x 16: standardised inputs (A of layer 1)
+#define TT_H1 26624       // 128 x 64
+#define TT_H2 43008       // 128 x 64
+#define TT_DY 59392       // 128 x 16: dY (outputs 3..15 zero)
+#define TT_DZ2 63488      // 128 x 64
+#define TT_TH2 79872      // 64 x 128: H2^T; its M = 128 operand runs on into TT_TZ (rows never read)
+#define TT_TZ 96256       // 128 x 128: dZ2^T (rows 0..63), dZ1^T (rows 64..127)
+#define TT_TB 129024      // 80 x 128: H1^T (rows 0..63), X^T (rows 64..79; inputs 12..15 zero)
+#define TT_TDY 149504     // 16 x 128: dY^T (rows 3..15 zero)
+#define TT_SMEM 153600    // 150 KB: one CTA per SM
 
-struct MlpTrainSmem {
-    MlpW w;
-    __nv_bfloat16 xs[MLP_TILE * WP16];
-    __nv_bfloat16 h1[MLP_TILE * WP64];
-    __nv_bfloat16 h2[MLP_TILE * WP64];
-    __nv_bfloat16 dz1[MLP_TILE * WP64];
-    __nv_bfloat16 dz2[MLP_TILE * WP64];
-    __nv_bfloat16 dy[MLP_TILE * WP16];
-    float db[MLP_WARPS][2 * MLP_HID + 8];
-    double loss[MLP_WARPS];
-};
-
-// One CTA per block of tiles: forward and back-propagation of each 128-row tile, then
-// the tile's weight gradients as MMAs over its rows; writes the CTA's gradient and loss
-// partials. The target of a row is its step's dv minus dv_prev (features 3..5),
-// standardised; dL/dy = (y - t) / n_total for L = 1/(2 n_total) sum (y - t)^2.
-__global__ void __launch_bounds__(MLP_THREADS) mlp_train_kernel(int64_t n, const int32_t *rows, const float *params,
-                                                                const float *stats, const float *feat,
-                                                                const float *target, float *part, double *loss_part)
+// Sum over the warp's 32 rows (lane 0 holds the total).
+__device__ __forceinline__ float tt_warp_sum(float v)
 {
-    extern __shared__ __align__(128) unsigned char mlp_smem_raw[];
-    MlpTrainSmem &S = *reinterpret_cast<MlpTrainSmem *>(mlp_smem_raw);
-    mlp_stage(S.w, params, stats, true);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
-    // zero the padding columns that no fragment store writes (x 12..15 stay from the pack,
-    // dY 8..15 are written as zero pairs below)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Thread 0 issues `nk` K-steps of an M = 128 product into tensor memory and commits; every
+// thread waits (bounded). A and B are K-major with K extents ka, kb (bytes per 8-row group:
+// 16 K). A thread whose wait gives up records it in *fail before the block barrier, so the
+// return value (no failure) is the same in every thread.
+__device__ __forceinline__ bool tt_mma(uint32_t d, const unsigned char *A, int ka, const unsigned char *B, int kb,
+                                       int nk, uint32_t idesc, bool acc_first, uint64_t *bar, uint32_t &phase,
+                                       volatile int *fail)
+{
+    fence_async_smem();
+    tc_fence_before();
     __syncthreads();
-    const float inv_n = 1.f / (float)n;
-    float gw2[4][4] = {}, gw1[4] = {}, gw3[4] = {};
-    float db1[8][2] = {}, db2[8][2] = {}, db3[2] = {0.f, 0.f};
-    double loss = 0.0;
-    const int64_t ntiles = (n + MLP_TILE - 1) / MLP_TILE;
-    __nv_bfloat16 *xs = S.xs + 16 * warp * WP16, *h1 = S.h1 + 16 * warp * WP64, *h2 = S.h2 + 16 * warp * WP64;
-    __nv_bfloat16 *dz1 = S.dz1 + 16 * warp * WP64, *dz2 = S.dz2 + 16 * warp * WP64, *dys = S.dy + 16 * warp * WP16;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t base = tile * MLP_TILE + 16 * warp;
-        // ---- forward
-        uint32_t ax[4], a[4][4], m1, m2;
-        float y[4];
-        mlp_load_x(S.w, feat, rows, n, base, ax);
-        st_pair(xs, g, WP16, 2 * c, ax[0]);
-        st_pair(xs, g + 8, WP16, 2 * c, ax[1]);
-        st_pair(xs, g, WP16, 8 + 2 * c, ax[2]);
-        st_pair(xs, g + 8, WP16, 8 + 2 * c, ax[3]);
-        mlp_forward(S.w, ax, y, m1, m2, a, h1, h2);
-        // ---- output error (columns 2c, 2c+1 of rows g, g+8)
-        float dyv[4];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t r = base + g + 8 * h;
-            for (int e = 0; e < 2; ++e) {
-                const int o = 2 * c + e;
-                float d = 0.f;
-                if (r < n && o < MLP_OUT) {
-                    const int64_t R = rows ? (int64_t)rows[r] : r;
-                    const float raw = target[3 * R + o] - feat[MLP_IN * R + 3 + o];  // dv - dv_prev
-                    const float tn = (raw - S.w.my[o]) / S.w.sy[o];
-                    const float err = y[2 * h + e] - tn;
-                    loss += (double)err * (double)err;
-                    d = err * inv_n;
-                }
-                dyv[2 * h + e] = d;
-            }
-        }
-        db3[0] += dyv[0] + dyv[2];
-        db3[1] += dyv[1] + dyv[3];
-        const uint32_t ady[4] = {pack_bf16(dyv[0], dyv[1]), pack_bf16(dyv[2], dyv[3]), 0u, 0u};
-        st_pair(dys, g, WP16, 2 * c, ady[0]);
-        st_pair(dys, g + 8, WP16, 2 * c, ady[1]);
-        st_pair(dys, g, WP16, 8 + 2 * c, 0u);
-        st_pair(dys, g + 8, WP16, 8 + 2 * c, 0u);
-        // ---- dZ2 = (dY W3) * [Z2 > 0]
-        float acc[8][4];
-        const uint32_t ady1[1][4] = {{ady[0], ady[1], ady[2], ady[3]}};
-        mlp_layer64<1, WP16>(ady1, S.w.w3t, nullptr, acc);
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (!((m2 >> (4 * nt + e)) & 1u)) acc[nt][e] = 0.f;
-            db2[nt][0] += acc[nt][0] + acc[nt][2];
-            db2[nt][1] += acc[nt][1] + acc[nt][3];
-            const uint32_t lo = pack_bf16(acc[nt][0], acc[nt][1]), hi = pack_bf16(acc[nt][2], acc[nt][3]);
-            a[nt >> 1][(nt & 1) * 2] = lo;
-            a[nt >> 1][(nt & 1) * 2 + 1] = hi;
-            st_pair(dz2, g, WP64, 8 * nt + 2 * c, lo);
-            st_pair(dz2, g + 8, WP64, 8 * nt + 2 * c, hi);
-        }
-        // ---- dZ1 = (dZ2 W2) * [Z1 > 0]
-        mlp_layer64<4, WP64>(a, S.w.w2t, nullptr, acc);
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (!((m1 >> (4 * nt + e)) & 1u)) acc[nt][e] = 0.f;
-            db1[nt][0] += acc[nt][0] + acc[nt][2];
-            db1[nt][1] += acc[nt][1] + acc[nt][3];
-            st_pair(dz1, g, WP64, 8 * nt + 2 * c, pack_bf16(acc[nt][0], acc[nt][1]));
-            st_pair(dz1, g + 8, WP64, 8 * nt + 2 * c, pack_bf16(acc[nt][2], acc[nt][3]));
-        }
-        __syncthreads();
-        // ---- weight gradients over the tile's 128 rows: dW = dZ^T H (K = rows)
-        // warp w: dW2 rows 16 (w/2).. (4 n-tiles from 32 (w%2)), dW1 rows 16 (w/2).. (n-tile w%2),
-        // dW3 (outputs padded to 16) n-tile w
-        const int mt = warp >> 1, i4 = lane >> 3, r8 = lane & 7;
-#pragma unroll 2
-        for (int ks = 0; ks < MLP_TILE / 16; ++ks) {
-            const int rA = 16 * ks + (i4 >> 1) * 8 + r8;  // rows of the transposed A operand
-            uint32_t af[4];
-            // dW2
-            ldsm_x4_t(af, S.dz2 + rA * WP64 + 16 * mt + (i4 & 1) * 8);
-#pragma unroll
-            for (int jj = 0; jj < 2; ++jj) {
-                uint32_t bf[4];
-                const int n0 = 32 * (warp & 1) + 16 * jj;
-                ldsm_x4_t(bf, S.h1 + (16 * ks + (i4 & 1) * 8 + r8) * WP64 + n0 + (i4 >> 1) * 8);
-                mma_bf16(gw2[2 * jj], af, bf[0], bf[1]);
-                mma_bf16(gw2[2 * jj + 1], af, bf[2], bf[3]);
-            }
-            // dW1
-            ldsm_x4_t(af, S.dz1 + rA * WP64 + 16 * mt + (i4 & 1) * 8);
-            {
-                uint32_t b0, b1;
-                ldsm_x2_t(b0, b1, S.xs + (16 * ks + (i4 & 1) * 8 + r8) * WP16 + 8 * (warp & 1));
-                mma_bf16(gw1, af, b0, b1);
-            }
-            // dW3
-            ldsm_x4_t(af, S.dy + rA * WP16 + (i4 & 1) * 8);
-            {
-                uint32_t b0, b1;
-                ldsm_x2_t(b0, b1, S.h2 + (16 * ks + (i4 & 1) * 8 + r8) * WP64 + 8 * warp);
-                mma_bf16(gw3, af, b0, b1);
-            }
-        }
-        __syncthreads();
-    }
-    // ---- write this CTA's partials
-    float *out = part + (int64_t)blockIdx.x * PC_MLP_NPARAMS;
-    {
-        // dW2 tile (mt, nt): rows 16 mt + g (+8), columns 8 nt + 2c (+1)
-        const int mt = warp >> 1;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int nt = 4 * (warp & 1) + j;
-            const int r0 = 16 * mt + g, col = 8 * nt + 2 * c;
-            out[OFF_W2 + r0 * MLP_HID + col] = gw2[j][0];
-            out[OFF_W2 + r0 * MLP_HID + col + 1] = gw2[j][1];
-            out[OFF_W2 + (r0 + 8) * MLP_HID + col] = gw2[j][2];
-            out[OFF_W2 + (r0 + 8) * MLP_HID + col + 1] = gw2[j][3];
-        }
-        // dW1 tile: rows 16 mt + g (+8), input columns 8 (w%2) + 2c (+1), only inputs < 12
-        const int col1 = 8 * (warp & 1) + 2 * c;
-        const int r1 = 16 * mt + g;
-        for (int e = 0; e < 2; ++e) {
-            if (col1 + e < MLP_IN) {
-                out[OFF_W1 + r1 * MLP_IN + col1 + e] = gw1[e];
-                out[OFF_W1 + (r1 + 8) * MLP_IN + col1 + e] = gw1[2 + e];
-            }
-        }
-        // dW3 tile: outputs g (< 3), hidden columns 8 w + 2c (+1)
-        if (g < MLP_OUT) {
-            out[OFF_W3 + g * MLP_HID + 8 * warp + 2 * c] = gw3[0];
-            out[OFF_W3 + g * MLP_HID + 8 * warp + 2 * c + 1] = gw3[1];
-        }
-    }
-    // bias gradients: columns summed over the rows held by lanes of equal c, then warps in order
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int e = 0; e < 2; ++e)
-#pragma unroll
-            for (int o = 4; o < 32; o <<= 1) {
-                db1[nt][e] += __shfl_xor_sync(0xffffffffu, db1[nt][e], o);
-                db2[nt][e] += __shfl_xor_sync(0xffffffffu, db2[nt][e], o);
-            }
-#pragma unroll
-    for (int e = 0; e < 2; ++e)
-#pragma unroll
-        for (int o = 4; o < 32; o <<= 1) db3[e] += __shfl_xor_sync(0xffffffffu, db3[e], o);
-    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
-    if (lane < 4) {
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt)
-            for (int e = 0; e < 2; ++e) {
-                S.db[warp][8 * nt + 2 * lane + e] = db1[nt][e];
-                S.db[warp][MLP_HID + 8 * nt + 2 * lane + e] = db2[nt][e];
-            }
-        S.db[warp][2 * MLP_HID + 2 * lane] = db3[0];
-        S.db[warp][2 * MLP_HID + 2 * lane + 1] = db3[1];
-    }
-    if (lane == 0) S.loss[warp] = loss;
-    __syncthreads();
-    for (int j = threadIdx.x; j < 2 * MLP_HID + MLP_OUT; j += blockDim.x) {
-        float t = 0.f;
-        for (int w = 0; w < MLP_WARPS; ++w) t += S.db[w][j];
-        const int dst = j < MLP_HID ? OFF_B1 + j : j < 2 * MLP_HID ? OFF_B2 + (j - MLP_HID) : OFF_B3 + (j - 2 * MLP_HID);
-        out[dst] = t;
-    }
+    tc_fence_after();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < MLP_WARPS; ++w) t += S.loss[w];
-        loss_part[blockIdx.x] = t;
+        for (int kk = 0; kk < nk; ++kk)
+            tc_mma_bf16(d, tc_smem_desc(A + 256 * kk, 128, 16 * ka), tc_smem_desc(B + 256 * kk, 128, 16 * kb), idesc,
+                        acc_first || kk > 0);
+        tc_commit(bar);
     }
+    const bool ok = mbar_wait_bounded(bar, phase, TC_WAIT_BUDGET);
+    phase ^= 1u;
+    if (!ok) *fail = 1;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    return *fail == 0;
+}
+
+__global__ void __launch_bounds__(TT_THREADS, 1) mlp_train_kernel(int64_t n, const int32_t *rows, const float *params,
+                                                                  const float *stats, const float *feat,
+                                                                  const float *target, float *part, double *loss_part,
+                                                                  uint32_t *err)
+{
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_fail;
+    __shared__ float b1[MLP_HID], b2[MLP_HID], b3[4], mx[MLP_IN], sx[MLP_IN], my[4], sy[4];
+    __shared__ float sdb[4][2 * MLP_HID + 4];  // per-warp bias-gradient sums: db1, db2, db3
+    __shared__ double sloss[4];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    // weights in the four layouts the products read; every other buffer starts at zero
+    // (the padding columns of X, dY, their transposes and of W3 are never written again)
+    for (int i = t; i < (TT_SMEM - TT_X) / 16; i += TT_THREADS)
+        reinterpret_cast<uint4 *>(tsm + TT_X)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = t; i < MLP_HID * 16; i += TT_THREADS) {
+        const int r = i >> 4, k = i & 15;
+        tc_put(tsm + TT_W1, r, k, 16, k < MLP_IN ? params[OFF_W1 + r * MLP_IN + k] : 0.f);
+        tc_put(tsm + TT_W3T, r, k, 16, k < MLP_OUT ? params[OFF_W3 + k * MLP_HID + r] : 0.f);
+    }
+    for (int i = t; i < MLP_HID * MLP_HID; i += TT_THREADS) {
+        const int r = i >> 6, k = i & 63;
+        tc_put(tsm + TT_W2, r, k, 64, params[OFF_W2 + r * MLP_HID + k]);
+        tc_put(tsm + TT_W2T, r, k, 64, params[OFF_W2 + k * MLP_HID + r]);
+    }
+    for (int i = t; i < 16 * MLP_HID; i += TT_THREADS) {
+        const int r = i >> 6, k = i & 63;
+        tc_put(tsm + TT_W3, r, k, 64, r < MLP_OUT ? params[OFF_W3 + r * MLP_HID + k] : 0.f);
+    }
+    if (t < MLP_HID) {
+        b1[t] = params[OFF_B1 + t];
+        b2[t] = params[OFF_B2 + t];
+    }
+    if (t < MLP_IN) {
+        mx[t] = stats[t];
+        sx[t] = stats[MLP_IN + t];
+    }
+    if (t < 4) {
+        b3[t] = t < MLP_OUT ? params[OFF_B3 + t] : 0.f;
+        my[t] = t < MLP_OUT ? stats[2 * MLP_IN + t] : 0.f;
+        sy[t] = t < MLP_OUT ? stats[2 * MLP_IN + MLP_OUT + t] : 1.f;
+    }
+    for (int i = t; i < 4 * (2 * MLP_HID + 4); i += TT_THREADS) (&sdb[0][0])[i] = 0.f;
+    if (t == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+        s_fail = 0;
+    }
+    if (warp == 0) tc_alloc(&tmem_slot, TT_TMEM_COLS);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot, lanes = (uint32_t)(32 * warp) << 16;
+    const uint32_t id64 = tc_idesc_bf16(TT_ROWS, 64), id16 = tc_idesc_bf16(TT_ROWS, 16);
+    const uint32_t id80 = tc_idesc_bf16(TT_ROWS, 80);
+    unsigned char *X = tsm + TT_X, *H1 = tsm + TT_H1, *H2 = tsm + TT_H2, *DY = tsm + TT_DY, *DZ2 = tsm + TT_DZ2;
+    unsigned char *TH2 = tsm + TT_TH2, *TZ = tsm + TT_TZ, *TB = tsm + TT_TB, *TDY = tsm + TT_TDY;
+    const float inv_n = 1.f / (float)n;
+    double loss = 0.0;
+    uint32_t phase = 0;
+    bool first = true;
+    const int64_t ntiles = (n + TT_ROWS - 1) / TT_ROWS;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r = tile * TT_ROWS + t;
+        const int64_t R = r < n ? (rows ? (int64_t)rows[r] : r) : 0;
+        // ---- standardised inputs: row t of X and column t of X^T (rows past n are zero)
+        {
+            float v[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] = 0.f;
+            if (r < n) {
+                const float *x = feat + (int64_t)MLP_IN * R;
+#pragma unroll
+                for (int k = 0; k < MLP_IN; ++k) v[k] = (x[k] - mx[k]) / sx[k];
+            }
+            uint32_t q[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) q[i] = pack_bf16(v[2 * i], v[2 * i + 1]);
+            *reinterpret_cast<uint4 *>(X + tc_off(t, 0, 16)) = make_uint4(q[0], q[1], q[2], q[3]);
+            *reinterpret_cast<uint4 *>(X + tc_off(t, 8, 16)) = make_uint4(q[4], q[5], q[6], q[7]);
+#pragma unroll
+            for (int k = 0; k < MLP_IN; ++k) tc_put(TB, 64 + k, t, 128, v[k]);
+        }
+        // ---- forward: layer 1 (K = 16), bias + ReLU into H1 and H1^T
+        uint64_t m1 = 0, m2 = 0;
+        if (!tt_mma(tmem, X, 16, tsm + TT_W1, 16, 1, id64, false, &bar, phase, &s_fail)) break;
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            tc_ld16(tmem + lanes + c, v);
+            uint32_t q[8];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float z = v[i] + b1[c + i];
+                m1 |= (uint64_t)(z > 0.f) << (c + i);
+                v[i] = fmaxf(z, 0.f);
+                tc_put(TB, c + i, t, 128, v[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) q[i] = pack_bf16(v[2 * i], v[2 * i + 1]);
+            *reinterpret_cast<uint4 *>(H1 + tc_off(t, c, 64)) = make_uint4(q[0], q[1], q[2], q[3]);
+            *reinterpret_cast<uint4 *>(H1 + tc_off(t, c + 8, 64)) = make_uint4(q[4], q[5], q[6], q[7]);
+        }
+        // ---- layer 2 (K = 64): H2 and H2^T
+        if (!tt_mma(tmem + 64, H1, 64, tsm + TT_W2, 64, 4, id64, false, &bar, phase, &s_fail)) break;
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            tc_ld16(tmem + lanes + 64 + c, v);
+            uint32_t q[8];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float z = v[i] + b2[c + i];
+                m2 |= (uint64_t)(z > 0.f) << (c + i);
+                v[i] = fmaxf(z, 0.f);
+                tc_put(TH2, c + i, t, 128, v[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) q[i] = pack_bf16(v[2 * i], v[2 * i + 1]);
+            *reinterpret_cast<uint4 *>(H2 + tc_off(t, c, 64)) = make_uint4(q[0], q[1], q[2], q[3]);
+            *reinterpret_cast<uint4 *>(H2 + tc_off(t, c + 8, 64)) = make_uint4(q[4], q[5], q[6], q[7]);
+        }
+        // ---- layer 3 (K = 64, N = 16): output error dY = (y - t) / n into dY and dY^T
+        if (!tt_mma(tmem + 128, H2, 64, tsm + TT_W3, 64, 4, id16, false, &bar, phase, &s_fail)) break;
+        {
+            float v[16];
+            tc_ld16(tmem + lanes + 128, v);
+            float dy[MLP_OUT] = {0.f, 0.f, 0.f};
+            if (r < n) {
+#pragma unroll
+                for (int o = 0; o < MLP_OUT; ++o) {
+                    const float raw = target[3 * R + o] - feat[(int64_t)MLP_IN * R + 3 + o];  // dv - dv_prev
+                    const float tn = (raw - my[o]) / sy[o];
+                    const float e = (v[o] + b3[o]) - tn;
+                    loss += (double)e * (double)e;
+                    dy[o] = e * inv_n;
+                }
+            }
+            *reinterpret_cast<uint4 *>(DY + tc_off(t, 0, 16)) =
+                make_uint4(pack_bf16(dy[0], dy[1]), pack_bf16(dy[2], 0.f), 0u, 0u);
+#pragma unroll
+            for (int o = 0; o < MLP_OUT; ++o) {
+                tc_put(TDY, o, t, 128, dy[o]);
+                const float s_ = tt_warp_sum(dy[o]);
+                if (lane == 0) sdb[warp][2 * MLP_HID + o] += s_;
+            }
+        }
+        // ---- dH2 = dY W3 (K = 16): dZ2 = dH2 [Z2 > 0] into dZ2 and dZ2^T (TZ rows 0..63)
+        if (!tt_mma(tmem, DY, 16, tsm + TT_W3T, 16, 1, id64, false, &bar, phase, &s_fail)) break;
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            tc_ld16(tmem + lanes + c, v);
+            uint32_t q[8];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                v[i] = ((m2 >> (c + i)) & 1u) ? v[i] : 0.f;
+                tc_put(TZ, c + i, t, 128, v[i]);
+                const float s_ = tt_warp_sum(v[i]);
+                if (lane == 0) sdb[warp][MLP_HID + c + i] += s_;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) q[i] = pack_bf16(v[2 * i], v[2 * i + 1]);
+            *reinterpret_cast<uint4 *>(DZ2 + tc_off(t, c, 64)) = make_uint4(q[0], q[1], q[2], q[3]);
+            *reinterpret_cast<uint4 *>(DZ2 + tc_off(t, c + 8, 64)) = make_uint4(q[4], q[5], q[6], q[7]);
+        }
+        // ---- dH1 = dZ2 W2 (K = 64): dZ1 = dH1 [Z1 > 0] into dZ1^T (TZ rows 64..127)
+        if (!tt_mma(tmem + 64, DZ2, 64, tsm + TT_W2T, 64, 4, id64, false, &bar, phase, &s_fail)) break;
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            tc_ld16(tmem + lanes + 64 + c, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                v[i] = ((m1 >> (c + i)) & 1u) ? v[i] : 0.f;
+                tc_put(TZ, 64 + c + i, t, 128, v[i]);
+                const float s_ = tt_warp_sum(v[i]);
+                if (lane == 0) sdb[warp][c + i] += s_;
+            }
+        }
+        // ---- weight gradients over the tile's rows (K = 128), accumulated in tensor memory
+        if (!tt_mma(tmem + TT_GW12, TZ, 128, TB, 128, 8, id80, !first, &bar, phase, &s_fail)) break;
+        if (!tt_mma(tmem + TT_GW3, TH2, 128, TDY, 128, 8, id16, !first, &bar, phase, &s_fail)) break;
+        first = false;
+    }
+    // ---- this CTA's partials: dW2 (rows 0..63, columns 0..63 of the first gradient),
+    // dW1 (rows 64..127, columns 64..75), dW3^T (rows 0..63 of the second)
+    float *out = part + (int64_t)blockIdx.x * PC_MLP_NPARAMS;
+    if (!s_fail) {
+        if (warp < 2) {
+            const int i = 32 * warp + lane;  // dW2 row (output unit) / dW3^T row (hidden unit)
+#pragma unroll
+            for (int c = 0; c < 64; c += 16) {
+                float v[16];
+                tc_ld16(tmem + lanes + TT_GW12 + c, v);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) out[OFF_W2 + i * MLP_HID + c + k] = first ? 0.f : v[k];
+            }
+            float w[16];
+            tc_ld16(tmem + lanes + TT_GW3, w);
+#pragma unroll
+            for (int o = 0; o < MLP_OUT; ++o) out[OFF_W3 + o * MLP_HID + i] = first ? 0.f : w[o];
+        } else {
+            const int o = 32 * (warp - 2) + lane;  // dW1 row (hidden unit)
+            float v[16];
+            tc_ld16(tmem + lanes + TT_GW12 + 64, v);
+#pragma unroll
+            for (int k = 0; k < MLP_IN; ++k) out[OFF_W1 + o * MLP_IN + k] = first ? 0.f : v[k];
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    if (lane == 0) sloss[warp] = loss;
+    // every tensor-memory read of this CTA is complete before the columns are released
+    tc_fence_before();
+    __syncthreads();
+    for (int j = t; j < 2 * MLP_HID + MLP_OUT; j += TT_THREADS) {
+        float s_ = 0.f;
+        for (int w = 0; w < 4; ++w) s_ += sdb[w][j];
+        const int dst = j < MLP_HID ? OFF_B1 + j : j < 2 * MLP_HID ? OFF_B2 + (j - MLP_HID) : OFF_B3 + (j - 2 * MLP_HID);
+        out[dst] = s_;
+    }
+    if (t == 0) {
+        loss_part[blockIdx.x] = sloss[0] + sloss[1] + sloss[2] + sloss[3];
+        if (s_fail) pc_set_err(err, PC_DERR_TIMEOUT);
+    }
+    if (warp == 0) tc_dealloc(tmem, TT_TMEM_COLS);
 }
 
 // grad = sum of the CTA partials in CTA order (FP64 accumulation); with adam != 0 also the
@@ -731,9 +649,9 @@ struct pc_mlp {
     double *stat_part = nullptr;
     float *m = nullptr, *v = nullptr;  // Adam moments
     int64_t t = 0;                     // Adam steps taken
+    uint32_t *err = nullptr;           // timeout flag of the training products
+    uint32_t *h_err = nullptr;         // pinned mirror
 };
-
-static size_t train_smem_bytes() { return sizeof(MlpTrainSmem); }
 
 extern "C" pc_status pc_mlp_create(pc_mlp **out)
 {
@@ -750,9 +668,12 @@ extern "C" pc_status pc_mlp_create(pc_mlp **out)
     if ((e = cudaDeviceGetAttribute(&M->num_sms, cudaDevAttrMultiProcessorCount, M->device)) != cudaSuccess)
         return fail(e, "cudaDeviceGetAttribute");
     M->max_parts = 2 * M->num_sms;
-    if ((e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)train_smem_bytes())) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TT_SMEM)) !=
+        cudaSuccess)
         return fail(e, "cudaFuncSetAttribute");
+    if ((e = cudaMalloc(&M->err, sizeof(uint32_t))) != cudaSuccess) return fail(e, "cudaMalloc");
+    if ((e = cudaMemset(M->err, 0, sizeof(uint32_t))) != cudaSuccess) return fail(e, "cudaMemset");
+    if ((e = cudaMallocHost(&M->h_err, sizeof(uint32_t))) != cudaSuccess) return fail(e, "cudaMallocHost");
     if ((e = cudaMalloc(&M->part, sizeof(float) * PC_MLP_NPARAMS * (size_t)M->max_parts)) != cudaSuccess)
         return fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&M->loss_part, sizeof(double) * (size_t)M->max_parts)) != cudaSuccess)
@@ -779,6 +700,8 @@ extern "C" pc_status pc_mlp_destroy(pc_mlp *M)
     cudaFree(M->stat_part);
     cudaFree(M->m);
     cudaFree(M->v);
+    cudaFree(M->err);
+    if (M->h_err) cudaFreeHost(M->h_err);
     delete M;
     return PC_OK;
 }
@@ -846,10 +769,11 @@ static pc_status mlp_grad_impl(pc_mlp *M, int64_t n, const int32_t *rows, const 
                                const pc_adam_opts *o, double *loss, cudaStream_t st)
 {
     if (!M || n <= 0 || !params || !stats || !feat || !target) return PC_ERR_ARG;
-    const int64_t tiles = (n + MLP_TILE - 1) / MLP_TILE;
-    const int grid = (int)std::min<int64_t>(tiles, M->max_parts);
-    MLP_LAUNCH(mlp_train_kernel, grid, MLP_THREADS, train_smem_bytes(), st, n, rows, params, stats, feat, target,
-               M->part, M->loss_part);
+    const int64_t tiles = (n + TT_ROWS - 1) / TT_ROWS;
+    // one CTA per SM at most: each holds all of its SM's tensor-memory columns
+    const int grid = (int)std::min<int64_t>(tiles, M->num_sms);
+    MLP_LAUNCH(mlp_train_kernel, grid, TT_THREADS, TT_SMEM, st, n, rows, params, stats, feat, target, M->part,
+               M->loss_part, M->err);
     float lr = 0.f, b1 = 0.f, b2 = 0.f, eps = 0.f, bc1 = 1.f, bc2 = 1.f;
     if (adam) {
         M->t += 1;
@@ -865,8 +789,13 @@ static pc_status mlp_grad_impl(pc_mlp *M, int64_t n, const int32_t *rows, const 
     if (loss) {
         MLP_LAUNCH(mlp_loss_sum_kernel, 1, 32, 0, st, grid, M->loss_part, M->loss);
         PC_CUDA_TRY(cudaMemcpyAsync(M->h_loss, M->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+        PC_CUDA_TRY(cudaMemcpyAsync(M->h_err, M->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         PC_CUDA_TRY(cudaStreamSynchronize(st));
         *loss = 0.5 * *M->h_loss / (double)n;
+        if (*M->h_err) {  // a product wait gave up (in this or an earlier unsynchronised call)
+            PC_CUDA_TRY(cudaMemsetAsync(M->err, 0, sizeof(uint32_t), st));
+            return PC_ERR_TIMEOUT;
+        }
     }
     return PC_OK;
 }
