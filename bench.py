@@ -488,7 +488,7 @@ def run_batched(args):
         torch.cuda.synchronize()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = pc.pc_launch_count(cl.ctx) - launches0
-    bps, order, width, tune_ms = pc.pc_batched_config(cl.ctx)
+    grid, order, width, grid_sizes, tune_ms = pc.pc_batched_config(cl.ctx)
     its = np.array(its)
     seq = None
     if not args.no_sequential:
@@ -517,8 +517,8 @@ def run_batched(args):
                       "l2": f"matrix {len(u.tris) * 13 * 40 / 1e6 / 2:.0f} MB (L2 is 129 MB)",
                       "iters_per_garment_min": int(its.min()), "iters_per_garment_mean": float(its.mean()),
                       "iters_per_garment_max": int(its.max()), "max_rel_res": float(max(rels)),
-                      "autotuned_ctas_per_sm": bps, "autotuned_spmv_order": ["strided", "chunked"][order],
-                      "autotuned_stage_blocks_per_row": width,
+                      "autotuned_grid_ctas": grid, "autotuned_spmv_order": ["strided", "chunked"][order],
+                      "autotuned_stage_blocks_per_row": width, "autotune_grids": grid_sizes,
                       "autotune_ms": {f"{w_} blocks/row {o_}": tune_ms[w_][i_] for w_ in (14, 18)
                                       for i_, o_ in enumerate(("strided", "chunked"))}},
            "sequential_steps_per_s": seq, "gpu_launches": int(launches), "clocks": clk.summary()}

@@ -301,7 +301,7 @@ PC_API pc_status pc_get_solution64(pc_ctx *ctx, double *dv64, void *stream);
  * continue. The launch is cooperative (all CTAs co-resident) with bounded grid-wide
  * waits (PC_ERR_TIMEOUT instead of a hang). On the first call for a matrix shape an
  * autotuner times short solves for each tile and schedule (the SpMV phase's stage width
- * x its entry order x 1..4 CTAs per SM) and keeps the fastest
+ * x its entry order x the grid: 16, 32, 64 CTAs or 1..4 per SM) and keeps the fastest
  * (pc_batched_config reports the choice). info: host array of n_inst results, may be
  * NULL. Returns the first non-OK instance status. Synchronizes `stream`.
  * (The paper solves one garment system per step; batching is this library's extension.) */
@@ -309,14 +309,15 @@ PC_API pc_status pc_pcg_solve_batched(pc_ctx *ctx, const pc_bsr *A, const float 
                                       const float *b, float *dv, int32_t n_inst, const int32_t *inst_rows,
                                       const pc_solve_opts *opts, pc_solve_info *info, void *stream);
 
-/* Tile and schedule chosen by the batched autotuner: CTAs per SM (0 if not tuned yet),
- * the SpMV entry order (0: strided, CTA b takes entries b, b+G, ...; 1: contiguous
- * chunks), the SpMV phase's stage width in blocks per row of a 32-row tile (14 or 18),
- * and the timings (ms) of every candidate,
- * tune_ms[8 * (width == 18) + 4 * order + (CTAs per SM - 1)] (0 where not tried: a shape
- * that does not fit the SM). Host pointers, may be NULL. */
-PC_API pc_status pc_batched_config(pc_ctx *ctx, int32_t *blocks_per_sm, int32_t *spmv_order, int32_t *stage_blocks,
-                                   float *tune_ms);
+/* Tile and schedule chosen by the batched autotuner: the grid in CTAs (0 if not tuned
+ * yet), the SpMV entry order (0: strided, CTA b takes entries b, b+G, ...; 1: contiguous
+ * chunks), the SpMV phase's stage width in blocks per row of a 32-row tile (14 or 18), the
+ * seven candidate grid sizes (grid_sizes[7]: 16, 32 and 64 CTAs where that is below one
+ * per SM, else 0; then 1..4 CTAs per SM) and the timings (ms) of every candidate,
+ * tune_ms[14 * (width == 18) + 7 * order + grid index] (0 where not tried: a grid that
+ * does not fit). Host pointers, may be NULL. */
+PC_API pc_status pc_batched_config(pc_ctx *ctx, int32_t *grid, int32_t *spmv_order, int32_t *stage_blocks,
+                                   int32_t *grid_sizes, float *tune_ms);
 
 /* Cycle budget of each grid-barrier wait in the persistent batched solver and in the
  * fused PCG update of pc_pcg_solve / pc_step (software barriers spinning on a generation

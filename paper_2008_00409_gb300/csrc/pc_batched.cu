@@ -950,6 +950,8 @@ __global__ void bt_state_update_kernel(int V, const int32_t *row_inst, const bt_
 
 // ------------------------------------------------------------------------- host side
 
+#define BT_GRIDS 7  // grid candidates: 16, 32, 64 CTAs (below one per SM), then 1..4 per SM
+
 struct pc_batched_state {
     int32_t *row_inst = nullptr;   // [V]
     double *part = nullptr;        // [(ntiles + max_inst) * 3]
@@ -958,12 +960,14 @@ struct pc_batched_state {
     bt_global *g = nullptr;
     int32_t *inst_rows = nullptr;  // [max_inst + 1]
     int max_inst = 0;
-    int blocks_per_sm = 0;         // autotuned launch shape (0 = not tuned yet)
+    int blocks_per_sm = 0;         // autotuned launch shape: CTAs per SM, rounded up (0 = not tuned yet)
+    int grid = 0;                  // autotuned launch shape: CTAs in the grid
     int spmv_order = 0;            // autotuned SpMV entry order: 0 strided, 1 chunked
     int capr = SP_CAP_PER_ROW;     // autotuned stage width of the SpMV phase (blocks per row)
     int64_t tuned_nnzb = -1;
     int tuned_inst = -1;
-    float tune_ms[2][2][5] = {};    // [stage width 14 / 18][order][CTAs per SM] timings of the tuning runs
+    int tune_grid[BT_GRIDS] = {};   // candidate grid sizes (CTAs; 0 = unused slot)
+    float tune_ms[2][2][BT_GRIDS] = {};  // [stage width 14 / 18][order][grid] timings of the tuning runs
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream the step graph is captured on
 };
@@ -983,12 +987,12 @@ static pc_status bt_prepare(pc_ctx *c, pc_batched_state **out)
 // more tiles instead of reading them from global memory.
 static int bt_capr(int i) { return i == 0 ? SP_CAP_PER_ROW : SP_CAPR_WIDE; }
 
-static pc_status bt_launch(pc_ctx *c, pc_batched_state *B, const BtArgs &args, bool diff, int blocks_per_sm,
-                           int capr, cudaStream_t st)
+static pc_status bt_launch(pc_ctx *c, pc_batched_state *B, const BtArgs &args, bool diff, int grid, int capr,
+                           cudaStream_t st)
 {
     const bool wide = capr > SP_CAP_PER_ROW;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(c->num_sms * blocks_per_sm));
+    cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(SP_THREADS);
     cfg.dynamicSmemBytes = wide ? SpShape<SP_CAPR_WIDE>::smem_bytes : SpShape<SP_CAP_PER_ROW>::smem_bytes;
     cfg.stream = st;
@@ -1025,7 +1029,7 @@ static int bt_max_blocks_per_sm(bool diff, int capr)
 // Solve part shared by pc_pcg_solve_batched and pc_step_batched (stream-ordered, no
 // host synchronisation, so it can be captured).
 static pc_status bt_enqueue(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, const float *vals, const float *dres,
-                            const float *b, float *dv, int n_inst, const pc_solve_opts &o, int blocks_per_sm,
+                            const float *b, float *dv, int n_inst, const pc_solve_opts &o, int grid,
                             int spmv_order, int capr, cudaStream_t st)
 {
     const int V = c->V;
@@ -1072,7 +1076,7 @@ static pc_status bt_enqueue(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, con
     a.refresh_every = o.refresh_every;
     a.spmv_chunked = spmv_order;
     a.bar_wait = c->bar_wait_cycles > 0 ? (long long)c->bar_wait_cycles : SP_WAIT_BUDGET;
-    return bt_launch(c, B, a, dres != nullptr, blocks_per_sm, capr, st);
+    return bt_launch(c, B, a, dres != nullptr, grid, capr, st);
 }
 
 static pc_status bt_setup_instances(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, int n_inst,
@@ -1095,12 +1099,14 @@ static pc_status bt_setup_instances(pc_ctx *c, pc_batched_state *B, const pc_bsr
 
 // Autotuner: on the first solve of a given shape, time a short solve (fixed iteration
 // budget) for each tile and schedule choice -- the SpMV phase's stage width (14 or 18
-// blocks per row of a 32-row tile) x its entry order (strided or chunked) x co-resident
-// CTAs per SM (1..4, as far as they fit) -- and keep the fastest.
+// blocks per row of a 32-row tile) x its entry order (strided or chunked) x the grid
+// (16, 32 or 64 CTAs, where that is below one per SM: a small system's grid barriers are
+// cheaper with fewer CTAs; then 1..4 co-resident CTAs per SM, as far as they fit) -- and
+// keep the fastest.
 static pc_status bt_autotune(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, const float *vals, const float *dres,
                              const float *b, int n_inst, const pc_solve_opts &o, cudaStream_t st)
 {
-    if (B->blocks_per_sm > 0 && B->tuned_nnzb == A->nnzb && B->tuned_inst == n_inst) return PC_OK;
+    if (B->grid > 0 && B->tuned_nnzb == A->nnzb && B->tuned_inst == n_inst) return PC_OK;
     pc_solve_opts t = o;
     t.max_iter = std::min(o.max_iter, 60);
     t.tol = 1e-30;  // run the whole budget
@@ -1110,14 +1116,21 @@ static pc_status bt_autotune(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, co
     PC_CUDA_TRY(cudaEventCreate(&e0));
     PC_CUDA_TRY(cudaEventCreate(&e1));
     float *scratch_dv = c->rhs32;  // float[V][3], a zero guess
+    for (int g = 0; g < BT_GRIDS; ++g) B->tune_grid[g] = 0;
+    for (int g = 0; g < 3; ++g)
+        if ((16 << g) < c->num_sms) B->tune_grid[g] = 16 << g;
     for (int w = 0; w < 2; ++w) {
         const int capr = bt_capr(w);
         const int maxb = std::min(4, bt_max_blocks_per_sm(dres != nullptr, capr));
         for (int order = 0; order < 2; ++order)
-            for (int nb = 1; nb <= maxb; ++nb) {
+            for (int gi = 0; gi < BT_GRIDS; ++gi) {
+                const int grid = gi < 3 ? B->tune_grid[gi] : (gi - 2 <= maxb ? (gi - 2) * c->num_sms : 0);
+                if (gi >= 3) B->tune_grid[gi] = (gi - 2) * c->num_sms;
+                B->tune_ms[w][order][gi] = 0.f;
+                if (grid <= 0 || maxb < 1) continue;
                 PC_CUDA_TRY(cudaMemsetAsync(scratch_dv, 0, sizeof(float) * 3 * (size_t)c->V, st));
                 PC_CUDA_TRY(cudaEventRecord(e0, st));
-                pc_status s = bt_enqueue(c, B, A, vals, dres, b, scratch_dv, n_inst, t, nb, order, capr, st);
+                pc_status s = bt_enqueue(c, B, A, vals, dres, b, scratch_dv, n_inst, t, grid, order, capr, st);
                 PC_CUDA_TRY(cudaEventRecord(e1, st));
                 if (s != PC_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
                 PC_CUDA_TRY(cudaEventSynchronize(e1));
@@ -1126,14 +1139,15 @@ static pc_status bt_autotune(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, co
                 if (aborted) { cudaEventDestroy(e0); cudaEventDestroy(e1); return PC_ERR_TIMEOUT; }
                 float ms = 0.f;
                 PC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-                B->tune_ms[w][order][nb] = ms;
-                if (ms < best) { best = ms; best_b = nb; best_order = order; best_capr = capr; }
+                B->tune_ms[w][order][gi] = ms;
+                if (ms < best) { best = ms; best_b = grid; best_order = order; best_capr = capr; }
             }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best_b < 1) return PC_ERR_CUDA;  // no launch shape fits an SM
-    B->blocks_per_sm = best_b;
+    B->grid = best_b;
+    B->blocks_per_sm = (best_b + c->num_sms - 1) / c->num_sms;
     B->spmv_order = best_order;
     B->capr = best_capr;
     B->tuned_nnzb = A->nnzb;
@@ -1182,7 +1196,7 @@ extern "C" pc_status pc_pcg_solve_batched(pc_ctx *ctx, const pc_bsr *A, const fl
     PC_TRY(bt_setup_instances(ctx, B, A, n_inst, inst_rows, st));
     PC_TRY(bt_autotune(ctx, B, A, vals, dres, b, n_inst, o, st));
     PC_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), st));
-    PC_TRY(bt_enqueue(ctx, B, A, vals, dres, b, dv, n_inst, o, B->blocks_per_sm, B->spmv_order, B->capr, st));
+    PC_TRY(bt_enqueue(ctx, B, A, vals, dres, b, dv, n_inst, o, B->grid, B->spmv_order, B->capr, st));
     return bt_collect(ctx, B, n_inst, info, st);
 }
 
@@ -1193,19 +1207,21 @@ extern "C" pc_status pc_set_barrier_wait(pc_ctx *ctx, int64_t cycles)
     return PC_OK;
 }
 
-extern "C" pc_status pc_batched_config(pc_ctx *ctx, int32_t *blocks_per_sm, int32_t *spmv_order,
-                                       int32_t *stage_blocks, float *tune_ms /*[16]*/)
+extern "C" pc_status pc_batched_config(pc_ctx *ctx, int32_t *grid, int32_t *spmv_order, int32_t *stage_blocks,
+                                       int32_t *grid_sizes /*[7]*/, float *tune_ms /*[28]*/)
 {
     if (!ctx) return PC_ERR_ARG;
     pc_batched_state *B = bt_state(ctx);
     if (!B) return PC_ERR_CUDA;
-    if (blocks_per_sm) *blocks_per_sm = B->blocks_per_sm;
+    if (grid) *grid = B->grid;
     if (spmv_order) *spmv_order = B->spmv_order;
     if (stage_blocks) *stage_blocks = B->capr;
+    if (grid_sizes)
+        for (int g = 0; g < BT_GRIDS; ++g) grid_sizes[g] = B->tune_grid[g];
     if (tune_ms)
         for (int w = 0; w < 2; ++w)
             for (int order = 0; order < 2; ++order)
-                for (int i = 0; i < 4; ++i) tune_ms[8 * w + 4 * order + i] = B->tune_ms[w][order][i + 1];
+                for (int g = 0; g < BT_GRIDS; ++g) tune_ms[2 * BT_GRIDS * w + BT_GRIDS * order + g] = B->tune_ms[w][order][g];
     return PC_OK;
 }
 
@@ -1234,7 +1250,7 @@ extern "C" pc_status pc_step_batched(pc_ctx *ctx, float *x, float *v, const pc_c
     PC_TRY(bt_setup_instances(ctx, B, &A, n_inst, inst_rows, st));
     if (opts->warm_start != PC_WARM_PREV || !ctx->has_prev_dv)
         PC_CUDA_TRY(cudaMemsetAsync(ctx->A_dv, 0, sizeof(float) * 3 * (size_t)ctx->V, st));
-    if (B->blocks_per_sm == 0 || B->tuned_nnzb < 0) {
+    if (B->grid == 0 || B->tuned_nnzb < 0) {
         // tune on this step's system (values assembled once outside the graph)
         PC_TRY(pc_assemble_values(ctx, &A, x, v, contacts, opts->h, ctx->A_vals, ctx->A_b, ctx->A_dres, stream));
         PC_TRY(bt_autotune(ctx, B, &A, ctx->A_vals, ctx->A_dres, ctx->A_b, n_inst, o, st));
@@ -1248,7 +1264,7 @@ extern "C" pc_status pc_step_batched(pc_ctx *ctx, float *x, float *v, const pc_c
     PC_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     pc_status s = pc_assemble_values(ctx, &A, x, v, contacts, opts->h, ctx->A_vals, ctx->A_b, ctx->A_dres, (void *)cs);
     if (s == PC_OK)
-        s = bt_enqueue(ctx, B, &A, ctx->A_vals, ctx->A_dres, ctx->A_b, ctx->A_dv, n_inst, o, B->blocks_per_sm,
+        s = bt_enqueue(ctx, B, &A, ctx->A_vals, ctx->A_dres, ctx->A_b, ctx->A_dv, n_inst, o, B->grid,
                        B->spmv_order, B->capr, cs);
     if (s == PC_OK) s = bt_update_state(ctx, B, x, v, opts->h, cs);
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);

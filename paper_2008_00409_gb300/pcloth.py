@@ -107,7 +107,7 @@ def _load():
                                        c_void_p, P(pc_solve_opts), c_void_p, c_void_p]
     L.pc_step_batched.argtypes = [c_void_p, c_void_p, c_void_p, P(pc_contacts), c_int32, c_void_p, P(pc_step_opts),
                                   c_void_p, c_void_p]
-    L.pc_batched_config.argtypes = [c_void_p, P(c_int32), P(c_int32), P(c_int32), c_void_p]
+    L.pc_batched_config.argtypes = [c_void_p, P(c_int32), P(c_int32), P(c_int32), c_void_p, c_void_p]
     L.pc_set_barrier_wait.argtypes = [c_void_p, c_int64]
     L.pc_get_prev_dv.argtypes = [c_void_p, c_void_p, P(c_int32), c_void_p]
     L.pc_set_prev_dv.argtypes = [c_void_p, c_void_p, c_void_p]
@@ -322,14 +322,15 @@ def pc_step_batched(ctx, x, v, pairs, w, inst_rows, opts: pc_step_opts, stream=N
 
 
 def pc_batched_config(ctx):
-    """(CTAs per SM, SpMV entry order 0 strided / 1 chunked, stage width in blocks per row,
-    timings {width: [order][CTAs per SM - 1]} in ms)."""
-    bps, order, width = c_int32(), c_int32(), c_int32()
-    ms = (c_float * 16)()
-    _check(_lib.pc_batched_config(ctx, ctypes.byref(bps), ctypes.byref(order), ctypes.byref(width),
-                                  ctypes.cast(ms, c_void_p)), "pc_batched_config")
-    return bps.value, order.value, width.value, {14: [list(ms[0:4]), list(ms[4:8])],
-                                                 18: [list(ms[8:12]), list(ms[12:16])]}
+    """(grid in CTAs, SpMV entry order 0 strided / 1 chunked, stage width in blocks per row,
+    candidate grid sizes [7], timings {width: [order][grid index]} in ms)."""
+    grid, order, width = c_int32(), c_int32(), c_int32()
+    sizes = (c_int32 * 7)()
+    ms = (c_float * 28)()
+    _check(_lib.pc_batched_config(ctx, ctypes.byref(grid), ctypes.byref(order), ctypes.byref(width),
+                                  ctypes.cast(sizes, c_void_p), ctypes.cast(ms, c_void_p)), "pc_batched_config")
+    return grid.value, order.value, width.value, list(sizes), {14: [list(ms[0:7]), list(ms[7:14])],
+                                                               18: [list(ms[14:21]), list(ms[21:28])]}
 
 
 def pc_proximity_query(ctx, x, delta, pairs, w, stream=None):

@@ -41,15 +41,16 @@ def test_batched_solve_matches_oracle_and_single_solves(pc):
                                         dv, u.inst_rows, opts)
     assert st == pc.PC_OK
     got = _np(dv).reshape(-1, 3)
-    bps, order, width, ms = pc.pc_batched_config(cl.ctx)
-    assert 1 <= bps <= 4 and order in (0, 1) and width in (14, 18) and ms[width][order][bps - 1] > 0
-    # the autotuner timed both stage widths (tile shapes) and both entry orders, and kept
-    # the fastest candidate
+    grid, order, width, sizes, ms = pc.pc_batched_config(cl.ctx)
+    assert grid in sizes and order in (0, 1) and width in (14, 18)
+    gi = sizes.index(grid)
+    assert ms[width][order][gi] > 0
+    # the autotuner timed both stage widths (tile shapes), both entry orders and several
+    # grids, and kept the fastest candidate
     for w_ in (14, 18):
-        assert any(t > 0 for row in ms[w_] for t in row), w_
-        assert all(any(t > 0 for t in ms[w_][o]) for o in (0, 1)), w_
+        assert all(sum(t > 0 for t in ms[w_][o]) >= 2 for o in (0, 1)), w_
     tried = [t for w_ in (14, 18) for row in ms[w_] for t in row if t > 0]
-    assert len(tried) >= 4 and ms[width][order][bps - 1] == min(tried)
+    assert len(tried) >= 8 and ms[width][order][gi] == min(tried)
     for k, part in enumerate(u.parts):
         r0, r1 = u.inst_rows[k], u.inst_rows[k + 1]
         # oracle on the garment alone, at the same state
