@@ -137,7 +137,27 @@ typedef struct {
                             kernel with a grid-wide barrier (z stays in registers; used when
                             every thread can carry its rows, up to about 0.9M rows on GB300);
                             0: two kernels. Same method, same stop tests. */
+    int32_t schedule;    /* PC_SCHED_AUTO (default), PC_SCHED_GRID or PC_SCHED_CLUSTER */
 } pc_solve_opts;
+
+/* How pc_pcg_solve (and pc_step, pc_pcg_solve_static) runs the iterations.
+ * PC_SCHED_CLUSTER: the whole solve is one launch of one thread-block cluster (16 CTAs,
+ * one per SM, else 8 where 16 cannot be co-scheduled). Each CTA keeps a contiguous range
+ * of rows -- their 3x3 blocks, diagonal data and vectors -- in shared memory for the
+ * length of the solve, gathers its neighbours' entries from the other CTAs' shared
+ * memory, and the dot products meet at cluster barriers: two per iteration, no kernel
+ * boundary. Same method and stop tests as the grid schedule (same preconditioners, FP64
+ * residual replacement in PC_PREC_MIXED, the FP64 iterate folded every check_every
+ * iterations); the first residual is formed in FP64 in both precisions, and storage and
+ * fuse do not apply. It takes systems up to about 6,000 rows at cloth density (at most
+ * 1,024 rows per CTA and every CTA's blocks within its shared memory); larger ones return
+ * PC_ERR_CAPACITY.
+ * PC_SCHED_GRID: kernels over the whole GPU, iterations launched from the host (the
+ * storage and fuse options apply).
+ * PC_SCHED_AUTO: the cluster schedule when the system fits it, else the grid schedule. */
+#define PC_SCHED_AUTO 0
+#define PC_SCHED_GRID 1
+#define PC_SCHED_CLUSTER 2
 
 /* PC_STORAGE_FULL: the products read the full BSR matrix.
  * PC_STORAGE_SYM: at the start of each pc_pcg_solve / pc_step the (bitwise symmetric)
@@ -572,6 +592,9 @@ PC_API pc_status pc_spmv_stats(pc_ctx *ctx, int64_t *launches, double *total_ms,
 /* Likewise for pc_step's assembly (pattern and values, Sec. 3.2.2): (steps timed, total
  * ms), then reset. */
 PC_API pc_status pc_assembly_stats(pc_ctx *ctx, int64_t *steps, double *total_ms);
+/* Likewise for solves run on the cluster schedule (PC_SCHED_CLUSTER): (solves timed,
+ * their PCG iterations, total ms of the solve kernel), then reset. */
+PC_API pc_status pc_cluster_stats(pc_ctx *ctx, int64_t *solves, int64_t *iters, double *total_ms);
 
 #ifdef __cplusplus
 }

@@ -76,7 +76,8 @@ def load(path, cloth, mlp=None):
 class StepLog:
     """Appends one JSON line per step: nnzb, PCG iterations, outer refinements, FP64
     relative residual, the guess the step started from, wall time, and (when the
-    context's profiling is on) assembly ms and SpMV GB/s since the previous line."""
+    context's profiling is on) assembly ms and, since the previous line, SpMV GB/s of the
+    grid schedule or microseconds per iteration of the cluster schedule (whichever ran)."""
 
     def __init__(self, path, cloth):
         self.path = path
@@ -84,11 +85,13 @@ class StepLog:
         self.t = time.perf_counter()
         self.asm = pc.pc_assembly_stats(cloth.ctx)
         self.spmv = pc.pc_spmv_stats(cloth.ctx)
+        self.cluster = pc.pc_cluster_stats(cloth.ctx)
 
     def record(self, step: int, info, status: int):
         now = time.perf_counter()
         asm = pc.pc_assembly_stats(self.cloth.ctx)
         spmv = pc.pc_spmv_stats(self.cloth.ctx)
+        cluster = pc.pc_cluster_stats(self.cloth.ctx)
         line = {"step": step, "status": int(status), "nnzb": int(info.nnzb), "iters": int(info.solve.iters),
                 "outer": int(info.solve.outer), "rel_res": float(info.solve.rel_res), "guess": int(info.guess),
                 "wall_ms": 1e3 * (now - self.t)}
@@ -99,6 +102,8 @@ class StepLog:
             nbytes = 40 * spmv[2] + 4 * (V + 1) + 36 * V + 32 * V
             line["spmv_us"] = 1e3 * spmv[1] / spmv[0]
             line["spmv_gbs"] = nbytes / (spmv[1] / spmv[0] / 1e3) / 1e9
+        if cluster[0] > 0 and cluster[1] > 0:
+            line["cluster_us_per_iter"] = 1e3 * cluster[2] / cluster[1]
         with open(self.path, "a") as fh:
             fh.write(json.dumps(line) + "\n")
         self.t = now

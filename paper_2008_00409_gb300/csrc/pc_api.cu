@@ -47,6 +47,18 @@ extern "C" pc_status pc_assembly_stats(pc_ctx *ctx, int64_t *steps, double *tota
     return PC_OK;
 }
 
+extern "C" pc_status pc_cluster_stats(pc_ctx *ctx, int64_t *solves, int64_t *iters, double *total_ms)
+{
+    if (!ctx) return PC_ERR_ARG;
+    if (solves) *solves = ctx->cl_solves;
+    if (iters) *iters = ctx->cl_iters;
+    if (total_ms) *total_ms = ctx->cl_ms;
+    ctx->cl_solves = 0;
+    ctx->cl_iters = 0;
+    ctx->cl_ms = 0.0;
+    return PC_OK;
+}
+
 extern "C" pc_status pc_step(pc_ctx *ctx, float *x, float *v, const pc_contacts *contacts, const pc_step_opts *opts,
                              float *dv_out, pc_step_info *info, void *stream)
 {

@@ -29,28 +29,10 @@
 #define RED_SLOTS 4
 #define BT_TILE 32  // rows per tile in every phase
 
-// local copy of the block reduction used by pc_spmv.cuh's kernel (not launched here)
 __device__ __forceinline__ double bt_warp_sum(double v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
-}
-__device__ __forceinline__ void block_sum_d(double *v, int n)
-{
-    __shared__ double s[RED_SLOTS][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int k = 0; k < n; ++k) {
-        double w = bt_warp_sum(v[k]);
-        if (lane == 0) s[k][warp] = w;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        for (int k = 0; k < n; ++k) {
-            double w = lane < nw ? s[k][lane] : 0.0;
-            v[k] = bt_warp_sum(w);
-        }
-    }
-    __syncthreads();
 }
 #include "pc_spmv.cuh"
 

@@ -35,8 +35,7 @@ __device__ __forceinline__ double ds_warp_sum(double v)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
-// block sum of n <= RED_SLOTS doubles in a fixed tree (thread 0 gets the totals); the
-// SpMV header below uses it for its p.q partial
+// block sum of n <= RED_SLOTS doubles in a fixed tree (thread 0 gets the totals)
 __device__ __forceinline__ void block_sum_d(double *v, int n)
 {
     __shared__ double s[RED_SLOTS][32];
@@ -372,11 +371,20 @@ __global__ void __launch_bounds__(DS_THREADS) ds_halo_kernel(int n_own, const in
 }
 
 // red[slot] = sum of n partials (stride apart) + sum of m extra partials, in a fixed order.
+// With `pair` the n partials are double-float pairs (float2 in the 8-byte slot; the
+// product kernel's p.q partials), else doubles.
 __global__ void ds_sum_kernel(int n, const double *__restrict__ part, int stride, int m,
-                              const double *__restrict__ extra, double *red, int slot)
+                              const double *__restrict__ extra, double *red, int slot, int pair)
 {
     double v[1] = {0.0};
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v[0] += part[(int64_t)i * stride];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (pair) {
+            const float2 w = reinterpret_cast<const float2 *>(part)[(int64_t)i * stride];
+            v[0] += pc_df_value(w.x, w.y);
+        } else {
+            v[0] += part[(int64_t)i * stride];
+        }
+    }
     for (int i = threadIdx.x; i < m; i += blockDim.x) v[0] += extra[i];
     block_sum_d(v, 1);
     if (threadIdx.x == 0) red[slot] = v[0];
@@ -807,7 +815,7 @@ static pc_status ds_residual(pc_dist *d, const pc_comm *comm, const float *dres,
                   d->halo_rp, d->halo_ci, d->halo_vals, dres, b, d->x64, d->dinv, d->r, d->z4, replace, d->partials);
     for (int k = 0; k < 3; ++k)
         DS_LAUNCH(d, ds_sum_kernel, 1, 256, 0, st, (int)g, d->partials + k, RED_SLOTS, 0, (const double *)nullptr,
-                  d->red, 1 + k);
+                  d->red, 1 + k, 0);
     return ds_allreduce(d, comm, 1, 3, st);
 }
 
@@ -859,13 +867,14 @@ static pc_status ds_iteration(pc_dist *d, const pc_comm *comm, const float *dres
         DS_LAUNCH(d, ds_halo_kernel<false>, g, DS_THREADS, 0, st, n, d->halo_rp, d->halo_ci, d->halo_vals,
                   (const float4 *)d->p_ext, d->q4, d->hpart, (const pc_scalars *)d->sc);
     DS_LAUNCH(d, ds_sum_kernel, 1, 256, 0, st, gs, d->partials + 3, RED_SLOTS, (int)g, (const double *)d->hpart,
-              d->red, 0);
+              d->red, 0, 1);
     PC_TRY(ds_allreduce(d, comm, 0, 1, st));
     DS_LAUNCH(d, ds_update_kernel, g, DS_THREADS, 0, st, n, d->x, (const float4 *)d->p_ext, d->r,
               (const float4 *)d->q4, d->dinv, d->z4, (const double *)d->red, d->partials, d->sc);
-    DS_LAUNCH(d, ds_sum_kernel, 1, 256, 0, st, (int)g, d->partials, RED_SLOTS, 0, (const double *)nullptr, d->red, 1);
+    DS_LAUNCH(d, ds_sum_kernel, 1, 256, 0, st, (int)g, d->partials, RED_SLOTS, 0, (const double *)nullptr, d->red, 1,
+              0);
     DS_LAUNCH(d, ds_sum_kernel, 1, 256, 0, st, (int)g, d->partials + 1, RED_SLOTS, 0, (const double *)nullptr, d->red,
-              2);
+              2, 0);
     PC_TRY(ds_allreduce(d, comm, 1, 2, st));
     DS_LAUNCH(d, ds_finish_kernel, 1, 1, 0, st, (const double *)d->red, d->sc);
     return PC_OK;

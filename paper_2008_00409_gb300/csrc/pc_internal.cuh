@@ -64,7 +64,7 @@ struct pc_scalars {
     int32_t done;     // 1 converged / stopped
     int32_t status;   // pc_status of the solve
     uint32_t counter; // last-block reduction ticket
-    uint32_t pad;
+    int32_t outer;    // FP64 residual replacements (the cluster solve reports them here)
 };
 
 // ------------------------------------------------------------------------- radix sort scratch
@@ -204,6 +204,10 @@ struct pc_ctx {
     double spmv_ms = 0.0;
     int64_t spmv_nnzb = 0;
     int64_t asm_steps = 0;         // pc_step calls timed (assembly: pattern + values)
+    int cl_size = 0;               // CTAs per cluster of the cluster solve (0: not queried, -1: none)
+    int64_t cl_solves = 0;         // cluster solves timed, their iterations and milliseconds
+    int64_t cl_iters = 0;
+    double cl_ms = 0.0;
     double asm_ms = 0.0;
     cudaEvent_t ev[2 * 64] = {};
     int ev_used = 0;
@@ -281,6 +285,13 @@ pc_status pc_warm_guess(pc_ctx *c, const pc_bsr *A, const float *v, float h, int
                         int32_t *guess, double *guess_res, double *guess_energy, double *guess_coef,
                         double *combo_energy, cudaStream_t st);
 void pc_mlp_ctx_free(pc_ctx *c);
+// The whole solve in one thread-block cluster (pc_cluster.cu). Runs when the system fits
+// the cluster's shared memory (*ran = true, returns the solve's status); otherwise
+// returns PC_OK with *ran = false, or PC_ERR_CAPACITY when `required`. Needs c->dinv
+// filled (and the pattern validated) for this matrix; `o` is normalised by the caller.
+pc_status pc_cluster_solve(pc_ctx *c, const pc_bsr *A, const float *vals, const float *dres, const float *b,
+                           float *dv, const pc_solve_opts &o, bool block, bool required, pc_solve_info *info,
+                           cudaStream_t st, bool *ran);
 
 inline int pc_bits_for(int64_t n)
 {
@@ -292,6 +303,58 @@ inline int pc_bits_for(int64_t n)
 // ------------------------------------------------------------------------- device helpers
 
 __device__ __forceinline__ void pc_set_err(uint32_t *err, uint32_t bit) { atomicOr(err, bit); }
+
+// ------------------------------------------------------------------------- double-float sums
+// GB300 issues FP64 at about 1/60 of its FP32 rate (and with long latency), so the
+// per-iteration dot-product reductions add their partial sums as unevaluated pairs of
+// floats, hi + lo (about 48 significant bits), with Knuth's error-free two-sum, and form
+// an FP64 value only once, in one thread. Each pair sum is commutative bit for bit, so an
+// xor butterfly leaves every lane with the same pair, and a fixed tree keeps every sum
+// reproducible.
+__device__ __forceinline__ void pc_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+// (hi, lo) += (h2, l2)
+__device__ __forceinline__ void pc_df_add(float &hi, float &lo, float h2, float l2)
+{
+    float s, e;
+    pc_two_sum(hi, h2, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, l2));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+__device__ __forceinline__ void pc_warp_sum_df(float &hi, float &lo)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        pc_df_add(hi, lo, h2, l2);
+    }
+}
+// Block sum of n <= 4 pairs in a fixed tree (warps, then warp 0 over the warp sums);
+// thread 0 gets the totals.
+__device__ __forceinline__ void pc_block_sum_df(float *hi, float *lo, int n)
+{
+    __shared__ float2 s_df[4][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k < n; ++k) {
+        pc_warp_sum_df(hi[k], lo[k]);
+        if (lane == 0) s_df[k][warp] = make_float2(hi[k], lo[k]);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int k = 0; k < n; ++k) {
+            float2 w = lane < nw ? s_df[k][lane] : make_float2(0.f, 0.f);
+            pc_warp_sum_df(w.x, w.y);
+            hi[k] = w.x;
+            lo[k] = w.y;
+        }
+    }
+    __syncthreads();
+}
+__device__ __forceinline__ double pc_df_value(float hi, float lo) { return (double)hi + (double)lo; }
 
 // lower_bound over a sorted uint64 array
 __device__ __forceinline__ int64_t pc_lower_bound_u64(const uint64_t *a, int64_t n, uint64_t key)

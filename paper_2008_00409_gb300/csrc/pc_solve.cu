@@ -84,6 +84,39 @@ static __device__ bool last_block_reduce(double *v, int n, double *partials, uin
     return true;
 }
 
+// last_block_reduce for n <= RED_SLOTS double-float pairs (float2 partials); the totals,
+// as pairs, in hi[] / lo[] of thread 0 of the last block.
+static __device__ bool last_block_reduce_df(float *hi, float *lo, int n, double *partials, uint32_t *counter)
+{
+    __shared__ bool s_last;
+    float2 *pf = reinterpret_cast<float2 *>(partials);
+    pc_block_sum_df(hi, lo, n);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < n; ++k) pf[(int64_t)blockIdx.x * RED_SLOTS + k] = make_float2(hi[k], lo[k]);
+        __threadfence();
+        uint32_t t = atomicAdd(counter, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    float ah[RED_SLOTS] = {0.f, 0.f, 0.f, 0.f}, al[RED_SLOTS] = {0.f, 0.f, 0.f, 0.f};
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
+        for (int k = 0; k < n; ++k) {
+            const float2 v = __ldcg(pf + (int64_t)i * RED_SLOTS + k);
+            pc_df_add(ah[k], al[k], v.x, v.y);
+        }
+    pc_block_sum_df(ah, al, n);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < n; ++k) {
+            hi[k] = ah[k];
+            lo[k] = al[k];
+        }
+        *counter = 0u;
+    }
+    return true;
+}
+
 #include "pc_spmv.cuh"
 #include "pc_spmv_sym.cuh"
 #include "pc_spmv_sell.cuh"
@@ -183,20 +216,26 @@ __global__ void dinv_kernel(int V, int64_t nnzb, const int32_t *__restrict__ rp,
 __device__ __forceinline__ float pcg_alpha(const double *partials, int n_pq, pc_scalars *sc)
 {
     __shared__ float s_alpha;
-    double v[1] = {0.0};
-    for (int i = threadIdx.x; i < n_pq; i += blockDim.x) v[0] += __ldcg(partials + (int64_t)i * RED_SLOTS + 3);
-    block_sum_d(v, 1);
+    const float2 *pf = reinterpret_cast<const float2 *>(partials);
+    float hi[1] = {0.f}, lo[1] = {0.f};
+    for (int i = threadIdx.x; i < n_pq; i += blockDim.x) {
+        const float2 v = __ldcg(pf + (int64_t)i * RED_SLOTS + 3);
+        pc_df_add(hi[0], lo[0], v.x, v.y);
+    }
+    pc_block_sum_df(hi, lo, 1);
     if (threadIdx.x == 0) {
-        const double pq = v[0];
-        double alpha = sc->rz / pq;
-        if (!(pq > 0.0) || !isfinite(alpha)) alpha = 0.0;
-        if (blockIdx.x == 0) {
-            sc->pq = pq;
-            sc->alpha = alpha;
-        }
-        s_alpha = (float)alpha;
+        // the quotient in FP32, the precision the iteration uses it in (an FP64 division
+        // in one thread is a long dependent chain on GB300's FP64 pipe)
+        const float pq = __fadd_rn(hi[0], lo[0]);
+        float alpha = (float)sc->rz / pq;
+        if (!(pq > 0.f) || !isfinite(alpha)) alpha = 0.f;
+        s_alpha = alpha;
     }
     __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->pq = pc_df_value(hi[0], lo[0]);
+        sc->alpha = (double)s_alpha;
+    }
     return s_alpha;
 }
 
@@ -272,14 +311,15 @@ __global__ void __launch_bounds__(EW_THREADS) pcg_update_kernel(int V, float *__
         }
     }
     pdl_trigger();
-    double v[2] = {(double)rz, (double)rr};
-    if (last_block_reduce(v, 2, partials, &sc->counter) && threadIdx.x == 0) {
-        double rz_new = v[0];
+    float hi[2] = {rz, rr}, lo[2] = {0.f, 0.f};
+    if (last_block_reduce_df(hi, lo, 2, partials, &sc->counter) && threadIdx.x == 0) {
+        const double rz_new = pc_df_value(hi[0], lo[0]), rr_new = pc_df_value(hi[1], lo[1]);
         const double pq = sc->pq;
-        sc->beta = rz_new / sc->rz;
+        sc->beta = (double)(__fadd_rn(hi[0], lo[0]) / (float)sc->rz);  // FP32, as the direction step uses it
         sc->rz = rz_new;
-        sc->rr = v[1];
+        sc->rr = rr_new;
         sc->iter += 1;
+        double v[2] = {rz_new, rr_new};
         if (!(pq > 0.0) || !isfinite(sc->alpha)) {
             sc->status = PC_ERR_NONFINITE;
             sc->done = 1;
@@ -522,11 +562,14 @@ __global__ void __launch_bounds__(FU_THREADS, FU_CTAS_PER_SM) pcg_update_dir_ker
             }
         }
     }
-    double v[2] = {(double)rz, (double)rr};
-    block_sum_d(v, 2);
-    if (threadIdx.x == 0) {
-        partials[(int64_t)blockIdx.x * RED_SLOTS] = v[0];
-        partials[(int64_t)blockIdx.x * RED_SLOTS + 1] = v[1];
+    float2 *pf = reinterpret_cast<float2 *>(partials);
+    {
+        float hi[2] = {rz, rr}, lo[2] = {0.f, 0.f};
+        pc_block_sum_df(hi, lo, 2);
+        if (threadIdx.x == 0) {
+            pf[(int64_t)blockIdx.x * RED_SLOTS] = make_float2(hi[0], lo[0]);
+            pf[(int64_t)blockIdx.x * RED_SLOTS + 1] = make_float2(hi[1], lo[1]);
+        }
     }
     if (!fu_grid_sync(bar, wait_budget)) {
         // a timeout outranks any status block 0 may record in this launch
@@ -538,37 +581,36 @@ __global__ void __launch_bounds__(FU_THREADS, FU_CTAS_PER_SM) pcg_update_dir_ker
         return;
     }
     // every CTA: the grid's r.z and r.r, summed in block order (the same value everywhere)
-    double t[2] = {0.0, 0.0};
+    float th[2] = {0.f, 0.f}, tl[2] = {0.f, 0.f};
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-        t[0] += __ldcg(partials + (int64_t)b * RED_SLOTS);
-        t[1] += __ldcg(partials + (int64_t)b * RED_SLOTS + 1);
+        const float2 a0 = __ldcg(pf + (int64_t)b * RED_SLOTS), a1 = __ldcg(pf + (int64_t)b * RED_SLOTS + 1);
+        pc_df_add(th[0], tl[0], a0.x, a0.y);
+        pc_df_add(th[1], tl[1], a1.x, a1.y);
     }
-    block_sum_d(t, 2);
-    __shared__ double s_beta;
-    if (threadIdx.x == 0) {
-        const double rz_new = t[0], beta = rz_new / rz_old;
-        s_beta = beta;
-        if (blockIdx.x == 0) {
-            const double pq = sc->pq;
-            sc->beta = beta;
-            sc->rz = rz_new;
-            sc->rr = t[1];
-            sc->iter += 1;
-            // status changes only from PC_OK, so a timeout another CTA recorded stays
-            int32_t st = PC_OK;
-            if (!(pq > 0.0) || !isfinite(sc->alpha)) st = PC_ERR_NONFINITE;
-            else if (!isfinite(t[1]) || !isfinite(beta)) st = PC_ERR_NONFINITE;
-            else if (sc->iter >= sc->max_iter && !(t[1] <= sc->tol2)) st = PC_ERR_NOT_CONVERGED;
-            if (st != PC_OK) atomicCAS(&sc->status, (int32_t)PC_OK, st);
-            if (st != PC_OK || t[1] <= sc->tol2) sc->done = 1;
-        }
-    }
+    pc_block_sum_df(th, tl, 2);
+    __shared__ float s_beta;
+    if (threadIdx.x == 0) s_beta = __fadd_rn(th[0], tl[0]) / (float)rz_old;  // FP32, as it is used
     __syncthreads();
-    const double beta_d = s_beta;
+    const float beta = s_beta;
+    // the scalars' FP64 bookkeeping while the other threads take the direction step
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double rz_new = pc_df_value(th[0], tl[0]), rr = pc_df_value(th[1], tl[1]);
+        const double pq = sc->pq;
+        sc->beta = (double)beta;
+        sc->rz = rz_new;
+        sc->rr = rr;
+        sc->iter += 1;
+        // status changes only from PC_OK, so a timeout another CTA recorded stays
+        int32_t st = PC_OK;
+        if (!(pq > 0.0) || !isfinite(sc->alpha)) st = PC_ERR_NONFINITE;
+        else if (!isfinite(rr) || !isfinite(beta)) st = PC_ERR_NONFINITE;
+        else if (sc->iter >= sc->max_iter && !(rr <= sc->tol2)) st = PC_ERR_NOT_CONVERGED;
+        if (st != PC_OK) atomicCAS(&sc->status, (int32_t)PC_OK, st);
+        if (st != PC_OK || rr <= sc->tol2) sc->done = 1;
+    }
     // the direction step even when this iteration stopped the solve: a residual
     // replacement that resumes it corrects p from z_old to the replaced z
-    if (isfinite(beta_d)) {
-        const float beta = (float)beta_d;
+    if (isfinite(beta)) {
 #pragma unroll
         for (int u = 0; u < FU_ROWS; ++u) {
             if (u >= R) break;
@@ -814,8 +856,8 @@ pc_status pc_solver_alloc(pc_ctx *c)
         PC_CUDA_TRY(cudaMemset(c->od_ci, 0, sizeof(int32_t) * (size_t)(c->od_cap + 4)));
         PC_CUDA_TRY(cudaMemset(c->od_vals, 0, sizeof(float) * (size_t)(9 * c->od_cap + 16)));
     }
-    for (int i = 0; i < 4; ++i) PC_CUDA_TRY(cudaEventCreate(&c->ev[i]));
-    c->ev_used = 4;
+    for (int i = 0; i < 6; ++i) PC_CUDA_TRY(cudaEventCreate(&c->ev[i]));
+    c->ev_used = 6;
     return PC_OK;
 }
 
@@ -876,6 +918,7 @@ extern "C" void pc_default_solve_opts(pc_solve_opts *o)
     o->precond = PC_PRECOND_JACOBI;
     o->storage = PC_STORAGE_OFFDIAG;
     o->fuse = 1;
+    o->schedule = PC_SCHED_AUTO;
 }
 
 struct SolveCtx {
@@ -1321,7 +1364,8 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
     pc_default_solve_opts(&o);
     if (opts) o = *opts;
     if (!(o.tol > 0.0) || o.max_iter < 0 || (o.precision != PC_PREC_FP32 && o.precision != PC_PREC_MIXED) ||
-        (o.precond != PC_PRECOND_JACOBI && o.precond != PC_PRECOND_BLOCK) || !(o.refresh > 0.0 && o.refresh < 1.0))
+        (o.precond != PC_PRECOND_JACOBI && o.precond != PC_PRECOND_BLOCK) || !(o.refresh > 0.0 && o.refresh < 1.0) ||
+        (o.schedule != PC_SCHED_AUTO && o.schedule != PC_SCHED_GRID && o.schedule != PC_SCHED_CLUSTER))
         return PC_ERR_ARG;
     if (o.check_every < 1) o.check_every = 32;
     if (o.refresh_every < 1) o.refresh_every = 1000;
@@ -1344,6 +1388,12 @@ static pc_status pcg_solve_impl(pc_ctx *ctx, const pc_bsr *A, const float *vals,
     PC_TRY(pc_read_errors(ctx, st, &bits));  // synchronises the stream
     if (bits & PC_DERR_INDEX) return PC_ERR_ARG;
     if (bits) return PC_ERR_NONFINITE;
+    if (o.schedule != PC_SCHED_GRID) {
+        bool ran = false;
+        const pc_status cs = pc_cluster_solve(ctx, A, vals, dres, b, dv, o, s.block, o.schedule == PC_SCHED_CLUSTER,
+                                              info, st, &ran);
+        if (ran || cs != PC_OK) return cs;
+    }
     if (o.storage == PC_STORAGE_SYM) PC_TRY(build_sym(ctx, A, vals, &s.sym, st));
     if (o.storage == PC_STORAGE_SELL) PC_TRY(build_sell(ctx, A, vals, &s.sell, st));
     // the diagonal blocks multiply p_i - p_i = 0 in the difference form only

@@ -13,9 +13,9 @@
 // are read directly from global memory.
 //
 // PCG mode computes q = A p and this CTA's p.q partial (slot 3 of the CTA's entry in the
-// partials array; the update kernel that follows sums the partials in CTA order and forms
-// alpha, so the SpMV ends without a grid-wide reduction tail), with p stored as float4 per
-// vertex so that each gather is one 16-byte load.
+// partials array, as a double-float pair (float2); the update kernel that follows sums the
+// partials in CTA order and forms alpha, so the SpMV ends without a grid-wide reduction
+// tail), with p stored as float4 per vertex so that each gather is one 16-byte load.
 // Difference form (dres given): y_j = D_j x_j + sum_i A_ji (x_i - x_j); the diagonal
 // block then multiplies x_j - x_j = 0 and needs no special case.
 #pragma once
@@ -74,7 +74,7 @@ struct SpmvArgs {
     const float4 *x4;     // PCG mode: the search direction p as float4[V]
     float *y;             // plain mode: result, float[V][3]
     float4 *y4;           // PCG mode: q = A p as float4[V]
-    double *partials;     // PCG mode: p.q partials
+    double *partials;     // PCG mode: p.q partials (slot 3 of each CTA's 4, a float2 pair)
     pc_scalars *sc;       // PCG mode: scalars
     uint32_t *err;        // error bits (timeouts)
 };
@@ -280,8 +280,9 @@ __global__ void __launch_bounds__(SP_THREADS, SpShape<CAPR>::ctas_per_sm) spmv_k
     }
     if (PCG) {
         pdl_trigger();
-        double v[1] = {(double)dot_acc - (double)dot_c};
-        block_sum_d(v, 1);
-        if (threadIdx.x == 0) a.partials[(int64_t)blockIdx.x * RED_SLOTS + 3] = v[0];
+        float hi[1] = {dot_acc}, lo[1] = {-dot_c};  // the thread's compensated sum as a pair
+        pc_block_sum_df(hi, lo, 1);
+        if (threadIdx.x == 0)
+            reinterpret_cast<float2 *>(a.partials)[(int64_t)blockIdx.x * RED_SLOTS + 3] = make_float2(hi[0], lo[0]);
     }
 }

@@ -245,7 +245,8 @@ __global__ void __launch_bounds__(SL_THREADS, SL_CTAS_PER_SM) spmv_sell_kernel(S
         }
     }
     pdl_trigger();
-    double v[1] = {(double)dot - (double)dot_c};
-    block_sum_d(v, 1);
-    if (threadIdx.x == 0) a.partials[(int64_t)blockIdx.x * RED_SLOTS + 3] = v[0];
+    float hi[1] = {dot}, lo[1] = {-dot_c};  // the thread's compensated sum as a pair
+    pc_block_sum_df(hi, lo, 1);
+    if (threadIdx.x == 0)
+        reinterpret_cast<float2 *>(a.partials)[(int64_t)blockIdx.x * RED_SLOTS + 3] = make_float2(hi[0], lo[0]);
 }

@@ -277,7 +277,8 @@ __global__ void __launch_bounds__(SP_THREADS, SY_CTAS_PER_SM) spmv_sym_kernel(Sy
         a.sc->done = 1;
     }
     pdl_trigger();
-    double v[1] = {(double)dot_acc - (double)dot_c};
-    block_sum_d(v, 1);
-    if (threadIdx.x == 0) a.partials[(int64_t)blockIdx.x * RED_SLOTS + 3] = v[0];
+    float hi[1] = {dot_acc}, lo[1] = {-dot_c};  // the thread's compensated sum as a pair
+    pc_block_sum_df(hi, lo, 1);
+    if (threadIdx.x == 0)
+        reinterpret_cast<float2 *>(a.partials)[(int64_t)blockIdx.x * RED_SLOTS + 3] = make_float2(hi[0], lo[0]);
 }

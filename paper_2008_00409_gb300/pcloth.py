@@ -21,6 +21,7 @@ PC_OK, PC_ERR_ARG, PC_ERR_CAPACITY, PC_ERR_NOT_CONVERGED, PC_ERR_NONFINITE, PC_E
 PC_PREC_FP32, PC_PREC_MIXED = 0, 1
 PC_PRECOND_JACOBI, PC_PRECOND_BLOCK = 0, 1
 PC_STORAGE_SYM, PC_STORAGE_FULL, PC_STORAGE_SELL, PC_STORAGE_OFFDIAG = 0, 1, 2, 3
+PC_SCHED_AUTO, PC_SCHED_GRID, PC_SCHED_CLUSTER = 0, 1, 2
 PC_WARM_ZERO, PC_WARM_PREV, PC_WARM_GIVEN, PC_WARM_MLP, PC_WARM_COMBINED = 0, 1, 2, 3, 4
 PC_MLP_IN, PC_MLP_HIDDEN, PC_MLP_OUT, PC_MLP_NPARAMS, PC_MLP_NSTATS = 12, 64, 3, 5187, 30
 
@@ -42,7 +43,7 @@ class pc_bsr(ctypes.Structure):
 class pc_solve_opts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("max_iter", c_int32), ("precision", c_int32), ("refresh", c_double),
                 ("refresh_every", c_int32), ("check_every", c_int32), ("precond", c_int32), ("storage", c_int32),
-                ("fuse", c_int32)]
+                ("fuse", c_int32), ("schedule", c_int32)]
 
 
 class pc_solve_info(ctypes.Structure):
@@ -133,6 +134,7 @@ def _load():
     L.pc_set_profiling.argtypes = [c_void_p, c_int32]
     L.pc_spmv_stats.argtypes = [c_void_p, P(c_int64), P(c_double), P(c_int64)]
     L.pc_assembly_stats.argtypes = [c_void_p, P(c_int64), P(c_double)]
+    L.pc_cluster_stats.argtypes = [c_void_p, P(c_int64), P(c_int64), P(c_double)]
     L.pc_get_solution64.argtypes = [c_void_p, c_void_p, c_void_p]
     for name in ("pc_create", "pc_destroy", "pc_get_sizes", "pc_get_rest", "pc_assemble_pattern",
                  "pc_assemble_values", "pc_bsr_spmv", "pc_pcg_solve", "pc_pcg_solve_static", "pc_step", "pc_step_host",
@@ -140,7 +142,7 @@ def _load():
                  "pc_mlp_get_state", "pc_mlp_set_state", "pc_mlp_features", "pc_mlp_create",
                  "pc_mlp_destroy", "pc_mlp_reset", "pc_mlp_stats", "pc_mlp_infer", "pc_mlp_grad", "pc_mlp_train_step",
                  "pc_mlp_adam_apply", "pc_set_warm_mlp",
-                 "pc_set_profiling", "pc_spmv_stats", "pc_assembly_stats", "pc_get_solution64"):
+                 "pc_set_profiling", "pc_spmv_stats", "pc_assembly_stats", "pc_cluster_stats", "pc_get_solution64"):
         getattr(L, name).restype = c_int32
     return L
 
@@ -207,12 +209,13 @@ def bsr_struct(row_ptr, col_idx, nnzb: int = 0) -> pc_bsr:
 
 
 def solve_opts(tol=1e-6, max_iter=20000, precision=PC_PREC_FP32, refresh=1e-2, refresh_every=1000, check_every=32,
-               precond=PC_PRECOND_JACOBI, storage=None, fuse=True):
+               precond=PC_PRECOND_JACOBI, storage=None, fuse=True, schedule=PC_SCHED_AUTO):
     o = pc_solve_opts()
     o.tol, o.max_iter, o.precision, o.refresh, o.refresh_every, o.check_every, o.precond = (
         tol, max_iter, precision, refresh, refresh_every, check_every, precond)
     o.storage = PC_STORAGE_OFFDIAG if storage is None else storage
     o.fuse = 1 if fuse else 0
+    o.schedule = schedule
     return o
 
 
@@ -473,6 +476,12 @@ def pc_assembly_stats(ctx):
     return n.value, ms.value
 
 
+def pc_cluster_stats(ctx):
+    n, it, ms = c_int64(), c_int64(), c_double()
+    _check(_lib.pc_cluster_stats(ctx, ctypes.byref(n), ctypes.byref(it), ctypes.byref(ms)), "pc_cluster_stats")
+    return n.value, it.value, ms.value
+
+
 def pc_spmv_stats(ctx):
     n, ms, nnzb = c_int64(), c_double(), c_int64()
     _check(_lib.pc_spmv_stats(ctx, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(nnzb)), "pc_spmv_stats")
@@ -553,11 +562,11 @@ class Cloth:
 
     def step(self, pairs=None, w=None, tol=1e-6, precision=PC_PREC_FP32, warm_start=PC_WARM_ZERO, max_iter=20000,
              dv_out=None, precond=PC_PRECOND_JACOBI, allow_not_converged=False, feat_out=None, storage=None,
-             fuse=True):
+             fuse=True, schedule=PC_SCHED_AUTO):
         o = pc_step_opts()
         o.h = self.h
         o.solve = solve_opts(tol=tol, max_iter=max_iter, precision=precision, precond=precond, storage=storage,
-                             fuse=fuse)
+                             fuse=fuse, schedule=schedule)
         o.warm_start = warm_start
         o.feat_out = _ptr(feat_out)
         info, st = pc_step(self.ctx, self.x, self.v, pairs, w, o, dv_out, allow_not_converged=allow_not_converged)

@@ -89,4 +89,5 @@ def test_adam_state_round_trip_and_log(pc, tmp_path):
     assert [d["step"] for d in lines] == [0, 1]
     for d in lines:
         assert d["status"] == 0 and d["iters"] > 0 and d["rel_res"] <= 1e-8 and d["nnzb"] > 0
-        assert d["assembly_ms"] > 0 and d["spmv_gbs"] > 0
+        # this small cloth solves on the cluster schedule by default
+        assert d["assembly_ms"] > 0 and d["cluster_us_per_iter"] > 0

@@ -126,11 +126,13 @@ def test_indefinite_system_is_reported_and_isolated(pc):
     rp, ci, nnzb, vals, b, dense, h = _two_instance_matrix(wl.V)
     t = [torch.from_numpy(a).cuda() for a in (rp, ci, vals.reshape(-1), b.reshape(-1))]
     opts = pc.solve_opts(tol=1e-10, max_iter=1000, precision=pc.PC_PREC_MIXED)
-    # the single-system solver on the whole matrix
+    # the single-system solver on the whole matrix, on both schedules
     dv = torch.zeros(wl.V * 3, device="cuda")
-    with pytest.raises(pc.PcError) as e:
-        pc.pc_pcg_solve(cl.ctx, t[0], t[1], nnzb, t[2], None, t[3], dv, opts)
-    assert e.value.status == pc.PC_ERR_NONFINITE
+    for sched in (pc.PC_SCHED_GRID, pc.PC_SCHED_CLUSTER):
+        with pytest.raises(pc.PcError) as e:
+            pc.pc_pcg_solve(cl.ctx, t[0], t[1], nnzb, t[2], None, t[3], dv,
+                            pc.solve_opts(tol=1e-10, max_iter=1000, precision=pc.PC_PREC_MIXED, schedule=sched))
+        assert e.value.status == pc.PC_ERR_NONFINITE
     # batched: the indefinite instance stops, the SPD one converges to the exact solution
     dv.zero_()
     with pytest.raises(pc.PcError) as e:
@@ -175,7 +177,7 @@ def test_fused_update_barrier_timeout_and_recovery(pc):
     cl = pc.Cloth(wl)
     s = cl.assemble(*cl.contacts_device(0))
     args = (cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"], s["dres"], s["b"])
-    opts = pc.solve_opts(tol=1e-9, precision=pc.PC_PREC_MIXED, max_iter=50000)
+    opts = pc.solve_opts(tol=1e-9, precision=pc.PC_PREC_MIXED, max_iter=50000, schedule=pc.PC_SCHED_GRID)
     ref = torch.zeros(cl.V * 3, device="cuda")
     info_ref, _ = pc.pc_pcg_solve(*args, ref, opts)
     pc.pc_set_barrier_wait(cl.ctx, 1)

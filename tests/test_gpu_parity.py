@@ -148,8 +148,10 @@ def test_difference_diagonal_and_spmv(pc, case):
 
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("precision", ["fp32", "mixed", "mixed-bench"])
-def test_pcg_solution_matches_oracle(pc, case, precision):
-    """dv against the oracle solved to 1e-12. "mixed-bench" is the configuration the
+@pytest.mark.parametrize("schedule", ["grid", "cluster"])
+def test_pcg_solution_matches_oracle(pc, case, precision, schedule):
+    """dv against the oracle solved to 1e-12, on both schedules (grid-wide kernels, and the
+    whole solve inside one thread-block cluster). "mixed-bench" is the configuration the
     benchmark times (mixed precision, tol 1e-6): on these small systems a 1e-6 residual
     already bounds the dv error by 1e-5."""
     wl = CASES[case]()
@@ -161,10 +163,11 @@ def test_pcg_solution_matches_oracle(pc, case, precision):
     prec = pc.PC_PREC_FP32 if precision == "fp32" else pc.PC_PREC_MIXED
     tol = 1e-9 if precision == "mixed" else 1e-6
     dv = torch.zeros(cl.V * 3, device="cuda")
+    sched = pc.PC_SCHED_GRID if schedule == "grid" else pc.PC_SCHED_CLUSTER
     info, st = pc.pc_pcg_solve(cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"], s["dres"], s["b"], dv,
-                               pc.solve_opts(tol=tol, precision=prec, max_iter=50000))
+                               pc.solve_opts(tol=tol, precision=prec, max_iter=50000, schedule=sched))
     err = H.rel_l2(_np(dv), dv_ref)
-    print(f"{case} {precision} tol {tol:g}: {info.iters} iterations, dv rel err {err:.3e}")
+    print(f"{case} {precision} {schedule} tol {tol:g}: {info.iters} iterations, dv rel err {err:.3e}")
     if precision != "fp32":
         assert info.rel_res <= 2 * tol
         assert err <= H.DV_RTOL, f"dv rel err {err:.3e}"
@@ -316,15 +319,18 @@ def test_host_buffer_step_matches_device_step(pc):
     np.testing.assert_array_equal(vh, _np(a.v))
 
 
-def test_deterministic_repeat(pc):
+@pytest.mark.parametrize("schedule", ["grid", "cluster"])
+def test_deterministic_repeat(pc, schedule):
     wl = H.small_contact_cloth()
+    sched = pc.PC_SCHED_GRID if schedule == "grid" else pc.PC_SCHED_CLUSTER
     outs = []
     for _ in range(2):
         cl = pc.Cloth(wl)
         pd, wd = cl.contacts_device(0)
         s = cl.assemble(pd, wd)
         dv = torch.zeros(cl.V * 3, device="cuda")
-        pc.pc_pcg_solve(cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"], s["dres"], s["b"], dv)
+        pc.pc_pcg_solve(cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"], s["dres"], s["b"], dv,
+                        pc.solve_opts(schedule=sched))
         outs.append((_np(s["vals"]).copy(), _np(s["b"]).copy(), _np(dv).copy()))
     for u, v in zip(outs[0], outs[1]):
         np.testing.assert_array_equal(u, v)
@@ -347,11 +353,13 @@ def test_all_storages_agree_with_oracle(pc, case, form):
     dv_ref, _, _ = oracle.pcg(rp, ci, vals_ref, b_ref, tol=1e-12)
     tol = 1e-9 if form == "difference" else 1e-11
     out = {}
-    for storage in (pc.PC_STORAGE_FULL, pc.PC_STORAGE_SYM, pc.PC_STORAGE_SELL, pc.PC_STORAGE_OFFDIAG):
+    for storage in (pc.PC_STORAGE_FULL, pc.PC_STORAGE_SYM, pc.PC_STORAGE_SELL, pc.PC_STORAGE_OFFDIAG, "cluster"):
         dv = torch.zeros(cl.V * 3, device="cuda")
-        info, st = pc.pc_pcg_solve(cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"], dres, s["b"], dv,
-                                   pc.solve_opts(tol=tol, precision=pc.PC_PREC_MIXED, max_iter=50000,
-                                                 storage=storage))
+        o = (pc.solve_opts(tol=tol, precision=pc.PC_PREC_MIXED, max_iter=50000, schedule=pc.PC_SCHED_CLUSTER)
+             if storage == "cluster" else
+             pc.solve_opts(tol=tol, precision=pc.PC_PREC_MIXED, max_iter=50000, storage=storage,
+                           schedule=pc.PC_SCHED_GRID))
+        info, st = pc.pc_pcg_solve(cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"], dres, s["b"], dv, o)
         assert st == pc.PC_OK and info.rel_res <= 2 * tol
         if form == "difference":
             assert H.rel_l2(_np(dv), dv_ref) <= H.DV_RTOL
@@ -363,7 +371,7 @@ def test_all_storages_agree_with_oracle(pc, case, form):
     # depends on summation order (measured: 809..931 on the 64^2 cloth for the four
     # layouts, fused or not; within 1% at 1e-6); the plain form at 1e-11 more so
     slack = 0.12 if form == "difference" else 0.15
-    for storage in (pc.PC_STORAGE_SYM, pc.PC_STORAGE_SELL, pc.PC_STORAGE_OFFDIAG):
+    for storage in (pc.PC_STORAGE_SYM, pc.PC_STORAGE_SELL, pc.PC_STORAGE_OFFDIAG, "cluster"):
         assert abs(out[storage][0] - out[pc.PC_STORAGE_FULL][0]) <= slack * out[pc.PC_STORAGE_FULL][0] + 5
     if form == "plain":  # the copy without diagonal blocks is for the difference form only
         assert out[pc.PC_STORAGE_OFFDIAG][0] == out[pc.PC_STORAGE_FULL][0]
@@ -390,7 +398,8 @@ def test_sliced_ell_product_and_fallback(pc):
     for storage in (pc.PC_STORAGE_FULL, pc.PC_STORAGE_SELL):
         dv = torch.zeros(V * 3, device="cuda")
         info, st = pc.pc_pcg_solve(cl.ctx, t[0], t[1], V * V, t[2], None, t[3], dv,
-                                   pc.solve_opts(tol=1e-7, precision=pc.PC_PREC_MIXED, max_iter=500, storage=storage))
+                                   pc.solve_opts(tol=1e-7, precision=pc.PC_PREC_MIXED, max_iter=500, storage=storage,
+                                                 schedule=pc.PC_SCHED_GRID))
         res[storage] = (st, info.iters, _np(dv))
     assert res[pc.PC_STORAGE_FULL][0] == pc.PC_OK
     assert res[pc.PC_STORAGE_SELL][1] == res[pc.PC_STORAGE_FULL][1]
@@ -407,7 +416,8 @@ def test_sliced_ell_product_and_fallback(pc):
         dv = torch.zeros(V * 3, device="cuda")
         pc.pc_pcg_solve(cl.ctx, s["row_ptr"], s["col_idx"], nnzb, s["vals"],
                         s["dres"] if form == "difference" else None, s["b"], dv,
-                        pc.solve_opts(tol=1e-12, precision=pc.PC_PREC_FP32, max_iter=1, storage=pc.PC_STORAGE_SELL),
+                        pc.solve_opts(tol=1e-12, precision=pc.PC_PREC_FP32, max_iter=1, storage=pc.PC_STORAGE_SELL,
+                                      schedule=pc.PC_SCHED_GRID),
                         allow_not_converged=True)
         np.testing.assert_allclose(_np(dv).astype(np.float64), alpha * z, rtol=2e-5, atol=1e-7 * np.abs(alpha * z).max())
 
@@ -441,7 +451,8 @@ def test_asymmetric_pattern_falls_back_to_full_storage(pc):
     for storage in (pc.PC_STORAGE_SYM, pc.PC_STORAGE_FULL):
         dv = torch.zeros(cl.V * 3, device="cuda")
         info, st = pc.pc_pcg_solve(cl.ctx, *args, dv, pc.solve_opts(tol=1e-9, precision=pc.PC_PREC_MIXED,
-                                                                      max_iter=50000, storage=storage))
+                                                                      max_iter=50000, storage=storage,
+                                                                      schedule=pc.PC_SCHED_GRID))
         res[storage] = (st, info.iters, _np(dv))
     assert res[pc.PC_STORAGE_FULL][0] == pc.PC_OK
     # the symmetric layout is refused and the full matrix gives the identical solve
@@ -452,9 +463,10 @@ def test_asymmetric_pattern_falls_back_to_full_storage(pc):
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("precond", ["jacobi", "block"])
 def test_fused_and_two_kernel_updates_agree(pc, case, precond):
-    """The fused update + direction kernel (one grid-wide barrier per iteration) and the
-    two-kernel form are the same method: both meet the tolerance and match the oracle,
-    with nearly the same iteration count (summation order differs)."""
+    """The fused update + direction kernel (one grid-wide barrier per iteration), the
+    two-kernel form and the cluster schedule are the same method: all meet the tolerance
+    and match the oracle, with nearly the same iteration count (summation order
+    differs)."""
     wl = CASES[case]()
     cl, om, pairs, w, pd, wd = _setup(pc, wl)
     s = cl.assemble(pd, wd)
@@ -462,15 +474,17 @@ def test_fused_and_two_kernel_updates_agree(pc, case, precond):
     dv_ref, _, _ = oracle.pcg(rp, ci, vals_ref, b_ref, tol=1e-12)
     pre = pc.PC_PRECOND_BLOCK if precond == "block" else pc.PC_PRECOND_JACOBI
     out = {}
-    for fuse in (True, False):
+    for form in (True, False, "cluster"):
         dv = torch.zeros(cl.V * 3, device="cuda")
+        sched = pc.PC_SCHED_CLUSTER if form == "cluster" else pc.PC_SCHED_GRID
         info, st = pc.pc_pcg_solve(cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"], s["dres"], s["b"], dv,
                                    pc.solve_opts(tol=1e-9, precision=pc.PC_PREC_MIXED, max_iter=50000, precond=pre,
-                                                 fuse=fuse))
+                                                 fuse=form is True, schedule=sched))
         assert st == pc.PC_OK and info.rel_res <= 2e-9
         assert H.rel_l2(_np(dv), dv_ref) <= H.DV_RTOL
-        out[fuse] = info.iters
-    assert abs(out[True] - out[False]) <= 0.12 * out[False] + 5  # see the storage test
+        out[form] = info.iters
+    for form in (True, "cluster"):
+        assert abs(out[form] - out[False]) <= 0.12 * out[False] + 5  # see the storage test
 
 
 def _banded_spd(V, extra_rows, n_extra, seed):
@@ -537,7 +551,7 @@ def test_product_stage_widths(pc, shape):
     dv = torch.zeros(cl.V * 3, device="cuda")
     info, st = pc.pc_pcg_solve(cl.ctx, t[0], t[1], nnzb, t[2], None, t[3], dv,
                                pc.solve_opts(tol=1e-10, precision=pc.PC_PREC_MIXED, max_iter=5000,
-                                             storage=pc.PC_STORAGE_FULL))
+                                             storage=pc.PC_STORAGE_FULL, schedule=pc.PC_SCHED_GRID))
     assert st == pc.PC_OK and info.rel_res <= 2e-10
     # the solve's matrix is the FP32 rounding of these blocks: solve that one in FP64
     A = oracle.dense(rp, ci, vals.astype(np.float32).astype(np.float64))

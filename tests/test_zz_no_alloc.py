@@ -53,14 +53,15 @@ def _static_solve(pc, cl, s, opts, dres, allow_not_converged=False):
 
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
 @pytest.mark.parametrize("precond", ["jacobi", "block"])
-@pytest.mark.parametrize("fuse", [True, False])
-def test_static_solve_matches_context_solve_on_two_calls(pc, system, precision, precond, fuse):
+@pytest.mark.parametrize("form", ["fused", "two-kernel", "cluster"])
+def test_static_solve_matches_context_solve_on_two_calls(pc, system, precision, precond, form):
     wl, cl, s = system
     prec = pc.PC_PREC_MIXED if precision == "mixed" else pc.PC_PREC_FP32
     pre = pc.PC_PRECOND_BLOCK if precond == "block" else pc.PC_PRECOND_JACOBI
     # the static entry point streams the caller's matrix: the context solve on the same layout
     opts = pc.solve_opts(tol=1e-9 if precision == "mixed" else 1e-6, precision=prec, max_iter=50000, precond=pre,
-                         storage=pc.PC_STORAGE_FULL, fuse=fuse)
+                         storage=pc.PC_STORAGE_FULL, fuse=form == "fused",
+                         schedule=pc.PC_SCHED_CLUSTER if form == "cluster" else pc.PC_SCHED_GRID)
     ref, info_ref = _context_solve(pc, cl, s, opts, s["dres"])
     for call in range(2):
         got, info, st = _static_solve(pc, cl, s, opts, s["dres"])
