@@ -3,37 +3,56 @@
 // solver; Sec. 3.1: the SpMV and the vector operations are data parallel).
 //
 // A system of a few thousand vertices leaves the grid-wide solver latency-bound: each
-// iteration pays two kernel boundaries and a grid-wide barrier for a few microseconds of
-// work. Here up to 16 CTAs of one cluster (one CTA per SM) hold the whole system in their
-// shared memory for the length of the solve:
-//   - CTA c owns rows [c Rc, (c+1) Rc). It copies its rows' 3x3 blocks (without the
-//     diagonal block in the difference form), its rows' difference-form diagonal and
-//     Jacobi inverse into shared memory once, and keeps x, r and q of its rows there.
-//   - Per row a record (ClRec) holds what the other CTAs read: the search direction
-//     (two copies, by iteration parity), z and the FP64 iterate. Each stored block keeps,
-//     instead of its column index, the distributed-shared-memory address of its column's
-//     record, so the product gathers p and z straight from the owning CTA's shared memory.
-//   - Dot products: FP32 within a thread, FP64 across threads; each CTA's sum goes to a
-//     shared slot, a cluster barrier (barrier.cluster arrive.release / wait.acquire)
-//     publishes it, and every warp of every CTA then adds the C slots in the same fixed
-//     order, so all threads hold bitwise the same scalars and take the same decisions.
-// Per iteration two cluster barriers: after q = A p (for p.q) and after the update (for
-// r.z and r.r). The direction step p = z + beta p needs no third one: the product forms
-// each gathered p_j = z_j + beta p_j itself from the owner's record (bitwise the value
-// the owner forms), and the owner stores its p into the record copy of the other parity,
-// which nobody reads in that iteration.
+// iteration pays kernel boundaries and grid-wide barriers for a few microseconds of work.
+// Here up to 16 CTAs of one cluster (one CTA per SM) hold the whole system in their shared
+// memory for the length of the solve. CTA c owns rows [c Rc, (c+1) Rc): their 3x3 blocks
+// (without the diagonal block in the difference form), difference-form diagonal, Jacobi
+// inverse and every vector of the iteration.
+//
+// Iteration: the Chronopoulos-Gear form of preconditioned CG (A. T. Chronopoulos and
+// C. W. Gear, "s-step iterative methods for symmetric linear systems", J. Comput. Appl.
+// Math. 25, 1989), which needs one reduction per iteration instead of two. With
+// u = M^-1 r and w = A u kept alongside p and s = A p:
+//     p = u + beta p,  s = w + beta s,  x += alpha p,  r -= alpha s,  u = M^-1 r,  w = A u
+//     gamma = (r, u),  delta = (u, w),  beta' = gamma / gamma_old,
+//     alpha' = gamma / (p', A p')  with  (p', A p') = delta + beta' ((u, s) + (p, w)) + beta'^2 (p, s)
+// -- the denominator expanded exactly from the stored vectors (p' = u + beta' p, A p' =
+// w + beta' s) rather than through the method's orthogonality relations, so it stays
+// right after a residual replacement. One iteration: the vector update, a cluster barrier
+// that publishes u, the product w = A u, and the reduction of (gamma, r.r, delta, the two
+// cross terms): two cluster barriers, one reduction.
+//
+// Distributed shared memory: a gather from another CTA's shared memory costs far more
+// than a local one (measured on GB300: six scattered 16-byte remote loads per thread take
+// about 30 times as long as local ones). So every CTA keeps ghost copies of the rows it
+// reads from other CTAs; set-up numbers them, tells each owner which of its rows to send
+// where, and each iteration the owners push those rows' u (and, for the FP64 residual,
+// x) into the consumers' ghost slots with remote stores. Every gather of the product is
+// then a plain shared-memory load. Reductions: FP32 per thread, double-float pairs across
+// threads (pc_df_add); each CTA's warp 0 pushes the CTA's sums into every CTA's slot
+// array, and after the barrier every warp adds the C slots in rank order, so all threads
+// hold bitwise the same sums and compute the same scalars and decisions with no further
+// barrier. The scalars are formed in FP32 after scaling the sums by a power of two fixed at
+// the start (exact), which keeps them far from the FP32 range limits.
 //
 // Mixed precision as in the grid-wide solver: the FP32 increment is folded into the FP64
-// iterate every check_every iterations, and the residual is recomputed in FP64 (the
-// product gathers the FP64 iterate) when the recurrence residual has dropped by
-// refresh^2, after refresh_every iterations, and to confirm convergence; the replaced z
-// enters the next direction step, the direction itself is kept.
+// iterate every check_every iterations, and the residual is recomputed in FP64 when the
+// recurrence residual has dropped by refresh^2, after refresh_every iterations, and to
+// confirm convergence. The replacement recomputes r and u = M^-1 r, and s = A p and w = A u
+// by the product (the recurrences for s and r drift); it keeps the direction p and the
+// recurrence's beta, and the replaced gamma enters alpha through the expanded denominator.
+// Near FP32's attainable accuracy this form needs more iterations than the two-reduction
+// form (its residual recurrence goes through the recurrence for s): the same count at a
+// relative residual of 1e-6 on the 64 x 64 cloth, about a quarter more at 1e-9.
 //
 // The kernel has no spin-waits: the cluster's CTAs are co-scheduled by the hardware and
-// its barriers are hardware barriers; every branch around a barrier depends only on the
-// shared scalars, so all threads of the cluster reach every barrier. The last barrier
-// keeps each CTA resident until no other CTA can still read its shared memory.
+// its barriers are hardware barriers; every branch around a barrier depends only on
+// values every thread of the cluster holds identically, so all threads reach every
+// barrier. The last barrier keeps each CTA resident until no other CTA can still touch
+// its shared memory.
 #include <math.h>
+
+#include <algorithm>
 
 #include "pc_internal.cuh"
 
@@ -41,20 +60,11 @@
 #define CL_TPR 4                         // threads per row in the products
 #define CL_GROUPS (CL_THREADS / CL_TPR)  // rows in flight per CTA
 #define CL_WARPS (CL_THREADS / 32)
-
-// Per row, in the owning CTA's shared memory: the entries other CTAs gather.
-struct __align__(16) ClRec {
-    float4 p[2];   // direction of the previous iteration, by iteration parity
-    float4 z;      // preconditioned residual
-    double x[3];   // FP64 iterate (mixed precision); the final solution for the last residual
-    double pad;
-};
-static_assert(sizeof(ClRec) == 80, "record layout");
-#define CL_REC_Z 32
-#define CL_REC_X 48
+#define CL_MAXC 16                       // CTAs per cluster at most
+#define CL_NV 6                          // values per reduction at most
 
 struct ClArgs {
-    int V, Rc, cap;
+    int V, Rc, cap, gcap, pcap, Vw;
     const int32_t *rp, *ci;
     const float *vals, *dres, *dinv, *b;
     float *dv;
@@ -62,23 +72,37 @@ struct ClArgs {
     double tol, refresh;
     int max_iter, check_every, refresh_every, mixed;
     pc_scalars *sc;
-    // byte offsets of the shared-memory arrays (the records start at 0)
-    uint32_t o_x, o_r, o_q, o_dres, o_dinv, o_rs, o_red, o_addr, o_vals;
+    // byte offsets of the shared-memory arrays (u starts at 0)
+    uint32_t o_x64, o_xv, o_r, o_w, o_p, o_s, o_dres, o_dinv, o_rs, o_bits, o_pref, o_push, o_red, o_idx, o_vals;
 };
 
+struct ClRed {
+    float2 warp[CL_WARPS][CL_NV];        // this CTA's warp sums
+    float2 slot[2][CL_MAXC][CL_NV];      // every CTA's sums, pushed here by that CTA (by parity)
+    int misc[40];                        // scan scratch (0..31), vote flags (32, 33), requests received (34)
+    // thread 0's scalars and stop state (the same in every CTA), and its word to its CTA
+    double rr64, bb64;                   // FP64 r.r of the last residual pass, b.b
+    float sigma, tol2;                   // the start's scale factor and scaled stop threshold
+    float gam_old, rr_last, alpha, beta;
+    int status, iter_last, outer, action;
+};
+#define CL_ACT_DONE 1
+#define CL_ACT_FOLD 2
+#define CL_ACT_REPLACE 4
+
 struct ClSmem {
-    ClRec *rec;
-    float4 *xv, *rv, *qv;  // FP32 increment, residual, A p
-    float *dres;           // [Rc][9]
-    float4 *dinv;          // [Rc] (scalar Jacobi: 3 used) or [Rc][3] (rows of the block inverse)
-    int *rs;               // [Rc + 1] row starts into the stored blocks
-    uint32_t *addr;        // [cap] cluster address of each block's column record
-    float *vals;           // [cap][9]
-    double *red_w;         // [CL_WARPS][4] warp sums
-    double *red_c;         // [2][4] this CTA's sums, read by every CTA (double-buffered)
-    int *misc;             // [40] scan scratch (0..31), capacity flag (32)
-    struct ClBcast *bc;    // thread 0's word to its CTA
-    struct ClCtl *ctl;     // thread 0's scalars
+    float4 *u;           // [Rc + gcap] M^-1 r: own rows, then ghost copies
+    double *x64;         // [Rc + gcap][4] FP64 iterate: own rows, then ghost copies
+    float4 *xv, *r, *w, *p, *s;  // [Rc] FP32 increment, residual, A u, direction, A p
+    float *dres;         // [Rc][9]
+    float *dinv;         // [Rc][9] (block) or [Rc][4] (scalar Jacobi)
+    int *rs;             // [Rc + 1] row starts into the stored blocks
+    uint32_t *bits;      // [Vw] rows other CTAs own that this CTA reads
+    int *pref;           // [Vw] ghost number of each word's first row
+    uint32_t *push;      // [pcap] rows to send: local row | rank << 10 | ghost << 14
+    ClRed *red;
+    uint16_t *idx;       // [cap] the column of each stored block as an index into u / x64
+    float *vals;         // [cap][9]
 };
 
 // ------------------------------------------------------------------------- cluster primitives
@@ -107,184 +131,252 @@ __device__ __forceinline__ uint32_t cl_map(uint32_t local, uint32_t rank)
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
     return r;
 }
-__device__ __forceinline__ float4 cl_ld_f4(uint32_t a)
-{
-    float4 v;
-    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"(a));
-    return v;
-}
-__device__ __forceinline__ double2 cl_ld_d2(uint32_t a)
-{
-    double2 v;
-    asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a));
-    return v;
-}
-__device__ __forceinline__ double cl_ld_d(uint32_t a)
-{
-    double v;
-    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a));
-    return v;
-}
 __device__ __forceinline__ uint32_t cl_ld_u32(uint32_t a)
 {
     uint32_t v;
-    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
     return v;
 }
-
-// xor butterfly: every lane ends with bitwise the same sum (addition commutes)
-__device__ __forceinline__ double cl_warp_sum(double v)
+__device__ __forceinline__ uint32_t cl_atom_add(uint32_t a, uint32_t v)
 {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    uint32_t old;
+    asm volatile("atom.shared::cluster.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void cl_st_u32(uint32_t a, uint32_t v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cl_st_f2(uint32_t a, float2 v)
+{
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void cl_st_f4(uint32_t a, float4 v)
+{
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ void cl_st_d2(uint32_t a, double x, double y)
+{
+    asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(x), "d"(y) : "memory");
 }
 
-// Sum N per-thread values over the cluster; the totals land in every lane of warp 0, in
-// every CTA bitwise the same: warp sums, this CTA's sum of its warp sums (warp 0, warp
-// order) into its slot of parity `par`, a cluster barrier, and the C slots added in rank
-// order by warp 0. The iterations' dot products (FP32 per thread) are added as
-// double-float pairs (pc_df_add: FP32 arithmetic only -- GB300 runs FP64 at about 1/60 of
-// its FP32 rate, and FP64 butterflies in every thread would cost more than the iteration
-// itself); the rare FP64 residual passes add doubles.
-template <int N>
-__device__ __forceinline__ void cl_reduce_df(const float (&v)[N], float2 (&tot)[N], const ClSmem &S, int &par,
-                                             uint32_t C)
+// Block-inclusive prefix sum of one int per thread; scratch[CL_WARPS - 1] holds the total
+// on return (read it before the next call, with a barrier in between).
+__device__ __forceinline__ int cl_scan(int v, int *scratch)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float2 *red_w = reinterpret_cast<float2 *>(S.red_w);
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += n;
+    }
+    if (lane == 31) scratch[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = scratch[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int n = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += n;
+        }
+        scratch[lane] = w;
+    }
+    __syncthreads();
+    if (warp > 0) incl += scratch[warp - 1];
+    return incl;
+}
+
+// Every CTA learns whether any CTA raised `flag` (a barrier, then each warp reads the C
+// CTAs' flags); the same answer in every thread.
+__device__ __forceinline__ bool cl_vote(int *flag, int mine, uint32_t C)
+{
+    if (threadIdx.x == 0) *flag = mine;
+    cl_sync();
+    const int lane = threadIdx.x & 31;
+    const uint32_t f = (uint32_t)lane < C ? cl_ld_u32(cl_map(cl_smem_addr(flag), lane)) : 0u;
+    return __any_sync(0xffffffffu, f != 0u);
+}
+
+// Sum N per-thread values over the cluster; the totals land in warp 0 (every lane), in
+// every CTA bitwise the same. Warp sums (FP32 butterflies for the iterations' FP32
+// partials; double-float pairs for the residual passes' FP64 partials); warp 0 adds the
+// warp sums (warp order) as double-float pairs and pushes the CTA's sums into
+// slot[par][rank] of every CTA; a cluster barrier; warp 0 adds the C slots in rank order.
+// Only warp 0 works past the warp sums: the kernel is bound by instruction issue on its
+// few SMs, and double-float butterflies in all 32 warps used to cost more than the product.
+template <int N, bool PAIRS>
+__device__ __forceinline__ void cl_reduce(const float2 (&v)[N], float2 (&tot)[N], const ClSmem &S, int &par,
+                                          uint32_t C, uint32_t rank)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        float hi = v[i], lo = 0.f;
-        pc_warp_sum_df(hi, lo);
-        if (lane == 0) red_w[4 * warp + i] = make_float2(hi, lo);
-    }
-    __syncthreads();
-    float2 *slot = reinterpret_cast<float2 *>(S.red_c + 4 * par);
-    if (warp == 0) {
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            float2 w = red_w[4 * lane + i];
-            pc_warp_sum_df(w.x, w.y);
-            if (lane == 0) slot[i] = w;
-        }
-    }
-    cl_sync();
-    if (warp == 0) {
-        const uint32_t base = cl_smem_addr(slot);
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            float hi = 0.f, lo = 0.f;
-            if ((uint32_t)lane < C) {
-                const double w = cl_ld_d(cl_map(base + 8u * i, lane));  // the pair's 8 bytes
-                const float2 f = *reinterpret_cast<const float2 *>(&w);
-                hi = f.x;
-                lo = f.y;
-            }
+        float hi = v[i].x, lo = v[i].y;
+        if (PAIRS) {
             pc_warp_sum_df(hi, lo);
-            tot[i] = make_float2(hi, lo);
+        } else {
+            for (int o = 16; o > 0; o >>= 1) hi += __shfl_xor_sync(0xffffffffu, hi, o);
         }
+        if (lane == 0) S.red->warp[warp][i] = make_float2(hi, lo);
     }
-    // the slots of this parity are rewritten two reductions later, after a barrier that
-    // every CTA reaches only once it has read them
-    par ^= 1;
-}
-template <int N>
-__device__ __forceinline__ void cl_reduce_d(double (&v)[N], double (&tot)[N], const ClSmem &S, int &par, uint32_t C)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < N; ++i) v[i] = cl_warp_sum(v[i]);
-    if (lane == 0)
-#pragma unroll
-        for (int i = 0; i < N; ++i) S.red_w[4 * warp + i] = v[i];
     __syncthreads();
-    double *slot = S.red_c + 4 * par;
     if (warp == 0) {
+        float2 cs[N];
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            const double s = cl_warp_sum(S.red_w[4 * lane + i]);
-            if (lane == 0) slot[i] = s;
+            float2 w = S.red->warp[lane][i];
+            pc_warp_sum_df(w.x, w.y);
+            cs[i] = w;
+        }
+        if ((uint32_t)lane < C) {
+            const uint32_t dst = cl_map(cl_smem_addr(&S.red->slot[par][rank][0]), lane);
+#pragma unroll
+            for (int i = 0; i < N; ++i) cl_st_f2(dst + 8u * i, cs[i]);
         }
     }
     cl_sync();
     if (warp == 0) {
-        const uint32_t base = cl_smem_addr(slot);
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            const double s = (uint32_t)lane < C ? cl_ld_d(cl_map(base + 8u * i, lane)) : 0.0;
-            tot[i] = cl_warp_sum(s);
+            float2 w = (uint32_t)lane < C ? S.red->slot[par][lane][i] : make_float2(0.f, 0.f);
+            pc_warp_sum_df(w.x, w.y);
+            tot[i] = w;
         }
     }
+    // slot[par] is pushed again two reductions later, after a barrier that warp 0 reaches
+    // only once it has read it
     par ^= 1;
 }
 
-// What thread 0 of each CTA (the same decision in every CTA) tells its CTA after a
-// reduction: the step length or direction coefficient and what comes next.
-struct ClBcast {
-    float alpha, beta;
-    int action;
-    int check;
-};
-// Thread 0's FP64 scalars and stop state, kept in shared memory rather than in registers
-// that every thread would have to reserve.
-struct ClCtl {
-    double rz, rr, bb, tol2, rr_last;
-    float rz_f;  // rz rounded, for the FP32 quotients
-    int status, iter_last, outer, bad_pq;
-};
-#define CL_ACT_DONE 1
-#define CL_ACT_FOLD 2
-#define CL_ACT_REPLACE 4
+// an FP64 value as a double-float pair (the residual passes' partial sums)
+__device__ __forceinline__ float2 cl_pair(double d)
+{
+    const float hi = (float)d;
+    return make_float2(hi, (float)(d - (double)hi));
+}
 
 // ------------------------------------------------------------------------- row arithmetic
 
 template <bool BLOCK>
-__device__ __forceinline__ float4 cl_precond(const float4 *dinv, int l, float4 r)
+__device__ __forceinline__ float4 cl_precond(const float *dinv, int l, float4 r)
 {
     if (BLOCK) {
-        const float4 a = dinv[3 * l], b = dinv[3 * l + 1], c = dinv[3 * l + 2];
-        return make_float4(a.x * r.x + a.y * r.y + a.z * r.z, b.x * r.x + b.y * r.y + b.z * r.z,
-                           c.x * r.x + c.y * r.y + c.z * r.z, 0.f);
+        const float *d = dinv + 9 * l;
+        return make_float4(d[0] * r.x + d[1] * r.y + d[2] * r.z, d[3] * r.x + d[4] * r.y + d[5] * r.z,
+                           d[6] * r.x + d[7] * r.y + d[8] * r.z, 0.f);
     }
-    const float4 d = dinv[l];
+    const float4 d = reinterpret_cast<const float4 *>(dinv)[l];
     return make_float4(d.x * r.x, d.y * r.y, d.z * r.z, 0.f);
 }
 
 __device__ __forceinline__ float cl_dot3(float4 a, float4 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
 
-// the direction step p = z + beta p_prev
-__device__ __forceinline__ float4 cl_dir(float beta, float4 p, float4 z)
+__device__ __forceinline__ float4 cl_axpy(float a, float4 x, float4 y)  // a x + y
 {
-    return make_float4(fmaf(beta, p.x, z.x), fmaf(beta, p.y, z.y), fmaf(beta, p.z, z.z), 0.f);
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), 0.f);
 }
 
-// FP64 residual b - A x of this CTA's rows, x gathered from the records' FP64 iterate.
-// Partials: t[1] += |r|^2, t[2] += |b|^2 and, with `install`, r = (float) r64 and
-// z = D^-1 r replace the recurrence's r and z (t[0] += r.z).
-template <bool DIFF, bool BLOCK>
-__device__ __forceinline__ void cl_residual(const ClSmem &S, const ClArgs &a, int row0, int nrows, bool install,
-                                            double t[3])
+// Send the rows other CTAs hold ghost copies of: u (float4), or the FP64 iterate.
+__device__ __forceinline__ void cl_push_u(const ClSmem &S, int Rc, int n_push)
+{
+    const uint32_t base = cl_smem_addr(S.u);
+    for (int e = threadIdx.x; e < n_push; e += CL_THREADS) {
+        const uint32_t ent = S.push[e];
+        const int l = ent & 0x3FF, d = (ent >> 10) & 0xF, g = ent >> 14;
+        cl_st_f4(cl_map(base + 16u * (uint32_t)(Rc + g), d), S.u[l]);
+    }
+}
+__device__ __forceinline__ void cl_push_x64(const ClSmem &S, int Rc, int n_push)
+{
+    const uint32_t base = cl_smem_addr(S.x64);
+    for (int e = threadIdx.x; e < n_push; e += CL_THREADS) {
+        const uint32_t ent = S.push[e];
+        const int l = ent & 0x3FF, d = (ent >> 10) & 0xF, g = ent >> 14;
+        const uint32_t dst = cl_map(base + 32u * (uint32_t)(Rc + g), d);
+        const double *x = S.x64 + 4 * l;
+        cl_st_d2(dst, x[0], x[1]);
+        cl_st_d2(dst + 16u, x[2], 0.0);
+    }
+}
+
+// w = A u for this CTA's rows (four threads per row), with the partial dot products of
+// the denominator's expansion: d += (u, w), e += (u, s) + (p, w), f += (p, s). TO_S: the
+// product of whatever u holds goes to s instead, without dot products.
+template <bool DIFF, bool TO_S = false>
+__device__ __forceinline__ void cl_product(const ClSmem &S, int nrows, float &d, float &e, float &f)
 {
     const int sub = threadIdx.x & (CL_TPR - 1), grp = threadIdx.x / CL_TPR;
-    t[0] = t[1] = t[2] = 0.0;
+    for (int l0 = 0; l0 < nrows; l0 += CL_GROUPS) {
+        const int l = l0 + grp;
+        const bool ok = l < nrows;
+        float4 ul = make_float4(0.f, 0.f, 0.f, 0.f);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+        if (ok) {
+            ul = S.u[l];
+            const int k1 = S.rs[l + 1];
+            for (int k = S.rs[l] + sub; k < k1; k += CL_TPR) {
+                float4 uj = S.u[S.idx[k]];
+                if (DIFF) {
+                    uj.x -= ul.x;
+                    uj.y -= ul.y;
+                    uj.z -= ul.z;
+                }
+                const float *B = S.vals + 9 * k;
+                a0 = fmaf(B[2], uj.z, fmaf(B[1], uj.y, fmaf(B[0], uj.x, a0)));
+                a1 = fmaf(B[5], uj.z, fmaf(B[4], uj.y, fmaf(B[3], uj.x, a1)));
+                a2 = fmaf(B[8], uj.z, fmaf(B[7], uj.y, fmaf(B[6], uj.x, a2)));
+            }
+        }
+        for (int o = 1; o < CL_TPR; o <<= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        }
+        if (ok && sub == 0) {
+            if (DIFF) {
+                const float *D = S.dres + 9 * l;
+                a0 = fmaf(D[2], ul.z, fmaf(D[1], ul.y, fmaf(D[0], ul.x, a0)));
+                a1 = fmaf(D[5], ul.z, fmaf(D[4], ul.y, fmaf(D[3], ul.x, a1)));
+                a2 = fmaf(D[8], ul.z, fmaf(D[7], ul.y, fmaf(D[6], ul.x, a2)));
+            }
+            const float4 w = make_float4(a0, a1, a2, 0.f);
+            if (TO_S) {
+                S.s[l] = w;
+            } else {
+                S.w[l] = w;
+                const float4 p = S.p[l], s = S.s[l];
+                d += cl_dot3(ul, w);
+                e += cl_dot3(ul, s) + cl_dot3(p, w);
+                f += cl_dot3(p, s);
+            }
+        }
+    }
+}
+
+// FP64 residual b - A x of this CTA's rows, x gathered from the FP64 iterate (own rows
+// and ghost copies). Partials (FP64): rr += |r|^2, bb += |b|^2 and, with `install`,
+// r = (float) r64 and u = M^-1 r replace the recurrence's r and u (gam += r.u, FP32 dot).
+template <bool DIFF, bool BLOCK>
+__device__ __forceinline__ void cl_residual(const ClSmem &S, const ClArgs &a, int row0, int nrows, bool install,
+                                            float &gam, double &rr, double &bb)
+{
+    const int sub = threadIdx.x & (CL_TPR - 1), grp = threadIdx.x / CL_TPR;
     for (int l0 = 0; l0 < nrows; l0 += CL_GROUPS) {
         const int l = l0 + grp;
         const bool ok = l < nrows;
         double xl0 = 0.0, xl1 = 0.0, xl2 = 0.0;
         if (ok && DIFF) {
-            xl0 = S.rec[l].x[0];
-            xl1 = S.rec[l].x[1];
-            xl2 = S.rec[l].x[2];
+            xl0 = S.x64[4 * l];
+            xl1 = S.x64[4 * l + 1];
+            xl2 = S.x64[4 * l + 2];
         }
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
         if (ok) {
             const int k1 = S.rs[l + 1];
             for (int k = S.rs[l] + sub; k < k1; k += CL_TPR) {
-                const uint32_t ad = S.addr[k];
-                const double2 x01 = cl_ld_d2(ad + CL_REC_X);
-                double d0 = x01.x, d1 = x01.y, d2 = cl_ld_d(ad + CL_REC_X + 16);
+                const double *xj = S.x64 + 4 * S.idx[k];
+                double d0 = xj[0], d1 = xj[1], d2 = xj[2];
                 if (DIFF) {
                     d0 -= xl0;
                     d1 -= xl1;
@@ -311,14 +403,14 @@ __device__ __forceinline__ void cl_residual(const ClSmem &S, const ClArgs &a, in
             const int64_t row = row0 + l;
             const double b0 = (double)a.b[3 * row], b1 = (double)a.b[3 * row + 1], b2 = (double)a.b[3 * row + 2];
             const double r0 = b0 - a0, r1 = b1 - a1, r2 = b2 - a2;
-            t[1] += r0 * r0 + r1 * r1 + r2 * r2;
-            t[2] += b0 * b0 + b1 * b1 + b2 * b2;
+            rr += r0 * r0 + r1 * r1 + r2 * r2;
+            bb += b0 * b0 + b1 * b1 + b2 * b2;
             if (install) {
                 const float4 r = make_float4((float)r0, (float)r1, (float)r2, 0.f);
-                const float4 z = cl_precond<BLOCK>(S.dinv, l, r);
-                S.rv[l] = r;
-                S.rec[l].z = z;
-                t[0] += (double)cl_dot3(r, z);
+                const float4 u = cl_precond<BLOCK>(S.dinv, l, r);
+                S.r[l] = r;
+                S.u[l] = u;
+                gam += cl_dot3(r, u);
             }
         }
     }
@@ -329,9 +421,9 @@ __device__ __forceinline__ void cl_fold(const ClSmem &S, int nrows)
 {
     for (int l = threadIdx.x; l < nrows; l += CL_THREADS) {
         const float4 d = S.xv[l];
-        S.rec[l].x[0] += (double)d.x;
-        S.rec[l].x[1] += (double)d.y;
-        S.rec[l].x[2] += (double)d.z;
+        S.x64[4 * l] += (double)d.x;
+        S.x64[4 * l + 1] += (double)d.y;
+        S.x64[4 * l + 2] += (double)d.z;
         S.xv[l] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
@@ -343,61 +435,60 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
 {
     extern __shared__ __align__(16) unsigned char cl_smem[];
     ClSmem S;
-    S.rec = reinterpret_cast<ClRec *>(cl_smem);
-    S.xv = reinterpret_cast<float4 *>(cl_smem + a.o_x);
-    S.rv = reinterpret_cast<float4 *>(cl_smem + a.o_r);
-    S.qv = reinterpret_cast<float4 *>(cl_smem + a.o_q);
+    S.u = reinterpret_cast<float4 *>(cl_smem);
+    S.x64 = reinterpret_cast<double *>(cl_smem + a.o_x64);
+    S.xv = reinterpret_cast<float4 *>(cl_smem + a.o_xv);
+    S.r = reinterpret_cast<float4 *>(cl_smem + a.o_r);
+    S.w = reinterpret_cast<float4 *>(cl_smem + a.o_w);
+    S.p = reinterpret_cast<float4 *>(cl_smem + a.o_p);
+    S.s = reinterpret_cast<float4 *>(cl_smem + a.o_s);
     S.dres = reinterpret_cast<float *>(cl_smem + a.o_dres);
-    S.dinv = reinterpret_cast<float4 *>(cl_smem + a.o_dinv);
+    S.dinv = reinterpret_cast<float *>(cl_smem + a.o_dinv);
     S.rs = reinterpret_cast<int *>(cl_smem + a.o_rs);
-    S.red_w = reinterpret_cast<double *>(cl_smem + a.o_red);
-    S.red_c = S.red_w + 4 * CL_WARPS;
-    S.misc = reinterpret_cast<int *>(S.red_c + 8);
-    S.ctl = reinterpret_cast<ClCtl *>(S.misc + 40);
-    S.bc = reinterpret_cast<ClBcast *>(S.ctl + 1);
-    S.addr = reinterpret_cast<uint32_t *>(cl_smem + a.o_addr);
+    S.bits = reinterpret_cast<uint32_t *>(cl_smem + a.o_bits);
+    S.pref = reinterpret_cast<int *>(cl_smem + a.o_pref);
+    S.push = reinterpret_cast<uint32_t *>(cl_smem + a.o_push);
+    S.red = reinterpret_cast<ClRed *>(cl_smem + a.o_red);
+    S.idx = reinterpret_cast<uint16_t *>(cl_smem + a.o_idx);
     S.vals = reinterpret_cast<float *>(cl_smem + a.o_vals);
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int sub = tid & (CL_TPR - 1), grp = tid / CL_TPR;
+    const int tid = threadIdx.x;
     const uint32_t rank = cl_rank(), C = cl_nranks();
     const int Rc = a.Rc, row0 = (int)rank * Rc;
     const int nrows = max(0, min(Rc, a.V - row0));
+    int *misc = S.red->misc;
     int par = 0;
 
     // 1. stored blocks per row (the difference form drops the diagonal block, which
-    //    multiplies p_i - p_i = 0) and their running sum: thread l owns row l (Rc <= threads)
+    //    multiplies u_i - u_i = 0) and their running sum: thread l owns row l (Rc <= threads)
     int cnt = 0;
     if (tid < nrows) {
         const int row = row0 + tid;
         for (int k = a.rp[row]; k < a.rp[row + 1]; ++k) cnt += (DIFF && a.ci[k] == row) ? 0 : 1;
     }
-    int incl = cnt;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int n = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += n;
-    }
-    if (lane == 31) S.misc[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        int w = S.misc[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            const int n = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += n;
-        }
-        S.misc[lane] = w;
-    }
-    __syncthreads();
-    if (warp > 0) incl += S.misc[warp - 1];
+    const int incl = cl_scan(cnt, misc);
     if (tid < nrows) S.rs[tid + 1] = incl;
-    if (tid == 0) {
-        S.rs[0] = 0;
-        S.misc[32] = S.misc[CL_WARPS - 1] > a.cap ? 1 : 0;
+    if (tid == 0) S.rs[0] = 0;
+    const int stored = misc[CL_WARPS - 1];
+    // 2. the rows this CTA reads from other CTAs, as a bitmap over all rows
+    for (int w = tid; w < a.Vw; w += CL_THREADS) S.bits[w] = 0u;
+    __syncthreads();
+    if (tid == 0) misc[34] = 0;  // requests received (other CTAs add to it after the next barrier)
+    if (tid < nrows) {
+        const int row = row0 + tid;
+        for (int k = a.rp[row]; k < a.rp[row + 1]; ++k) {
+            const int c = a.ci[k];
+            if (c < row0 || c >= row0 + nrows) atomicOr(&S.bits[c >> 5], 1u << (c & 31));
+        }
     }
-    cl_sync();
-    // every CTA learns whether any CTA's blocks exceed its stage (then nobody runs)
-    const uint32_t flag = (uint32_t)lane < C ? cl_ld_u32(cl_map(cl_smem_addr(S.misc + 32), lane)) : 0u;
-    if (__any_sync(0xffffffffu, flag != 0u)) {
+    __syncthreads();
+    // 3. ghost numbers: a prefix sum of the words' populations (Vw <= threads)
+    const int pop = tid < a.Vw ? __popc(S.bits[tid]) : 0;
+    const int gincl = cl_scan(pop, misc);
+    if (tid < a.Vw) S.pref[tid] = gincl - pop;
+    const int n_ghost = misc[CL_WARPS - 1];
+    if (cl_vote(&misc[32], stored > a.cap || n_ghost > a.gcap, C)) {
+        // some CTA's blocks or ghost rows exceed its shared memory: nobody runs
         if (rank == 0 && tid == 0) {
             a.sc->status = PC_ERR_CAPACITY;
             a.sc->done = 1;
@@ -406,17 +497,36 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
         cl_sync();
         return;
     }
-
-    // 2. the rows into shared memory; each block's column becomes its record's address
+    // 4. ask each ghost row's owner to send it: (owner's local row, this rank, ghost number)
+    for (int w = tid; w < a.Vw; w += CL_THREADS) {
+        uint32_t word = S.bits[w];
+        int g = S.pref[w];
+        while (word) {
+            const int c = 32 * w + __ffs(word) - 1;
+            word &= word - 1;
+            const int o = c / Rc;
+            const uint32_t pos = cl_atom_add(cl_map(cl_smem_addr(&misc[34]), (uint32_t)o), 1u);
+            if ((int)pos < a.pcap)
+                cl_st_u32(cl_map(cl_smem_addr(&S.push[pos]), (uint32_t)o),
+                          (uint32_t)(c - o * Rc) | (rank << 10) | ((uint32_t)g << 14));
+            ++g;
+        }
+    }
+    // 5. the rows into shared memory; each block's column becomes an index into u / x64
     if (tid < nrows) {
         const int row = row0 + tid;
         int pos = S.rs[tid];
-        const uint32_t rec0 = cl_smem_addr(S.rec);
         for (int k = a.rp[row]; k < a.rp[row + 1]; ++k) {
             const int c = a.ci[k];
             if (DIFF && c == row) continue;
-            const int owner = c / Rc;
-            S.addr[pos] = cl_map(rec0 + (uint32_t)(c - owner * Rc) * (uint32_t)sizeof(ClRec), (uint32_t)owner);
+            int j;
+            if (c >= row0 && c < row0 + nrows) {
+                j = c - row0;
+            } else {
+                const uint32_t word = S.bits[c >> 5], below = (1u << (c & 31)) - 1u;
+                j = Rc + S.pref[c >> 5] + __popc(word & below);
+            }
+            S.idx[pos] = (uint16_t)j;
             const float *B = a.vals + 9ll * k;
 #pragma unroll
             for (int e = 0; e < 9; ++e) S.vals[9 * pos + e] = B[e];
@@ -427,221 +537,243 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
             for (int e = 0; e < 9; ++e) S.dres[9 * tid + e] = a.dres[9ll * row + e];
         if (BLOCK) {
             const float4 *d4 = reinterpret_cast<const float4 *>(a.dinv);
-            for (int j = 0; j < 3; ++j) S.dinv[3 * tid + j] = d4[3ll * row + j];
+            for (int q = 0; q < 3; ++q) {
+                const float4 d = d4[3ll * row + q];
+                S.dinv[9 * tid + 3 * q] = d.x;
+                S.dinv[9 * tid + 3 * q + 1] = d.y;
+                S.dinv[9 * tid + 3 * q + 2] = d.z;
+            }
         } else {
-            S.dinv[tid] = make_float4(a.dinv[3ll * row], a.dinv[3ll * row + 1], a.dinv[3ll * row + 2], 0.f);
+            reinterpret_cast<float4 *>(S.dinv)[tid] =
+                make_float4(a.dinv[3ll * row], a.dinv[3ll * row + 1], a.dinv[3ll * row + 2], 0.f);
         }
-        ClRec &R = S.rec[tid];
-        R.p[0] = R.p[1] = R.z = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int e = 0; e < 3; ++e) R.x[e] = (double)a.dv[3ll * row + e];
-        R.pad = 0.0;
-        S.xv[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int e = 0; e < 3; ++e) S.x64[4 * tid + e] = (double)a.dv[3ll * row + e];
+        S.x64[4 * tid + 3] = 0.0;
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        S.xv[tid] = zero;
+        S.p[tid] = zero;
+        S.s[tid] = zero;
     }
-    cl_sync();
+    // every request has landed after this barrier; an owner asked for more rows than it
+    // can list stops everybody
+    if (cl_vote(&misc[33], misc[34] > a.pcap, C)) {
+        if (rank == 0 && tid == 0) {
+            a.sc->status = PC_ERR_CAPACITY;
+            a.sc->done = 1;
+            a.sc->iter = 0;
+        }
+        cl_sync();
+        return;
+    }
+    const int n_push = misc[34];
 
-    // 3. the start: r = b - A dv in FP64 (rounded to FP32), z = D^-1 r, p_prev = 0.
-    // The FP64 scalars and the stop logic belong to thread 0 of each CTA (S.ctl); the CTA
-    // learns alpha, beta and the next action from it (S.bc).
-    ClCtl &K = *S.ctl;
+    // 6. the start: r = b - A dv in FP64 (rounded to FP32), u = M^-1 r, w = A u; p = s = 0.
+    // Thread 0 of each CTA (the same values in every CTA) keeps the scalars and the stop
+    // logic and tells its CTA alpha, beta and what comes next.
+    ClRed &K = *S.red;
+    float2 tot[5];
     {
-        double t[3], tot[3];
-        cl_residual<DIFF, BLOCK>(S, a, row0, nrows, true, t);
-        cl_reduce_d<3>(t, tot, S, par, C);
+        cl_push_x64(S, Rc, n_push);
+        cl_sync();
+        float gam = 0.f, d = 0.f, e = 0.f, f = 0.f;
+        double rr = 0.0, bb = 0.0;
+        cl_residual<DIFF, BLOCK>(S, a, row0, nrows, true, gam, rr, bb);
+        __syncthreads();
+        cl_push_u(S, Rc, n_push);
+        cl_sync();
+        cl_product<DIFF>(S, nrows, d, e, f);
+        const float2 v[4] = {make_float2(gam, 0.f), cl_pair(rr), make_float2(d, 0.f), cl_pair(bb)};
+        float2 t4[4];
+        cl_reduce<4, true>(v, t4, S, par, C, rank);
         if (tid == 0) {
-            K.rz = tot[0];
-            K.rz_f = (float)K.rz;
-            K.rr = tot[1];
-            K.bb = tot[2];
-            K.tol2 = a.tol * a.tol * K.bb;
-            K.rr_last = K.rr;
+            // a power of two that brings b.b near 1 keeps the FP32 scalars far from the
+            // range limits (the scaling is exact)
+            const double bbv = pc_df_value(t4[3].x, t4[3].y);
+            int ex = 0;
+            if (isfinite(bbv) && bbv > 0.0) frexp(bbv, &ex);
+            K.sigma = ldexpf(1.f, -ex);
+            K.tol2 = (float)ldexp(a.tol * a.tol * bbv, -ex);
+            K.bb64 = bbv;
+            K.rr64 = pc_df_value(t4[1].x, t4[1].y);
+            const float gam0 = __fadd_rn(t4[0].x, t4[0].y) * K.sigma, rr0 = __fadd_rn(t4[1].x, t4[1].y) * K.sigma;
+            const float del0 = __fadd_rn(t4[2].x, t4[2].y) * K.sigma;
+            K.alpha = gam0 / del0;
+            K.beta = 0.f;
+            K.gam_old = gam0;
+            K.rr_last = rr0;
             K.status = PC_OK;
             K.iter_last = 0;
             K.outer = 0;
-            K.bad_pq = 0;
             int act = 0;
-            if (!isfinite(K.bb) || !isfinite(K.rr)) {
+            if (!isfinite(rr0) || !isfinite(gam0)) {
                 K.status = PC_ERR_NONFINITE;
                 act = CL_ACT_DONE;
-            } else if (K.rr <= K.tol2) {
+            } else if (rr0 <= K.tol2) {
                 act = CL_ACT_DONE;
             } else if (a.max_iter <= 0) {
                 K.status = PC_ERR_NOT_CONVERGED;
                 act = CL_ACT_DONE;
+            } else if (!(del0 > 0.f) || !isfinite(K.alpha)) {
+                K.status = PC_ERR_NONFINITE;
+                act = CL_ACT_DONE;
             }
-            S.bc->action = act;
+            K.action = act;
         }
         __syncthreads();
     }
-    int action = S.bc->action;
-    float beta = 0.f;
-    int cur = 0, iter = 0;
+    int iter = 0;
+    int action = K.action;
 
     while (!(action & CL_ACT_DONE)) {
-        // q = A p, p = z + beta p_prev formed per gathered row; p.q
-        float pqf = 0.f;
-        const uint32_t poff = cur ? 16u : 0u;
-        for (int l0 = 0; l0 < nrows; l0 += CL_GROUPS) {
-            const int l = l0 + grp;
-            const bool ok = l < nrows;
-            float4 pl = make_float4(0.f, 0.f, 0.f, 0.f);
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-            if (ok) {
-                pl = cl_dir(beta, S.rec[l].p[cur], S.rec[l].z);
-                const int k1 = S.rs[l + 1];
-                for (int k = S.rs[l] + sub; k < k1; k += CL_TPR) {
-                    const uint32_t ad = S.addr[k];
-                    float4 d = cl_dir(beta, cl_ld_f4(ad + poff), cl_ld_f4(ad + CL_REC_Z));
-                    if (DIFF) {
-                        d.x -= pl.x;
-                        d.y -= pl.y;
-                        d.z -= pl.z;
-                    }
-                    const float *B = S.vals + 9 * k;
-                    a0 = fmaf(B[2], d.z, fmaf(B[1], d.y, fmaf(B[0], d.x, a0)));
-                    a1 = fmaf(B[5], d.z, fmaf(B[4], d.y, fmaf(B[3], d.x, a1)));
-                    a2 = fmaf(B[8], d.z, fmaf(B[7], d.y, fmaf(B[6], d.x, a2)));
-                }
-            }
-            for (int o = 1; o < CL_TPR; o <<= 1) {
-                a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-                a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-            }
-            if (ok && sub == 0) {
-                if (DIFF) {
-                    const float *D = S.dres + 9 * l;
-                    a0 = fmaf(D[2], pl.z, fmaf(D[1], pl.y, fmaf(D[0], pl.x, a0)));
-                    a1 = fmaf(D[5], pl.z, fmaf(D[4], pl.y, fmaf(D[3], pl.x, a1)));
-                    a2 = fmaf(D[8], pl.z, fmaf(D[7], pl.y, fmaf(D[6], pl.x, a2)));
-                }
-                const float4 q = make_float4(a0, a1, a2, 0.f);
-                S.rec[l].p[cur ^ 1] = pl;
-                S.qv[l] = q;
-                pqf += cl_dot3(pl, q);
-            }
-        }
-        {
-            const float v[1] = {pqf};
-            float2 tot[1];
-            cl_reduce_df<1>(v, tot, S, par, C);
-            if (tid == 0) {
-                // the quotient in FP32, the precision the update uses it in
-                const float pq = __fadd_rn(tot[0].x, tot[0].y);
-                float alpha = K.rz_f / pq;
-                K.bad_pq = !(pq > 0.f) || !isfinite(alpha);
-                if (K.bad_pq) alpha = 0.f;
-                S.bc->alpha = alpha;
-            }
-            __syncthreads();
-        }
-        const float alpha = S.bc->alpha;
-
-        // x += alpha p, r -= alpha q, z = D^-1 r; r.z, r.r
-        float rzf = 0.f, rrf = 0.f;
+        const float alpha = K.alpha, beta = K.beta;
+        // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = M^-1 r; (r, u), (r, r)
+        float g = 0.f, q = 0.f;
         for (int l = tid; l < nrows; l += CL_THREADS) {
-            const float4 p = S.rec[l].p[cur ^ 1], q = S.qv[l];
-            float4 x = S.xv[l], r = S.rv[l];
-            x.x = fmaf(alpha, p.x, x.x);
-            x.y = fmaf(alpha, p.y, x.y);
-            x.z = fmaf(alpha, p.z, x.z);
-            r.x = fmaf(-alpha, q.x, r.x);
-            r.y = fmaf(-alpha, q.y, r.y);
-            r.z = fmaf(-alpha, q.z, r.z);
-            const float4 z = cl_precond<BLOCK>(S.dinv, l, r);
+            const float4 p = cl_axpy(beta, S.p[l], S.u[l]), s = cl_axpy(beta, S.s[l], S.w[l]);
+            const float4 x = cl_axpy(alpha, p, S.xv[l]), r = cl_axpy(-alpha, s, S.r[l]);
+            const float4 u = cl_precond<BLOCK>(S.dinv, l, r);
+            S.p[l] = p;
+            S.s[l] = s;
             S.xv[l] = x;
-            S.rv[l] = r;
-            S.rec[l].z = z;
-            rzf += cl_dot3(r, z);
-            rrf += cl_dot3(r, r);
+            S.r[l] = r;
+            S.u[l] = u;
+            g += cl_dot3(r, u);
+            q += cl_dot3(r, r);
         }
+        __syncthreads();
+        cl_push_u(S, Rc, n_push);
+        cl_sync();
+        float d = 0.f, e = 0.f, f = 0.f;
+        cl_product<DIFF>(S, nrows, d, e, f);
         {
-            const float v[2] = {rzf, rrf};
-            float2 tot[2];
-            cl_reduce_df<2>(v, tot, S, par, C);
-            if (tid == 0) {
-                const float rz_new = __fadd_rn(tot[0].x, tot[0].y);
-                const float beta_d = rz_new / K.rz_f;
-                K.rz_f = rz_new;
-                K.rz = pc_df_value(tot[0].x, tot[0].y);
-                K.rr = pc_df_value(tot[1].x, tot[1].y);
-                const double rr = K.rr;
-                const int it = iter + 1;
-                int act = 0;
-                bool conv = false;
-                if (K.bad_pq || !isfinite(rr) || !isfinite(beta_d)) {
+            const float2 v[5] = {make_float2(g, 0.f), make_float2(q, 0.f), make_float2(d, 0.f), make_float2(e, 0.f),
+                                 make_float2(f, 0.f)};
+            cl_reduce<5, false>(v, tot, S, par, C, rank);
+        }
+        ++iter;
+        // thread 0: the stop tests, then either the next step's scalars or a replacement
+        if (tid == 0) {
+            const float gam = __fadd_rn(tot[0].x, tot[0].y) * K.sigma, rr = __fadd_rn(tot[1].x, tot[1].y) * K.sigma;
+            int act = 0;
+            bool conv = false;
+            if (!isfinite(rr) || !isfinite(gam)) {
+                K.status = PC_ERR_NONFINITE;
+                act = CL_ACT_DONE;
+            } else if (rr <= K.tol2) {
+                conv = true;
+            } else if (iter >= a.max_iter) {
+                K.status = PC_ERR_NOT_CONVERGED;
+                act = CL_ACT_DONE;
+            }
+            if (!act) {
+                if (!a.mixed) {
+                    act = conv ? CL_ACT_DONE : 0;
+                } else if (conv) {
+                    // a converged recurrence residual is confirmed by an FP64 replacement
+                    act = (rr > 0.f && iter > K.iter_last) ? CL_ACT_REPLACE : CL_ACT_DONE;
+                } else if (iter % a.check_every == 0) {
+                    act = CL_ACT_FOLD;
+                    if (rr <= K.rr_last * (float)(a.refresh * a.refresh) || iter - K.iter_last >= a.refresh_every)
+                        act |= CL_ACT_REPLACE;
+                }
+            }
+            // beta' = gamma / gamma_old from the recurrence, also when a replacement follows:
+            // as in the grid-wide solver the replacement keeps the direction and beta and
+            // takes the replaced gamma only into alpha (with the replaced gamma in beta the
+            // iteration stalls after a replacement near FP32's attainable accuracy)
+            K.beta = gam / K.gam_old;
+            if (!(act & (CL_ACT_DONE | CL_ACT_REPLACE))) {
+                // alpha' = gamma / (p', A p')
+                const float bt = K.beta;
+                const float pap = fmaf(bt, fmaf(bt, __fadd_rn(tot[4].x, tot[4].y) * K.sigma,
+                                                __fadd_rn(tot[3].x, tot[3].y) * K.sigma),
+                                       __fadd_rn(tot[2].x, tot[2].y) * K.sigma);
+                K.alpha = gam / pap;
+                K.gam_old = gam;
+                if (!(pap > 0.f) || !isfinite(K.alpha) || !isfinite(bt)) {
                     K.status = PC_ERR_NONFINITE;
                     act = CL_ACT_DONE;
-                } else if (rr <= K.tol2) {
-                    conv = true;
-                } else if (it >= a.max_iter) {
-                    K.status = PC_ERR_NOT_CONVERGED;
-                    act = CL_ACT_DONE;
                 }
-                if (!act) {
-                    if (!a.mixed) {
-                        act = conv ? CL_ACT_DONE : 0;
-                    } else if (conv) {
-                        // a converged recurrence residual is confirmed by an FP64 replacement
-                        act = (rr > 0.0 && it > K.iter_last) ? CL_ACT_REPLACE : CL_ACT_DONE;
-                    } else if (it % a.check_every == 0) {
-                        act = CL_ACT_FOLD;
-                        if (rr <= K.rr_last * a.refresh * a.refresh || it - K.iter_last >= a.refresh_every)
-                            act |= CL_ACT_REPLACE;
-                    }
-                }
-                S.bc->beta = beta_d;
-                S.bc->action = act;
             }
-            __syncthreads();
+            K.action = act;
         }
-        beta = S.bc->beta;
-        action = S.bc->action;
-        cur ^= 1;
-        ++iter;
+        __syncthreads();
+        action = K.action;
         if (action & (CL_ACT_FOLD | CL_ACT_REPLACE)) cl_fold(S, nrows);
         if (action & CL_ACT_REPLACE) {
-            cl_sync();  // every CTA's folded iterate before any CTA gathers it
-            double t[3], tot[3];
-            cl_residual<DIFF, BLOCK>(S, a, row0, nrows, true, t);
-            cl_reduce_d<3>(t, tot, S, par, C);
+            // r = b - A x in FP64, u = M^-1 r, and the products s = A p and w = A u anew
+            // (the recurrences for s and r drift; p stays)
+            __syncthreads();  // every row folded before any is sent
+            cl_push_x64(S, Rc, n_push);
+            cl_sync();
+            float gr = 0.f, d2 = 0.f, e2 = 0.f, f2 = 0.f;
+            double rr64 = 0.0, bb_unused = 0.0;
+            cl_residual<DIFF, BLOCK>(S, a, row0, nrows, true, gr, rr64, bb_unused);
+            __syncthreads();
+            for (int l = tid; l < nrows; l += CL_THREADS) {  // u aside in w, p through the product
+                S.w[l] = S.u[l];
+                S.u[l] = S.p[l];
+            }
+            __syncthreads();
+            cl_push_u(S, Rc, n_push);
+            cl_sync();
+            cl_product<DIFF, true>(S, nrows, d2, e2, f2);
+            __syncthreads();
+            for (int l = tid; l < nrows; l += CL_THREADS) S.u[l] = S.w[l];
+            cl_sync();  // every CTA's product of p done before u overwrites the ghost copies
+            cl_push_u(S, Rc, n_push);
+            cl_sync();
+            cl_product<DIFF>(S, nrows, d2, e2, f2);
+            const float2 v[5] = {make_float2(gr, 0.f), cl_pair(rr64), make_float2(d2, 0.f), make_float2(e2, 0.f),
+                                 make_float2(f2, 0.f)};
+            cl_reduce<5, true>(v, tot, S, par, C, rank);
             if (tid == 0) {
-                K.rz = tot[0];
-                K.rz_f = (float)K.rz;
-                K.rr = tot[1];
-                K.rr_last = K.rr;
+                K.rr64 = pc_df_value(tot[1].x, tot[1].y);
+                const float gam = __fadd_rn(tot[0].x, tot[0].y) * K.sigma;
+                const float rr = __fadd_rn(tot[1].x, tot[1].y) * K.sigma;
+                K.rr_last = rr;
                 K.iter_last = iter;
                 ++K.outer;
                 int act = 0;
-                if (!isfinite(K.rr)) {
+                if (!isfinite(rr) || !isfinite(gam)) {
                     K.status = PC_ERR_NONFINITE;
                     act = CL_ACT_DONE;
-                } else if (K.rr <= K.tol2) {
+                } else if (rr <= K.tol2) {
                     act = CL_ACT_DONE;
                 } else if (iter >= a.max_iter) {
                     K.status = PC_ERR_NOT_CONVERGED;
                     act = CL_ACT_DONE;
+                } else {
+                    const float bt = K.beta;  // the recurrence's
+                    const float pap = fmaf(bt, fmaf(bt, __fadd_rn(tot[4].x, tot[4].y) * K.sigma,
+                                                    __fadd_rn(tot[3].x, tot[3].y) * K.sigma),
+                                           __fadd_rn(tot[2].x, tot[2].y) * K.sigma);
+                    K.alpha = gam / pap;
+                    K.gam_old = gam;
+                    if (!(pap > 0.f) || !isfinite(K.alpha) || !isfinite(bt)) {
+                        K.status = PC_ERR_NONFINITE;
+                        act = CL_ACT_DONE;
+                    }
                 }
-                S.bc->action = act;
+                K.action = act;
             }
             __syncthreads();
-            action = S.bc->action;
+            action = K.action;
         }
     }
 
-    // 4. the solution, and its FP64 residual unless the last replacement measured it
-    if (tid == 0) S.bc->check = a.mixed ? (iter > K.iter_last ? 1 : 0) : 1;
-    __syncthreads();
-    const bool check = S.bc->check != 0;
+    // 7. the solution, and its FP64 residual unless the last replacement measured it
+    const bool check = a.mixed ? iter > K.iter_last : true;
     if (a.mixed) {
         if (check) cl_fold(S, nrows);
         for (int l = tid; l < nrows; l += CL_THREADS) {
             const int64_t row = row0 + l;
             for (int e = 0; e < 3; ++e) {
-                const double x = S.rec[l].x[e];
+                const double x = S.x64[4 * l + e];
                 const float d = (float)x;
                 a.dv[3 * row + e] = d;
                 if (a.x64) a.x64[3 * row + e] = x;
-                if (check) S.rec[l].x[e] = (double)d;
+                if (check) S.x64[4 * l + e] = (double)d;
             }
         }
     } else {
@@ -652,30 +784,35 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
             a.dv[3 * row] = d0;
             a.dv[3 * row + 1] = d1;
             a.dv[3 * row + 2] = d2;
-            S.rec[l].x[0] = (double)d0;
-            S.rec[l].x[1] = (double)d1;
-            S.rec[l].x[2] = (double)d2;
+            S.x64[4 * l] = (double)d0;
+            S.x64[4 * l + 1] = (double)d1;
+            S.x64[4 * l + 2] = (double)d2;
         }
     }
     if (check) {
+        __syncthreads();
+        cl_push_x64(S, Rc, n_push);
         cl_sync();
-        double t[3], tot[3];
-        cl_residual<DIFF, BLOCK>(S, a, row0, nrows, false, t);
-        cl_reduce_d<3>(t, tot, S, par, C);
+        float g_unused = 0.f;
+        double rr64 = 0.0, bb = 0.0;
+        cl_residual<DIFF, BLOCK>(S, a, row0, nrows, false, g_unused, rr64, bb);
+        const float2 v[2] = {cl_pair(rr64), cl_pair(bb)};
+        float2 t2[2];
+        cl_reduce<2, true>(v, t2, S, par, C, rank);
         if (tid == 0) {
-            K.rr = tot[1];
-            K.bb = tot[2];
+            K.rr64 = pc_df_value(t2[0].x, t2[0].y);
+            K.bb64 = pc_df_value(t2[1].x, t2[1].y);
         }
     }
     cl_sync();
     if (rank == 0 && tid == 0) {
         pc_scalars *sc = a.sc;
-        sc->rz = K.rz;
-        sc->rr = K.rr;
-        sc->bb = K.bb;
-        sc->tol2 = K.tol2;
-        sc->alpha = 0.0;
-        sc->beta = (double)beta;
+        sc->rz = (double)(K.gam_old / K.sigma);
+        sc->rr = K.rr64;
+        sc->bb = K.bb64;
+        sc->tol2 = a.tol * a.tol * K.bb64;
+        sc->alpha = (double)K.alpha;
+        sc->beta = (double)K.beta;
         sc->pq = 0.0;
         sc->iter = iter;
         sc->max_iter = a.max_iter;
@@ -730,34 +867,60 @@ static pc_status cl_size(size_t smem, int *C)
     return PC_OK;
 }
 
-// Shared-memory layout for V rows over C CTAs; false when the rows do not fit.
+// Shared-memory layout for V rows over C CTAs; false when the rows do not fit. The room
+// left after the per-row arrays goes to the blocks (the average CTA's share and a quarter
+// more) and then to ghost rows; the kernel itself refuses a CTA whose blocks, ghost rows
+// or send list exceed what it got, and the automatic schedule then solves on the grid.
 static bool cl_layout(int V, int C, bool diff, bool block, size_t smax, int64_t stored, ClArgs *a, size_t *smem)
 {
     const int Rc = (V + C - 1) / C;
-    if (Rc < 1 || Rc > CL_THREADS) return false;
-    size_t o = 0;
-    auto take = [&](size_t bytes) {
-        const size_t at = o;
-        o += (bytes + 15) & ~(size_t)15;
-        return (uint32_t)at;
+    const int Vw = (V + 31) / 32;
+    if (Rc < 1 || Rc > CL_THREADS || Vw > CL_THREADS) return false;
+    auto layout = [&](int gcap, int pcap, size_t *end) {
+        size_t o = 0;
+        auto take = [&](size_t bytes) {
+            const size_t at = o;
+            o += (bytes + 15) & ~(size_t)15;
+            return (uint32_t)at;
+        };
+        take(16ull * (Rc + gcap));
+        a->o_x64 = take(32ull * (Rc + gcap));
+        a->o_xv = take(16ull * Rc);
+        a->o_r = take(16ull * Rc);
+        a->o_w = take(16ull * Rc);
+        a->o_p = take(16ull * Rc);
+        a->o_s = take(16ull * Rc);
+        a->o_dres = take(diff ? 36ull * Rc : 0);
+        a->o_dinv = take((block ? 36ull : 16ull) * Rc);
+        a->o_rs = take(4ull * (Rc + 1));
+        a->o_bits = take(4ull * Vw);
+        a->o_pref = take(4ull * Vw);
+        a->o_push = take(4ull * pcap);
+        a->o_red = take(sizeof(ClRed));
+        *end = o;
     };
-    take(sizeof(ClRec) * Rc);
-    a->o_x = take(16ull * Rc);
-    a->o_r = take(16ull * Rc);
-    a->o_q = take(16ull * Rc);
-    a->o_dres = take(diff ? 36ull * Rc : 0);
-    a->o_dinv = take((block ? 48ull : 16ull) * Rc);
-    a->o_rs = take(4ull * (Rc + 1));
-    a->o_red = take(8ull * (4 * CL_WARPS + 8) + 4ull * 40 + sizeof(ClCtl) + sizeof(ClBcast));
-    if (o >= smax) return false;
-    const int64_t cap = (int64_t)((smax - o) / 40) & ~(int64_t)3;
-    // the average CTA's blocks must fit (the kernel checks every CTA's exactly)
-    if (cap < 4 || (stored + C - 1) / C > cap) return false;
-    a->o_addr = (uint32_t)o;
-    a->o_vals = (uint32_t)(o + 4 * cap);
+    size_t fixed = 0;
+    layout(0, 0, &fixed);
+    const int64_t share = (stored + C - 1) / C;
+    const int64_t want = share + share / 4 + 64;
+    if ((int64_t)fixed + 38 * want + 64 >= (int64_t)smax) return false;
+    // a ghost row costs 16 (u) + 32 (FP64 iterate) + 4 (a send-list entry) bytes
+    const int64_t room = ((int64_t)smax - (int64_t)fixed - 38 * want - 64) / 52;
+    const int gcap = (int)std::min<int64_t>(std::min(V, 2048), room);
+    const int pcap = gcap;
+    size_t o = 0;
+    layout(gcap, pcap, &o);
+    int64_t cap = (int64_t)((smax - o - 16) / 38) & ~(int64_t)7;
+    if (cap < 8 || share > cap) return false;
+    a->o_idx = (uint32_t)o;
+    a->o_vals = (uint32_t)(o + ((2 * cap + 15) & ~(int64_t)15));
+    *smem = a->o_vals + 36 * (size_t)cap;
+    if (*smem > smax) return false;
     a->Rc = Rc;
+    a->Vw = Vw;
     a->cap = (int)cap;
-    *smem = o + 40 * (size_t)cap;
+    a->gcap = gcap;
+    a->pcap = pcap;
     return true;
 }
 

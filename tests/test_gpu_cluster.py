@@ -77,9 +77,27 @@ def test_cluster_solve_matches_oracle_and_grid(pc, case, precond, precision):
     else:
         # as for the grid schedule: FP32 PCG stops on its recurrence residual
         assert info_c.rel_res <= 1e-4 and err <= 1e-4 and info_c.outer == 0
-    # the same method, dot products summed in another order
-    assert abs(info_c.iters - info_g.iters) <= 0.12 * info_g.iters + 5
+    # the cluster schedule runs the single-reduction (Chronopoulos-Gear) form of the same
+    # method: the same count in FP32 and at moderate tolerances; near FP32's attainable
+    # accuracy (the mixed form at 1e-9) its residual recurrence, which goes through the
+    # recurrence for A p, needs up to about a third more iterations
+    slack = 0.35 if precision == "mixed" else 0.05
+    assert info_c.iters <= (1 + slack) * info_g.iters + 5 and info_c.iters >= 0.9 * info_g.iters - 5
     assert (_np(dv_c).reshape(-1, 3)[wl.pins] == 0).all()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_cluster_iterations_at_the_benchmark_tolerance(pc, case):
+    """At a relative residual of 1e-6 (the benchmark's) the single-reduction form takes the
+    iterations of the grid schedule's two-reduction form, within a few."""
+    wl = CASES[case]()
+    cl, s, _ = _system(pc, wl)
+    kw = dict(tol=1e-6, precision=pc.PC_PREC_MIXED, max_iter=50000)
+    _, info_c, st_c = _solve(pc, cl, s, s["dres"], schedule=pc.PC_SCHED_CLUSTER, **kw)
+    _, info_g, st_g = _solve(pc, cl, s, s["dres"], schedule=pc.PC_SCHED_GRID, **kw)
+    print(f"{case}: cluster {info_c.iters}, grid {info_g.iters} iterations at 1e-6")
+    assert st_c == pc.PC_OK and st_g == pc.PC_OK and info_c.rel_res <= 1e-6
+    assert abs(info_c.iters - info_g.iters) <= 0.03 * info_g.iters + 3
 
 
 def test_cluster_plain_form_matches_grid(pc):

@@ -371,8 +371,11 @@ def test_all_storages_agree_with_oracle(pc, case, form):
     # depends on summation order (measured: 809..931 on the 64^2 cloth for the four
     # layouts, fused or not; within 1% at 1e-6); the plain form at 1e-11 more so
     slack = 0.12 if form == "difference" else 0.15
-    for storage in (pc.PC_STORAGE_SYM, pc.PC_STORAGE_SELL, pc.PC_STORAGE_OFFDIAG, "cluster"):
+    for storage in (pc.PC_STORAGE_SYM, pc.PC_STORAGE_SELL, pc.PC_STORAGE_OFFDIAG):
         assert abs(out[storage][0] - out[pc.PC_STORAGE_FULL][0]) <= slack * out[pc.PC_STORAGE_FULL][0] + 5
+    # the cluster schedule's single-reduction form needs up to about a third more
+    # iterations this close to FP32's attainable accuracy (tests/test_gpu_cluster.py)
+    assert out["cluster"][0] <= 1.35 * out[pc.PC_STORAGE_FULL][0] + 5
     if form == "plain":  # the copy without diagonal blocks is for the difference form only
         assert out[pc.PC_STORAGE_OFFDIAG][0] == out[pc.PC_STORAGE_FULL][0]
         assert np.array_equal(out[pc.PC_STORAGE_OFFDIAG][1], out[pc.PC_STORAGE_FULL][1])
@@ -483,8 +486,8 @@ def test_fused_and_two_kernel_updates_agree(pc, case, precond):
         assert st == pc.PC_OK and info.rel_res <= 2e-9
         assert H.rel_l2(_np(dv), dv_ref) <= H.DV_RTOL
         out[form] = info.iters
-    for form in (True, "cluster"):
-        assert abs(out[form] - out[False]) <= 0.12 * out[False] + 5  # see the storage test
+    assert abs(out[True] - out[False]) <= 0.12 * out[False] + 5  # see the storage test
+    assert out["cluster"] <= 1.35 * out[False] + 5  # the single-reduction form, see the storage test
 
 
 def _banded_spd(V, extra_rows, n_extra, seed):
