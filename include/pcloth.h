@@ -143,15 +143,18 @@ typedef struct {
 /* How pc_pcg_solve (and pc_step, pc_pcg_solve_static) runs the iterations.
  * PC_SCHED_CLUSTER: the whole solve is one launch of one thread-block cluster (16 CTAs,
  * one per SM, else 8 where 16 cannot be co-scheduled). Each CTA keeps a contiguous range
- * of rows -- their 3x3 blocks, diagonal data and vectors -- in shared memory for the
- * length of the solve, gathers its neighbours' entries from the other CTAs' shared
- * memory, and the dot products meet at cluster barriers: two per iteration, no kernel
- * boundary. Same method and stop tests as the grid schedule (same preconditioners, FP64
- * residual replacement in PC_PREC_MIXED, the FP64 iterate folded every check_every
+ * of rows -- their 3x3 blocks, diagonal data and vectors, and copies of the rows of other
+ * CTAs that its rows reference -- in shared memory for the length of the solve. The
+ * iteration is the single-reduction (Chronopoulos-Gear) form of the same preconditioned
+ * CG: per iteration one product, one reduction and two cluster barriers, no kernel
+ * boundary. Same preconditioners, stop tests and mixed precision as the grid schedule
+ * (FP64 residual replacement in PC_PREC_MIXED, the FP64 iterate folded every check_every
  * iterations); the first residual is formed in FP64 in both precisions, and storage and
- * fuse do not apply. It takes systems up to about 6,000 rows at cloth density (at most
- * 1,024 rows per CTA and every CTA's blocks within its shared memory); larger ones return
- * PC_ERR_CAPACITY.
+ * fuse do not apply. At a relative residual of 1e-6 it takes the grid schedule's
+ * iteration count; near FP32's attainable accuracy (PC_PREC_MIXED at 1e-9) up to about a
+ * third more. It takes systems up to about 6,000 rows at cloth density (at most 512 rows
+ * per CTA, and every CTA's blocks and copied rows within its shared memory); larger ones
+ * return PC_ERR_CAPACITY.
  * PC_SCHED_GRID: kernels over the whole GPU, iterations launched from the host (the
  * storage and fuse options apply).
  * PC_SCHED_AUTO: the cluster schedule when the system fits it, else the grid schedule. */

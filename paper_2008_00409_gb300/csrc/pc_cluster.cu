@@ -53,11 +53,12 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstddef>
 
 #include "pc_internal.cuh"
 
-#define CL_THREADS 1024
-#define CL_TPR 4                         // threads per row in the products
+#define CL_THREADS 512
+#define CL_TPR 2                         // threads per row in the products
 #define CL_GROUPS (CL_THREADS / CL_TPR)  // rows in flight per CTA
 #define CL_WARPS (CL_THREADS / 32)
 #define CL_MAXC 16                       // CTAs per cluster at most
@@ -73,7 +74,7 @@ struct ClArgs {
     int max_iter, check_every, refresh_every, mixed;
     pc_scalars *sc;
     // byte offsets of the shared-memory arrays (u starts at 0)
-    uint32_t o_x64, o_xv, o_r, o_w, o_p, o_s, o_dres, o_dinv, o_rs, o_bits, o_pref, o_push, o_red, o_idx, o_vals;
+    uint32_t o_x64, o_xv, o_r, o_w, o_p, o_s, o_dres, o_dinv, o_rs, o_bits, o_pref, o_push, o_red, o_blk;
 };
 
 struct ClRed {
@@ -86,6 +87,8 @@ struct ClRed {
     float gam_old, rr_last, alpha, beta;
     int status, iter_last, outer, action;
 };
+static_assert(offsetof(ClRed, slot) % 16 == 0 && (CL_NV * sizeof(float2)) % 16 == 0,
+              "slot rows take 16-byte remote stores");
 #define CL_ACT_DONE 1
 #define CL_ACT_FOLD 2
 #define CL_ACT_REPLACE 4
@@ -101,8 +104,9 @@ struct ClSmem {
     int *pref;           // [Vw] ghost number of each word's first row
     uint32_t *push;      // [pcap] rows to send: local row | rank << 10 | ghost << 14
     ClRed *red;
-    uint16_t *idx;       // [cap] the column of each stored block as an index into u / x64
-    float *vals;         // [cap][9]
+    float4 *blk;         // [cap][3] each stored block: its nine values, then the index of its
+                         // column into u / x64 (an int's bits) and two pad words, so that
+                         // three 16-byte loads fetch a block
 };
 
 // ------------------------------------------------------------------------- cluster primitives
@@ -175,7 +179,7 @@ __device__ __forceinline__ int cl_scan(int v, int *scratch)
     if (lane == 31) scratch[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        int w = scratch[lane];
+        int w = lane < CL_WARPS ? scratch[lane] : 0;
         for (int o = 1; o < 32; o <<= 1) {
             const int n = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += n;
@@ -199,12 +203,13 @@ __device__ __forceinline__ bool cl_vote(int *flag, int mine, uint32_t C)
 }
 
 // Sum N per-thread values over the cluster; the totals land in warp 0 (every lane), in
-// every CTA bitwise the same. Warp sums (FP32 butterflies for the iterations' FP32
-// partials; double-float pairs for the residual passes' FP64 partials); warp 0 adds the
-// warp sums (warp order) as double-float pairs and pushes the CTA's sums into
-// slot[par][rank] of every CTA; a cluster barrier; warp 0 adds the C slots in rank order.
-// Only warp 0 works past the warp sums: the kernel is bound by instruction issue on its
-// few SMs, and double-float butterflies in all 32 warps used to cost more than the product.
+// every CTA bitwise the same: warp sums, warp 0 adds the warp sums (warp order) and pushes
+// the CTA's sums into slot[par][rank] of every CTA, a cluster barrier, warp 0 adds the C
+// slots in rank order. The iterations' dot products (FP32 partials) are summed in FP32 in
+// that fixed tree (13 levels for 512 threads in 16 CTAs: a relative error below 1e-6,
+// far below what the CG scalars tolerate); each double-float stage cost a few hundred
+// cycles of the one warp on the critical path. The FP64 residual passes' partials are
+// summed as double-float pairs (PAIRS).
 template <int N, bool PAIRS>
 __device__ __forceinline__ void cl_reduce(const float2 (&v)[N], float2 (&tot)[N], const ClSmem &S, int &par,
                                           uint32_t C, uint32_t rank)
@@ -225,14 +230,21 @@ __device__ __forceinline__ void cl_reduce(const float2 (&v)[N], float2 (&tot)[N]
         float2 cs[N];
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            float2 w = S.red->warp[lane][i];
-            pc_warp_sum_df(w.x, w.y);
+            float2 w = lane < CL_WARPS ? S.red->warp[lane][i] : make_float2(0.f, 0.f);
+            if (PAIRS) {
+                pc_warp_sum_df(w.x, w.y);
+            } else {
+                for (int o = 16; o > 0; o >>= 1) w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
+            }
             cs[i] = w;
         }
         if ((uint32_t)lane < C) {
+            // the slot row is 16-byte aligned: two pairs per 16-byte remote store
             const uint32_t dst = cl_map(cl_smem_addr(&S.red->slot[par][rank][0]), lane);
 #pragma unroll
-            for (int i = 0; i < N; ++i) cl_st_f2(dst + 8u * i, cs[i]);
+            for (int i = 0; i + 1 < N; i += 2)
+                cl_st_f4(dst + 8u * i, make_float4(cs[i].x, cs[i].y, cs[i + 1].x, cs[i + 1].y));
+            if (N & 1) cl_st_f2(dst + 8u * (N - 1), cs[N - 1]);
         }
     }
     cl_sync();
@@ -240,7 +252,11 @@ __device__ __forceinline__ void cl_reduce(const float2 (&v)[N], float2 (&tot)[N]
 #pragma unroll
         for (int i = 0; i < N; ++i) {
             float2 w = (uint32_t)lane < C ? S.red->slot[par][lane][i] : make_float2(0.f, 0.f);
-            pc_warp_sum_df(w.x, w.y);
+            if (PAIRS) {
+                pc_warp_sum_df(w.x, w.y);
+            } else {
+                for (int o = 16; o > 0; o >>= 1) w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
+            }
             tot[i] = w;
         }
     }
@@ -315,18 +331,46 @@ __device__ __forceinline__ void cl_product(const ClSmem &S, int nrows, float &d,
         if (ok) {
             ul = S.u[l];
             const int k1 = S.rs[l + 1];
-            for (int k = S.rs[l] + sub; k < k1; k += CL_TPR) {
-                float4 uj = S.u[S.idx[k]];
+            // two blocks per step with their own accumulators: two independent chains of
+            // shared-memory loads (block, then its column's u) in flight per thread
+            float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+            int k = S.rs[l] + sub;
+            for (; k + CL_TPR < k1; k += 2 * CL_TPR) {
+                const float4 B2 = S.blk[3 * k + 2], E2 = S.blk[3 * (k + CL_TPR) + 2];
+                float4 uj = S.u[__float_as_int(B2.y)], vj = S.u[__float_as_int(E2.y)];
+                const float4 B0 = S.blk[3 * k], B1 = S.blk[3 * k + 1];
+                const float4 E0 = S.blk[3 * (k + CL_TPR)], E1 = S.blk[3 * (k + CL_TPR) + 1];
+                if (DIFF) {
+                    uj.x -= ul.x;
+                    uj.y -= ul.y;
+                    uj.z -= ul.z;
+                    vj.x -= ul.x;
+                    vj.y -= ul.y;
+                    vj.z -= ul.z;
+                }
+                a0 = fmaf(B0.z, uj.z, fmaf(B0.y, uj.y, fmaf(B0.x, uj.x, a0)));
+                a1 = fmaf(B1.y, uj.z, fmaf(B1.x, uj.y, fmaf(B0.w, uj.x, a1)));
+                a2 = fmaf(B2.x, uj.z, fmaf(B1.w, uj.y, fmaf(B1.z, uj.x, a2)));
+                c0 = fmaf(E0.z, vj.z, fmaf(E0.y, vj.y, fmaf(E0.x, vj.x, c0)));
+                c1 = fmaf(E1.y, vj.z, fmaf(E1.x, vj.y, fmaf(E0.w, vj.x, c1)));
+                c2 = fmaf(E2.x, vj.z, fmaf(E1.w, vj.y, fmaf(E1.z, vj.x, c2)));
+            }
+            if (k < k1) {
+                const float4 B2 = S.blk[3 * k + 2];
+                float4 uj = S.u[__float_as_int(B2.y)];
+                const float4 B0 = S.blk[3 * k], B1 = S.blk[3 * k + 1];
                 if (DIFF) {
                     uj.x -= ul.x;
                     uj.y -= ul.y;
                     uj.z -= ul.z;
                 }
-                const float *B = S.vals + 9 * k;
-                a0 = fmaf(B[2], uj.z, fmaf(B[1], uj.y, fmaf(B[0], uj.x, a0)));
-                a1 = fmaf(B[5], uj.z, fmaf(B[4], uj.y, fmaf(B[3], uj.x, a1)));
-                a2 = fmaf(B[8], uj.z, fmaf(B[7], uj.y, fmaf(B[6], uj.x, a2)));
+                a0 = fmaf(B0.z, uj.z, fmaf(B0.y, uj.y, fmaf(B0.x, uj.x, a0)));
+                a1 = fmaf(B1.y, uj.z, fmaf(B1.x, uj.y, fmaf(B0.w, uj.x, a1)));
+                a2 = fmaf(B2.x, uj.z, fmaf(B1.w, uj.y, fmaf(B1.z, uj.x, a2)));
             }
+            a0 += c0;
+            a1 += c1;
+            a2 += c2;
         }
         for (int o = 1; o < CL_TPR; o <<= 1) {
             a0 += __shfl_xor_sync(0xffffffffu, a0, o);
@@ -375,17 +419,17 @@ __device__ __forceinline__ void cl_residual(const ClSmem &S, const ClArgs &a, in
         if (ok) {
             const int k1 = S.rs[l + 1];
             for (int k = S.rs[l] + sub; k < k1; k += CL_TPR) {
-                const double *xj = S.x64 + 4 * S.idx[k];
+                const float4 B0 = S.blk[3 * k], B1 = S.blk[3 * k + 1], B2 = S.blk[3 * k + 2];
+                const double *xj = S.x64 + 4 * __float_as_int(B2.y);
                 double d0 = xj[0], d1 = xj[1], d2 = xj[2];
                 if (DIFF) {
                     d0 -= xl0;
                     d1 -= xl1;
                     d2 -= xl2;
                 }
-                const float *B = S.vals + 9 * k;
-                a0 += (double)B[0] * d0 + (double)B[1] * d1 + (double)B[2] * d2;
-                a1 += (double)B[3] * d0 + (double)B[4] * d1 + (double)B[5] * d2;
-                a2 += (double)B[6] * d0 + (double)B[7] * d1 + (double)B[8] * d2;
+                a0 += (double)B0.x * d0 + (double)B0.y * d1 + (double)B0.z * d2;
+                a1 += (double)B0.w * d0 + (double)B1.x * d1 + (double)B1.y * d2;
+                a2 += (double)B1.z * d0 + (double)B1.w * d1 + (double)B2.x * d2;
             }
         }
         for (int o = 1; o < CL_TPR; o <<= 1) {
@@ -449,8 +493,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
     S.pref = reinterpret_cast<int *>(cl_smem + a.o_pref);
     S.push = reinterpret_cast<uint32_t *>(cl_smem + a.o_push);
     S.red = reinterpret_cast<ClRed *>(cl_smem + a.o_red);
-    S.idx = reinterpret_cast<uint16_t *>(cl_smem + a.o_idx);
-    S.vals = reinterpret_cast<float *>(cl_smem + a.o_vals);
+    S.blk = reinterpret_cast<float4 *>(cl_smem + a.o_blk);
 
     const int tid = threadIdx.x;
     const uint32_t rank = cl_rank(), C = cl_nranks();
@@ -526,10 +569,10 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
                 const uint32_t word = S.bits[c >> 5], below = (1u << (c & 31)) - 1u;
                 j = Rc + S.pref[c >> 5] + __popc(word & below);
             }
-            S.idx[pos] = (uint16_t)j;
             const float *B = a.vals + 9ll * k;
-#pragma unroll
-            for (int e = 0; e < 9; ++e) S.vals[9 * pos + e] = B[e];
+            S.blk[3 * pos] = make_float4(B[0], B[1], B[2], B[3]);
+            S.blk[3 * pos + 1] = make_float4(B[4], B[5], B[6], B[7]);
+            S.blk[3 * pos + 2] = make_float4(B[8], __int_as_float(j), 0.f, 0.f);
             ++pos;
         }
         if (DIFF)
@@ -681,14 +724,14 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
             // as in the grid-wide solver the replacement keeps the direction and beta and
             // takes the replaced gamma only into alpha (with the replaced gamma in beta the
             // iteration stalls after a replacement near FP32's attainable accuracy)
-            K.beta = gam / K.gam_old;
+            K.beta = __fdividef(gam, K.gam_old);
             if (!(act & (CL_ACT_DONE | CL_ACT_REPLACE))) {
                 // alpha' = gamma / (p', A p')
                 const float bt = K.beta;
                 const float pap = fmaf(bt, fmaf(bt, __fadd_rn(tot[4].x, tot[4].y) * K.sigma,
                                                 __fadd_rn(tot[3].x, tot[3].y) * K.sigma),
                                        __fadd_rn(tot[2].x, tot[2].y) * K.sigma);
-                K.alpha = gam / pap;
+                K.alpha = __fdividef(gam, pap);
                 K.gam_old = gam;
                 if (!(pap > 0.f) || !isfinite(K.alpha) || !isfinite(bt)) {
                     K.status = PC_ERR_NONFINITE;
@@ -748,7 +791,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
                     const float pap = fmaf(bt, fmaf(bt, __fadd_rn(tot[4].x, tot[4].y) * K.sigma,
                                                     __fadd_rn(tot[3].x, tot[3].y) * K.sigma),
                                            __fadd_rn(tot[2].x, tot[2].y) * K.sigma);
-                    K.alpha = gam / pap;
+                    K.alpha = __fdividef(gam, pap);
                     K.gam_old = gam;
                     if (!(pap > 0.f) || !isfinite(K.alpha) || !isfinite(bt)) {
                         K.status = PC_ERR_NONFINITE;
@@ -868,7 +911,7 @@ static pc_status cl_size(size_t smem, int *C)
 }
 
 // Shared-memory layout for V rows over C CTAs; false when the rows do not fit. The room
-// left after the per-row arrays goes to the blocks (the average CTA's share and a quarter
+// left after the per-row arrays goes to the blocks (the average CTA's share and an eighth
 // more) and then to ghost rows; the kernel itself refuses a CTA whose blocks, ghost rows
 // or send list exceed what it got, and the automatic schedule then solves on the grid.
 static bool cl_layout(int V, int C, bool diff, bool block, size_t smax, int64_t stored, ClArgs *a, size_t *smem)
@@ -902,19 +945,19 @@ static bool cl_layout(int V, int C, bool diff, bool block, size_t smax, int64_t 
     size_t fixed = 0;
     layout(0, 0, &fixed);
     const int64_t share = (stored + C - 1) / C;
-    const int64_t want = share + share / 4 + 64;
-    if ((int64_t)fixed + 38 * want + 64 >= (int64_t)smax) return false;
+    const int64_t want = share + share / 8 + 32;
+    if ((int64_t)fixed + 48 * want >= (int64_t)smax) return false;
     // a ghost row costs 16 (u) + 32 (FP64 iterate) + 4 (a send-list entry) bytes
-    const int64_t room = ((int64_t)smax - (int64_t)fixed - 38 * want - 64) / 52;
+    const int64_t room = ((int64_t)smax - (int64_t)fixed - 48 * want) / 52;
     const int gcap = (int)std::min<int64_t>(std::min(V, 2048), room);
     const int pcap = gcap;
     size_t o = 0;
     layout(gcap, pcap, &o);
-    int64_t cap = (int64_t)((smax - o - 16) / 38) & ~(int64_t)7;
+    // blocks: 48 bytes each (nine values, the column's index, two pad words)
+    const int64_t cap = (int64_t)((smax - o) / 48);
     if (cap < 8 || share > cap) return false;
-    a->o_idx = (uint32_t)o;
-    a->o_vals = (uint32_t)(o + ((2 * cap + 15) & ~(int64_t)15));
-    *smem = a->o_vals + 36 * (size_t)cap;
+    a->o_blk = (uint32_t)o;
+    *smem = o + 48 * (size_t)cap;
     if (*smem > smax) return false;
     a->Rc = Rc;
     a->Vw = Vw;
