@@ -37,6 +37,10 @@ if HERE not in sys.path:
 
 METRIC = "steps/s at 1.65M tris (assemble+PCG to 1e-6); BSR SpMV GB/s vs 8 TB/s"
 FALLBACK_HBM_GBS = 6800.0
+# shared-memory bandwidth per SM and clock (bytes), the peak of the cluster solve, which
+# works out of the shared memory of the 16 SMs of one thread-block cluster
+SMEM_BYTES_PER_CLK = 128
+CLUSTER_SMS = 16
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the PCG SpMV,
 # from one ncu capture of the current kernel on that workload (mean of 3 launches).
 # ncu DRAM read + write bytes per launch of the PCG product, by (workload, storage)
@@ -63,6 +67,9 @@ def parse():
     ap.add_argument("--train-steps", type=int, default=2000, help="warmstart form: Adam steps")
     ap.add_argument("--garments", type=int, default=64, help="batched form: number of garments")
     ap.add_argument("--no-fuse", action="store_true", help="two-kernel PCG update (no fused direction step)")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "grid", "cluster"],
+                    help="PCG schedule: whole solve in one thread-block cluster when the system fits (auto), "
+                         "grid-wide kernels, or the cluster only")
     ap.add_argument("--damp-mass", type=float, default=0.0, help="Rayleigh damping alpha (1/s)")
     ap.add_argument("--damp-stiff", type=float, default=0.0, help="Rayleigh damping beta (s)")
     return ap.parse_args()
@@ -287,6 +294,7 @@ def run_ours(args):
     precond = pc.PC_PRECOND_BLOCK if args.precond == "block" else pc.PC_PRECOND_JACOBI
     storage = {"sym": pc.PC_STORAGE_SYM, "sell": pc.PC_STORAGE_SELL,
                "offdiag": pc.PC_STORAGE_OFFDIAG}.get(args.storage, pc.PC_STORAGE_FULL)
+    schedule = {"grid": pc.PC_SCHED_GRID, "cluster": pc.PC_SCHED_CLUSTER}.get(args.schedule, pc.PC_SCHED_AUTO)
     nsteps = args.warmup + args.steps
     proximity = wl.contact_kind == "proximity"
     # random contact sets are inputs (generated before timing); proximity contacts are
@@ -304,7 +312,8 @@ def run_ours(args):
         else:
             pd, wd = contacts[k]
         info, st = cl.step(pd, wd, tol=args.tol, precision=prec, warm_start=pc.PC_WARM_PREV,
-                           max_iter=args.max_iter, precond=precond, storage=storage, fuse=not args.no_fuse, allow_not_converged=True)
+                           max_iter=args.max_iter, precond=precond, storage=storage, fuse=not args.no_fuse,
+                           schedule=schedule, allow_not_converged=True)
         return info
 
     for k in range(args.warmup):
@@ -314,6 +323,7 @@ def run_ours(args):
     launches0 = pc.pc_launch_count(cl.ctx)
     pc.pc_spmv_stats(cl.ctx)  # reset
     pc.pc_assembly_stats(cl.ctx)
+    pc.pc_cluster_stats(cl.ctx)
     pc.pc_set_profiling(cl.ctx, True)
     iters, rels, nnzbs = [], [], []
     if world > 1:
@@ -334,6 +344,7 @@ def run_ours(args):
     n_spmv, spmv_ms, spmv_blocks = pc.pc_spmv_stats(cl.ctx)
     nnzb = int(nnzbs[-1]) if nnzbs else 0
     n_asm, asm_ms = pc.pc_assembly_stats(cl.ctx)
+    n_cl, cl_iters, cl_ms = pc.pc_cluster_stats(cl.ctx)
     elapsed = max_over_ranks(elapsed, world)
     value = aggregate_steps_per_s(world, args.steps, elapsed)
 
@@ -349,6 +360,38 @@ def run_ours(args):
     avg_spmv_s = (spmv_ms / 1e3) / max(n_spmv, 1)
     achieved = spmv_bytes / avg_spmv_s / 1e9 if n_spmv else None
     peak, peak_src = measured_hbm()
+    clocks = clk.summary()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": SPMV_DRAM_BYTES.get((wl.name, args.storage)),
+                "kernel": {"sell": "spmv_sell_kernel<true>", "sym": "spmv_sym_kernel<true>"}.get(
+                    args.storage, "spmv_kernel<true,true,CAPR>") + " (q = A p, difference form, with p.q; "
+                    + args.storage + " storage; CAPR = 14 or 18 blocks per row per stage, chosen per "
+                    "solve from the largest tile)",
+                "blocks_per_launch": int(spmv_blocks),
+                "bytes_per_launch": spmv_bytes, "peak_source": peak_src,
+                "avg_launch_us": avg_spmv_s * 1e6, "timed_launches": n_spmv}
+    if n_cl and cl_iters:
+        # the whole solve ran in one thread-block cluster: its roofline is the shared memory
+        # of the cluster's SMs. Algorithmic shared-memory bytes per iteration: per stored
+        # block (off-diagonal blocks in the difference form) 40 (nine values and the
+        # column index) + 16 (the gathered u); per row 192 (the update: p, u, s, w, x, r and
+        # the Jacobi inverse read, p, s, x, r, u written) + 100 (the product's own row: u,
+        # p, s read, w written, and the 36-byte difference diagonal)
+        stored = max(nnzb - V, 0)
+        it_bytes = 56 * stored + 292 * V
+        us_per_it = 1e3 * cl_ms / cl_iters
+        mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2032.0
+        smem_peak = SMEM_BYTES_PER_CLK * CLUSTER_SMS * mhz * 1e6 / 1e9
+        ach = it_bytes / (us_per_it * 1e-6) / 1e9
+        roofline = {"bound": "smem", "achieved": ach, "peak": smem_peak, "unit": "GB/s", "frac": ach / smem_peak,
+                    "traffic": None,
+                    "kernel": "cluster_pcg_kernel<true,false> (whole Chronopoulos-Gear PCG solve in one 16-CTA "
+                              "cluster; unit: one iteration)",
+                    "bytes_per_iteration": it_bytes,
+                    "peak_source": f"derived: {SMEM_BYTES_PER_CLK} B/clk/SM x {CLUSTER_SMS} SMs x "
+                                   f"{mhz:.0f} MHz (median SM clock under load)",
+                    "us_per_iteration": us_per_it, "timed_launches": int(n_cl), "timed_iterations": int(cl_iters)}
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
@@ -363,7 +406,8 @@ def run_ours(args):
             cl_e.v.copy_(vh, non_blocking=True)
             pd, wd = cl_e.proximity()
             cl_e.step(pd, wd, tol=args.tol, precision=prec, warm_start=pc.PC_WARM_PREV, max_iter=args.max_iter,
-                      precond=precond, storage=storage, fuse=not args.no_fuse, allow_not_converged=True)
+                      precond=precond, storage=storage, fuse=not args.no_fuse, schedule=schedule,
+                      allow_not_converged=True)
             xh.copy_(cl_e.x)
             vh.copy_(cl_e.v)
 
@@ -390,7 +434,7 @@ def run_ours(args):
         o = pc.pc_step_opts()
         o.h = wl.h
         o.solve = pc.solve_opts(tol=args.tol, precision=prec, max_iter=args.max_iter, precond=precond,
-                                storage=storage, fuse=not args.no_fuse)
+                                storage=storage, fuse=not args.no_fuse, schedule=schedule)
         o.warm_start = pc.PC_WARM_PREV
         for k in range(args.warmup):
             pc.pc_step_host(cl_e.ctx, xh, vh, host_contacts[k][0], host_contacts[k][1], o, allow_not_converged=True)
@@ -417,7 +461,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl.name, "V": V, "T": wl.T, "H": cl.H, "nnzb": int(nnzb), "storage": args.storage, "fused_update": not args.no_fuse,
+            "config": {"workload": wl.name, "V": V, "T": wl.T, "H": cl.H, "nnzb": int(nnzb), "storage": args.storage, "fused_update": not args.no_fuse, "schedule": args.schedule,
                        "contacts_per_step": (float(np.mean(n_pairs[-args.steps:])) if proximity else wl.n_contacts),
                        "contact_model": (f"one-sided thickness {wl.material.contact_thickness * 1e3:.2f} mm, "
                                          "pairs from the GPU proximity query each step") if proximity
@@ -425,21 +469,14 @@ def run_ours(args):
                        "query_ms_per_step": (1e3 * float(np.mean(query_s[-args.steps:])) if proximity else None),
                        "precision": args.precision, "tol": args.tol,
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2": f"inputs larger than L2 (about {spmv_bytes / 1e6:.0f} MB per SpMV)",
+                       "l2": (f"inputs larger than L2 (about {spmv_bytes / 1e6:.0f} MB per SpMV)" if not n_cl else
+                              f"the system ({spmv_bytes / 1e6:.1f} MB) fits L2; the solve runs from the shared "
+                              "memory of one cluster, filled from global memory at each solve's start"),
                        "pcg_iters_per_step": float(np.mean(iters)), "max_rel_res": float(np.max(rels)),
                        "assembly_ms_per_step": asm_ms / max(n_asm, 1),
                        "rayleigh_damping": [wl.material.damp_mass, wl.material.damp_stiff]},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None,
-                         "traffic": SPMV_DRAM_BYTES.get((wl.name, args.storage)),
-                         "kernel": {"sell": "spmv_sell_kernel<true>", "sym": "spmv_sym_kernel<true>"}.get(
-                             args.storage, "spmv_kernel<true,true,CAPR>") + " (q = A p, difference form, with p.q; "
-                             + args.storage + " storage; CAPR = 14 or 18 blocks per row per stage, chosen per "
-                             "solve from the largest tile)",
-                         "blocks_per_launch": int(spmv_blocks),
-                         "bytes_per_launch": spmv_bytes, "peak_source": peak_src,
-                         "avg_launch_us": avg_spmv_s * 1e6, "timed_launches": n_spmv},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
+            "roofline": roofline,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
         }
         print(json.dumps(out), flush=True)
     cl.close()
