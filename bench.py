@@ -370,7 +370,9 @@ def run_ours(args):
                     "solve from the largest tile)",
                 "blocks_per_launch": int(spmv_blocks),
                 "bytes_per_launch": spmv_bytes, "peak_source": peak_src,
-                "avg_launch_us": avg_spmv_s * 1e6, "timed_launches": n_spmv}
+                "avg_launch_us": avg_spmv_s * 1e6, "timed_launches": n_spmv,
+                "sampling": "CUDA events around the first and the middle product of each 32-iteration chunk; "
+                            "the middle one stands for the chunk's other products"}
     if n_cl and cl_iters:
         # the whole solve ran in one thread-block cluster: its roofline is the shared memory
         # of the cluster's SMs. Algorithmic shared-memory bytes per iteration: per stored

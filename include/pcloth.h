@@ -586,10 +586,12 @@ PC_API pc_status pc_set_warm_mlp(pc_ctx *ctx, const float *params, const float *
 /* Kernel launches issued by this context since creation (all entry points). */
 PC_API int64_t pc_launch_count(const pc_ctx *ctx);
 
-/* When enabled, the PCG loop brackets every SpMV launch with CUDA events on its stream
- * and accumulates their durations, and pc_step brackets its assembly the same way;
- * pc_spmv_stats returns (launches, total ms, block count of the last matrix) and resets
- * the counters. */
+/* When enabled, the PCG loop brackets two SpMV launches of each chunk of iterations
+ * (check_every) with CUDA events on its stream: the chunk's first launch, which follows
+ * the host's convergence check, and its middle one, which stands for the chunk's other
+ * launches (weighted by the iterations the chunk ran); pc_step brackets its assembly the
+ * same way. pc_spmv_stats returns (launches represented, their total ms, block count of
+ * the last matrix) and resets the counters. */
 PC_API pc_status pc_set_profiling(pc_ctx *ctx, int32_t enable);
 PC_API pc_status pc_spmv_stats(pc_ctx *ctx, int64_t *launches, double *total_ms, int64_t *nnzb);
 /* Likewise for pc_step's assembly (pattern and values, Sec. 3.2.2): (steps timed, total

@@ -211,7 +211,9 @@ struct pc_ctx {
     double asm_ms = 0.0;
     cudaEvent_t ev[2 * 64] = {};
     int ev_used = 0;
-    int ev_pending = 0;            // SpMV events recorded, not yet read
+    int ev_pending = 0;            // SpMV events recorded, not yet read (1: first of the chunk, 2: and middle)
+    int ev_iter0 = 0;              // PCG iterations done before the chunk
+    int ev_mid = 0;                // index of the chunk's sampled middle product
 };
 
 // launch bookkeeping: every kernel launch in the library goes through this

@@ -856,8 +856,8 @@ pc_status pc_solver_alloc(pc_ctx *c)
         PC_CUDA_TRY(cudaMemset(c->od_ci, 0, sizeof(int32_t) * (size_t)(c->od_cap + 4)));
         PC_CUDA_TRY(cudaMemset(c->od_vals, 0, sizeof(float) * (size_t)(9 * c->od_cap + 16)));
     }
-    for (int i = 0; i < 6; ++i) PC_CUDA_TRY(cudaEventCreate(&c->ev[i]));
-    c->ev_used = 6;
+    for (int i = 0; i < 8; ++i) PC_CUDA_TRY(cudaEventCreate(&c->ev[i]));
+    c->ev_used = 8;
     return PC_OK;
 }
 
@@ -1264,12 +1264,17 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
     a.sc = c->sc;
     a.err = c->d_err;
     const int n_pq = s.sell ? sell_grid(c) : s.sym ? sym_grid(c) : spmv_grid(c, s.capr);
+    c->ev_iter0 = c->sc_host->iter;  // the scalars were read before this chunk
     for (int k = 0; k < count; ++k) {
-        bool timed = c->profiling && k == 0;
+        // two sampled products per chunk: the first (after the host's check and the fold of
+        // the increment) and one in the middle (between two updates, the steady state)
+        const int slot = !c->profiling ? -1 : k == 0 ? 0 : (count > 1 && k == count / 2) ? 1 : -1;
+        const bool timed = slot >= 0;
+        if (slot == 1) c->ev_mid = k;
         if (!s.fuse)  // with fusion the previous update already formed p
             PC_LAUNCH_PDL(c, pcg_direction_kernel, dir_grid(c, c->V), EW_THREADS, 0, s.st, c->V,
                           (const float4 *)c->z, (float4 *)c->p0, (const pc_scalars *)c->sc);
-        if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[0], s.st));
+        if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[slot ? 6 : 0], s.st));
         if (s.sym) {
             SymArgs y{};
             y.V = c->V;
@@ -1304,7 +1309,7 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
         } else {
             PC_TRY(launch_spmv(c, a, s.diff, true, s.st, s.capr));
         }
-        if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[1], s.st));
+        if (timed) PC_CUDA_TRY(cudaEventRecord(c->ev[slot ? 7 : 1], s.st));
         if (s.fuse && s.block)
             PC_LAUNCH_PDL(c, pcg_update_dir_kernel<true>, s.fu_grid, FU_THREADS, 0, s.st, c->V, s.fu_rows,
                           x, (float4 *)c->p0, c->r, (const float4 *)c->q, c->dinv,
@@ -1324,7 +1329,8 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
                       (const float4 *)c->p0, c->r, (const float4 *)c->q, c->dinv,
                       (float4 *)c->z, c->partials, n_pq, c->sc);
         if (timed) {
-            c->ev_pending = 1;  // read after the chunk's synchronisation (no stall here)
+            // read after the chunk's synchronisation (no stall here)
+            c->ev_pending = slot ? 2 : 1;
             c->spmv_nnzb = s.offdiag ? c->od_nnzb : s.A->nnzb;
         }
     }
@@ -1335,12 +1341,24 @@ static pc_status launch_iterations(const SolveCtx &s, float *x, int count)
 // caller has synchronised the stream.
 static pc_status collect_spmv_timing(pc_ctx *c)
 {
+    // ev_pending: 1 = the chunk's first product was timed; 2 = its middle one too. The
+    // middle one stands for the chunk's other products, counted from the iterations the
+    // chunk ran (products launched after the solve stopped return at once and are not
+    // counted; a middle one among them is not used)
     if (!c->ev_pending) return PC_OK;
+    const int pending = c->ev_pending;
     c->ev_pending = 0;
+    const int ran = c->sc_host->iter - c->ev_iter0;
+    if (ran < 1) return PC_OK;
     float ms = 0.f;
     PC_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
     c->spmv_ms += ms;
     c->spmv_launches += 1;
+    if (pending == 2 && ran > c->ev_mid) {
+        PC_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[6], c->ev[7]));
+        c->spmv_ms += (double)ms * (ran - 1);
+        c->spmv_launches += ran - 1;
+    }
     return PC_OK;
 }
 
