@@ -59,6 +59,7 @@
 
 #define CL_THREADS 512
 #define CL_TPR 2                         // threads per row in the products
+#define CL_SL 4                          // rows per slice of the block layout (CL_SL * CL_TPR = 8 lanes)
 #define CL_GROUPS (CL_THREADS / CL_TPR)  // rows in flight per CTA
 #define CL_WARPS (CL_THREADS / 32)
 #define CL_MAXC 16                       // CTAs per cluster at most
@@ -99,14 +100,20 @@ struct ClSmem {
     float4 *xv, *r, *w, *p, *s;  // [Rc] FP32 increment, residual, A u, direction, A p
     float *dres;         // [Rc][9]
     float *dinv;         // [Rc][9] (block) or [Rc][4] (scalar Jacobi)
-    int *rs;             // [Rc + 1] row starts into the stored blocks
+    int *rl;             // [Rc] stored blocks per row
+    int *sb;             // [Rc / CL_SL + 1] first record of each slice of CL_SL rows
     uint32_t *bits;      // [Vw] rows other CTAs own that this CTA reads
     int *pref;           // [Vw] ghost number of each word's first row
     uint32_t *push;      // [pcap] rows to send: local row | rank << 10 | ghost << 14
     ClRed *red;
     float4 *blk;         // [cap][3] each stored block: its nine values, then the index of its
                          // column into u / x64 (an int's bits) and two pad words, so that
-                         // three 16-byte loads fetch a block
+                         // three 16-byte loads fetch a block. Sliced: the blocks of CL_SL
+                         // consecutive rows interleave, block k of row l at record
+                         // sb[l / CL_SL] + ((k / CL_TPR) * CL_SL + l % CL_SL) * CL_TPR + k % CL_TPR,
+                         // so the eight lanes that take a step of four rows together read
+                         // eight consecutive records (no shared-memory bank conflicts), and on
+                         // a regular mesh the rows those blocks gather are consecutive too
 };
 
 // ------------------------------------------------------------------------- cluster primitives
@@ -330,16 +337,19 @@ __device__ __forceinline__ void cl_product(const ClSmem &S, int nrows, float &d,
         float a0 = 0.f, a1 = 0.f, a2 = 0.f;
         if (ok) {
             ul = S.u[l];
-            const int k1 = S.rs[l + 1];
+            const int len = S.rl[l];
+            // this thread's records: block sub, sub + CL_TPR, ... of the row, STEP float4s apart
+            constexpr int STEP = 3 * CL_SL * CL_TPR;
+            const float4 *q = S.blk + 3 * (S.sb[l / CL_SL] + (l % CL_SL) * CL_TPR + sub);
             // two blocks per step with their own accumulators: two independent chains of
             // shared-memory loads (block, then its column's u) in flight per thread
             float c0 = 0.f, c1 = 0.f, c2 = 0.f;
-            int k = S.rs[l] + sub;
-            for (; k + CL_TPR < k1; k += 2 * CL_TPR) {
-                const float4 B2 = S.blk[3 * k + 2], E2 = S.blk[3 * (k + CL_TPR) + 2];
+            int k = sub;
+            for (; k + CL_TPR < len; k += 2 * CL_TPR, q += 2 * STEP) {
+                const float4 B2 = q[2], E2 = q[STEP + 2];
                 float4 uj = S.u[__float_as_int(B2.y)], vj = S.u[__float_as_int(E2.y)];
-                const float4 B0 = S.blk[3 * k], B1 = S.blk[3 * k + 1];
-                const float4 E0 = S.blk[3 * (k + CL_TPR)], E1 = S.blk[3 * (k + CL_TPR) + 1];
+                const float4 B0 = q[0], B1 = q[1];
+                const float4 E0 = q[STEP], E1 = q[STEP + 1];
                 if (DIFF) {
                     uj.x -= ul.x;
                     uj.y -= ul.y;
@@ -355,10 +365,10 @@ __device__ __forceinline__ void cl_product(const ClSmem &S, int nrows, float &d,
                 c1 = fmaf(E1.y, vj.z, fmaf(E1.x, vj.y, fmaf(E0.w, vj.x, c1)));
                 c2 = fmaf(E2.x, vj.z, fmaf(E1.w, vj.y, fmaf(E1.z, vj.x, c2)));
             }
-            if (k < k1) {
-                const float4 B2 = S.blk[3 * k + 2];
+            if (k < len) {
+                const float4 B2 = q[2];
                 float4 uj = S.u[__float_as_int(B2.y)];
-                const float4 B0 = S.blk[3 * k], B1 = S.blk[3 * k + 1];
+                const float4 B0 = q[0], B1 = q[1];
                 if (DIFF) {
                     uj.x -= ul.x;
                     uj.y -= ul.y;
@@ -417,9 +427,11 @@ __device__ __forceinline__ void cl_residual(const ClSmem &S, const ClArgs &a, in
         }
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
         if (ok) {
-            const int k1 = S.rs[l + 1];
-            for (int k = S.rs[l] + sub; k < k1; k += CL_TPR) {
-                const float4 B0 = S.blk[3 * k], B1 = S.blk[3 * k + 1], B2 = S.blk[3 * k + 2];
+            const int len = S.rl[l];
+            constexpr int STEP = 3 * CL_SL * CL_TPR;
+            const float4 *q = S.blk + 3 * (S.sb[l / CL_SL] + (l % CL_SL) * CL_TPR + sub);
+            for (int k = sub; k < len; k += CL_TPR, q += STEP) {
+                const float4 B0 = q[0], B1 = q[1], B2 = q[2];
                 const double *xj = S.x64 + 4 * __float_as_int(B2.y);
                 double d0 = xj[0], d1 = xj[1], d2 = xj[2];
                 if (DIFF) {
@@ -488,7 +500,8 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
     S.s = reinterpret_cast<float4 *>(cl_smem + a.o_s);
     S.dres = reinterpret_cast<float *>(cl_smem + a.o_dres);
     S.dinv = reinterpret_cast<float *>(cl_smem + a.o_dinv);
-    S.rs = reinterpret_cast<int *>(cl_smem + a.o_rs);
+    S.rl = reinterpret_cast<int *>(cl_smem + a.o_rs);
+    S.sb = S.rl + a.Rc;
     S.bits = reinterpret_cast<uint32_t *>(cl_smem + a.o_bits);
     S.pref = reinterpret_cast<int *>(cl_smem + a.o_pref);
     S.push = reinterpret_cast<uint32_t *>(cl_smem + a.o_push);
@@ -503,15 +516,27 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
     int par = 0;
 
     // 1. stored blocks per row (the difference form drops the diagonal block, which
-    //    multiplies u_i - u_i = 0) and their running sum: thread l owns row l (Rc <= threads)
-    int cnt = 0;
+    //    multiplies u_i - u_i = 0; thread l owns row l, Rc <= threads), then the records of
+    //    each slice of CL_SL rows and their running sum
     if (tid < nrows) {
         const int row = row0 + tid;
+        int cnt = 0;
         for (int k = a.rp[row]; k < a.rp[row + 1]; ++k) cnt += (DIFF && a.ci[k] == row) ? 0 : 1;
+        S.rl[tid] = cnt;
     }
-    const int incl = cl_scan(cnt, misc);
-    if (tid < nrows) S.rs[tid + 1] = incl;
-    if (tid == 0) S.rs[0] = 0;
+    __syncthreads();
+    // records per slice: its longest row's blocks, rounded up to CL_TPR, for each of its rows
+    const int nsl = (nrows + CL_SL - 1) / CL_SL;
+    int ssz = 0;
+    if (tid < nsl) {
+        int mx = 0;
+        for (int i = 0; i < CL_SL; ++i)
+            if (tid * CL_SL + i < nrows) mx = max(mx, S.rl[tid * CL_SL + i]);
+        ssz = (mx + CL_TPR - 1) / CL_TPR * CL_SL * CL_TPR;
+    }
+    const int incl = cl_scan(ssz, misc);
+    if (tid < nsl) S.sb[tid + 1] = incl;
+    if (tid == 0) S.sb[0] = 0;
     const int stored = misc[CL_WARPS - 1];
     // 2. the rows this CTA reads from other CTAs, as a bitmap over all rows
     for (int w = tid; w < a.Vw; w += CL_THREADS) S.bits[w] = 0u;
@@ -558,10 +583,12 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
     // 5. the rows into shared memory; each block's column becomes an index into u / x64
     if (tid < nrows) {
         const int row = row0 + tid;
-        int pos = S.rs[tid];
+        const int base = S.sb[tid / CL_SL] + (tid % CL_SL) * CL_TPR;
+        int n = 0;  // stored blocks of the row so far
         for (int k = a.rp[row]; k < a.rp[row + 1]; ++k) {
             const int c = a.ci[k];
             if (DIFF && c == row) continue;
+            const int pos = base + (n / CL_TPR) * (CL_SL * CL_TPR) + n % CL_TPR;
             int j;
             if (c >= row0 && c < row0 + nrows) {
                 j = c - row0;
@@ -573,7 +600,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
             S.blk[3 * pos] = make_float4(B[0], B[1], B[2], B[3]);
             S.blk[3 * pos + 1] = make_float4(B[4], B[5], B[6], B[7]);
             S.blk[3 * pos + 2] = make_float4(B[8], __int_as_float(j), 0.f, 0.f);
-            ++pos;
+            ++n;
         }
         if (DIFF)
 #pragma unroll
@@ -935,7 +962,7 @@ static bool cl_layout(int V, int C, bool diff, bool block, size_t smax, int64_t 
         a->o_s = take(16ull * Rc);
         a->o_dres = take(diff ? 36ull * Rc : 0);
         a->o_dinv = take((block ? 36ull : 16ull) * Rc);
-        a->o_rs = take(4ull * (Rc + 1));
+        a->o_rs = take(4ull * (Rc + Rc / CL_SL + 2));
         a->o_bits = take(4ull * Vw);
         a->o_pref = take(4ull * Vw);
         a->o_push = take(4ull * pcap);
