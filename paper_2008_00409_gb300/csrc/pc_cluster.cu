@@ -82,11 +82,8 @@ struct ClRed {
     float2 warp[CL_WARPS][CL_NV];        // this CTA's warp sums
     float2 slot[2][CL_MAXC][CL_NV];      // every CTA's sums, pushed here by that CTA (by parity)
     int misc[40];                        // scan scratch (0..31), vote flags (32, 33), requests received (34)
-    // thread 0's scalars and stop state (the same in every CTA), and its word to its CTA
-    double rr64, bb64;                   // FP64 r.r of the last residual pass, b.b
-    float sigma, tol2;                   // the start's scale factor and scaled stop threshold
-    float gam_old, rr_last, alpha, beta;
-    int status, iter_last, outer, action;
+    double rr64, bb64;                   // thread 0: FP64 r.r of the last residual pass, b.b
+    float scal[12];                      // thread 0's scalars (a ClScal) for its CTA to copy
 };
 static_assert(offsetof(ClRed, slot) % 16 == 0 && (CL_NV * sizeof(float2)) % 16 == 0,
               "slot rows take 16-byte remote stores");
@@ -209,10 +206,10 @@ __device__ __forceinline__ bool cl_vote(int *flag, int mine, uint32_t C)
     return __any_sync(0xffffffffu, f != 0u);
 }
 
-// Sum N per-thread values over the cluster; the totals land in warp 0 (every lane), in
-// every CTA bitwise the same: warp sums, warp 0 adds the warp sums (warp order) and pushes
-// the CTA's sums into slot[par][rank] of every CTA, a cluster barrier, warp 0 adds the C
-// slots in rank order. The iterations' dot products (FP32 partials) are summed in FP32 in
+// Sum N per-thread values over the cluster; the totals land in every thread (FP32 sums) or
+// in warp 0 (pairs), in every CTA bitwise the same: warp sums, warp 0 adds the warp sums
+// (warp order) and pushes the CTA's sums into slot[par][rank] of every CTA, a cluster
+// barrier, and the C slots added in rank order. The iterations' dot products (FP32 partials) are summed in FP32 in
 // that fixed tree (13 levels for 512 threads in 16 CTAs: a relative error below 1e-6,
 // far below what the CG scalars tolerate); each double-float stage cost a few hundred
 // cycles of the one warp on the critical path. The FP64 residual passes' partials are
@@ -255,7 +252,9 @@ __device__ __forceinline__ void cl_reduce(const float2 (&v)[N], float2 (&tot)[N]
         }
     }
     cl_sync();
-    if (warp == 0) {
+    // FP32 sums: every warp adds the slots (every thread then forms the scalars itself,
+    // with no broadcast); pairs: warp 0 only (thread 0 uses them)
+    if (!PAIRS || warp == 0) {
 #pragma unroll
         for (int i = 0; i < N; ++i) {
             float2 w = (uint32_t)lane < C ? S.red->slot[par][lane][i] : make_float2(0.f, 0.f);
@@ -267,8 +266,8 @@ __device__ __forceinline__ void cl_reduce(const float2 (&v)[N], float2 (&tot)[N]
             tot[i] = w;
         }
     }
-    // slot[par] is pushed again two reductions later, after a barrier that warp 0 reaches
-    // only once it has read it
+    // slot[par] is pushed again two reductions later, after a barrier that this CTA's warps
+    // reach only once they have read it
     par ^= 1;
 }
 
@@ -484,6 +483,66 @@ __device__ __forceinline__ void cl_fold(const ClSmem &S, int nrows)
     }
 }
 
+// ------------------------------------------------------------------------- the scalars
+
+// The iteration's scalars and stop state. Every thread holds a copy and updates it from
+// the same sums in the same way, so all threads of the cluster take the same decisions;
+// after the start and after a residual replacement thread 0 forms them (FP64 work) and the
+// CTA copies them from shared memory.
+struct ClScal {
+    float sigma, tol2, ref2;  // scale of the sums, scaled stop threshold, refresh^2
+    float gam_old, rr_last, alpha, beta;
+    int iter_last, outer, status, action;
+};
+
+__device__ __forceinline__ float cl_scaled(float2 t, float sigma) { return __fadd_rn(t.x, t.y) * sigma; }
+
+// After an iteration's reduction (gamma, r.r, delta, (u,s) + (p,w), (p,s)): the stop tests
+// and, unless the solve stops or a replacement follows, the next step's alpha and beta.
+__device__ __forceinline__ void cl_step(ClScal &c, const float2 (&tot)[5], int iter, const ClArgs &a)
+{
+    const float gam = cl_scaled(tot[0], c.sigma), rr = cl_scaled(tot[1], c.sigma);
+    int act = 0;
+    bool conv = false;
+    if (!isfinite(rr) || !isfinite(gam)) {
+        c.status = PC_ERR_NONFINITE;
+        act = CL_ACT_DONE;
+    } else if (rr <= c.tol2) {
+        conv = true;
+    } else if (iter >= a.max_iter) {
+        c.status = PC_ERR_NOT_CONVERGED;
+        act = CL_ACT_DONE;
+    }
+    if (!act) {
+        if (!a.mixed) {
+            act = conv ? CL_ACT_DONE : 0;
+        } else if (conv) {
+            // a converged recurrence residual is confirmed by an FP64 replacement
+            act = (rr > 0.f && iter > c.iter_last) ? CL_ACT_REPLACE : CL_ACT_DONE;
+        } else if (iter % a.check_every == 0) {
+            act = CL_ACT_FOLD;
+            if (rr <= c.rr_last * c.ref2 || iter - c.iter_last >= a.refresh_every) act |= CL_ACT_REPLACE;
+        }
+    }
+    // beta' = gamma / gamma_old from the recurrence, also when a replacement follows: as in
+    // the grid-wide solver the replacement keeps the direction and beta and takes the
+    // replaced gamma only into alpha (with the replaced gamma in beta the iteration stalls
+    // after a replacement near FP32's attainable accuracy)
+    c.beta = __fdividef(gam, c.gam_old);
+    if (!(act & (CL_ACT_DONE | CL_ACT_REPLACE))) {
+        // alpha' = gamma / (p', A p')
+        const float pap = fmaf(c.beta, fmaf(c.beta, cl_scaled(tot[4], c.sigma), cl_scaled(tot[3], c.sigma)),
+                               cl_scaled(tot[2], c.sigma));
+        c.alpha = __fdividef(gam, pap);
+        c.gam_old = gam;
+        if (!(pap > 0.f) || !isfinite(c.alpha) || !isfinite(c.beta)) {
+            c.status = PC_ERR_NONFINITE;
+            act = CL_ACT_DONE;
+        }
+    }
+    c.action = act;
+}
+
 // ------------------------------------------------------------------------- the solve
 
 template <bool DIFF, bool BLOCK>
@@ -637,10 +696,15 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
     }
     const int n_push = misc[34];
 
-    // 6. the start: r = b - A dv in FP64 (rounded to FP32), u = M^-1 r, w = A u; p = s = 0.
-    // Thread 0 of each CTA (the same values in every CTA) keeps the scalars and the stop
-    // logic and tells its CTA alpha, beta and what comes next.
+    // 6. the start: r = b - A dv in FP64 (rounded to FP32), u = M^-1 r, w = A u; p = s = 0
     ClRed &K = *S.red;
+    ClScal c;
+    static_assert(sizeof(ClScal) <= sizeof(K.scal), "scalars fit their broadcast slot");
+    auto from_thread0 = [&]() {  // thread 0's scalars to the whole CTA
+        if (tid == 0) *reinterpret_cast<ClScal *>(K.scal) = c;
+        __syncthreads();
+        c = *reinterpret_cast<const ClScal *>(K.scal);
+    };
     float2 tot[5];
     {
         cl_push_x64(S, Rc, n_push);
@@ -661,41 +725,41 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
             const double bbv = pc_df_value(t4[3].x, t4[3].y);
             int ex = 0;
             if (isfinite(bbv) && bbv > 0.0) frexp(bbv, &ex);
-            K.sigma = ldexpf(1.f, -ex);
-            K.tol2 = (float)ldexp(a.tol * a.tol * bbv, -ex);
+            c.sigma = ldexpf(1.f, -ex);
+            c.tol2 = (float)ldexp(a.tol * a.tol * bbv, -ex);
+            c.ref2 = (float)(a.refresh * a.refresh);
             K.bb64 = bbv;
             K.rr64 = pc_df_value(t4[1].x, t4[1].y);
-            const float gam0 = __fadd_rn(t4[0].x, t4[0].y) * K.sigma, rr0 = __fadd_rn(t4[1].x, t4[1].y) * K.sigma;
-            const float del0 = __fadd_rn(t4[2].x, t4[2].y) * K.sigma;
-            K.alpha = gam0 / del0;
-            K.beta = 0.f;
-            K.gam_old = gam0;
-            K.rr_last = rr0;
-            K.status = PC_OK;
-            K.iter_last = 0;
-            K.outer = 0;
+            const float gam0 = cl_scaled(t4[0], c.sigma), rr0 = cl_scaled(t4[1], c.sigma);
+            const float del0 = cl_scaled(t4[2], c.sigma);
+            c.alpha = gam0 / del0;
+            c.beta = 0.f;
+            c.gam_old = gam0;
+            c.rr_last = rr0;
+            c.status = PC_OK;
+            c.iter_last = 0;
+            c.outer = 0;
             int act = 0;
             if (!isfinite(rr0) || !isfinite(gam0)) {
-                K.status = PC_ERR_NONFINITE;
+                c.status = PC_ERR_NONFINITE;
                 act = CL_ACT_DONE;
-            } else if (rr0 <= K.tol2) {
+            } else if (rr0 <= c.tol2) {
                 act = CL_ACT_DONE;
             } else if (a.max_iter <= 0) {
-                K.status = PC_ERR_NOT_CONVERGED;
+                c.status = PC_ERR_NOT_CONVERGED;
                 act = CL_ACT_DONE;
-            } else if (!(del0 > 0.f) || !isfinite(K.alpha)) {
-                K.status = PC_ERR_NONFINITE;
+            } else if (!(del0 > 0.f) || !isfinite(c.alpha)) {
+                c.status = PC_ERR_NONFINITE;
                 act = CL_ACT_DONE;
             }
-            K.action = act;
+            c.action = act;
         }
-        __syncthreads();
+        from_thread0();
     }
     int iter = 0;
-    int action = K.action;
 
-    while (!(action & CL_ACT_DONE)) {
-        const float alpha = K.alpha, beta = K.beta;
+    while (!(c.action & CL_ACT_DONE)) {
+        const float alpha = c.alpha, beta = c.beta;
         // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = M^-1 r; (r, u), (r, r)
         float g = 0.f, q = 0.f;
         for (int l = tid; l < nrows; l += CL_THREADS) {
@@ -721,56 +785,9 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
             cl_reduce<5, false>(v, tot, S, par, C, rank);
         }
         ++iter;
-        // thread 0: the stop tests, then either the next step's scalars or a replacement
-        if (tid == 0) {
-            const float gam = __fadd_rn(tot[0].x, tot[0].y) * K.sigma, rr = __fadd_rn(tot[1].x, tot[1].y) * K.sigma;
-            int act = 0;
-            bool conv = false;
-            if (!isfinite(rr) || !isfinite(gam)) {
-                K.status = PC_ERR_NONFINITE;
-                act = CL_ACT_DONE;
-            } else if (rr <= K.tol2) {
-                conv = true;
-            } else if (iter >= a.max_iter) {
-                K.status = PC_ERR_NOT_CONVERGED;
-                act = CL_ACT_DONE;
-            }
-            if (!act) {
-                if (!a.mixed) {
-                    act = conv ? CL_ACT_DONE : 0;
-                } else if (conv) {
-                    // a converged recurrence residual is confirmed by an FP64 replacement
-                    act = (rr > 0.f && iter > K.iter_last) ? CL_ACT_REPLACE : CL_ACT_DONE;
-                } else if (iter % a.check_every == 0) {
-                    act = CL_ACT_FOLD;
-                    if (rr <= K.rr_last * (float)(a.refresh * a.refresh) || iter - K.iter_last >= a.refresh_every)
-                        act |= CL_ACT_REPLACE;
-                }
-            }
-            // beta' = gamma / gamma_old from the recurrence, also when a replacement follows:
-            // as in the grid-wide solver the replacement keeps the direction and beta and
-            // takes the replaced gamma only into alpha (with the replaced gamma in beta the
-            // iteration stalls after a replacement near FP32's attainable accuracy)
-            K.beta = __fdividef(gam, K.gam_old);
-            if (!(act & (CL_ACT_DONE | CL_ACT_REPLACE))) {
-                // alpha' = gamma / (p', A p')
-                const float bt = K.beta;
-                const float pap = fmaf(bt, fmaf(bt, __fadd_rn(tot[4].x, tot[4].y) * K.sigma,
-                                                __fadd_rn(tot[3].x, tot[3].y) * K.sigma),
-                                       __fadd_rn(tot[2].x, tot[2].y) * K.sigma);
-                K.alpha = __fdividef(gam, pap);
-                K.gam_old = gam;
-                if (!(pap > 0.f) || !isfinite(K.alpha) || !isfinite(bt)) {
-                    K.status = PC_ERR_NONFINITE;
-                    act = CL_ACT_DONE;
-                }
-            }
-            K.action = act;
-        }
-        __syncthreads();
-        action = K.action;
-        if (action & (CL_ACT_FOLD | CL_ACT_REPLACE)) cl_fold(S, nrows);
-        if (action & CL_ACT_REPLACE) {
+        cl_step(c, tot, iter, a);  // every thread, the same values
+        if (c.action & (CL_ACT_FOLD | CL_ACT_REPLACE)) cl_fold(S, nrows);
+        if (c.action & CL_ACT_REPLACE) {
             // r = b - A x in FP64, u = M^-1 r, and the products s = A p and w = A u anew
             // (the recurrences for s and r drift; p stays)
             __syncthreads();  // every row folded before any is sent
@@ -799,41 +816,38 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
             cl_reduce<5, true>(v, tot, S, par, C, rank);
             if (tid == 0) {
                 K.rr64 = pc_df_value(tot[1].x, tot[1].y);
-                const float gam = __fadd_rn(tot[0].x, tot[0].y) * K.sigma;
-                const float rr = __fadd_rn(tot[1].x, tot[1].y) * K.sigma;
-                K.rr_last = rr;
-                K.iter_last = iter;
-                ++K.outer;
+                const float gam = cl_scaled(tot[0], c.sigma), rr = cl_scaled(tot[1], c.sigma);
+                c.rr_last = rr;
+                c.iter_last = iter;
+                ++c.outer;
                 int act = 0;
                 if (!isfinite(rr) || !isfinite(gam)) {
-                    K.status = PC_ERR_NONFINITE;
+                    c.status = PC_ERR_NONFINITE;
                     act = CL_ACT_DONE;
-                } else if (rr <= K.tol2) {
+                } else if (rr <= c.tol2) {
                     act = CL_ACT_DONE;
                 } else if (iter >= a.max_iter) {
-                    K.status = PC_ERR_NOT_CONVERGED;
+                    c.status = PC_ERR_NOT_CONVERGED;
                     act = CL_ACT_DONE;
                 } else {
-                    const float bt = K.beta;  // the recurrence's
-                    const float pap = fmaf(bt, fmaf(bt, __fadd_rn(tot[4].x, tot[4].y) * K.sigma,
-                                                    __fadd_rn(tot[3].x, tot[3].y) * K.sigma),
-                                           __fadd_rn(tot[2].x, tot[2].y) * K.sigma);
-                    K.alpha = __fdividef(gam, pap);
-                    K.gam_old = gam;
-                    if (!(pap > 0.f) || !isfinite(K.alpha) || !isfinite(bt)) {
-                        K.status = PC_ERR_NONFINITE;
+                    // the recurrence's beta, the replaced gamma in alpha
+                    const float pap = fmaf(c.beta, fmaf(c.beta, cl_scaled(tot[4], c.sigma), cl_scaled(tot[3], c.sigma)),
+                                           cl_scaled(tot[2], c.sigma));
+                    c.alpha = __fdividef(gam, pap);
+                    c.gam_old = gam;
+                    if (!(pap > 0.f) || !isfinite(c.alpha) || !isfinite(c.beta)) {
+                        c.status = PC_ERR_NONFINITE;
                         act = CL_ACT_DONE;
                     }
                 }
-                K.action = act;
+                c.action = act;
             }
-            __syncthreads();
-            action = K.action;
+            from_thread0();
         }
     }
 
     // 7. the solution, and its FP64 residual unless the last replacement measured it
-    const bool check = a.mixed ? iter > K.iter_last : true;
+    const bool check = a.mixed ? iter > c.iter_last : true;
     if (a.mixed) {
         if (check) cl_fold(S, nrows);
         for (int l = tid; l < nrows; l += CL_THREADS) {
@@ -877,18 +891,18 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
     cl_sync();
     if (rank == 0 && tid == 0) {
         pc_scalars *sc = a.sc;
-        sc->rz = (double)(K.gam_old / K.sigma);
+        sc->rz = (double)(c.gam_old / c.sigma);
         sc->rr = K.rr64;
         sc->bb = K.bb64;
         sc->tol2 = a.tol * a.tol * K.bb64;
-        sc->alpha = (double)K.alpha;
-        sc->beta = (double)K.beta;
+        sc->alpha = (double)c.alpha;
+        sc->beta = (double)c.beta;
         sc->pq = 0.0;
         sc->iter = iter;
         sc->max_iter = a.max_iter;
-        sc->status = K.status;
+        sc->status = c.status;
         sc->done = 1;
-        sc->outer = K.outer;
+        sc->outer = c.outer;
     }
 }
 
