@@ -391,7 +391,10 @@ PC_API pc_status pc_step_batched(pc_ctx *ctx, float *x, float *v, const pc_conta
  * except opts->storage: there is no room for a second layout of the matrix, so every
  * storage choice (including the default PC_STORAGE_OFFDIAG) is read as PC_STORAGE_FULL
  * -- the products stream the caller's matrix; the solution is the same up to summation
- * order. The stage shape of the product is chosen per solve as in pc_pcg_solve.
+ * order. The stage shape of the product is chosen per solve as in pc_pcg_solve, and so is
+ * opts->schedule: the cluster schedule keeps its working set in the cluster's shared
+ * memory and needs no scratch beyond the scalars, so small systems solve there as with a
+ * context (its cluster-size query and shared-memory set-up are host-side, no allocation).
  * Each call looks up the array's device address on the current device and sets the
  * kernels' shared-memory limit (host-side set-up, no allocation); make the first call on
  * a device before any stream capture. Every call on a device shares the array, which
