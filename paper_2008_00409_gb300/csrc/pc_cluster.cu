@@ -101,7 +101,8 @@ struct ClSmem {
     int *sb;             // [Rc / CL_SL + 1] first record of each slice of CL_SL rows
     uint32_t *bits;      // [Vw] rows other CTAs own that this CTA reads
     int *pref;           // [Vw] ghost number of each word's first row
-    uint32_t *push;      // [pcap] rows to send: local row | rank << 10 | ghost << 14
+    uint32_t *push;      // [pcap rounded up to a power of two] rows to send:
+                         // rank << 28 | ghost << 10 | local row, sorted
     ClRed *red;
     float4 *blk;         // [cap][3] each stored block: its nine values, then the index of its
                          // column into u / x64 (an int's bits) and two pad words, so that
@@ -305,7 +306,7 @@ __device__ __forceinline__ void cl_push_u(const ClSmem &S, int Rc, int n_push)
     const uint32_t base = cl_smem_addr(S.u);
     for (int e = threadIdx.x; e < n_push; e += CL_THREADS) {
         const uint32_t ent = S.push[e];
-        const int l = ent & 0x3FF, d = (ent >> 10) & 0xF, g = ent >> 14;
+        const int l = ent & 0x3FF, g = (ent >> 10) & 0x3FFFF, d = ent >> 28;
         cl_st_f4(cl_map(base + 16u * (uint32_t)(Rc + g), d), S.u[l]);
     }
 }
@@ -314,7 +315,7 @@ __device__ __forceinline__ void cl_push_x64(const ClSmem &S, int Rc, int n_push)
     const uint32_t base = cl_smem_addr(S.x64);
     for (int e = threadIdx.x; e < n_push; e += CL_THREADS) {
         const uint32_t ent = S.push[e];
-        const int l = ent & 0x3FF, d = (ent >> 10) & 0xF, g = ent >> 14;
+        const int l = ent & 0x3FF, g = (ent >> 10) & 0x3FFFF, d = ent >> 28;
         const uint32_t dst = cl_map(base + 32u * (uint32_t)(Rc + g), d);
         const double *x = S.x64 + 4 * l;
         cl_st_d2(dst, x[0], x[1]);
@@ -635,7 +636,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
             const uint32_t pos = cl_atom_add(cl_map(cl_smem_addr(&misc[34]), (uint32_t)o), 1u);
             if ((int)pos < a.pcap)
                 cl_st_u32(cl_map(cl_smem_addr(&S.push[pos]), (uint32_t)o),
-                          (uint32_t)(c - o * Rc) | (rank << 10) | ((uint32_t)g << 14));
+                          (rank << 28) | ((uint32_t)g << 10) | (uint32_t)(c - o * Rc));
             ++g;
         }
     }
@@ -695,6 +696,30 @@ __global__ void __launch_bounds__(CL_THREADS, 1) cluster_pcg_kernel(const ClArgs
         return;
     }
     const int n_push = misc[34];
+    // sort the send list by (destination, ghost number): consecutive lanes then send
+    // consecutive rows into consecutive ghost slots of one CTA, and the remote stores
+    // coalesce (the requests arrived in the order of the requesters' atomics). A bitonic
+    // sort over the list padded to a power of two with entries that sort last.
+    {
+        int n2 = 1;
+        while (n2 < n_push) n2 <<= 1;
+        for (int i = n_push + tid; i < n2; i += CL_THREADS) S.push[i] = 0xFFFFFFFFu;
+        __syncthreads();
+        for (int k = 2; k <= n2; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = tid; i < n2; i += CL_THREADS) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const uint32_t x = S.push[i], y = S.push[ixj];
+                        if ((i & k) == 0 ? x > y : x < y) {
+                            S.push[i] = y;
+                            S.push[ixj] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+    }
 
     // 6. the start: r = b - A dv in FP64 (rounded to FP32), u = M^-1 r, w = A u; p = s = 0
     ClRed &K = *S.red;
@@ -979,7 +1004,9 @@ static bool cl_layout(int V, int C, bool diff, bool block, size_t smax, int64_t 
         a->o_rs = take(4ull * (Rc + Rc / CL_SL + 2));
         a->o_bits = take(4ull * Vw);
         a->o_pref = take(4ull * Vw);
-        a->o_push = take(4ull * pcap);
+        int p2 = 1;
+        while (p2 < pcap) p2 <<= 1;
+        a->o_push = take(4ull * p2);
         a->o_red = take(sizeof(ClRed));
         *end = o;
     };
