@@ -314,7 +314,7 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 // ------------------------------------------------------------------------- phases
 
 #ifndef BT_U
-#define BT_U 2  // rows per thread in flight in the vector phases
+#define BT_U 2  // rows per thread in flight in the direction phase
 #endif
 #ifndef BT_MIN_CTAS
 #define BT_MIN_CTAS 4  // register budget: four co-resident CTAs per SM
@@ -430,7 +430,7 @@ __device__ __forceinline__ bt_sched bt_spmv_sched(const BtArgs &a, const bt_list
 // autotuner chose (bt_spmv_sched). A CTA meets each instance in one run of its entries
 // (an instance's entries are contiguous); each consumer warp stores its p.q over the run
 // in the slot of the run's first entry, and the slots are summed where alpha is needed
-// (bt_alpha). Strided order: the run starts at p0 + ((b - p0) mod G), so the instance's
+// (bt_alpha_warp). Strided order: the run starts at p0 + ((b - p0) mod G), so the instance's
 // slots are entries p0 .. p0 + min(G, p1 - p0) - 1; chunked order: max(b * chunk, p0)
 // for the CTAs b whose chunk meets [p0, p1). `kbase` continues the mbarrier phase count
 // across calls.
@@ -606,41 +606,34 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
     }
 }
 
-// alpha of the instance at list position m from its p.q slots, summed in slot order by
-// every CTA that needs it (all get the same value); the CTA holding the instance's first
-// entry records it. Returns alpha to all threads.
-__device__ float bt_alpha(const BtArgs &a, const bt_list &L, const bt_seg &sg)
+#define BT_WARPS (SP_THREADS / 32)  // warps per CTA: instances a CTA's update phase handles at once
+
+// alpha of the instance at list position m, computed by one warp from the instance's p.q
+// slots (summed in slot order, so every CTA that needs it gets the same value); the CTA
+// holding the instance's first entry records it. Returns alpha in every lane.
+__device__ float bt_alpha_warp(const BtArgs &a, const bt_list &L, int m, int j)
 {
-    __shared__ float s_alpha;
-    const int p0 = L.pref[sg.m], p1 = L.pref[sg.m + 1];
+    const int lane = threadIdx.x & 31;
+    const int k = L.id[m], p0 = L.pref[m], p1 = L.pref[m + 1];
     static_assert(SP_CWARPS == 4, "a p.q slot is four doubles (two double2)");
+    bt_inst &I = a.inst[k];
+    const double rz = lane == 0 ? __ldcg(&I.rz) : 0.0;  // in flight with the slot loads
     const int c = L.chunk;
     const int n = a.spmv_chunked ? (p1 - 1) / c - p0 / c + 1 : min((int)gridDim.x, p1 - p0);
-    auto slot = [&](int i) -> int64_t { return a.spmv_chunked ? max((p0 / c + i) * c, p0) : p0 + i; };
     const double2 *slots = reinterpret_cast<const double2 *>(a.part_pq);
-    double acc0 = 0.0, acc1 = 0.0;
-    for (int i = threadIdx.x; i < n; i += 2 * blockDim.x) {
-        const int i2 = i + blockDim.x;
-        const int64_t s0 = 2 * slot(i);
+    double acc = 0.0;
+    for (int i = lane; i < n; i += 32) {
+        const int64_t s0 = 2 * (a.spmv_chunked ? max((p0 / c + i) * c, p0) : p0 + i);
         const double2 x0 = __ldcg(slots + s0), x1 = __ldcg(slots + s0 + 1);
-        double2 y0 = make_double2(0.0, 0.0), y1 = make_double2(0.0, 0.0);
-        if (i2 < n) {
-            const int64_t s1 = 2 * slot(i2);
-            y0 = __ldcg(slots + s1);
-            y1 = __ldcg(slots + s1 + 1);
-        }
-        acc0 += (x0.x + x0.y) + (x1.x + x1.y);
-        acc1 += (y0.x + y0.y) + (y1.x + y1.y);
+        acc += (x0.x + x0.y) + (x1.x + x1.y);
     }
-    double v[1] = {acc0 + acc1};
-    bt_group_sum<1>(v, false);
-    if (threadIdx.x == 0) {
-        bt_inst &I = a.inst[sg.k];
-        const double pq = v[0];
-        double alpha = __ldcg(&I.rz) / pq;
+    const double pq = bt_warp_sum(acc);
+    float alpha32 = 0.f;
+    if (lane == 0) {
+        double alpha = rz / pq;
         const bool bad = !(pq > 0.0) || !isfinite(alpha);
         if (bad) alpha = 0.0;
-        if (sg.j == p0) {  // the instance's first entry is in this CTA's chunk
+        if (j == p0) {  // the instance's first entry is in this CTA's chunk
             I.refresh = 0;  // the direction phase has folded the increment
             I.pq = pq;
             I.alpha = alpha;
@@ -650,78 +643,122 @@ __device__ float bt_alpha(const BtArgs &a, const bt_list &L, const bt_seg &sg)
                 atomicAdd(&a.g->gen, 1u);
             }
         }
-        s_alpha = (float)alpha;
+        alpha32 = (float)alpha;
     }
-    __syncthreads();
-    return s_alpha;
+    return __shfl_sync(0xffffffffu, alpha32, 0);
 }
 
 // x += alpha p; r -= alpha q; z = D^-1 r; (r.z, r.r) per instance. The CTA completing an
 // instance's sums sets beta and decides: go on, refresh with an FP64 residual, or stop.
+// A CTA whose chunk meets several instances takes them BT_WARPS at a time: warp w finds the
+// alpha of the group's instance w, all threads update the rows of the group, and warp w
+// delivers instance w's sums, so the scalar steps (L2 round trips and FP64 arithmetic) of
+// the instances overlap instead of adding up.
 __device__ void bt_phase_update(const BtArgs &a, const bt_list &L, int par)
 {
+    __shared__ float s_alpha[BT_WARPS];
+    __shared__ int s_row[BT_WARPS][2];
+    __shared__ double s_part[BT_WARPS][BT_WARPS][2];
     const int c = L.chunk, j0 = blockIdx.x * c, j1 = min(L.total, j0 + c);
     if (j0 >= j1) return;
-    const int T = blockDim.x;
-    for (int m = bt_find(L, j0), j = j0; j < j1; ++m) {
-        bt_seg sg;
-        bt_seg_at(a, L, m, j, j1, sg);
-        j = sg.je;
-        const float alpha = bt_alpha(a, L, sg);
-        float rz = 0.f, rz_c = 0.f, rr = 0.f, rr_c = 0.f;
-        for (int base = sg.ra + (int)threadIdx.x; base < sg.rb; base += BT_U * T) {
-            float4 p[BT_U], q[BT_U], x[BT_U], r[BT_U], d[BT_U];
-#pragma unroll
-            for (int u = 0; u < BT_U; ++u) {
-                const int row = base + u * T;
-                if (row < sg.rb) {
-                    p[u] = a.p4[row];
-                    q[u] = a.q4[row];
-                    x[u] = a.x4[row];
-                    r[u] = a.r4[row];
-                    d[u] = a.dinv4[row];
+    const int T = blockDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int m0 = bt_find(L, j0), nseg = bt_find(L, j1 - 1) - m0 + 1;
+    for (int g0 = 0; g0 < nseg; g0 += BT_WARPS) {
+        const int gs = min(BT_WARPS, nseg - g0);
+        if (warp < gs) {
+            const int m = m0 + g0 + warp;
+            bt_seg sg;
+            bt_seg_at(a, L, m, max(j0, L.pref[m]), j1, sg);
+            const float alpha = bt_alpha_warp(a, L, m, sg.j);
+            if (lane == 0) {
+                s_alpha[warp] = alpha;
+                s_row[warp][0] = sg.ra;
+                s_row[warp][1] = sg.rb;
+            }
+        }
+        __syncthreads();
+        for (int q = 0; q < gs; ++q) {
+            const float alpha = s_alpha[q];
+            const int rb = s_row[q][1];
+            float rz = 0.f, rz_c = 0.f, rr = 0.f, rr_c = 0.f;
+            // one row per thread at a time: two in flight would need ten float4 registers,
+            // and the persistent kernel's budget (four CTAs per SM) would spill in every phase
+            for (int row = s_row[q][0] + (int)threadIdx.x; row < rb; row += T) {
+                const float4 p = a.p4[row], qv = a.q4[row], d = a.dinv4[row];
+                float4 x = a.x4[row], r = a.r4[row];
+                x.x = fmaf(alpha, p.x, x.x); x.y = fmaf(alpha, p.y, x.y); x.z = fmaf(alpha, p.z, x.z);
+                r.x = fmaf(-alpha, qv.x, r.x); r.y = fmaf(-alpha, qv.y, r.y); r.z = fmaf(-alpha, qv.z, r.z);
+                const float4 z = make_float4(d.x * r.x, d.y * r.y, d.z * r.z, 0.f);
+                a.x4[row] = x;
+                a.r4[row] = r;
+                a.z4[row] = z;
+                kahan_add(rz, rz_c, fmaf(r.x, z.x, fmaf(r.y, z.y, r.z * z.z)));
+                kahan_add(rr, rr_c, fmaf(r.x, r.x, fmaf(r.y, r.y, r.z * r.z)));
+            }
+            const double w0 = bt_warp_sum((double)rz - (double)rz_c), w1 = bt_warp_sum((double)rr - (double)rr_c);
+            if (lane == 0) {
+                s_part[q][warp][0] = w0;
+                s_part[q][warp][1] = w1;
+            }
+        }
+        __syncthreads();
+        if (warp < gs) {
+            // deliver into the slot of the CTA's first entry of the instance (CTA b takes
+            // entries [b*chunk, (b+1)*chunk)); the CTA that delivers last sums the slots in
+            // CTA order and sets the instance's scalars
+            const int m = m0 + g0 + warp;
+            const int k = L.id[m], p0 = L.pref[m], p1 = L.pref[m + 1];
+            const int jm = max(j0, p0);
+            const int blo = p0 / c, bhi = (p1 - 1) / c;
+            int last = 0;
+            if (lane == 0) {
+                double v0 = 0.0, v1 = 0.0;
+                for (int w = 0; w < T / 32; ++w) {
+                    v0 += s_part[warp][w][0];
+                    v1 += s_part[warp][w][1];
+                }
+                a.part[3ll * jm] = v0;
+                a.part[3ll * jm + 1] = v1;
+                __threadfence();
+                const int old = atomicAdd(&a.inst[k].arrive, 1);
+                last = old == bhi - blo;
+                if (last) {
+                    a.inst[k].arrive = 0;
+                    __threadfence();
                 }
             }
-#pragma unroll
-            for (int u = 0; u < BT_U; ++u) {
-                const int row = base + u * T;
-                if (row < sg.rb) {
-                    float4 xx = x[u], rv = r[u];
-                    xx.x = fmaf(alpha, p[u].x, xx.x); xx.y = fmaf(alpha, p[u].y, xx.y); xx.z = fmaf(alpha, p[u].z, xx.z);
-                    rv.x = fmaf(-alpha, q[u].x, rv.x); rv.y = fmaf(-alpha, q[u].y, rv.y); rv.z = fmaf(-alpha, q[u].z, rv.z);
-                    const float4 z = make_float4(d[u].x * rv.x, d[u].y * rv.y, d[u].z * rv.z, 0.f);
-                    a.x4[row] = xx;
-                    a.r4[row] = rv;
-                    a.z4[row] = z;
-                    kahan_add(rz, rz_c, fmaf(rv.x, z.x, fmaf(rv.y, z.y, rv.z * z.z)));
-                    kahan_add(rr, rr_c, fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, rv.z * rv.z)));
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                double v0 = 0.0, v1 = 0.0;
+                for (int bb = blo + lane; bb <= bhi; bb += 32) {
+                    const int64_t slot = max(bb * c, p0);
+                    v0 += __ldcg(a.part + 3 * slot);
+                    v1 += __ldcg(a.part + 3 * slot + 1);
+                }
+                const double rzn = bt_warp_sum(v0), rrn = bt_warp_sum(v1);
+                bt_inst &I = a.inst[k];
+                if (lane == 0 && !I.done) {
+                    I.beta = rzn / I.rz;
+                    I.rz = rzn;
+                    I.rr = rrn;
+                    I.iter += 1;
+                    if (!isfinite(rrn) || !isfinite(I.beta)) {
+                        I.status = PC_ERR_NONFINITE;
+                        I.done = 1;
+                        atomicAdd(&a.g->gen, 1u);
+                    } else if (rrn <= I.tol2 || rrn <= I.rr_last * a.refresh * a.refresh ||
+                               I.iter - I.iter_last >= a.refresh_every) {
+                        I.refresh = 1;  // confirm or refresh with an FP64 residual
+                        atomicAdd(&a.g->n_refresh[par], 1u);
+                    } else if (I.iter >= a.max_iter) {
+                        I.status = PC_ERR_NOT_CONVERGED;
+                        I.done = 1;
+                        atomicAdd(&a.g->gen, 1u);
+                    }
                 }
             }
         }
-        double v[2] = {(double)rz - (double)rz_c, (double)rr - (double)rr_c};
-        if (bt_deliver<2>(a, L, sg, v, false) && threadIdx.x == 0) {
-            bt_inst &I = a.inst[sg.k];
-            if (!I.done) {
-                const double rzn = v[0], rrn = v[1];
-                I.beta = rzn / I.rz;
-                I.rz = rzn;
-                I.rr = rrn;
-                I.iter += 1;
-                if (!isfinite(rrn) || !isfinite(I.beta)) {
-                    I.status = PC_ERR_NONFINITE;
-                    I.done = 1;
-                    atomicAdd(&a.g->gen, 1u);
-                } else if (rrn <= I.tol2 || rrn <= I.rr_last * a.refresh * a.refresh ||
-                           I.iter - I.iter_last >= a.refresh_every) {
-                    I.refresh = 1;  // confirm or refresh with an FP64 residual
-                    atomicAdd(&a.g->n_refresh[par], 1u);
-                } else if (I.iter >= a.max_iter) {
-                    I.status = PC_ERR_NOT_CONVERGED;
-                    I.done = 1;
-                    atomicAdd(&a.g->gen, 1u);
-                }
-            }
-        }
+        __syncthreads();  // the group's shared arrays are reused by the next group
     }
 }
 
