@@ -343,8 +343,8 @@ PC_API pc_status pc_batched_config(pc_ctx *ctx, int32_t *grid, int32_t *spmv_ord
                                    int32_t *grid_sizes, float *tune_ms);
 
 /* Cycle budget of each grid-barrier wait in the persistent batched solver and in the
- * fused PCG update of pc_pcg_solve / pc_step (software barriers spinning on a generation
- * word). A wait longer than the budget aborts: in the batched solver every CTA leaves at
+ * fused PCG update of pc_pcg_solve / pc_step (software barriers polling an arrival
+ * counter). A wait longer than the budget aborts: in the batched solver every CTA leaves at
  * its next barrier, no result is written back and dv keeps its initial guess; in the
  * single-system solve the iteration stops; the calls return PC_ERR_TIMEOUT with the
  * context still usable. cycles <= 0 restores the default of 2^31 SM cycles (about

@@ -49,9 +49,8 @@ struct bt_inst {
 };
 
 struct bt_global {
-    uint32_t bar_count;     // grid barrier arrivals
-    uint32_t bar_gen;       // grid barrier generation
-    uint32_t abort;         // set on timeout
+    unsigned long long bar; // grid barrier arrivals (pc_grid_barrier; bit 63 set on abort)
+    uint32_t abort;         // set on timeout (read by the host and the state update)
     uint32_t gen;           // bumped whenever an instance finishes
     uint32_t n_refresh[2];  // refresh requests, by iteration parity
     uint32_t pad[2];
@@ -191,40 +190,21 @@ __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p)
     return v;
 }
 
+// Marks the launch aborted: the host and the state update read `abort`; every CTA leaves
+// at its next grid barrier.
+__device__ __forceinline__ void bt_abort(bt_global *g)
+{
+    atomicExch(&g->abort, 1u);
+    pc_grid_abort(&g->bar);
+}
+
 // All CTAs of the (co-resident) grid meet; returns false everywhere once any CTA gave
-// up waiting (the launch then unwinds without further waits).
+// up waiting or the launch was aborted (the launch then unwinds without further waits).
 __device__ bool bt_grid_sync(bt_global *g, long long budget)
 {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = ld_acquire_gpu(&g->abort) == 0u;
-        if (ok) {
-            const uint32_t gen = ld_acquire_gpu(&g->bar_gen);
-            __threadfence();
-            const uint32_t arrived = atomicAdd(&g->bar_count, 1u);
-            if (arrived == gridDim.x - 1) {
-                g->bar_count = 0u;
-                __threadfence();
-                atomicAdd(&g->bar_gen, 1u);
-            } else {
-                const long long t0 = clock64();
-                while (ld_acquire_gpu(&g->bar_gen) == gen) {
-                    if (ld_acquire_gpu(&g->abort) != 0u) { ok = 0; break; }
-                    if (clock64() - t0 > budget) {
-                        atomicExch(&g->abort, 1u);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(40);
-                }
-            }
-        }
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
+    const bool ok = pc_grid_barrier(&g->bar, budget);
+    if (!ok && threadIdx.x == 0) atomicExch(&g->abort, 1u);
+    return ok;
 }
 
 // ------------------------------------------------------------------------- per-instance sums
@@ -601,7 +581,7 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
         }
     }
     if (timed_out) {
-        atomicExch(&a.g->abort, 1u);
+        bt_abort(a.g);
         atomicOr(a.err, PC_DERR_TIMEOUT);
     }
 }

@@ -306,6 +306,54 @@ inline int pc_bits_for(int64_t n)
 
 __device__ __forceinline__ void pc_set_err(uint32_t *err, uint32_t bit) { atomicOr(err, bit); }
 
+// ------------------------------------------------------------------------- software grid barrier
+
+// Grid-wide barrier of co-resident CTAs on a 64-bit arrival counter that only grows
+// (zeroed before the first launch that uses it, and every launch sharing it has the same
+// grid): the k-th barrier is complete once the counter reaches k * gridDim.x. Arriving is
+// one acquire-release atomic that also tells the CTA which barrier it is at, and waiting
+// is one acquire load per poll: no generation word, no reset by the last CTA. Bit 63 is the
+// abort flag: a CTA whose wait exceeds `budget` SM cycles sets it (pc_grid_abort), and every
+// CTA that arrives or polls afterwards leaves with false, so the launch unwinds at its next
+// barrier. Called by all threads of the CTA; returns the same value to all of them.
+#define PC_BAR_ABORT (1ull << 63)
+
+__device__ __forceinline__ void pc_grid_abort(unsigned long long *count)
+{
+    atomicOr(count, PC_BAR_ABORT);
+}
+
+__device__ __forceinline__ bool pc_grid_barrier(unsigned long long *count, long long budget)
+{
+    __shared__ int s_ok;
+    __syncthreads();  // every thread's writes precede thread 0's release
+    if (threadIdx.x == 0) {
+        unsigned long long old;
+        asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], 1;" : "=l"(old) : "l"(count) : "memory");
+        int ok = (old & PC_BAR_ABORT) == 0ull;
+        const unsigned long long n = gridDim.x;
+        const unsigned long long target = ((old & ~PC_BAR_ABORT) / n + 1ull) * n;
+        if (ok && (old & ~PC_BAR_ABORT) + 1ull != target) {
+            const long long t0 = clock64();
+            for (unsigned k = 1;; ++k) {
+                unsigned long long c;
+                asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(count) : "memory");
+                if (c & PC_BAR_ABORT) { ok = 0; break; }
+                if (c >= target) break;
+                if ((k & 15u) == 1u && clock64() - t0 > budget) {  // first poll, then every 16th
+                    pc_grid_abort(count);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // ------------------------------------------------------------------------- double-float sums
 // GB300 issues FP64 at about 1/60 of its FP32 rate (and with long latency), so the
 // per-iteration dot-product reductions add their partial sums as unevaluated pairs of

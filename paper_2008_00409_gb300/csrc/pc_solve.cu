@@ -462,50 +462,9 @@ __global__ void __launch_bounds__(EW_THREADS) residual_check_kernel(int V, const
 static_assert(FU_ROWS % FU_GROUP == 0, "a thread's rows come in whole groups");
 
 struct pc_fuse_bar {
-    uint32_t count, gen, abort, pad;
+    unsigned long long count;  // arrivals at the grid barrier (pc_grid_barrier; zeroed per solve)
+    uint64_t pad;
 };
-
-__device__ __forceinline__ uint32_t fu_ld_acquire(const uint32_t *p)
-{
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// All CTAs meet; false everywhere once a CTA gave up waiting.
-__device__ bool fu_grid_sync(pc_fuse_bar *g, long long budget)
-{
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = fu_ld_acquire(&g->abort) == 0u;
-        if (ok) {
-            const uint32_t gen = fu_ld_acquire(&g->gen);
-            __threadfence();
-            const uint32_t arrived = atomicAdd(&g->count, 1u);
-            if (arrived == gridDim.x - 1) {
-                g->count = 0u;
-                __threadfence();
-                atomicAdd(&g->gen, 1u);
-            } else {
-                const long long t0 = clock64();
-                while (fu_ld_acquire(&g->gen) == gen) {
-                    if (fu_ld_acquire(&g->abort) != 0u) { ok = 0; break; }
-                    if (clock64() - t0 > budget) {
-                        atomicExch(&g->abort, 1u);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(32);
-                }
-            }
-        }
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
 
 template <bool BLOCK>
 __global__ void __launch_bounds__(FU_THREADS, FU_CTAS_PER_SM) pcg_update_dir_kernel(
@@ -571,7 +530,7 @@ __global__ void __launch_bounds__(FU_THREADS, FU_CTAS_PER_SM) pcg_update_dir_ker
             pf[(int64_t)blockIdx.x * RED_SLOTS + 1] = make_float2(hi[1], lo[1]);
         }
     }
-    if (!fu_grid_sync(bar, wait_budget)) {
+    if (!pc_grid_barrier(&bar->count, wait_budget)) {
         // a timeout outranks any status block 0 may record in this launch
         if (threadIdx.x == 0) {
             atomicOr(err, PC_DERR_TIMEOUT);
