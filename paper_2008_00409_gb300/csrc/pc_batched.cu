@@ -70,7 +70,7 @@ struct BtArgs {
     double *x64;
     float *dv;
     double *part;              // [(ntiles + n_inst) * 3] partial sums, one slot per (CTA, instance)
-    double *part_pq;           // [(ntiles + n_inst) * SP_CWARPS] p.q per (strided run, consumer warp)
+    double *part_pq;           // [(ntiles + n_inst) * SP_CWARPS] p.q per (CTA's run, consumer warp)
     bt_inst *inst;
     bt_global *g;
     uint32_t *err;
@@ -409,11 +409,13 @@ __device__ __forceinline__ bt_sched bt_spmv_sched(const BtArgs &a, const bt_list
 // q = A p over the listed rows with the bulk-copy stage ring, entries in the order the
 // autotuner chose (bt_spmv_sched). A CTA meets each instance in one run of its entries
 // (an instance's entries are contiguous); each consumer warp stores its p.q over the run
-// in the slot of the run's first entry, and the slots are summed where alpha is needed
-// (bt_alpha_warp). Strided order: the run starts at p0 + ((b - p0) mod G), so the instance's
-// slots are entries p0 .. p0 + min(G, p1 - p0) - 1; chunked order: max(b * chunk, p0)
-// for the CTAs b whose chunk meets [p0, p1). `kbase` continues the mbarrier phase count
-// across calls.
+// in the CTA's slot of the instance, and the slots are summed where alpha is needed
+// (bt_alpha_warp). The instance's slots are contiguous from its first entry p0, one per
+// CTA: strided order, the run's first entry p0 + ((b - p0) mod G), so slots p0 .. p0 +
+// min(G, p1 - p0) - 1; chunked order, p0 + b - p0 / chunk for the CTAs b whose chunk meets
+// [p0, p1). Contiguous slots keep the sum that every CTA of the instance makes one
+// coalesced read (late in a solve one instance spans hundreds of CTAs). `kbase` continues
+// the mbarrier phase count across calls.
 template <bool DIFF, int CAPR>
 __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *smem_raw, uint64_t *full_bar,
                               uint64_t *empty_bar, int (*stage_info)[4], int kbase, int par)
@@ -572,7 +574,10 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
             // end of this instance's run: the warp's p.q goes to the run's slot
             if (j + G >= cu.p1 || e + 1 == nent) {
                 const double w = bt_warp_sum((double)dot - (double)dot_c);
-                if (lane == 0) a.part_pq[(int64_t)SP_CWARPS * seg_start + warp] = w;
+                // the instance's slots are contiguous from p0, one per CTA holding a run of
+                // it: strided order, the run's first entry; chunked, p0 + b - p0 / chunk
+                const int64_t slot = a.spmv_chunked ? cu.p0 + ((int)blockIdx.x - cu.p0 / L.chunk) : seg_start;
+                if (lane == 0) a.part_pq[(int64_t)SP_CWARPS * slot + warp] = w;
                 dot = 0.f;
                 dot_c = 0.f;
                 seg_start = j + G;
@@ -587,6 +592,7 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
 }
 
 #define BT_WARPS (SP_THREADS / 32)  // warps per CTA: instances a CTA's update phase handles at once
+#define BT_SLOT_BATCH 4             // slot loads per lane issued together in the per-warp sums
 
 // alpha of the instance at list position m, computed by one warp from the instance's p.q
 // slots (summed in slot order, so every CTA that needs it gets the same value); the CTA
@@ -601,11 +607,25 @@ __device__ float bt_alpha_warp(const BtArgs &a, const bt_list &L, int m, int j)
     const int c = L.chunk;
     const int n = a.spmv_chunked ? (p1 - 1) / c - p0 / c + 1 : min((int)gridDim.x, p1 - p0);
     const double2 *slots = reinterpret_cast<const double2 *>(a.part_pq);
+    // lane l adds slots l, l + 32, l + 64, ... in that order; the loads of BT_SLOT_BATCH
+    // slots are issued before their adds (a garment late in a solve has a slot in
+    // hundreds of CTAs, and one L2 round trip per slot would dominate the phase)
     double acc = 0.0;
-    for (int i = lane; i < n; i += 32) {
-        const int64_t s0 = 2 * (a.spmv_chunked ? max((p0 / c + i) * c, p0) : p0 + i);
-        const double2 x0 = __ldcg(slots + s0), x1 = __ldcg(slots + s0 + 1);
-        acc += (x0.x + x0.y) + (x1.x + x1.y);
+    for (int i0 = lane; i0 < n; i0 += 32 * BT_SLOT_BATCH) {
+        double v[BT_SLOT_BATCH];
+#pragma unroll
+        for (int u = 0; u < BT_SLOT_BATCH; ++u) {
+            const int i = i0 + 32 * u;
+            v[u] = 0.0;
+            if (i < n) {
+                const int64_t s0 = 2 * (int64_t)(p0 + i);
+                const double2 x0 = __ldcg(slots + s0), x1 = __ldcg(slots + s0 + 1);
+                v[u] = (x0.x + x0.y) + (x1.x + x1.y);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < BT_SLOT_BATCH; ++u)
+            if (i0 + 32 * u < n) acc += v[u];
     }
     const double pq = bt_warp_sum(acc);
     float alpha32 = 0.f;
@@ -683,13 +703,13 @@ __device__ void bt_phase_update(const BtArgs &a, const bt_list &L, int par)
         }
         __syncthreads();
         if (warp < gs) {
-            // deliver into the slot of the CTA's first entry of the instance (CTA b takes
+            // deliver into the CTA's slot of the instance, p0 + b - p0 / chunk (CTA b takes
             // entries [b*chunk, (b+1)*chunk)); the CTA that delivers last sums the slots in
             // CTA order and sets the instance's scalars
             const int m = m0 + g0 + warp;
             const int k = L.id[m], p0 = L.pref[m], p1 = L.pref[m + 1];
-            const int jm = max(j0, p0);
             const int blo = p0 / c, bhi = (p1 - 1) / c;
+            const int64_t jm = p0 + ((int)blockIdx.x - blo);  // slots p0 .. p0 + bhi - blo
             int last = 0;
             if (lane == 0) {
                 double v0 = 0.0, v1 = 0.0;
@@ -710,10 +730,24 @@ __device__ void bt_phase_update(const BtArgs &a, const bt_list &L, int par)
             last = __shfl_sync(0xffffffffu, last, 0);
             if (last) {
                 double v0 = 0.0, v1 = 0.0;
-                for (int bb = blo + lane; bb <= bhi; bb += 32) {
-                    const int64_t slot = max(bb * c, p0);
-                    v0 += __ldcg(a.part + 3 * slot);
-                    v1 += __ldcg(a.part + 3 * slot + 1);
+                for (int b0 = blo + lane; b0 <= bhi; b0 += 32 * BT_SLOT_BATCH) {
+                    double w0[BT_SLOT_BATCH], w1[BT_SLOT_BATCH];
+#pragma unroll
+                    for (int u = 0; u < BT_SLOT_BATCH; ++u) {
+                        const int bb = b0 + 32 * u;
+                        w0[u] = w1[u] = 0.0;
+                        if (bb <= bhi) {
+                            const int64_t slot = p0 + (bb - blo);
+                            w0[u] = __ldcg(a.part + 3 * slot);
+                            w1[u] = __ldcg(a.part + 3 * slot + 1);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < BT_SLOT_BATCH; ++u)
+                        if (b0 + 32 * u <= bhi) {
+                            v0 += w0[u];
+                            v1 += w1[u];
+                        }
                 }
                 const double rzn = bt_warp_sum(v0), rrn = bt_warp_sum(v1);
                 bt_inst &I = a.inst[k];

@@ -336,15 +336,17 @@ __device__ __forceinline__ bool pc_grid_barrier(unsigned long long *count, long 
         if (ok && (old & ~PC_BAR_ABORT) + 1ull != target) {
             const long long t0 = clock64();
             for (unsigned k = 1;; ++k) {
-                unsigned long long c;
-                asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(count) : "memory");
-                if (c & PC_BAR_ABORT) { ok = 0; break; }
-                if (c >= target) break;
-                if ((k & 15u) == 1u && clock64() - t0 > budget) {  // first poll, then every 16th
+                // the budget is checked before the first poll and then before every 16th, so
+                // a budget of a few cycles makes every CTA but the last to arrive give up
+                if ((k & 15u) == 1u && clock64() - t0 > budget) {
                     pc_grid_abort(count);
                     ok = 0;
                     break;
                 }
+                unsigned long long c;
+                asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(count) : "memory");
+                if (c & PC_BAR_ABORT) { ok = 0; break; }
+                if (c >= target) break;
                 __nanosleep(32);
             }
         }
