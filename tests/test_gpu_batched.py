@@ -120,3 +120,30 @@ def test_batched_not_converged_reports_per_instance(pc):
     assert st == pc.PC_ERR_NOT_CONVERGED
     assert all(i.iters == 5 for i in infos)
     assert np.isfinite(_np(dv)).all()
+
+
+def test_batched_solve_is_deterministic_and_plain_form_agrees(pc):
+    """Each garment's sums are taken in a fixed order (its CTA slots in order, the same in
+    every CTA that needs them), so two solves of the same systems on the tuned launch shape
+    give bit-identical dv and iteration counts. The plain form (no difference diagonal: the
+    product streams A itself, the kernel's other instantiation) solves the same systems."""
+    u = small_batch()
+    cl = pc.Cloth(u)
+    s = cl.assemble(*cl.contacts_device(0))
+    opts = pc.solve_opts(tol=1e-9, max_iter=50000)
+    args = (cl.ctx, s["row_ptr"], s["col_idx"], s["nnzb"], s["vals"])
+    runs = []
+    for _ in range(2):
+        dv = torch.zeros(cl.V * 3, device="cuda")
+        infos, st = pc.pc_pcg_solve_batched(*args, s["dres"], s["b"], dv, u.inst_rows, opts)
+        assert st == pc.PC_OK
+        runs.append((dv.clone(), [i.iters for i in infos]))
+    assert torch.equal(runs[0][0], runs[1][0])
+    assert runs[0][1] == runs[1][1]
+    plain = torch.zeros(cl.V * 3, device="cuda")
+    infos, st = pc.pc_pcg_solve_batched(*args, None, s["b"], plain, u.inst_rows, opts)
+    assert st == pc.PC_OK and all(i.rel_res <= 2e-9 for i in infos)
+    got, ref = _np(plain).reshape(-1, 3), _np(runs[0][0]).reshape(-1, 3)
+    for k in range(len(u.parts)):
+        r0, r1 = u.inst_rows[k], u.inst_rows[k + 1]
+        assert H.rel_l2(got[r0:r1], ref[r0:r1]) <= H.DV_RTOL, f"instance {k}"
