@@ -324,7 +324,7 @@ PC_API pc_status pc_get_solution64(pc_ctx *ctx, double *dv64, void *stream);
  * continue. The launch is cooperative (all CTAs co-resident) with bounded grid-wide
  * waits (PC_ERR_TIMEOUT instead of a hang). On the first call for a matrix shape an
  * autotuner times short solves for each tile and schedule (the SpMV phase's stage width
- * x its entry order x the grid: 16, 32, 64 CTAs or 1..4 per SM) and keeps the fastest
+ * x its entry order x the grid: 16, 32, 64 CTAs or 2..5 per SM) and keeps the fastest
  * (pc_batched_config reports the choice). info: host array of n_inst results, may be
  * NULL. Returns the first non-OK instance status. Synchronizes `stream`.
  * (The paper solves one garment system per step; batching is this library's extension.) */
@@ -336,7 +336,7 @@ PC_API pc_status pc_pcg_solve_batched(pc_ctx *ctx, const pc_bsr *A, const float 
  * yet), the SpMV entry order (0: strided, CTA b takes entries b, b+G, ...; 1: contiguous
  * chunks), the SpMV phase's stage width in blocks per row of a 32-row tile (14 or 18), the
  * seven candidate grid sizes (grid_sizes[7]: 16, 32 and 64 CTAs where that is below one
- * per SM, else 0; then 1..4 CTAs per SM) and the timings (ms) of every candidate,
+ * per SM, else 0; then 2..5 CTAs per SM) and the timings (ms) of every candidate,
  * tune_ms[14 * (width == 18) + 7 * order + grid index] (0 where not tried: a grid that
  * does not fit). Host pointers, may be NULL. */
 PC_API pc_status pc_batched_config(pc_ctx *ctx, int32_t *grid, int32_t *spmv_order, int32_t *stage_blocks,

@@ -297,8 +297,9 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 #define BT_U 2  // rows per thread in flight in the direction phase
 #endif
 #ifndef BT_MIN_CTAS
-#define BT_MIN_CTAS 4  // register budget: four co-resident CTAs per SM
+#define BT_MIN_CTAS 5  // register budget: five co-resident CTAs per SM (72 registers, no spills)
 #endif
+#define BT_WIN 3  // gathers in flight per thread in the product phase (12 blocks per row per round)
 
 // Direction p = z + beta p over the listed rows; rows of an instance that has just
 // taken an FP64 residual, or has done another 32 iterations, also fold the FP32
@@ -504,22 +505,15 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
                 const int tile2 = tb2 + (jn - p02);
                 bt_load_row(a, tile2, max(r02, tile2 * BT_TILE), min(r12, tile2 * BT_TILE + BT_TILE), t, nxt);
             }
-            // the row's own p and difference-form diagonal: in flight while the stage lands
+            // the row's own p and the scalar of its difference-form diagonal (D = s I for all
+            // but a few rows): in flight while the stage lands; a row without the scalar
+            // reads its 3x3 diagonal after the gathers (holding nine floats across the loop
+            // would cost the registers of the fifth CTA per SM)
             float4 xj = make_float4(0.f, 0.f, 0.f, 0.f);
-            float D[9];
+            float sd = 0.f;
             if (cur.on) {
                 xj = a.p4[cur.row];
-                if (DIFF && jl == 0) {
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) D[q] = 0.f;
-                    const float sd = a.dsc ? a.dsc[cur.row] : -1.f;
-                    if (sd > 0.f) {
-                        D[0] = D[4] = D[8] = sd;
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 9; ++q) D[q] = a.dres[9ll * cur.row + q];
-                    }
-                }
+                if (DIFF && jl == 0) sd = a.dsc ? a.dsc[cur.row] : -1.f;
             }
             const int kg = kbase + e;
             const int s = kg % SP_STAGES;
@@ -536,18 +530,19 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
                     reinterpret_cast<const int32_t *>(smem_raw + s * SpShape<CAPR>::stage_bytes +
                                                       SpShape<CAPR>::val_bytes) + co;
                 float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
-                // up to four blocks per thread in flight; p is not written in this phase, so
-                // the gathers may hit L1 (the grid barrier's acquire orders them after the
-                // direction phase's writes)
-                for (int bb = cur.rb + jl; bb < cur.re; bb += 4 * SP_TPR) {
-                    float4 u[4];
+                // up to BT_WIN blocks per thread in flight (rows average about 12 off-diagonal
+                // blocks: one round for most); p is not written in this phase, so the gathers
+                // may hit L1 (the grid barrier's acquire orders them after the direction
+                // phase's writes)
+                for (int bb = cur.rb + jl; bb < cur.re; bb += BT_WIN * SP_TPR) {
+                    float4 u[BT_WIN];
 #pragma unroll
-                    for (int w = 0; w < 4; ++w) {
+                    for (int w = 0; w < BT_WIN; ++w) {
                         const int bw = bb + w * SP_TPR;
                         if (bw < cur.re) u[w] = a.p4[staged ? s_cols[bw - b0] : a.sci[bw]];
                     }
 #pragma unroll
-                    for (int w = 0; w < 4; ++w) {
+                    for (int w = 0; w < BT_WIN; ++w) {
                         const int bw = bb + w * SP_TPR;
                         if (bw < cur.re) {
                             const float *B = staged ? s_vals + 9 * (bw - b0) : a.svals + 9ll * bw;
@@ -566,7 +561,15 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
                     acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
                 }
                 if (cur.on && jl == 0) {
-                    if (DIFF) spmv_fma(D, xj, acc0, acc1, acc2);
+                    if (DIFF) {
+                        if (sd > 0.f) {
+                            acc0 = fmaf(sd, xj.x, acc0);
+                            acc1 = fmaf(sd, xj.y, acc1);
+                            acc2 = fmaf(sd, xj.z, acc2);
+                        } else {
+                            spmv_fma(a.dres + 9ll * cur.row, xj, acc0, acc1, acc2);
+                        }
+                    }
                     a.q4[cur.row] = make_float4(acc0, acc1, acc2, 0.f);
                     kahan_add(dot, dot_c, fmaf(xj.x, acc0, fmaf(xj.y, acc1, xj.z * acc2)));
                 }
@@ -983,7 +986,7 @@ __global__ void bt_state_update_kernel(int V, const int32_t *row_inst, const bt_
 
 // ------------------------------------------------------------------------- host side
 
-#define BT_GRIDS 7  // grid candidates: 16, 32, 64 CTAs (below one per SM), then 1..4 per SM
+#define BT_GRIDS 7  // grid candidates: 16, 32, 64 CTAs (below one per SM), then 2..5 per SM
 
 struct pc_batched_state {
     int32_t *row_inst = nullptr;   // [V]
@@ -1154,11 +1157,14 @@ static pc_status bt_autotune(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, co
         if ((16 << g) < c->num_sms) B->tune_grid[g] = 16 << g;
     for (int w = 0; w < 2; ++w) {
         const int capr = bt_capr(w);
-        const int maxb = std::min(4, bt_max_blocks_per_sm(dres != nullptr, capr));
+        const int maxb = std::min(5, bt_max_blocks_per_sm(dres != nullptr, capr));
         for (int order = 0; order < 2; ++order)
             for (int gi = 0; gi < BT_GRIDS; ++gi) {
-                const int grid = gi < 3 ? B->tune_grid[gi] : (gi - 2 <= maxb ? (gi - 2) * c->num_sms : 0);
-                if (gi >= 3) B->tune_grid[gi] = (gi - 2) * c->num_sms;
+                // 16, 32, 64 CTAs, then 2..5 per SM (one per SM never won: the small grids
+                // serve the small systems, more CTAs the large ones)
+                const int per = gi - 1;
+                const int grid = gi < 3 ? B->tune_grid[gi] : (per <= maxb ? per * c->num_sms : 0);
+                if (gi >= 3) B->tune_grid[gi] = per * c->num_sms;
                 B->tune_ms[w][order][gi] = 0.f;
                 if (grid <= 0 || maxb < 1) continue;
                 PC_CUDA_TRY(cudaMemsetAsync(scratch_dv, 0, sizeof(float) * 3 * (size_t)c->V, st));
