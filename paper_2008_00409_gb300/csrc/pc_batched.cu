@@ -65,8 +65,9 @@ struct BtArgs {
     const int32_t *srp, *sci;
     const float *svals, *dsc;
     const int32_t *inst_rows;  // [n_inst + 1]
-    float4 *r4, *z4, *p4, *q4, *x4;
-    const float4 *dinv4;
+    float4 *p4, *q4;           // gathered by the product: one 16-byte load per row
+    float *r3, *z3, *x3;       // only streamed: three floats per row (12 bytes, not 16)
+    const float *dinv3;
     double *x64;
     float *dv;
     double *part;              // [(ntiles + n_inst) * 3] partial sums, one slot per (CTA, instance)
@@ -79,6 +80,25 @@ struct BtArgs {
     int spmv_chunked;          // SpMV entry order: 0 strided, 1 contiguous chunks (autotuned)
     long long bar_wait;        // cycles a grid-barrier wait may take before the launch aborts
 };
+
+// Rows of the streamed vectors (three floats each).
+__device__ __forceinline__ float4 bt_ld3(const float *v, int64_t row)
+{
+    const float *q = v + 3 * row;
+    return make_float4(q[0], q[1], q[2], 0.f);
+}
+__device__ __forceinline__ float4 bt_ldcg3(const float *v, int64_t row)
+{
+    const float *q = v + 3 * row;
+    return make_float4(__ldcg(q), __ldcg(q + 1), __ldcg(q + 2), 0.f);
+}
+__device__ __forceinline__ void bt_st3(float *v, int64_t row, float4 x)
+{
+    float *q = v + 3 * row;
+    q[0] = x.x;
+    q[1] = x.y;
+    q[2] = x.z;
+}
 
 // The work list of one phase: the listed instances in order, each contributing one entry
 // per 32-row tile it touches (a tile shared by two instances gives one entry to each, and
@@ -324,7 +344,7 @@ __device__ void bt_phase_direction(const BtArgs &a, const bt_list &L)
             for (int u = 0; u < BT_U; ++u) {
                 const int row = base + u * T;
                 if (row < sg.rb) {
-                    z[u] = a.z4[row];
+                    z[u] = bt_ld3(a.z3, row);
                     p[u] = a.p4[row];
                 }
             }
@@ -340,11 +360,11 @@ __device__ void bt_phase_direction(const BtArgs &a, const bt_list &L)
                 for (int u = 0; u < BT_U; ++u) {
                     const int row = base + u * T;
                     if (row < sg.rb) {
-                        const float4 d = a.x4[row];
+                        const float4 d = bt_ld3(a.x3, row);
                         a.x64[3ll * row] += (double)d.x;
                         a.x64[3ll * row + 1] += (double)d.y;
                         a.x64[3ll * row + 2] += (double)d.z;
-                        a.x4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        bt_st3(a.x3, row, make_float4(0.f, 0.f, 0.f, 0.f));
                     }
                 }
             }
@@ -687,14 +707,14 @@ __device__ void bt_phase_update(const BtArgs &a, const bt_list &L, int par)
             // one row per thread at a time: two in flight would need ten float4 registers,
             // and the persistent kernel's budget (four CTAs per SM) would spill in every phase
             for (int row = s_row[q][0] + (int)threadIdx.x; row < rb; row += T) {
-                const float4 p = a.p4[row], qv = a.q4[row], d = a.dinv4[row];
-                float4 x = a.x4[row], r = a.r4[row];
+                const float4 p = a.p4[row], qv = a.q4[row], d = bt_ld3(a.dinv3, row);
+                float4 x = bt_ld3(a.x3, row), r = bt_ld3(a.r3, row);
                 x.x = fmaf(alpha, p.x, x.x); x.y = fmaf(alpha, p.y, x.y); x.z = fmaf(alpha, p.z, x.z);
                 r.x = fmaf(-alpha, qv.x, r.x); r.y = fmaf(-alpha, qv.y, r.y); r.z = fmaf(-alpha, qv.z, r.z);
                 const float4 z = make_float4(d.x * r.x, d.y * r.y, d.z * r.z, 0.f);
-                a.x4[row] = x;
-                a.r4[row] = r;
-                a.z4[row] = z;
+                bt_st3(a.x3, row, x);
+                bt_st3(a.r3, row, r);
+                bt_st3(a.z3, row, z);
                 kahan_add(rz, rz_c, fmaf(r.x, z.x, fmaf(r.y, z.y, r.z * z.z)));
                 kahan_add(rr, rr_c, fmaf(r.x, r.x, fmaf(r.y, r.y, r.z * r.z)));
             }
@@ -794,7 +814,7 @@ __device__ void bt_phase_residual(const BtArgs &a, const bt_list &L, bool start)
         j = sg.je;
         double rz = 0.0, rr = 0.0, bb = 0.0;
         for (int row = sg.ra + (int)threadIdx.x; row < sg.rb; row += T) {
-            const float4 xo = __ldcg(a.x4 + row);
+            const float4 xo = bt_ldcg3(a.x3, row);
             const double xj[3] = {__ldcg(a.x64 + 3ll * row) + (double)xo.x, __ldcg(a.x64 + 3ll * row + 1) + (double)xo.y,
                                   __ldcg(a.x64 + 3ll * row + 2) + (double)xo.z};
             double acc[3] = {0.0, 0.0, 0.0};
@@ -802,7 +822,7 @@ __device__ void bt_phase_residual(const BtArgs &a, const bt_list &L, bool start)
                 const int col = a.ci[kk];
                 if (DIFF && col == row) continue;
                 const float *B = a.vals + 9ll * kk;
-                const float4 xc4 = __ldcg(a.x4 + col);
+                const float4 xc4 = bt_ldcg3(a.x3, col);
                 double xc[3] = {__ldcg(a.x64 + 3ll * col) + (double)xc4.x, __ldcg(a.x64 + 3ll * col + 1) + (double)xc4.y,
                                 __ldcg(a.x64 + 3ll * col + 2) + (double)xc4.z};
                 if (DIFF)
@@ -823,11 +843,11 @@ __device__ void bt_phase_residual(const BtArgs &a, const bt_list &L, bool start)
                 bb += bv * bv;
                 rf[q] = (float)rv;
             }
-            const float4 d = a.dinv4[row];
+            const float4 d = bt_ld3(a.dinv3, row);
             const float4 r = make_float4(rf[0], rf[1], rf[2], 0.f);
             const float4 z = make_float4(d.x * r.x, d.y * r.y, d.z * r.z, 0.f);
-            a.r4[row] = r;
-            a.z4[row] = z;
+            bt_st3(a.r3, row, r);
+            bt_st3(a.z3, row, z);
             if (start) a.p4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
             rz += (double)fmaf(r.x, z.x, fmaf(r.y, z.y, r.z * z.z));
         }
@@ -914,7 +934,7 @@ __global__ void __launch_bounds__(SP_THREADS, BT_MIN_CTAS) batched_pcg_kernel(Bt
     // ---- finish: dv = x64 + x (FP32)
     const int stride = gridDim.x * blockDim.x;
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < a.V; row += stride) {
-        const float4 d = __ldcg(a.x4 + row);
+        const float4 d = bt_ldcg3(a.x3, row);
         for (int q = 0; q < 3; ++q) {
             const double xv = __ldcg(a.x64 + 3ll * row + q) + (double)(&d.x)[q];
             a.x64[3ll * row + q] = xv;
@@ -943,7 +963,7 @@ __global__ void bt_check_blocks_kernel(int V, const int32_t *rp, const int32_t *
         if (row_inst[ci[s]] != k) { pc_set_err(err, PC_DERR_INDEX); return; }
 }
 
-__global__ void bt_dinv_kernel(int V, const int32_t *rp, const int32_t *ci, const float *vals, float4 *dinv4,
+__global__ void bt_dinv_kernel(int V, const int32_t *rp, const int32_t *ci, const float *vals, float *dinv3,
                                uint32_t *err)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -954,15 +974,17 @@ __global__ void bt_dinv_kernel(int V, const int32_t *rp, const int32_t *ci, cons
     const float d0 = s >= 0 ? vals[9ll * s] : 0.f, d1 = s >= 0 ? vals[9ll * s + 4] : 0.f,
                 d2 = s >= 0 ? vals[9ll * s + 8] : 0.f;
     const bool ok = d0 > 0.f && d1 > 0.f && d2 > 0.f && isfinite(d0 + d1 + d2);
-    dinv4[r] = ok ? make_float4(1.f / d0, 1.f / d1, 1.f / d2, 0.f) : make_float4(1.f, 1.f, 1.f, 0.f);
+    bt_st3(dinv3, r, ok ? make_float4(1.f / d0, 1.f / d1, 1.f / d2, 0.f) : make_float4(1.f, 1.f, 1.f, 0.f));
     if (!ok) pc_set_err(err, PC_DERR_NONFINITE);
 }
 
-__global__ void bt_start_kernel(int V, const float *dv, double *x64, float4 *x4)
+__global__ void bt_start_kernel(int V, const float *dv, double *x64, float *x3)
 {
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < V; row += gridDim.x * blockDim.x) {
-        for (int q = 0; q < 3; ++q) x64[3ll * row + q] = (double)dv[3ll * row + q];
-        x4[row] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = 0; q < 3; ++q) {
+            x64[3ll * row + q] = (double)dv[3ll * row + q];
+            x3[3ll * row + q] = 0.f;
+        }
     }
 }
 
@@ -1070,8 +1092,8 @@ static pc_status bt_enqueue(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, con
 {
     const int V = c->V;
     PC_LAUNCH(c, bt_dinv_kernel, pc_blocks(V, 256), 256, 0, st, V, A->row_ptr, A->col_idx, vals,
-              (float4 *)c->dinv, c->d_err);
-    PC_LAUNCH(c, bt_start_kernel, pc_blocks(V, 256), 256, 0, st, V, dv, c->x64, (float4 *)c->dtmp);
+              c->dinv, c->d_err);
+    PC_LAUNCH(c, bt_start_kernel, pc_blocks(V, 256), 256, 0, st, V, dv, c->x64, c->dtmp);
     BtArgs a{};
     a.V = V;
     a.n_inst = n_inst;
@@ -1093,12 +1115,12 @@ static pc_status bt_enqueue(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, con
         a.dsc = c->dsc;
     }
     a.inst_rows = B->inst_rows;
-    a.r4 = (float4 *)c->r;
-    a.z4 = (float4 *)c->z;
+    a.r3 = c->r;
+    a.z3 = c->z;
     a.p4 = (float4 *)c->p0;
     a.q4 = (float4 *)c->q;
-    a.x4 = (float4 *)c->dtmp;
-    a.dinv4 = (const float4 *)c->dinv;
+    a.x3 = c->dtmp;
+    a.dinv3 = c->dinv;
     a.x64 = c->x64;
     a.dv = dv;
     a.part = B->part;
