@@ -65,8 +65,8 @@ struct BtArgs {
     const int32_t *srp, *sci;
     const float *svals, *dsc;
     const int32_t *inst_rows;  // [n_inst + 1]
-    float4 *p4, *q4;           // gathered by the product: one 16-byte load per row
-    float *r3, *z3, *x3;       // only streamed: three floats per row (12 bytes, not 16)
+    float4 *p4;                // gathered by the product: one 16-byte load per row
+    float *q3, *r3, *z3, *x3;  // only streamed: three floats per row (12 bytes, not 16)
     const float *dinv3;
     double *x64;
     float *dv;
@@ -590,7 +590,7 @@ __device__ void bt_phase_spmv(const BtArgs &a, const bt_list &L, unsigned char *
                             spmv_fma(a.dres + 9ll * cur.row, xj, acc0, acc1, acc2);
                         }
                     }
-                    a.q4[cur.row] = make_float4(acc0, acc1, acc2, 0.f);
+                    bt_st3(a.q3, cur.row, make_float4(acc0, acc1, acc2, 0.f));
                     kahan_add(dot, dot_c, fmaf(xj.x, acc0, fmaf(xj.y, acc1, xj.z * acc2)));
                 }
             }
@@ -707,7 +707,7 @@ __device__ void bt_phase_update(const BtArgs &a, const bt_list &L, int par)
             // one row per thread at a time: two in flight would need ten float4 registers,
             // and the persistent kernel's budget (four CTAs per SM) would spill in every phase
             for (int row = s_row[q][0] + (int)threadIdx.x; row < rb; row += T) {
-                const float4 p = a.p4[row], qv = a.q4[row], d = bt_ld3(a.dinv3, row);
+                const float4 p = a.p4[row], qv = bt_ld3(a.q3, row), d = bt_ld3(a.dinv3, row);
                 float4 x = bt_ld3(a.x3, row), r = bt_ld3(a.r3, row);
                 x.x = fmaf(alpha, p.x, x.x); x.y = fmaf(alpha, p.y, x.y); x.z = fmaf(alpha, p.z, x.z);
                 r.x = fmaf(-alpha, qv.x, r.x); r.y = fmaf(-alpha, qv.y, r.y); r.z = fmaf(-alpha, qv.z, r.z);
@@ -1118,7 +1118,7 @@ static pc_status bt_enqueue(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, con
     a.r3 = c->r;
     a.z3 = c->z;
     a.p4 = (float4 *)c->p0;
-    a.q4 = (float4 *)c->q;
+    a.q3 = c->q;
     a.x3 = c->dtmp;
     a.dinv3 = c->dinv;
     a.x64 = c->x64;
