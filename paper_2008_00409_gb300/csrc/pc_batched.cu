@@ -704,8 +704,9 @@ __device__ void bt_phase_update(const BtArgs &a, const bt_list &L, int par)
             const float alpha = s_alpha[q];
             const int rb = s_row[q][1];
             float rz = 0.f, rz_c = 0.f, rr = 0.f, rr_c = 0.f;
-            // one row per thread at a time: two in flight would need ten float4 registers,
-            // and the persistent kernel's budget (four CTAs per SM) would spill in every phase
+            // one row per thread at a time: two rows' vectors in flight would not fit the
+            // persistent kernel's register budget (five CTAs per SM), which spills in every
+            // phase once exceeded; prefetching them through shared memory was slower
             for (int row = s_row[q][0] + (int)threadIdx.x; row < rb; row += T) {
                 const float4 p = a.p4[row], qv = bt_ld3(a.q3, row), d = bt_ld3(a.dinv3, row);
                 float4 x = bt_ld3(a.x3, row), r = bt_ld3(a.r3, row);
@@ -1159,7 +1160,7 @@ static pc_status bt_setup_instances(pc_ctx *c, pc_batched_state *B, const pc_bsr
 // budget) for each tile and schedule choice -- the SpMV phase's stage width (14 or 18
 // blocks per row of a 32-row tile) x its entry order (strided or chunked) x the grid
 // (16, 32 or 64 CTAs, where that is below one per SM: a small system's grid barriers are
-// cheaper with fewer CTAs; then 1..4 co-resident CTAs per SM, as far as they fit) -- and
+// cheaper with fewer CTAs; then 2..5 co-resident CTAs per SM, as far as they fit) -- and
 // keep the fastest.
 static pc_status bt_autotune(pc_ctx *c, pc_batched_state *B, const pc_bsr *A, const float *vals, const float *dres,
                              const float *b, int n_inst, const pc_solve_opts &o, cudaStream_t st)
